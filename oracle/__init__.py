@@ -1,0 +1,304 @@
+"""CPU oracle for the ray-traced sphere-splat image warping (Zellmann 2020, arXiv 2006.14726).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's CPU-baseline leg
+are the only callers.  The CUDA library and its Python binding never import this package.
+
+The arithmetic lives in ``oracle.c`` (plain C, binary64 for continuous quantities, binary32 for
+every discrete decision as the written spec fixes it).  This module compiles it with gcc and
+marshals numpy arrays through ctypes.  Functions and the paper passage each one follows:
+
+* :func:`primary_ray` -- the ray ``r = o + d t`` of a pixel (Eq. 1, spec S1).
+* :func:`raycast` -- the server's volume ray marcher with the first-hit depth heuristic
+  (§4.1, §4.2, Fig. 2; the heuristic itself is cited from earlier work, §2).
+* :func:`unproject` -- object-space samples ``p = o + d t_i`` (Eq. 1), footprint radius (§4.1),
+  zero-radius compaction (§4.1).
+* :func:`trace` -- first-hit / multi-hit ray tracing of the samples as semi-transparent spheres
+  with constant colour (Fig. 2 caption, §4), front-to-back compositing (spec S6).
+* :func:`trace_backward` -- the adjoint of that compositing (spec S7; not in the paper).
+* :func:`lbvh` -- Morton codes, sorted order and the binary radix tree of the LBVH (§4.1, §4.2).
+
+Every function here is pinned by ``tests/test_oracle_*.py`` against closed forms, invariants and
+brute force, never against the CUDA path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+CFLAGS = ["-O2", "-fPIC", "-shared", "-pthread", "-std=gnu11", "-ffp-contract=off",
+          "-frounding-math", "-fno-fast-math"]
+
+RADIUS_FOOTPRINT = 0
+RADIUS_VOXEL = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so next to it (gcc, no GPU needed)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Cam(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_float * 3), ("right", ctypes.c_float * 3),
+                ("up", ctypes.c_float * 3), ("fwd", ctypes.c_float * 3),
+                ("tan_half_fovy", ctypes.c_float), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32)]
+
+
+class _Scene(ctypes.Structure):
+    _fields_ = [("pos_r", ctypes.c_void_p), ("rgba", ctypes.c_void_p), ("id", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("scale", ctypes.c_void_p), ("global_scale", ctypes.c_float),
+                ("opacity", ctypes.c_void_p), ("max_hits", ctypes.c_int32),
+                ("t_stop", ctypes.c_double), ("beta", ctypes.c_double)]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        lib.orc_primary_ray.argtypes = [ctypes.POINTER(_Cam), ctypes.c_int, ctypes.c_int, P, P]
+        lib.orc_raycast.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
+                                    ctypes.POINTER(_Cam), ctypes.c_float, ctypes.c_float, P,
+                                    ctypes.c_int64, P, P, ctypes.c_int]
+        lib.orc_unproject.argtypes = [P, P, ctypes.POINTER(_Cam), ctypes.c_int, ctypes.c_float,
+                                      P, P, P, ctypes.c_int64]
+        lib.orc_unproject.restype = ctypes.c_int64
+        lib.orc_bvh_build.argtypes = [P, P, ctypes.c_float, ctypes.c_int64, ctypes.c_int]
+        lib.orc_bvh_build.restype = P
+        lib.orc_bvh_free.argtypes = [P]
+        lib.orc_trace.argtypes = [ctypes.POINTER(_Scene), P, ctypes.POINTER(_Cam), P,
+                                  ctypes.c_int64, P, P, P, P, P, P, ctypes.c_int]
+        lib.orc_trace_backward.argtypes = [ctypes.POINTER(_Scene), P, ctypes.POINTER(_Cam), P, P,
+                                           P, P, ctypes.c_int]
+        lib.orc_lbvh.argtypes = [P, P, ctypes.c_float, ctypes.c_int64, ctypes.c_int32, P, P, P, P,
+                                 P, P]
+        lib.orc_default_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def default_threads() -> int:
+    return int(_load().orc_default_threads())
+
+
+def _cam(cam) -> _Cam:
+    c = _Cam()
+    for f in ("eye", "right", "up", "fwd"):
+        v = np.asarray(getattr(cam, f), dtype=np.float32)
+        getattr(c, f)[:] = [float(x) for x in v]
+    c.tan_half_fovy = float(np.float32(cam.tan_half_fovy))
+    c.width = int(cam.width)
+    c.height = int(cam.height)
+    return c
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data
+
+
+def _c(a, dtype) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def primary_ray(cam, x: int, y: int):
+    """Spec S1 ray of pixel (x, y): returns (o, d) as float32[3] arrays."""
+    o = np.zeros(3, np.float32)
+    d = np.zeros(3, np.float32)
+    _load().orc_primary_ray(ctypes.byref(_cam(cam)), int(x), int(y), o.ctypes.data, d.ctypes.data)
+    return o, d
+
+
+def raycast(vol: np.ndarray, tf: np.ndarray, cam, step_vox: float = 0.5, tau: float = 0.1,
+            pixels: Optional[np.ndarray] = None, threads: int = 0):
+    """Server volume ray caster + first-hit depth heuristic (spec S2).
+
+    vol: [nz, ny, nx] float32 in [0,1] or uint8.  Returns (rgba float64 [npix,4] premultiplied,
+    depth float32 [npix]) for ``pixels`` (flat indices y*W+x), or images [H,W,4] / [H,W] if None.
+    """
+    lib = _load()
+    if vol.dtype == np.uint8:
+        dtype = 1
+    else:
+        dtype = 0
+        vol = _c(vol, np.float32)
+    vol = np.ascontiguousarray(vol)
+    nz, ny, nx = vol.shape
+    tf = _c(tf, np.float32)
+    assert tf.shape == (256, 4)
+    if pixels is None:
+        npix = cam.width * cam.height
+        pix = None
+    else:
+        pix = _c(pixels, np.int32)
+        npix = pix.size
+    rgba = np.zeros((npix, 4), np.float64)
+    depth = np.zeros(npix, np.float32)
+    rc = lib.orc_raycast(vol.ctypes.data, dtype, nx, ny, nz, tf.ctypes.data, ctypes.byref(_cam(cam)),
+                         float(step_vox), float(tau), _ptr(pix), int(npix), rgba.ctypes.data,
+                         depth.ctypes.data, int(threads))
+    if rc != 0:
+        raise ValueError("orc_raycast: bad arguments")
+    if pixels is None:
+        return rgba.reshape(cam.height, cam.width, 4), depth.reshape(cam.height, cam.width)
+    return rgba, depth
+
+
+@dataclass
+class Splats:
+    """Compacted splats in server-pixel order: pos_r [N,4] (x,y,z,r0), rgba [N,4], id [N]."""
+    pos_r: np.ndarray
+    rgba: np.ndarray
+    id: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return int(self.id.shape[0])
+
+
+def unproject(rgba: np.ndarray, depth: np.ndarray, cam, mode: int = RADIUS_FOOTPRINT,
+              voxel_diag: float = 0.0) -> Splats:
+    """Eq. 1 unprojection with footprint / voxel radius and stable compaction (spec S3)."""
+    rgba = _c(rgba, np.float32).reshape(-1, 4)
+    depth = _c(depth, np.float32).reshape(-1)
+    cap = depth.size
+    pos_r = np.zeros((cap, 4), np.float32)
+    out = np.zeros((cap, 4), np.float32)
+    ids = np.zeros(cap, np.uint32)
+    n = _load().orc_unproject(rgba.ctypes.data, depth.ctypes.data, ctypes.byref(_cam(cam)), int(mode),
+                              float(voxel_diag), pos_r.ctypes.data, out.ctypes.data, ids.ctypes.data,
+                              cap)
+    if n < 0:
+        raise ValueError(f"orc_unproject failed ({n})")
+    return Splats(pos_r[:n].copy(), out[:n].copy(), ids[:n].copy())
+
+
+@dataclass
+class Scene:
+    """Everything the compositing reads: splats + per-splat parameters + compositing settings."""
+    splats: Splats
+    scale: Optional[np.ndarray] = None    # per-splat radius scale (compacted order) or None
+    global_scale: float = 1.0
+    opacity: Optional[np.ndarray] = None  # per-splat opacity or None (= 1)
+    max_hits: int = 0                     # H: 1 = first hit (the paper), 0 = all hits
+    t_stop: float = 1e-5
+    beta: float = 0.0                     # soft-edge width (0 = hard spheres)
+
+    def _c(self):
+        self._keep = [_c(self.splats.pos_r, np.float32), _c(self.splats.rgba, np.float32),
+                      _c(self.splats.id, np.uint32),
+                      None if self.scale is None else _c(self.scale, np.float32),
+                      None if self.opacity is None else _c(self.opacity, np.float32)]
+        k = self._keep
+        return _Scene(_ptr(k[0]), _ptr(k[1]), _ptr(k[2]), self.splats.n, _ptr(k[3]),
+                      float(self.global_scale), _ptr(k[4]), int(self.max_hits), float(self.t_stop),
+                      float(self.beta))
+
+
+class BVH:
+    """The oracle's own top-down median-split BVH (an accelerator only: images equal brute force)."""
+
+    def __init__(self, scene: Scene, leaf: int = 4):
+        self._keep = [_c(scene.splats.pos_r, np.float32),
+                      None if scene.scale is None else _c(scene.scale, np.float32)]
+        self.h = _load().orc_bvh_build(_ptr(self._keep[0]), _ptr(self._keep[1]),
+                                       float(scene.global_scale), scene.splats.n, int(leaf))
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _load().orc_bvh_free(self.h)
+            self.h = None
+
+
+def trace(scene: Scene, cam, pixels: Optional[np.ndarray] = None, bvh="auto", threads: int = 0):
+    """Trace the client camera's rays through the spheres (spec S5, S6).
+
+    Returns dict: rgba float64 [npix,4] (premultiplied), T [npix], nused [npix] (hits composited),
+    nhits [npix] (all hits), amb [npix] (bit 1: a binary64 hit test would disagree, bit 2: a binary64
+    key would reorder the hits -- a diagnostic of the binary32 reading, not an exclusion), hash [npix]
+    (FNV-1a of the ids of the composited hits, in order).
+    ``bvh``: "auto" builds the oracle BVH, None = brute force, or a :class:`BVH`.
+    """
+    lib = _load()
+    if isinstance(bvh, str):
+        bvh = BVH(scene) if scene.splats.n > 0 else None
+    if pixels is None:
+        npix = cam.width * cam.height
+        pix = None
+    else:
+        pix = _c(pixels, np.int32)
+        npix = pix.size
+    rgba = np.zeros((npix, 4), np.float64)
+    T = np.zeros(npix, np.float64)
+    nused = np.zeros(npix, np.int32)
+    nhits = np.zeros(npix, np.int32)
+    amb = np.zeros(npix, np.uint8)
+    hsh = np.zeros(npix, np.uint64)
+    sc = scene._c()
+    rc = lib.orc_trace(ctypes.byref(sc), None if bvh is None else bvh.h, ctypes.byref(_cam(cam)),
+                       _ptr(pix), int(npix), rgba.ctypes.data, T.ctypes.data, nused.ctypes.data,
+                       nhits.ctypes.data, amb.ctypes.data, hsh.ctypes.data, int(threads))
+    if rc != 0:
+        raise ValueError("orc_trace failed")
+    return {"rgba": rgba, "T": T, "nused": nused, "nhits": nhits, "amb": amb, "hash": hsh}
+
+
+def trace_backward(scene: Scene, cam, dL_dimg: np.ndarray, bvh="auto", threads: int = 0):
+    """Adjoint of :func:`trace` (spec S7): returns (g_rgba [N,4], g_opacity [N], g_scale [N])
+    in compacted splat order, for the upstream gradient dL_dimg [H*W,4] (float64)."""
+    lib = _load()
+    if isinstance(bvh, str):
+        bvh = BVH(scene) if scene.splats.n > 0 else None
+    n = scene.splats.n
+    g = _c(dL_dimg, np.float64).reshape(-1, 4)
+    assert g.shape[0] == cam.width * cam.height
+    gr = np.zeros((max(n, 1), 4), np.float64)
+    go = np.zeros(max(n, 1), np.float64)
+    gs = np.zeros(max(n, 1), np.float64)
+    sc = scene._c()
+    rc = lib.orc_trace_backward(ctypes.byref(sc), None if bvh is None else bvh.h,
+                                ctypes.byref(_cam(cam)), g.ctypes.data, gr.ctypes.data,
+                                go.ctypes.data, gs.ctypes.data, int(threads))
+    if rc != 0:
+        raise ValueError("orc_trace_backward failed")
+    return gr[:n], go[:n], gs[:n]
+
+
+def lbvh(pos_r: np.ndarray, scale: Optional[np.ndarray] = None, global_scale: float = 1.0,
+         leaf: int = 1):
+    """LBVH reference (spec S8): Morton codes, stable order, radix-tree children, child boxes.
+
+    Returns dict: codes (sorted, uint32 [N]), order (uint32 [N], sorted -> compacted index),
+    child (int32 [M-1, 2], bit 31 set = leaf index), boxes (float32 [M-1, 2, 6]: child lo xyz, hi xyz),
+    root (int32), cbounds (float32 [6]).
+    """
+    pos_r = _c(pos_r, np.float32)
+    n = pos_r.shape[0]
+    M = (n + leaf - 1) // leaf
+    codes = np.zeros(n, np.uint32)
+    order = np.zeros(n, np.uint32)
+    child = np.zeros((max(M - 1, 1), 2), np.int32)
+    boxes = np.zeros((max(M - 1, 1), 2, 6), np.float32)
+    root = np.zeros(1, np.int32)
+    cb = np.zeros(6, np.float32)
+    sc = None if scale is None else _c(scale, np.float32)
+    rc = _load().orc_lbvh(pos_r.ctypes.data, _ptr(sc), float(global_scale), n, int(leaf),
+                          codes.ctypes.data, order.ctypes.data, child.ctypes.data, boxes.ctypes.data,
+                          root.ctypes.data, cb.ctypes.data)
+    if rc != 0:
+        raise ValueError("orc_lbvh failed")
+    return {"codes": codes, "order": order, "child": child[:M - 1], "boxes": boxes[:M - 1],
+            "root": int(root[0]), "cbounds": cb}
