@@ -1,0 +1,205 @@
+/*
+ * wrs.h -- C ABI of libwrs: ray-traced sphere-splat image warping for remote volume rendering
+ * (Zellmann, "Augmenting Image Warping-Based Remote Volume Rendering with Ray Tracing", 2020).
+ *
+ * The client side of the method (§4): each pixel of a server-rendered colour + depth image becomes
+ * an object-space sphere (Eq. 1, §4.1); an LBVH is built over the spheres (§4.1, §4.2); every
+ * frame the spheres are ray traced from the newer camera and composited front to back (Fig. 2
+ * caption, §4).  The server-side volume ray caster with its depth heuristic (§4.1, §4.2) is also
+ * exported because it produces the inputs.
+ *
+ * Conventions for every entry point:
+ *  - All array pointers are DEVICE pointers owned by the caller, unless a comment says "host".
+ *    The library never allocates, frees or keeps device memory; work buffers ("scratch") are
+ *    passed in by the caller, sized by the matching *_bytes() query, 256-byte aligned.
+ *  - Every call is asynchronous on the given stream (a cudaStream_t; NULL = the legacy default
+ *    stream), performs no host synchronisation and no allocation, and can be captured in a CUDA
+ *    graph -- except wrs_check_status(), which synchronises the stream.
+ *  - The splat count lives on the device (uint32_t* n) so that unproject -> build -> trace needs
+ *    no host round trip; kernels are sized by capacity and skip work beyond *n.
+ *  - Return value: WRS_OK (0) or a negative WRS_ERR_* code; wrs_last_error() then describes the
+ *    failure (per host thread).  Argument errors are detected on the host before any launch.
+ *    Errors found by a kernel (a traversal stack overflow, a backward hit list longer than its
+ *    chunk table) are OR-ed into the caller's device status word (int32_t* status, may be NULL
+ *    where noted) and surface through wrs_check_status().
+ *  - Numerics follow a written spec: discrete decisions (hit/miss, hit order, depth threshold,
+ *    Morton code) in binary32 with a fixed operation order; see each function.
+ *  - Layouts: images are row-major, y = 0 the top row, RGBA interleaved float32 (16 B / pixel),
+ *    premultiplied.  Volumes are x-fastest [nz][ny][nx] over the unit cube [0,1]^3.
+ */
+#ifndef WRS_H
+#define WRS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void* wrs_stream_t; /* cudaStream_t */
+
+/* return codes */
+#define WRS_OK 0
+#define WRS_ERR_ARG -1       /* bad argument (NULL pointer, size, camera, parameter) */
+#define WRS_ERR_CUDA -2      /* a CUDA runtime call or launch failed */
+#define WRS_ERR_CAPACITY -3  /* an output or buffer is smaller than the input requires */
+#define WRS_ERR_SCRATCH -4   /* scratch buffer too small */
+#define WRS_ERR_DEVICE -5    /* a kernel reported an error in the status word */
+
+/* bits of the device status word */
+#define WRS_STATUS_STACK_OVERFLOW 1u  /* BVH traversal stack exceeded; the ray was cut short */
+#define WRS_STATUS_CHUNK_OVERFLOW 2u  /* backward: more hit chunks than its table holds */
+#define WRS_STATUS_MALFORMED_TREE 4u  /* traversal met an impossible node reference or revisit */
+
+/* volume scalar types */
+#define WRS_F32 0
+#define WRS_U8 1
+
+/* radius rules for wrs_unproject */
+#define WRS_RADIUS_FOOTPRINT 0 /* half diagonal of the pixel footprint at the sample's depth */
+#define WRS_RADIUS_VOXEL 1     /* half a voxel's diagonal, the paper's rule (§4.1) */
+
+/* Pinhole camera.  right/up/fwd: orthonormal basis, view along +fwd.  Pixel (x, y), y = 0 top,
+ * one ray through each pixel centre: u = ((2x+1)/W - 1) tan_half_fovy W/H,
+ * v = (1 - (2y+1)/H) tan_half_fovy, d = normalize(fwd + u right + v up), origin eye (Eq. 1). */
+typedef struct {
+    float eye[3], right[3], up[3], fwd[3];
+    float tan_half_fovy;
+    int32_t width, height;
+} wrs_camera;
+
+/* A splat set.  pos_r[i] = (x, y, z, r), rgba[i] = premultiplied colour, id[i] = server pixel
+ * index y*Ws + x (the tie-break of equal hit distances).  src[i] is filled only for sorted sets
+ * (output of wrs_build_lbvh): the compacted index the sorted splat came from; NULL otherwise.
+ * n: device uint32 holding the number of valid splats.  capacity: entries allocated. */
+typedef struct {
+    float* pos_r;     /* [capacity][4] */
+    float* rgba;      /* [capacity][4] */
+    uint32_t* id;     /* [capacity] */
+    uint32_t* src;    /* [capacity] or NULL */
+    uint32_t* n;      /* [1] */
+    uint32_t capacity;
+} wrs_splats;
+
+/* An LBVH: one device buffer of wrs_lbvh_bytes(capacity, leaf_size) bytes holding a 64-byte
+ * header and the internal nodes (64 B each: both children's boxes and references). */
+typedef struct {
+    void* nodes;
+    uint32_t capacity;  /* maximum splats */
+    uint32_t leaf_size; /* splats per leaf, 1..16 */
+} wrs_lbvh;
+
+/* Compositing (spec S6) and performance parameters of a trace.  Results do not depend on
+ * k_chunk or block (bitwise). */
+typedef struct {
+    int32_t max_hits;     /* H: hits composited at most; 1 = first hit (the paper), 0 = all */
+    float t_stop;         /* stop once transmittance <= t_stop (default 1e-5) */
+    float edge_softness;  /* beta in [0,1): soft sphere edge for differentiation; 0 = hard */
+    const float* opacity; /* device [n] per-splat opacity in COMPACTED order, or NULL (= 1) */
+    int32_t k_chunk;      /* hits gathered per traversal pass: 1, 2, 4, 8 or 16 */
+    int32_t block;        /* threads per block: 64, 128 or 256 */
+} wrs_trace_params;
+
+/* One client session of wrs_trace_batched (device array of these). */
+typedef struct {
+    const void* nodes;     /* the session's LBVH buffer */
+    const float* pos_r;    /* its sorted splats */
+    const float* rgba;
+    const uint32_t* id;
+    const uint32_t* src;
+    const float* opacity;  /* or NULL */
+    float* rgba_out;       /* [height][width][4] */
+    wrs_camera cam;
+    uint32_t tile_begin;   /* first work item of this session (prefix sum of wrs_session_tiles) */
+    uint32_t pad;
+} wrs_session;
+
+const char* wrs_version(void);
+/* Description of the last error on this host thread ("" if none). */
+const char* wrs_last_error(void);
+/* sizeof(wrs_session) and sizeof(wrs_camera), for bindings that lay the structs out by hand. */
+size_t wrs_session_size(void);
+size_t wrs_camera_size(void);
+
+/* Read the device status word (synchronises the stream), clear it, and return WRS_OK or
+ * WRS_ERR_DEVICE (with the set bits described by wrs_last_error). */
+int wrs_check_status(int32_t* status, wrs_stream_t stream);
+
+/* Server-side volume ray caster with the first-hit depth heuristic (§4.1, §4.2, Fig. 2; the
+ * heuristic is cited from earlier work, §2).  Spec S2: samples every step_vox voxels from the ray's
+ * entry into the unit cube, trilinear reconstruction, 256-entry RGBA transfer function (tf, device
+ * [256][4]), opacity correction to a one-voxel step, front-to-back compositing without early
+ * termination, at most 2^24 samples per ray; step_vox in [1e-3, 1e3].  depth_out = first sample distance whose transfer-function alpha >= tau, else the
+ * first with alpha > 0, else +inf.  rgba_out: [H][W][4] premultiplied; depth_out: [H][W]. */
+int wrs_raycast_volume(const void* vol, int32_t dtype, int32_t nx, int32_t ny, int32_t nz,
+                       const float* tf, const wrs_camera* cam, float step_vox, float tau,
+                       float* rgba_out, float* depth_out, wrs_stream_t stream);
+
+/* Unprojection with footprint radius and stable compaction (Eq. 1, §4.1).  For every server
+ * pixel with finite depth t >= 0 and alpha > 0: p = eye + d t (d the pixel's ray of cam), radius
+ * by radius_mode (voxel_diag = length of a voxel's diagonal, used by WRS_RADIUS_VOXEL), colour
+ * copied.  Kept pixels are written to out in pixel order, id = pixel index; *out->n = count.
+ * Requires out->capacity >= width * height.  Scratch: wrs_unproject_scratch_bytes(w, h). */
+size_t wrs_unproject_scratch_bytes(int32_t width, int32_t height);
+int wrs_unproject(const float* rgba, const float* depth, const wrs_camera* cam,
+                  int32_t radius_mode, float voxel_diag, wrs_splats* out, void* scratch,
+                  size_t scratch_bytes, wrs_stream_t stream);
+
+/* LBVH over the spheres (§4.1, §4.2; spec S8): 30-bit Morton codes of the centres over their
+ * bounds, stable LSD radix sort of (code, index), binary radix tree (Karras 2012) over leaves of
+ * leaf_size consecutive sorted splats, bottom-up refit of the sphere boxes.  The effective radius
+ * r = max(s, 0) * r0 (s = radius_scale[i] in compacted order, or global_scale if radius_scale is
+ * NULL) is baked into sorted->pos_r[.].w; sorted also receives rgba, id, src (= compacted index)
+ * and *sorted->n (*in->n is clamped to in->capacity).  bvh->capacity and sorted->capacity must be
+ * >= in->capacity.
+ * Buffer sizes: wrs_lbvh_bytes() for bvh->nodes, wrs_lbvh_scratch_bytes() for scratch. */
+size_t wrs_lbvh_bytes(uint32_t capacity, uint32_t leaf_size);
+size_t wrs_lbvh_scratch_bytes(uint32_t capacity, uint32_t leaf_size);
+int wrs_build_lbvh(const wrs_splats* in, const float* radius_scale, float global_scale,
+                   const wrs_lbvh* bvh, wrs_splats* sorted, void* scratch, size_t scratch_bytes,
+                   wrs_stream_t stream);
+
+/* Trace the client camera's primary rays through the spheres and composite (spec S5, S6; the
+ * paper's first-hit query is max_hits = 1).  Hits ordered by (entry distance, id); each
+ * composited hit adds T (o w) rgb and multiplies T by 1 - clamp(o a w, 0, 1).  rgba_out:
+ * [H][W][4] premultiplied.  status: device word for traversal errors (may be NULL). */
+int wrs_trace(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* cam,
+              const wrs_trace_params* params, float* rgba_out, int32_t* status,
+              wrs_stream_t stream);
+
+/* Same traversal, counting instead of writing an image: counters (device uint64[6]) receive the
+ * totals over all rays of nodes visited, boxes tested, spheres tested, hits gathered, hits
+ * composited and traversal passes.  Used for the roofline's algorithmic byte and flop counts. */
+int wrs_trace_count(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* cam,
+                    const wrs_trace_params* params, unsigned long long* counters,
+                    int32_t* status, wrs_stream_t stream);
+
+/* Work items (16x16 pixel tiles) of one session with the given client size. */
+uint32_t wrs_session_tiles(int32_t width, int32_t height);
+
+/* Many client sessions, each with its own LBVH, splats, camera and output, traced in ONE
+ * persistent launch: blocks pop (session, tile) items from *work_counter (device uint32, reset by
+ * this call).  sessions: device array of n_sessions descriptors whose tile_begin are the prefix
+ * sums of wrs_session_tiles; total_tiles = their sum.  Each session's image equals wrs_trace's
+ * bitwise. */
+int wrs_trace_batched(const wrs_session* sessions, int32_t n_sessions, uint32_t total_tiles,
+                      const wrs_trace_params* params, uint32_t* work_counter, int32_t* status,
+                      wrs_stream_t stream);
+
+/* Adjoint of wrs_trace (spec S7): given dL/d(rgba_out) (device [H][W][4]), re-traverse every ray
+ * to rebuild its hit list (nothing is stored by the forward pass) and accumulate, in COMPACTED
+ * splat order, g_rgba[n][4] (dL/d rgba), g_opacity[n] (dL/d opacity, may be NULL) and
+ * g_scale[n] (dL/d radius scale, may be NULL; zero when edge_softness = 0).  radius_scale /
+ * global_scale must be the values the LBVH was built with.  The outputs are zeroed by this call
+ * over the first in-capacity entries; accumulation uses float atomics (summation order is not
+ * fixed).  status: device word (CHUNK_OVERFLOW if a ray has more than 64 * k_chunk hits). */
+int wrs_trace_backward(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* cam,
+                       const wrs_trace_params* params, const float* radius_scale,
+                       float global_scale, const float* dL_drgba, float* g_rgba,
+                       float* g_opacity, float* g_scale, int32_t* status, wrs_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WRS_H */

@@ -200,7 +200,7 @@ static void rc_pixel(void* vctx, int64_t slot, int tid) {
 
     float t_first = INFINITY, t_any = INFINITY;
     double C[3] = {0, 0, 0}, A = 0;
-    for (int j = 0;; j++) {
+    for (int j = 0; j < (1 << 24); j++) { /* at most 2^24 samples per ray */
         float tj = fmaf((float)j + 0.5f, dt, lo);
         if (!(tj < hi)) break;
         /* decision path, binary32 */
@@ -343,14 +343,26 @@ static void prim_box(const prim_src* s, int32_t i, double lo[3], double hi[3]) {
     }
 }
 
-static const float* g_sort_pos;
-static int g_sort_axis;
-static int cmp_axis(const void* a, const void* b) {
-    int32_t i = *(const int32_t*)a, j = *(const int32_t*)b;
-    float x = g_sort_pos[4 * i + g_sort_axis], y = g_sort_pos[4 * j + g_sort_axis];
-    if (x < y) return -1;
-    if (x > y) return 1;
-    return (i > j) - (i < j);
+/* Partition prim[first, first+count) so that the element of rank k (by centre coordinate on
+ * `axis`, ties by index) is in place, smaller before it, larger after it (quickselect). */
+static int prim_less(const float* pos, int axis, int32_t i, int32_t j) {
+    float x = pos[4 * (int64_t)i + axis], y = pos[4 * (int64_t)j + axis];
+    return x < y || (x == y && i < j);
+}
+static void select_kth(int32_t* a, int32_t n, int32_t k, const float* pos, int axis) {
+    int32_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int32_t pivot = a[lo + (hi - lo) / 2];
+        int32_t i = lo, j = hi;
+        while (i <= j) {
+            while (prim_less(pos, axis, a[i], pivot)) i++;
+            while (prim_less(pos, axis, pivot, a[j])) j--;
+            if (i <= j) { int32_t t = a[i]; a[i] = a[j]; a[j] = t; i++; j--; }
+        }
+        if (k <= j) hi = j;
+        else if (k >= i) lo = i;
+        else return;
+    }
 }
 
 static int32_t obvh_build_rec(orc_bvh* B, const prim_src* s, int32_t first, int32_t count,
@@ -377,10 +389,8 @@ static int32_t obvh_build_rec(orc_bvh* B, const prim_src* s, int32_t first, int3
     int axis = 0;
     for (int k = 1; k < 3; k++)
         if (chi[k] - clo[k] > chi[axis] - clo[axis]) axis = k;
-    g_sort_pos = s->pos_r;
-    g_sort_axis = axis;
-    qsort(B->prim + first, (size_t)count, sizeof(int32_t), cmp_axis);
     int32_t half = count / 2;
+    select_kth(B->prim + first, count, half, s->pos_r, axis);
     int32_t l = obvh_build_rec(B, s, first, half, leaf);
     int32_t r = obvh_build_rec(B, s, first + half, count - half, leaf);
     B->nodes[me].left = l;

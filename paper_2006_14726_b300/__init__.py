@@ -1,0 +1,421 @@
+"""Python binding of libwrs: ray-traced sphere-splat image warping on B300 (sm_103a).
+
+Zellmann, "Augmenting Image Warping-Based Remote Volume Rendering with Ray Tracing" (2020):
+each pixel of a server-rendered colour + depth image becomes an object-space sphere (Eq. 1,
+§4.1), an LBVH is built over the spheres (§4.1, §4.2), and every client frame ray-traces them
+from the newer camera, compositing the hits front to back (Fig. 2 caption, §4).
+
+This module only marshals arguments: every step runs in the CUDA kernels of ``libwrs.so``
+(built from ``csrc/`` by ``python -m paper_2006_14726_b300._build``).  PyTorch provides device
+memory and streams.  There is no CPU fallback: importing this package without the built library
+raises ImportError, and every call needs CUDA tensors.
+
+Entry points (same names as the C ABI in ``include/wrs.h``): :func:`raycast_volume`,
+:func:`unproject`, :func:`build_lbvh`, :func:`trace`, :func:`trace_count`, :func:`trace_batched`,
+:func:`trace_backward`, plus :class:`TraceFunction` (torch.autograd) and :mod:`.autotune`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import List, Optional, Sequence, Tuple
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwrs.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2006_14726_b300._build` "
+                      "(there is no CPU fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+WRS_OK = 0
+WRS_ERR_ARG = -1
+WRS_ERR_CUDA = -2
+WRS_ERR_CAPACITY = -3
+WRS_ERR_SCRATCH = -4
+WRS_ERR_DEVICE = -5
+STATUS_STACK_OVERFLOW = 1
+STATUS_CHUNK_OVERFLOW = 2
+F32 = 0
+U8 = 1
+RADIUS_FOOTPRINT = 0
+RADIUS_VOXEL = 1
+
+
+class WrsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_float * 3), ("right", ctypes.c_float * 3),
+                ("up", ctypes.c_float * 3), ("fwd", ctypes.c_float * 3),
+                ("tan_half_fovy", ctypes.c_float), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32)]
+
+
+class _Splats(ctypes.Structure):
+    _fields_ = [("pos_r", ctypes.c_void_p), ("rgba", ctypes.c_void_p), ("id", ctypes.c_void_p),
+                ("src", ctypes.c_void_p), ("n", ctypes.c_void_p), ("capacity", ctypes.c_uint32)]
+
+
+class _Lbvh(ctypes.Structure):
+    _fields_ = [("nodes", ctypes.c_void_p), ("capacity", ctypes.c_uint32),
+                ("leaf_size", ctypes.c_uint32)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("max_hits", ctypes.c_int32), ("t_stop", ctypes.c_float),
+                ("edge_softness", ctypes.c_float), ("opacity", ctypes.c_void_p),
+                ("k_chunk", ctypes.c_int32), ("block", ctypes.c_int32)]
+
+
+class Session(ctypes.Structure):
+    _fields_ = [("nodes", ctypes.c_void_p), ("pos_r", ctypes.c_void_p), ("rgba", ctypes.c_void_p),
+                ("id", ctypes.c_void_p), ("src", ctypes.c_void_p), ("opacity", ctypes.c_void_p),
+                ("rgba_out", ctypes.c_void_p), ("cam", Camera), ("tile_begin", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32)]
+
+
+def _sig(name, res, *args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = list(args)
+    return f
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int32
+_U = ctypes.c_uint32
+_F = ctypes.c_float
+_Z = ctypes.c_size_t
+_sig("wrs_version", ctypes.c_char_p)
+_sig("wrs_last_error", ctypes.c_char_p)
+_sig("wrs_session_size", _Z)
+_sig("wrs_camera_size", _Z)
+_sig("wrs_check_status", _I, _P, _P)
+_sig("wrs_raycast_volume", _I, _P, _I, _I, _I, _I, _P, ctypes.POINTER(Camera), _F, _F, _P, _P, _P)
+_sig("wrs_unproject_scratch_bytes", _Z, _I, _I)
+_sig("wrs_unproject", _I, _P, _P, ctypes.POINTER(Camera), _I, _F, ctypes.POINTER(_Splats), _P, _Z, _P)
+_sig("wrs_lbvh_bytes", _Z, _U, _U)
+_sig("wrs_lbvh_scratch_bytes", _Z, _U, _U)
+_sig("wrs_build_lbvh", _I, ctypes.POINTER(_Splats), _P, _F, ctypes.POINTER(_Lbvh),
+     ctypes.POINTER(_Splats), _P, _Z, _P)
+_sig("wrs_trace", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats), ctypes.POINTER(Camera),
+     ctypes.POINTER(_Params), _P, _P, _P)
+_sig("wrs_trace_count", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats), ctypes.POINTER(Camera),
+     ctypes.POINTER(_Params), _P, _P, _P)
+_sig("wrs_session_tiles", _U, _I, _I)
+_sig("wrs_trace_batched", _I, _P, _I, _U, ctypes.POINTER(_Params), _P, _P, _P)
+_sig("wrs_trace_backward", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats), ctypes.POINTER(Camera),
+     ctypes.POINTER(_Params), _P, _F, _P, _P, _P, _P, _P, _P)
+
+lib = _lib
+assert _lib.wrs_session_size() == ctypes.sizeof(Session), "wrs_session layout mismatch"
+assert _lib.wrs_camera_size() == ctypes.sizeof(Camera), "wrs_camera layout mismatch"
+
+
+def version() -> str:
+    return _lib.wrs_version().decode()
+
+
+def last_error() -> str:
+    return _lib.wrs_last_error().decode()
+
+
+def _check(rc: int, fn: str):
+    if rc != WRS_OK:
+        raise WrsError(rc, f"{fn}: {last_error()}")
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libwrs takes CUDA tensors only (there is no CPU path)")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def make_camera(cam) -> Camera:
+    """Any object with eye/right/up/fwd/tan_half_fovy/width/height -> the C struct."""
+    c = Camera()
+    for f in ("eye", "right", "up", "fwd"):
+        getattr(c, f)[:] = [float(x) for x in getattr(cam, f)]
+    c.tan_half_fovy = float(cam.tan_half_fovy)
+    c.width = int(cam.width)
+    c.height = int(cam.height)
+    return c
+
+
+def _cam(cam) -> Camera:
+    return cam if isinstance(cam, Camera) else make_camera(cam)
+
+
+# ----------------------------------------------------------------------------------------------
+# buffers
+# ----------------------------------------------------------------------------------------------
+class SplatBuffers:
+    """Device splat set (see wrs_splats): pos_r [cap,4], rgba [cap,4], id [cap], src [cap], n [1].
+
+    ``id`` and ``src`` are int32 tensors holding uint32 values (< 2^31)."""
+
+    def __init__(self, capacity: int, device=None, sorted: bool = False):
+        device = device or torch.device("cuda")
+        cap = max(int(capacity), 1)
+        self.capacity = int(capacity)
+        self.pos_r = torch.zeros(cap, 4, dtype=torch.float32, device=device)
+        self.rgba = torch.zeros(cap, 4, dtype=torch.float32, device=device)
+        self.id = torch.zeros(cap, dtype=torch.int32, device=device)
+        self.src = torch.zeros(cap, dtype=torch.int32, device=device) if sorted else None
+        self.n = torch.zeros(1, dtype=torch.int32, device=device)
+
+    def c(self) -> _Splats:
+        return _Splats(_ptr(self.pos_r), _ptr(self.rgba), _ptr(self.id), _ptr(self.src),
+                       _ptr(self.n), self.capacity)
+
+    def count(self) -> int:
+        return int(self.n.item())
+
+    def view(self):
+        """(pos_r, rgba, id[, src]) trimmed to the current count (synchronises)."""
+        k = self.count()
+        out = [self.pos_r[:k], self.rgba[:k], self.id[:k]]
+        if self.src is not None:
+            out.append(self.src[:k])
+        return tuple(out)
+
+
+class LBVH:
+    """Device LBVH buffer (see wrs_lbvh)."""
+
+    def __init__(self, capacity: int, leaf_size: int = 1, device=None):
+        device = device or torch.device("cuda")
+        nbytes = _lib.wrs_lbvh_bytes(int(capacity), int(leaf_size))
+        if nbytes == 0:
+            raise ValueError(f"leaf_size {leaf_size} not in 1..16")
+        self.capacity = int(capacity)
+        self.leaf_size = int(leaf_size)
+        self.nodes = torch.zeros(nbytes, dtype=torch.uint8, device=device)
+
+    def c(self) -> _Lbvh:
+        return _Lbvh(_ptr(self.nodes), self.capacity, self.leaf_size)
+
+    def header(self) -> dict:
+        h = self.nodes[:64].cpu()
+        u = h.view(torch.int32)
+        f = h.view(torch.float32)
+        return {"n": int(u[0]), "m": int(u[1]), "leaf": int(u[2]), "root": int(u[3]),
+                "cmin": f[4:7].tolist(), "cmax": f[7:10].tolist(), "maxabs": float(f[10]),
+                "rmax": float(f[11])}
+
+    def node_table(self) -> Tuple[torch.Tensor, torch.Tensor]:
+        """(boxes [M-1, 2, 6] float32, child refs [M-1, 2] int32) of the internal nodes."""
+        m = self.header()["m"]
+        k = max(m - 1, 0)
+        raw = self.nodes[64:64 + 64 * k].view(torch.float32).view(k, 16)
+        boxes = raw[:, :12].reshape(k, 2, 6)
+        refs = raw[:, 12:14].contiguous().view(torch.int32)
+        return boxes, refs
+
+
+def _scratch(nbytes: int, device=None) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device or torch.device("cuda"))
+
+
+# ----------------------------------------------------------------------------------------------
+# entry points
+# ----------------------------------------------------------------------------------------------
+def raycast_volume(vol: torch.Tensor, tf: torch.Tensor, cam, step_vox: float = 0.5,
+                   tau: float = 0.1, rgba_out: Optional[torch.Tensor] = None,
+                   depth_out: Optional[torch.Tensor] = None, stream=None):
+    """Server volume ray caster + first-hit depth heuristic.  vol: CUDA [nz,ny,nx] float32 or
+    uint8; tf: CUDA [256,4] float32.  Returns (rgba [H,W,4], depth [H,W])."""
+    c = _cam(cam)
+    if vol.dtype == torch.uint8:
+        dt = U8
+    elif vol.dtype == torch.float32:
+        dt = F32
+    else:
+        raise TypeError("volume must be float32 or uint8")
+    nz, ny, nx = vol.shape
+    if rgba_out is None:
+        rgba_out = torch.empty(c.height, c.width, 4, dtype=torch.float32, device=vol.device)
+    if depth_out is None:
+        depth_out = torch.empty(c.height, c.width, dtype=torch.float32, device=vol.device)
+    _check(_lib.wrs_raycast_volume(_ptr(vol), dt, nx, ny, nz, _ptr(tf), ctypes.byref(c),
+                                   float(step_vox), float(tau), _ptr(rgba_out), _ptr(depth_out),
+                                   _stream(stream)), "wrs_raycast_volume")
+    return rgba_out, depth_out
+
+
+def unproject_scratch_bytes(width: int, height: int) -> int:
+    return int(_lib.wrs_unproject_scratch_bytes(int(width), int(height)))
+
+
+def unproject(rgba: torch.Tensor, depth: torch.Tensor, cam, radius_mode: int = RADIUS_FOOTPRINT,
+              voxel_diag: float = 0.0, out: Optional[SplatBuffers] = None,
+              scratch: Optional[torch.Tensor] = None, stream=None) -> SplatBuffers:
+    """Eq. 1 unprojection + radius + stable compaction of a server image into splats."""
+    c = _cam(cam)
+    if out is None:
+        out = SplatBuffers(c.width * c.height, device=rgba.device)
+    need = unproject_scratch_bytes(c.width, c.height)
+    if scratch is None:
+        scratch = _scratch(need, rgba.device)
+    sp = out.c()
+    _check(_lib.wrs_unproject(_ptr(rgba), _ptr(depth), ctypes.byref(c), int(radius_mode),
+                              float(voxel_diag), ctypes.byref(sp), _ptr(scratch), scratch.numel(),
+                              _stream(stream)), "wrs_unproject")
+    return out
+
+
+def lbvh_scratch_bytes(capacity: int, leaf_size: int) -> int:
+    return int(_lib.wrs_lbvh_scratch_bytes(int(capacity), int(leaf_size)))
+
+
+def build_lbvh(splats: SplatBuffers, leaf_size: int = 1, radius_scale: Optional[torch.Tensor] = None,
+               global_scale: float = 1.0, bvh: Optional[LBVH] = None,
+               sorted: Optional[SplatBuffers] = None, scratch: Optional[torch.Tensor] = None,
+               stream=None) -> Tuple[LBVH, SplatBuffers]:
+    """LBVH over the splats; returns (bvh, sorted splats with baked effective radius)."""
+    dev = splats.pos_r.device
+    if bvh is None:
+        bvh = LBVH(splats.capacity, leaf_size, device=dev)
+    if sorted is None:
+        sorted = SplatBuffers(splats.capacity, device=dev, sorted=True)
+    need = lbvh_scratch_bytes(splats.capacity, bvh.leaf_size)
+    if scratch is None:
+        scratch = _scratch(need, dev)
+    a, b, o = splats.c(), bvh.c(), sorted.c()
+    _check(_lib.wrs_build_lbvh(ctypes.byref(a), _ptr(radius_scale), float(global_scale), ctypes.byref(b),
+                               ctypes.byref(o), _ptr(scratch), scratch.numel(), _stream(stream)),
+           "wrs_build_lbvh")
+    return bvh, sorted
+
+
+@dataclass
+class TraceParams:
+    max_hits: int = 0            # 1 = first hit (the paper), 0 = all hits
+    t_stop: float = 1e-5
+    edge_softness: float = 0.0
+    k_chunk: int = 8
+    block: int = 128
+
+    def c(self, opacity: Optional[torch.Tensor] = None) -> _Params:
+        return _Params(int(self.max_hits), float(self.t_stop), float(self.edge_softness),
+                       _ptr(opacity), int(self.k_chunk), int(self.block))
+
+
+def trace(bvh: LBVH, sorted: SplatBuffers, cam, params: TraceParams = TraceParams(),
+          opacity: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None,
+          status: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Trace the client camera through the spheres; returns premultiplied RGBA [H,W,4]."""
+    c = _cam(cam)
+    if out is None:
+        out = torch.empty(c.height, c.width, 4, dtype=torch.float32, device=sorted.pos_r.device)
+    b, s, p = bvh.c(), sorted.c(), params.c(opacity)
+    _check(_lib.wrs_trace(ctypes.byref(b), ctypes.byref(s), ctypes.byref(c), ctypes.byref(p),
+                          _ptr(out), _ptr(status), _stream(stream)), "wrs_trace")
+    return out
+
+
+COUNTER_NAMES = ("nodes", "boxes", "spheres", "gathered", "composited", "passes")
+
+
+def trace_count(bvh: LBVH, sorted: SplatBuffers, cam, params: TraceParams = TraceParams(),
+                opacity: Optional[torch.Tensor] = None, status: Optional[torch.Tensor] = None,
+                stream=None) -> dict:
+    """Traversal statistics over all rays (synchronises)."""
+    c = _cam(cam)
+    cnt = torch.zeros(6, dtype=torch.int64, device=sorted.pos_r.device)
+    b, s, p = bvh.c(), sorted.c(), params.c(opacity)
+    _check(_lib.wrs_trace_count(ctypes.byref(b), ctypes.byref(s), ctypes.byref(c), ctypes.byref(p),
+                                _ptr(cnt), _ptr(status), _stream(stream)), "wrs_trace_count")
+    return dict(zip(COUNTER_NAMES, [int(v) for v in cnt.cpu()]))
+
+
+def session_tiles(width: int, height: int) -> int:
+    return int(_lib.wrs_session_tiles(int(width), int(height)))
+
+
+class Batch:
+    """Descriptors of many client sessions for :func:`trace_batched` (device array + outputs)."""
+
+    def __init__(self, sessions: Sequence[Tuple[LBVH, SplatBuffers, object]],
+                 opacity: Optional[Sequence[Optional[torch.Tensor]]] = None, device=None):
+        device = device or torch.device("cuda")
+        n = len(sessions)
+        arr = (Session * n)()
+        self.outputs: List[torch.Tensor] = []
+        self._keep = []
+        tile = 0
+        for i, (bvh, sp, cam) in enumerate(sessions):
+            c = _cam(cam)
+            out = torch.empty(c.height, c.width, 4, dtype=torch.float32, device=device)
+            op = opacity[i] if opacity is not None else None
+            arr[i] = Session(_ptr(bvh.nodes), _ptr(sp.pos_r), _ptr(sp.rgba), _ptr(sp.id),
+                             _ptr(sp.src), _ptr(op), _ptr(out), c, tile, 0)
+            self.outputs.append(out)
+            self._keep.append((bvh, sp, op))
+            tile += session_tiles(c.width, c.height)
+        self.total_tiles = tile
+        self.n_sessions = n
+        raw = bytes(memoryview(arr).cast("B"))
+        self.desc = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device)
+        self.work = torch.zeros(1, dtype=torch.int32, device=device)
+
+
+def trace_batched(batch: Batch, params: TraceParams = TraceParams(),
+                  status: Optional[torch.Tensor] = None, stream=None) -> List[torch.Tensor]:
+    """All sessions of ``batch`` in one persistent launch; returns the per-session images."""
+    p = params.c(None)
+    _check(_lib.wrs_trace_batched(_ptr(batch.desc), batch.n_sessions, batch.total_tiles,
+                                  ctypes.byref(p), _ptr(batch.work), _ptr(status), _stream(stream)),
+           "wrs_trace_batched")
+    return batch.outputs
+
+
+def trace_backward(bvh: LBVH, sorted: SplatBuffers, cam, dL_drgba: torch.Tensor,
+                   params: TraceParams = TraceParams(), opacity: Optional[torch.Tensor] = None,
+                   radius_scale: Optional[torch.Tensor] = None, global_scale: float = 1.0,
+                   want_opacity: bool = True, want_scale: bool = True,
+                   status: Optional[torch.Tensor] = None, stream=None):
+    """Adjoint of :func:`trace`: returns (g_rgba [cap,4], g_opacity [cap] | None, g_scale [cap] | None)
+    in compacted splat order."""
+    c = _cam(cam)
+    dev = sorted.pos_r.device
+    cap = max(sorted.capacity, 1)
+    g_rgba = torch.empty(cap, 4, dtype=torch.float32, device=dev)
+    g_op = torch.empty(cap, dtype=torch.float32, device=dev) if want_opacity else None
+    g_sc = torch.empty(cap, dtype=torch.float32, device=dev) if want_scale else None
+    b, s, p = bvh.c(), sorted.c(), params.c(opacity)
+    _check(_lib.wrs_trace_backward(ctypes.byref(b), ctypes.byref(s), ctypes.byref(c), ctypes.byref(p),
+                                   _ptr(radius_scale), float(global_scale), _ptr(dL_drgba.contiguous()),
+                                   _ptr(g_rgba), _ptr(g_op), _ptr(g_sc), _ptr(status), _stream(stream)),
+           "wrs_trace_backward")
+    return g_rgba, g_op, g_sc
+
+
+def check_status(status: torch.Tensor, stream=None):
+    """Raise WrsError if a kernel reported an error in the status word (synchronises)."""
+    _check(_lib.wrs_check_status(_ptr(status), _stream(stream)), "wrs_check_status")
+
+
+def new_status(device=None) -> torch.Tensor:
+    return torch.zeros(1, dtype=torch.int32, device=device or torch.device("cuda"))
+
+
+from .autograd import TraceFunction, render  # noqa: E402,F401

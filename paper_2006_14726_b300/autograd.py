@@ -1,0 +1,52 @@
+"""torch.autograd binding of the sphere-splat renderer (forward: wrs_build_lbvh + wrs_trace,
+backward: wrs_trace_backward).
+
+The differentiable quantities are the per-splat colour (premultiplied RGBA), opacity and radius
+scale, all in compacted splat order.  The forward pass stores no hit lists: the backward kernel
+re-traverses every ray (spec S7).  The radius scale changes the spheres, so every forward call
+rebuilds the LBVH with the current scales.
+"""
+from __future__ import annotations
+
+from typing import Optional
+
+import torch
+
+from . import SplatBuffers, TraceParams, build_lbvh, trace, trace_backward
+
+
+class TraceFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, rgba: torch.Tensor, opacity: Optional[torch.Tensor],
+                radius_scale: Optional[torch.Tensor], splats: SplatBuffers, cam,
+                params: TraceParams, leaf_size: int):
+        n = rgba.shape[0]
+        if n > splats.capacity:
+            raise ValueError("more colours than splats")
+        splats.rgba[:n].copy_(rgba.detach())
+        op = None if opacity is None else opacity.detach().contiguous()
+        sc = None if radius_scale is None else radius_scale.detach().contiguous()
+        bvh, sorted_ = build_lbvh(splats, leaf_size, radius_scale=sc)
+        img = trace(bvh, sorted_, cam, params, opacity=op)
+        ctx.state = (bvh, sorted_, cam, params, op, sc, n)
+        return img
+
+    @staticmethod
+    def backward(ctx, g_img: torch.Tensor):
+        bvh, sorted_, cam, params, op, sc, n = ctx.state
+        need_rgba, need_op, need_sc = ctx.needs_input_grad[:3]
+        g_rgba, g_op, g_sc = trace_backward(bvh, sorted_, cam, g_img.contiguous(), params,
+                                            opacity=op, radius_scale=sc,
+                                            want_opacity=need_op, want_scale=need_sc)
+        return (g_rgba[:n] if need_rgba else None,
+                g_op[:n] if need_op else None,
+                g_sc[:n] if need_sc else None,
+                None, None, None, None)
+
+
+def render(splats: SplatBuffers, cam, rgba: torch.Tensor, opacity: Optional[torch.Tensor] = None,
+           radius_scale: Optional[torch.Tensor] = None, params: TraceParams = TraceParams(),
+           leaf_size: int = 1) -> torch.Tensor:
+    """Differentiable client image [H,W,4] of the splats (geometry from ``splats``; colour,
+    opacity and radius scale from the given per-splat tensors, compacted order)."""
+    return TraceFunction.apply(rgba, opacity, radius_scale, splats, cam, params, leaf_size)

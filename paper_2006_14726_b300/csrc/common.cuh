@@ -1,0 +1,170 @@
+// common.cuh -- device-side definitions shared by the libwrs kernels.
+//
+// Decision arithmetic (primary rays, the ray-sphere test, Morton quantisation, volume samples)
+// follows the written spec's binary32 operation order exactly.  It is spelled with the __f*_rn
+// intrinsics so that nvcc can neither contract a multiply-add nor re-associate: a hit, a hit
+// order or a threshold crossing is then decided the same way by every correct implementation of
+// the spec.  Continuous quantities (colours, transmittance, gradients) use ordinary arithmetic.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "wrs.h"
+
+namespace wrs {
+
+constexpr uint32_t kLeafBit = 0x80000000u;
+constexpr int kStack = 64;         // traversal stack entries (tree depth <= 30 + log2(leaves) + 1)
+constexpr int kMaxLeaf = 16;
+constexpr int kBwdChunks = 64;     // backward: traversal passes per ray it can replay
+
+// 64-byte header at the start of an LBVH buffer; internal nodes follow it.
+struct LbvhHeader {
+    uint32_t n;        // splats
+    uint32_t m;        // leaves = ceil(n / leaf)
+    uint32_t leaf;     // splats per leaf
+    int32_t root;      // internal node 0, or kLeafBit | 0 when there is a single leaf
+    float cmin[3];     // centre bounds used by the Morton quantisation
+    float cmax[3];
+    float maxabs;      // largest |coordinate| of any sphere bound (traversal epsilon scale)
+    float rmax;        // largest effective radius
+    uint32_t pad[4];
+};
+static_assert(sizeof(LbvhHeader) == 64, "header must be 64 bytes");
+
+// Internal node = 4 x float4 = 64 B:
+//   floats 0..5  : child 0 box (lo.xyz, hi.xyz)
+//   floats 6..11 : child 1 box
+//   floats 12,13 : child references (int bits; kLeafBit set = leaf index)
+//   floats 14,15 : unused
+__host__ __device__ inline float4* lbvh_nodes(void* buf) {
+    return reinterpret_cast<float4*>(reinterpret_cast<char*>(buf) + sizeof(LbvhHeader));
+}
+__host__ __device__ inline const float4* lbvh_nodes(const void* buf) {
+    return reinterpret_cast<const float4*>(reinterpret_cast<const char*>(buf) + sizeof(LbvhHeader));
+}
+
+// ---------------------------------------------------------------------------------------------
+// Spec S1: primary ray of pixel (x, y).
+// ---------------------------------------------------------------------------------------------
+struct Ray {
+    float3 o, d;
+};
+
+__device__ __forceinline__ Ray primary_ray(const wrs_camera& c, int x, int y) {
+    const float W = (float)c.width, H = (float)c.height;
+    const float aspect = __fdiv_rn(W, H);
+    const float sx = __fmul_rn(c.tan_half_fovy, aspect);
+    const float u = __fmul_rn(__fsub_rn(__fdiv_rn((float)(2 * x + 1), W), 1.0f), sx);
+    const float v = __fmul_rn(__fsub_rn(1.0f, __fdiv_rn((float)(2 * y + 1), H)), c.tan_half_fovy);
+    const float ex = __fmaf_rn(v, c.up[0], __fmaf_rn(u, c.right[0], c.fwd[0]));
+    const float ey = __fmaf_rn(v, c.up[1], __fmaf_rn(u, c.right[1], c.fwd[1]));
+    const float ez = __fmaf_rn(v, c.up[2], __fmaf_rn(u, c.right[2], c.fwd[2]));
+    const float len2 = __fmaf_rn(ez, ez, __fmaf_rn(ey, ey, __fmul_rn(ex, ex)));
+    const float inv = __fdiv_rn(1.0f, __fsqrt_rn(len2));
+    Ray r;
+    r.o = make_float3(c.eye[0], c.eye[1], c.eye[2]);
+    r.d = make_float3(__fmul_rn(ex, inv), __fmul_rn(ey, inv), __fmul_rn(ez, inv));
+    return r;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Spec S5: ray-sphere test.  s = (centre, effective radius).  On a hit returns the entry key
+// max(b - sqrt(q), 0) and |f|^2 (the squared distance of the centre from the ray).
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ bool sphere_hit(const Ray& r, const float4 s, float& key, float& ff) {
+    const float ocx = __fsub_rn(s.x, r.o.x);
+    const float ocy = __fsub_rn(s.y, r.o.y);
+    const float ocz = __fsub_rn(s.z, r.o.z);
+    const float b = __fmaf_rn(ocz, r.d.z, __fmaf_rn(ocy, r.d.y, __fmul_rn(ocx, r.d.x)));
+    const float nb = -b;
+    const float fx = __fmaf_rn(nb, r.d.x, ocx);
+    const float fy = __fmaf_rn(nb, r.d.y, ocy);
+    const float fz = __fmaf_rn(nb, r.d.z, ocz);
+    ff = __fmaf_rn(fz, fz, __fmaf_rn(fy, fy, __fmul_rn(fx, fx)));
+    const float q = __fmaf_rn(s.w, s.w, -ff);
+    if (!(q > 0.0f)) return false;
+    const float sq = __fsqrt_rn(q);
+    if (!(__fadd_rn(b, sq) > 0.0f)) return false;
+    const float k0 = __fsub_rn(b, sq);
+    key = k0 > 0.0f ? k0 : 0.0f;
+    return true;
+}
+
+// (key, id) strict lexicographic order of hits (spec S5).
+__device__ __forceinline__ bool hit_less(float ka, uint32_t ia, float kb, uint32_t ib) {
+    return ka < kb || (ka == kb && ia < ib);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Conservative ray-box slab test.  Boxes are widened by eps so that no sphere the binary32 test
+// would hit is ever culled (the box test only prunes; it never decides a result).
+// ---------------------------------------------------------------------------------------------
+struct BoxRay {
+    float ix, iy, iz;      // 1 / d (guarded against zero components)
+    float lx, ly, lz;      // -(o + eps) / d  : offset for the low planes
+    float hx, hy, hz;      // -(o - eps) / d  : offset for the high planes
+};
+
+__device__ __forceinline__ BoxRay make_box_ray(const Ray& r, float eps) {
+    auto guard = [](float v) { return fabsf(v) < 1e-12f ? copysignf(1e-12f, v) : v; };
+    BoxRay b;
+    b.ix = 1.0f / guard(r.d.x);
+    b.iy = 1.0f / guard(r.d.y);
+    b.iz = 1.0f / guard(r.d.z);
+    b.lx = -(r.o.x + eps) * b.ix;
+    b.ly = -(r.o.y + eps) * b.iy;
+    b.lz = -(r.o.z + eps) * b.iz;
+    b.hx = -(r.o.x - eps) * b.ix;
+    b.hy = -(r.o.y - eps) * b.iy;
+    b.hz = -(r.o.z - eps) * b.iz;
+    return b;
+}
+
+__device__ __forceinline__ void box_test(const BoxRay& r, float lox, float loy, float loz,
+                                         float hix, float hiy, float hiz, float& tn, float& tf) {
+    const float ax = fmaf(lox, r.ix, r.lx), bx = fmaf(hix, r.ix, r.hx);
+    const float ay = fmaf(loy, r.iy, r.ly), by = fmaf(hiy, r.iy, r.hy);
+    const float az = fmaf(loz, r.iz, r.lz), bz = fmaf(hiz, r.iz, r.hz);
+    tn = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), 0.0f));
+    tf = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fmaxf(az, bz));
+}
+
+// Traversal epsilon: far above the binary32 error of the sphere test (a few units in the last
+// place of |o| + |c|), far below a sphere radius.
+__device__ __forceinline__ float traversal_eps(const Ray& r, float scene_maxabs) {
+    const float om = fmaxf(fmaxf(fabsf(r.o.x), fabsf(r.o.y)), fabsf(r.o.z));
+    return 1e-6f * (1.0f + om + scene_maxabs);
+}
+
+// Soft edge weight W(rho) of spec S6 and its derivative.
+__device__ __forceinline__ float soft_w(float rho, float beta) {
+    if (beta <= 0.0f || rho <= 1.0f - beta) return 1.0f;
+    float u = fmaxf((1.0f - rho) / beta, 0.0f);
+    return u * u * (3.0f - 2.0f * u);
+}
+__device__ __forceinline__ float soft_dw(float rho, float beta) {
+    if (beta <= 0.0f || rho <= 1.0f - beta) return 0.0f;
+    float u = (1.0f - rho) / beta;
+    if (u < 0.0f) return 0.0f;
+    return -6.0f * u * (1.0f - u) / beta;
+}
+
+__device__ __forceinline__ void set_status(int32_t* status, uint32_t bits) {
+    if (status) atomicOr(reinterpret_cast<unsigned int*>(status), bits);
+}
+
+}  // namespace wrs
+
+// host-side error plumbing shared by the entry points
+namespace wrs {
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+}  // namespace wrs
+
+#define WRS_LAUNCH_CHECK(what)                                         \
+    do {                                                               \
+        cudaError_t e_ = cudaGetLastError();                           \
+        if (e_ != cudaSuccess) return ::wrs::cuda_fail(e_, what);      \
+    } while (0)

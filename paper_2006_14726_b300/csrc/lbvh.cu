@@ -1,0 +1,475 @@
+// lbvh.cu -- LBVH over the sphere splats (§4.1, §4.2: the LBVH of Lauterbach et al. 2009 as used
+// by Zellmann et al. 2019; spec S8).
+//
+//   k_bounds_partial / k_bounds_final : centre bounds and the largest radius (two-level reduction)
+//   k_morton                          : 30-bit Morton code of each centre (binary32 quantisation)
+//   k_rs_hist / k_rs_scan / k_rs_scatter (x4) : stable LSD radix sort of (code, index), 8-bit digits
+//   k_karras                          : binary radix tree over leaf keys (Karras 2012)
+//   k_leaves_refit                    : gathers the splats into leaf order with their effective
+//                                       radius, computes leaf boxes and refits the internal nodes
+//                                       bottom-up (second thread to reach a node continues)
+//
+// The splat count is read on the device from the header, so the whole build runs without a host
+// synchronisation and can be captured into a CUDA graph.  No kernel waits on another block.
+#include "common.cuh"
+
+namespace {
+
+using wrs::LbvhHeader;
+using wrs::kLeafBit;
+
+constexpr int kBoundsBlocks = 512;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;  // keys per sort tile
+constexpr int kSortWarps = kSortThreads / 32;
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+struct Scratch {
+    uint32_t *keys0, *keys1, *vals0, *vals1, *hist, *leaf_parent, *node_parent, *visit;
+    float* partials;
+    uint32_t tiles;
+};
+
+uint32_t leaves_for(uint32_t cap, uint32_t leaf) { return cap == 0 ? 1 : (cap + leaf - 1) / leaf; }
+
+size_t scratch_layout(uint32_t cap, uint32_t leaf, char* base, Scratch* s) {
+    const uint32_t tiles = (cap + kSortTile - 1) / kSortTile;
+    const uint32_t m = leaves_for(cap, leaf);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char* p = base ? base + off : nullptr;
+        off += align256(bytes);
+        return p;
+    };
+    char* k0 = take(sizeof(uint32_t) * cap);
+    char* k1 = take(sizeof(uint32_t) * cap);
+    char* v0 = take(sizeof(uint32_t) * cap);
+    char* v1 = take(sizeof(uint32_t) * cap);
+    char* h = take(sizeof(uint32_t) * 256 * (size_t)(tiles ? tiles : 1));
+    char* lp = take(sizeof(uint32_t) * m);
+    char* np = take(sizeof(uint32_t) * m);
+    char* vi = take(sizeof(uint32_t) * m);
+    char* pa = take(sizeof(float) * 8 * kBoundsBlocks);
+    if (s) {
+        s->keys0 = (uint32_t*)k0; s->keys1 = (uint32_t*)k1;
+        s->vals0 = (uint32_t*)v0; s->vals1 = (uint32_t*)v1;
+        s->hist = (uint32_t*)h; s->leaf_parent = (uint32_t*)lp; s->node_parent = (uint32_t*)np;
+        s->visit = (uint32_t*)vi; s->partials = (float*)pa; s->tiles = tiles;
+    }
+    return off;
+}
+
+__device__ __forceinline__ float eff_radius(const float* __restrict__ scale, float gscale,
+                                            uint32_t i, float r0) {
+    float s = scale ? __ldg(scale + i) : gscale;
+    s = s > 0.0f ? s : 0.0f;  // also maps NaN to 0
+    return __fmul_rn(s, r0);
+}
+
+// ---- bounds --------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_bounds_partial(const float4* __restrict__ pos_r,
+                                                        const float* __restrict__ scale,
+                                                        float gscale, const uint32_t* __restrict__ n_in,
+                                                        uint32_t cap, float* __restrict__ partials) {
+    const uint32_t n = min(*n_in, cap);
+    float v[7] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0f};
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 p = pos_r[i];
+        v[0] = fminf(v[0], p.x); v[1] = fminf(v[1], p.y); v[2] = fminf(v[2], p.z);
+        v[3] = fmaxf(v[3], p.x); v[4] = fmaxf(v[4], p.y); v[5] = fmaxf(v[5], p.z);
+        v[6] = fmaxf(v[6], eff_radius(scale, gscale, i, p.w));
+    }
+    __shared__ float s[7][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 7; k++) {
+        float x = v[k];
+        for (int o = 16; o > 0; o >>= 1) {
+            const float y = __shfl_xor_sync(0xffffffffu, x, o);
+            x = (k < 3) ? fminf(x, y) : fmaxf(x, y);
+        }
+        if (lane == 0) s[k][warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        const int k = threadIdx.x;
+        float x = s[k][0];
+        for (int w = 1; w < 8; w++) x = (k < 3) ? fminf(x, s[k][w]) : fmaxf(x, s[k][w]);
+        partials[blockIdx.x * 8 + k] = x;
+    }
+}
+
+__global__ void k_bounds_final(const float* __restrict__ partials, const uint32_t* __restrict__ n_in,
+                               uint32_t cap, uint32_t leaf, LbvhHeader* __restrict__ hdr,
+                               uint32_t* __restrict__ n_sorted) {
+    if (threadIdx.x != 0) return;
+    float v[7] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0f};
+    for (int b = 0; b < kBoundsBlocks; b++)
+        for (int k = 0; k < 7; k++)
+            v[k] = (k < 3) ? fminf(v[k], partials[b * 8 + k]) : fmaxf(v[k], partials[b * 8 + k]);
+    const uint32_t n = min(*n_in, cap);  // a count beyond the capacity is clamped
+    LbvhHeader h = {};
+    h.n = n;
+    h.leaf = leaf;
+    h.m = n == 0 ? 0 : (n + leaf - 1) / leaf;
+    h.root = h.m <= 1 ? (int32_t)kLeafBit : 0;
+    float mx = 0.0f;
+    for (int k = 0; k < 3; k++) {
+        h.cmin[k] = n ? v[k] : 0.0f;
+        h.cmax[k] = n ? v[3 + k] : 0.0f;
+        mx = fmaxf(mx, fmaxf(fabsf(h.cmin[k]), fabsf(h.cmax[k])));
+    }
+    h.rmax = v[6];
+    h.maxabs = mx + v[6];
+    *hdr = h;
+    *n_sorted = n;
+}
+
+// ---- Morton codes (spec S8) ----------------------------------------------------------------
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {
+    v = (v * 0x00010001u) & 0xFF0000FFu;
+    v = (v * 0x00000101u) & 0x0F00F00Fu;
+    v = (v * 0x00000011u) & 0xC30C30C3u;
+    v = (v * 0x00000005u) & 0x49249249u;
+    return v;
+}
+
+__global__ void __launch_bounds__(256) k_morton(const float4* __restrict__ pos_r,
+                                                const LbvhHeader* __restrict__ hdr,
+                                                uint32_t* __restrict__ keys,
+                                                uint32_t* __restrict__ vals) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t n = hdr->n;
+    if (i >= n) return;
+    const float4 p = pos_r[i];
+    const float c[3] = {p.x, p.y, p.z};
+    uint32_t q[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const float ext = __fsub_rn(hdr->cmax[k], hdr->cmin[k]);
+        const float sc = ext > 0.0f ? __fdiv_rn(1024.0f, ext) : 0.0f;
+        const float v = floorf(__fmul_rn(__fsub_rn(c[k], hdr->cmin[k]), sc));
+        q[k] = v >= 1023.0f ? 1023u : (uint32_t)v;
+    }
+    keys[i] = (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+    vals[i] = i;
+}
+
+// ---- stable LSD radix sort, 8-bit digits ---------------------------------------------------
+// Histogram layout is digit-major: hist[d * tiles + tile], so one exclusive scan over the whole
+// array yields each (digit, tile) pair's first output position.
+__global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t* __restrict__ keys,
+                                                          const LbvhHeader* __restrict__ hdr,
+                                                          int shift, uint32_t tiles,
+                                                          uint32_t* __restrict__ hist) {
+    __shared__ uint32_t s_cnt[256];
+    s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t n = hdr->n;
+    const uint32_t base = blockIdx.x * kSortTile;
+    for (int k = 0; k < kSortItems; k++) {
+        const uint32_t i = base + k * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&s_cnt[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[threadIdx.x * tiles + blockIdx.x] = s_cnt[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* __restrict__ hist, uint32_t total) {
+    __shared__ uint32_t s[1024];
+    const uint32_t per = (total + 1023) / 1024;
+    const uint32_t lo = min(threadIdx.x * per, total), hi = min(lo + per, total);
+    uint32_t sum = 0;
+    for (uint32_t i = lo; i < hi; i++) sum += hist[i];
+    s[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const uint32_t v = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0;
+        __syncthreads();
+        s[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = s[threadIdx.x] - sum;
+    for (uint32_t i = lo; i < hi; i++) {
+        const uint32_t c = hist[i];
+        hist[i] = run;
+        run += c;
+    }
+}
+
+// Rank every key of the tile stably by digit (warp match + per-warp digit counters), stage the
+// tile in shared memory in digit order, then write each digit run to its global position.
+__global__ void __launch_bounds__(kSortThreads) k_rs_scatter(
+    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+    const uint32_t* __restrict__ offsets, const LbvhHeader* __restrict__ hdr, int shift,
+    uint32_t tiles) {
+    __shared__ uint32_t s_wcnt[kSortWarps][256];
+    __shared__ uint32_t s_start[256];
+    __shared__ uint32_t s_glob[256];
+    __shared__ uint32_t s_keys[kSortTile];
+    __shared__ uint32_t s_vals[kSortTile];
+    const uint32_t n = hdr->n;
+    const uint32_t base = blockIdx.x * kSortTile;
+    if (base >= n) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = lane; d < 256; d += 32) s_wcnt[warp][d] = 0;
+    __syncwarp();
+
+    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+    const uint32_t wbase = base + warp * 32 * kSortItems;
+#pragma unroll
+    for (int k = 0; k < kSortItems; k++) {
+        const uint32_t i = wbase + k * 32 + lane;
+        const bool valid = i < n;
+        key[k] = valid ? keys_in[i] : 0u;
+        val[k] = valid ? vals_in[i] : 0u;
+        const uint32_t d = (key[k] >> shift) & 255u;
+        const uint32_t label = valid ? d : (256u + lane);  // invalid lanes match nobody
+        const uint32_t peers = __match_any_sync(0xffffffffu, label);
+        const uint32_t before = __popc(peers & ((1u << lane) - 1u));
+        const uint32_t prev = valid ? s_wcnt[warp][d] : 0u;
+        __syncwarp();
+        if (valid && before == 0) s_wcnt[warp][d] = prev + __popc(peers);
+        __syncwarp();
+        rank[k] = valid ? prev + before : 0xFFFFFFFFu;
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps, then exclusive scan over digits (local starts)
+    {
+        const int d = threadIdx.x;  // kSortThreads == 256 digits
+        uint32_t run = 0;
+        for (int w = 0; w < kSortWarps; w++) {
+            const uint32_t c = s_wcnt[w][d];
+            s_wcnt[w][d] = run;
+            run += c;
+        }
+        s_start[d] = run;  // digit total, scanned below
+        s_glob[d] = offsets[d * tiles + blockIdx.x];
+    }
+    __syncthreads();
+    if (warp == 0) {  // exclusive scan of the 256 digit totals by one warp (8 per lane)
+        uint32_t t[8], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) { t[j] = s_start[lane * 8 + j]; sum += t[j]; }
+        uint32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        uint32_t run = inc - sum;
+#pragma unroll
+        for (int j = 0; j < 8; j++) { const uint32_t c = t[j]; s_start[lane * 8 + j] = run; run += c; }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kSortItems; k++) {
+        if (rank[k] == 0xFFFFFFFFu) continue;
+        const uint32_t d = (key[k] >> shift) & 255u;
+        const uint32_t pos = s_start[d] + s_wcnt[warp][d] + rank[k];
+        s_keys[pos] = key[k];
+        s_vals[pos] = val[k];
+    }
+    __syncthreads();
+    const uint32_t cnt = min((uint32_t)kSortTile, n - base);
+    for (uint32_t j = threadIdx.x; j < cnt; j += kSortThreads) {
+        const uint32_t kk = s_keys[j];
+        const uint32_t d = (kk >> shift) & 255u;
+        const uint32_t dst = s_glob[d] + (j - s_start[d]);
+        keys_out[dst] = kk;
+        vals_out[dst] = s_vals[j];
+    }
+}
+
+// ---- Karras 2012 binary radix tree over the leaf keys --------------------------------------
+__device__ __forceinline__ int delta(const uint32_t* __restrict__ codes, uint32_t leaf, int m,
+                                     int i, int j) {
+    if (j < 0 || j >= m) return -1;
+    const uint32_t a = __ldg(codes + (size_t)i * leaf), b = __ldg(codes + (size_t)j * leaf);
+    if (a != b) return __clz(a ^ b);
+    return 32 + __clz((uint32_t)i ^ (uint32_t)j);
+}
+
+__global__ void __launch_bounds__(256) k_karras(const uint32_t* __restrict__ codes,
+                                                const LbvhHeader* __restrict__ hdr,
+                                                float4* __restrict__ nodes,
+                                                uint32_t* __restrict__ leaf_parent,
+                                                uint32_t* __restrict__ node_parent) {
+    const int m = (int)hdr->m;
+    const uint32_t leaf = hdr->leaf;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m - 1) return;
+    const int d = (delta(codes, leaf, m, i, i + 1) - delta(codes, leaf, m, i, i - 1)) >= 0 ? 1 : -1;
+    const int dmin = delta(codes, leaf, m, i, i - d);
+    int lmax = 2;
+    while (delta(codes, leaf, m, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(codes, leaf, m, i, i + (l + t) * d) > dmin) l += t;
+    const int j = i + l * d;
+    const int dnode = delta(codes, leaf, m, i, j);
+    int s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (s + t < l && delta(codes, leaf, m, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    const int g = i + s * d + min(d, 0);
+    const int lo = min(i, j), hi = max(i, j);
+    const uint32_t left = (lo == g) ? (kLeafBit | (uint32_t)g) : (uint32_t)g;
+    const uint32_t right = (hi == g + 1) ? (kLeafBit | (uint32_t)(g + 1)) : (uint32_t)(g + 1);
+    nodes[4 * i + 3] = make_float4(__uint_as_float(left), __uint_as_float(right), 0.0f, 0.0f);
+    if (lo == g) leaf_parent[g] = (uint32_t)i << 1;
+    else node_parent[g] = (uint32_t)i << 1;
+    if (hi == g + 1) leaf_parent[g + 1] = ((uint32_t)i << 1) | 1u;
+    else node_parent[g + 1] = ((uint32_t)i << 1) | 1u;
+}
+
+// ---- leaf gather + bottom-up refit ---------------------------------------------------------
+__device__ __forceinline__ void store_box(float4* nodes, uint32_t node, uint32_t slot,
+                                          const float lo[3], const float hi[3]) {
+    float* f = reinterpret_cast<float*>(nodes + 4 * (size_t)node) + 6 * slot;
+    __stcg(f + 0, lo[0]); __stcg(f + 1, lo[1]); __stcg(f + 2, lo[2]);
+    __stcg(f + 3, hi[0]); __stcg(f + 4, hi[1]); __stcg(f + 5, hi[2]);
+}
+
+__global__ void __launch_bounds__(256) k_leaves_refit(
+    const uint32_t* __restrict__ order, const float4* __restrict__ pos_r,
+    const float4* __restrict__ rgba, const uint32_t* __restrict__ id,
+    const float* __restrict__ scale, float gscale, const LbvhHeader* __restrict__ hdr,
+    float4* __restrict__ nodes, const uint32_t* __restrict__ leaf_parent,
+    const uint32_t* __restrict__ node_parent, uint32_t* __restrict__ visit,
+    float4* __restrict__ s_pos, float4* __restrict__ s_rgba, uint32_t* __restrict__ s_id,
+    uint32_t* __restrict__ s_src) {
+    const uint32_t n = hdr->n, m = hdr->m, leaf = hdr->leaf;
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    const uint32_t first = j * leaf, last = min(first + leaf, n);
+    for (uint32_t k = first; k < last; k++) {
+        const uint32_t src = order[k];
+        const float4 p = pos_r[src];
+        const float r = eff_radius(scale, gscale, src, p.w);
+        lo[0] = fminf(lo[0], __fsub_rd(p.x, r)); hi[0] = fmaxf(hi[0], __fadd_ru(p.x, r));
+        lo[1] = fminf(lo[1], __fsub_rd(p.y, r)); hi[1] = fmaxf(hi[1], __fadd_ru(p.y, r));
+        lo[2] = fminf(lo[2], __fsub_rd(p.z, r)); hi[2] = fmaxf(hi[2], __fadd_ru(p.z, r));
+        s_pos[k] = make_float4(p.x, p.y, p.z, r);
+        s_rgba[k] = rgba[src];
+        s_id[k] = id[src];
+        s_src[k] = src;
+    }
+    if (m < 2) return;
+    uint32_t pp = leaf_parent[j];
+    uint32_t node = pp >> 1;
+    if (node + 1 >= m) return;  // never taken for a well-formed tree
+    store_box(nodes, node, pp & 1u, lo, hi);
+    __threadfence();
+    uint32_t old = atomicAdd(visit + node, 1u);
+    while (old == 1u) {  // second arrival: both children are final
+        __threadfence();
+        const float* f = reinterpret_cast<const float*>(nodes + 4 * (size_t)node);
+        float a[12];
+#pragma unroll
+        for (int k = 0; k < 12; k++) a[k] = __ldcg(f + k);
+        lo[0] = fminf(a[0], a[6]); lo[1] = fminf(a[1], a[7]); lo[2] = fminf(a[2], a[8]);
+        hi[0] = fmaxf(a[3], a[9]); hi[1] = fmaxf(a[4], a[10]); hi[2] = fmaxf(a[5], a[11]);
+        if (node == 0) break;
+        pp = node_parent[node];
+        node = pp >> 1;
+        if (node + 1 >= m) break;  // never taken for a well-formed tree
+        store_box(nodes, node, pp & 1u, lo, hi);
+        __threadfence();
+        old = atomicAdd(visit + node, 1u);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t wrs_lbvh_bytes(uint32_t capacity, uint32_t leaf_size) {
+    if (leaf_size < 1 || leaf_size > (uint32_t)wrs::kMaxLeaf) return 0;
+    const uint32_t m = leaves_for(capacity, leaf_size);
+    return sizeof(LbvhHeader) + 64 * (size_t)(m > 1 ? m - 1 : 1);
+}
+
+size_t wrs_lbvh_scratch_bytes(uint32_t capacity, uint32_t leaf_size) {
+    if (leaf_size < 1 || leaf_size > (uint32_t)wrs::kMaxLeaf) return 0;
+    return scratch_layout(capacity, leaf_size, nullptr, nullptr);
+}
+
+int wrs_build_lbvh(const wrs_splats* in, const float* radius_scale, float global_scale,
+                   const wrs_lbvh* bvh, wrs_splats* sorted, void* scratch, size_t scratch_bytes,
+                   wrs_stream_t stream) {
+    const char* fn = "wrs_build_lbvh";
+    if (!in || !bvh || !sorted) return wrs::fail(WRS_ERR_ARG, "%s: NULL struct", fn);
+    if (!in->pos_r || !in->rgba || !in->id || !in->n)
+        return wrs::fail(WRS_ERR_ARG, "%s: NULL input splat array", fn);
+    if (!sorted->pos_r || !sorted->rgba || !sorted->id || !sorted->src || !sorted->n)
+        return wrs::fail(WRS_ERR_ARG, "%s: NULL sorted splat array (src is required)", fn);
+    if (!bvh->nodes) return wrs::fail(WRS_ERR_ARG, "%s: bvh->nodes is NULL", fn);
+    const uint32_t leaf = bvh->leaf_size;
+    if (leaf < 1 || leaf > (uint32_t)wrs::kMaxLeaf)
+        return wrs::fail(WRS_ERR_ARG, "%s: leaf_size %u not in 1..16", fn, leaf);
+    if (bvh->capacity < in->capacity || sorted->capacity < in->capacity)
+        return wrs::fail(WRS_ERR_CAPACITY, "%s: bvh/sorted capacity below input capacity %u", fn,
+                         in->capacity);
+    if (in->capacity >= 0x80000000u) return wrs::fail(WRS_ERR_ARG, "%s: capacity >= 2^31", fn);
+    if ((reinterpret_cast<uintptr_t>(in->pos_r) | reinterpret_cast<uintptr_t>(in->rgba) |
+         reinterpret_cast<uintptr_t>(sorted->pos_r) | reinterpret_cast<uintptr_t>(sorted->rgba) |
+         reinterpret_cast<uintptr_t>(bvh->nodes)) & 15)
+        return wrs::fail(WRS_ERR_ARG, "%s: float4 arrays and nodes must be 16-byte aligned", fn);
+    if (!radius_scale && !(global_scale == global_scale))
+        return wrs::fail(WRS_ERR_ARG, "%s: global_scale is NaN", fn);
+    const uint32_t cap = in->capacity;
+    const size_t need = scratch_layout(cap, leaf, nullptr, nullptr);
+    if (!scratch || scratch_bytes < need)
+        return wrs::fail(WRS_ERR_SCRATCH, "%s: scratch needs %zu bytes, got %zu", fn, need,
+                         scratch_bytes);
+    if (reinterpret_cast<uintptr_t>(scratch) & 255)
+        return wrs::fail(WRS_ERR_ARG, "%s: scratch must be 256-byte aligned", fn);
+    Scratch S;
+    scratch_layout(cap, leaf, static_cast<char*>(scratch), &S);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    LbvhHeader* hdr = static_cast<LbvhHeader*>(bvh->nodes);
+    float4* nodes = wrs::lbvh_nodes(bvh->nodes);
+    const float4* pos4 = reinterpret_cast<const float4*>(in->pos_r);
+    const uint32_t m_cap = leaves_for(cap, leaf);
+    const uint32_t g256 = (cap + 255) / 256 ? (cap + 255) / 256 : 1;
+    const uint32_t gm = (m_cap + 255) / 256;
+
+    k_bounds_partial<<<kBoundsBlocks, 256, 0, s>>>(pos4, radius_scale, global_scale, in->n, cap,
+                                                   S.partials);
+    WRS_LAUNCH_CHECK("wrs_build_lbvh bounds");
+    k_bounds_final<<<1, 32, 0, s>>>(S.partials, in->n, cap, leaf, hdr, sorted->n);
+    WRS_LAUNCH_CHECK("wrs_build_lbvh bounds final");
+    if (cap == 0) return WRS_OK;
+    k_morton<<<g256, 256, 0, s>>>(pos4, hdr, S.keys0, S.vals0);
+    WRS_LAUNCH_CHECK("wrs_build_lbvh morton");
+    uint32_t *ki = S.keys0, *vi = S.vals0, *ko = S.keys1, *vo = S.vals1;
+    for (int shift = 0; shift < 32; shift += 8) {
+        k_rs_hist<<<S.tiles, kSortThreads, 0, s>>>(ki, hdr, shift, S.tiles, S.hist);
+        k_rs_scan<<<1, 1024, 0, s>>>(S.hist, 256 * S.tiles);
+        k_rs_scatter<<<S.tiles, kSortThreads, 0, s>>>(ki, vi, ko, vo, S.hist, hdr, shift, S.tiles);
+        WRS_LAUNCH_CHECK("wrs_build_lbvh radix sort");
+        uint32_t* t = ki; ki = ko; ko = t;
+        t = vi; vi = vo; vo = t;
+    }
+    // four passes: the sorted keys / values are back in keys0 / vals0
+    k_karras<<<gm, 256, 0, s>>>(ki, hdr, nodes, S.leaf_parent, S.node_parent);
+    WRS_LAUNCH_CHECK("wrs_build_lbvh karras");
+    cudaError_t e = cudaMemsetAsync(S.visit, 0, sizeof(uint32_t) * m_cap, s);
+    if (e != cudaSuccess) return wrs::cuda_fail(e, "wrs_build_lbvh memset");
+    k_leaves_refit<<<gm, 256, 0, s>>>(vi, pos4, reinterpret_cast<const float4*>(in->rgba), in->id,
+                                      radius_scale, global_scale, hdr, nodes, S.leaf_parent,
+                                      S.node_parent, S.visit,
+                                      reinterpret_cast<float4*>(sorted->pos_r),
+                                      reinterpret_cast<float4*>(sorted->rgba), sorted->id,
+                                      sorted->src);
+    WRS_LAUNCH_CHECK("wrs_build_lbvh refit");
+    return WRS_OK;
+}
+
+}  // extern "C"

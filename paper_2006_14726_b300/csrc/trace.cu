@@ -1,0 +1,617 @@
+// trace.cu -- ray tracing of the splat spheres (Fig. 2 caption, §4; spec S5, S6), its counting
+// variant, the persistent multi-session launch, and the adjoint (spec S7).
+//
+// Per ray: ordered BVH traversal with a short stack; the K nearest hits beyond the previous pass
+// are kept sorted by (key, id) in registers; nodes whose entry lies beyond the K-th key (or whose
+// exit lies before the previous pass's last key) are culled; after each pass the K hits are
+// composited front to back.  A ray stops once its transmittance reaches t_stop, H hits are used,
+// or a pass finds fewer than K hits.  Node records are 64 B (four float4 loads through the
+// read-only path); a splat is one float4 for the test and one float4 for its colour.
+//
+// Results do not depend on K, the block shape or the LBVH leaf size: the hit set and order are
+// fixed by the binary32 sphere test, and the compositing visits them in the same order.
+#include "common.cuh"
+
+namespace wrs {
+int check_camera(const wrs_camera* c, const char* fn);
+}
+
+namespace {
+
+using wrs::kLeafBit;
+using wrs::LbvhHeader;
+using wrs::Ray;
+
+struct Scene {
+    const LbvhHeader* hdr;
+    const float4* __restrict__ nodes;
+    const float4* __restrict__ pos_r;
+    const float4* __restrict__ rgba;
+    const uint32_t* __restrict__ id;
+    const uint32_t* __restrict__ src;
+    const float* __restrict__ opacity;
+};
+
+struct Comp {
+    int max_hits;
+    float t_stop;
+    float beta;
+};
+
+struct Counts {
+    uint32_t nodes, boxes, spheres, gathered, composited, passes;
+};
+
+constexpr float kInf = __builtin_huge_valf();
+
+// One traversal pass: the K smallest hits (key, id) strictly after (last_key, last_id).
+// Returns the number gathered (<= K); -1 if the stack overflowed; -2 if the pass met a reference
+// outside the tree or visited more nodes than the tree has (impossible for a well-formed tree; it
+// bounds the loop regardless).
+template <int K, bool COUNT>
+__device__ __forceinline__ int gather(const Scene& sc, const Ray& ray, const wrs::BoxRay& br,
+                                      uint32_t n, uint32_t leaf, int32_t root, bool has_last,
+                                      float last_key, uint32_t last_id, float (&kk)[K],
+                                      uint32_t (&ki)[K], uint32_t (&kid)[K], Counts& cnt) {
+#pragma unroll
+    for (int s = 0; s < K; s++) { kk[s] = kInf; ki[s] = 0xFFFFFFFFu; kid[s] = 0xFFFFFFFFu; }
+    int count = 0;
+    int stack[wrs::kStack];
+    int sp = 0;
+    uint32_t ref = (uint32_t)root;
+    const float lower = has_last ? last_key : -kInf;
+    const uint32_t m = (n + leaf - 1) / leaf;  // leaves; internal nodes = m - 1
+    uint32_t budget = 2 * m + 2;              // node visits allowed in one pass
+    while (true) {
+        if (budget-- == 0) return -2;
+        if (!(ref & kLeafBit)) {
+            if (ref + 1 >= m) return -2;  // not an internal node of this tree
+            const float4* nd = sc.nodes + 4 * (size_t)ref;
+            const float4 a = __ldg(nd + 0), b = __ldg(nd + 1), c = __ldg(nd + 2), r = __ldg(nd + 3);
+            float tn0, tf0, tn1, tf1;
+            wrs::box_test(br, a.x, a.y, a.z, a.w, b.x, b.y, tn0, tf0);
+            wrs::box_test(br, b.z, b.w, c.x, c.y, c.z, c.w, tn1, tf1);
+            if (COUNT) { cnt.nodes++; cnt.boxes += 2; }
+            const float cut = kk[K - 1];
+            const bool h0 = tn0 <= tf0 && tn0 <= cut && tf0 >= lower;
+            const bool h1 = tn1 <= tf1 && tn1 <= cut && tf1 >= lower;
+            const uint32_t c0 = __float_as_uint(r.x), c1 = __float_as_uint(r.y);
+            if (h0 && h1) {
+                const bool first0 = tn0 <= tn1;
+                if (sp >= wrs::kStack) return -1;
+                stack[sp++] = (int)(first0 ? c1 : c0);
+                ref = first0 ? c0 : c1;
+                continue;
+            }
+            if (h0) { ref = c0; continue; }
+            if (h1) { ref = c1; continue; }
+        } else {
+            const uint32_t first = (ref & ~kLeafBit) * leaf;
+            const uint32_t last = min(first + leaf, n);  // empty if the reference is out of range
+            for (uint32_t k = first; k < last; k++) {
+                const float4 s = __ldg(sc.pos_r + k);
+                float key, ff;
+                if (COUNT) cnt.spheres++;
+                if (!wrs::sphere_hit(ray, s, key, ff)) continue;
+                if (key > kk[K - 1] || key < lower) continue;
+                const uint32_t hid = __ldg(sc.id + k);
+                if (has_last && !wrs::hit_less(last_key, last_id, key, hid)) continue;
+                if (!wrs::hit_less(key, hid, kk[K - 1], kid[K - 1])) continue;
+                // bubble the new hit into the sorted buffer; the old K-th entry drops out
+                float nk = key;
+                uint32_t ni = k, nid = hid;
+#pragma unroll
+                for (int s2 = 0; s2 < K; s2++) {
+                    const bool lt = wrs::hit_less(nk, nid, kk[s2], kid[s2]);
+                    const float tk = kk[s2];
+                    const uint32_t ti = ki[s2], tid = kid[s2];
+                    kk[s2] = lt ? nk : tk; ki[s2] = lt ? ni : ti; kid[s2] = lt ? nid : tid;
+                    nk = lt ? tk : nk; ni = lt ? ti : ni; nid = lt ? tid : nid;
+                }
+                count = min(count + 1, K);
+                if (COUNT) cnt.gathered++;
+            }
+        }
+        if (sp == 0) break;
+        ref = (uint32_t)stack[--sp];
+    }
+    return count;
+}
+
+// Per-hit compositing quantities (spec S6).
+struct HitTerms {
+    float4 c;   // premultiplied rgba
+    float op;   // opacity
+    float w;    // soft-edge weight
+    float rho;  // |f| / r
+    float x;    // op * a * w (before the clamp)
+    float a;    // clamped alpha
+};
+
+__device__ __forceinline__ HitTerms hit_terms(const Scene& sc, const Comp& cp, const Ray& ray,
+                                              uint32_t k) {
+    HitTerms h;
+    h.c = __ldg(sc.rgba + k);
+    h.op = sc.opacity ? __ldg(sc.opacity + __ldg(sc.src + k)) : 1.0f;
+    h.w = 1.0f;
+    h.rho = 0.0f;
+    if (cp.beta > 0.0f) {
+        const float4 s = __ldg(sc.pos_r + k);
+        float key, ff;
+        wrs::sphere_hit(ray, s, key, ff);
+        h.rho = s.w > 0.0f ? sqrtf(ff) / s.w : 1.0f;
+        h.w = wrs::soft_w(h.rho, cp.beta);
+    }
+    h.x = h.op * h.c.w * h.w;
+    h.a = fminf(fmaxf(h.x, 0.0f), 1.0f);
+    return h;
+}
+
+struct RayCtx {
+    Ray ray;
+    wrs::BoxRay br;
+    uint32_t n, leaf;
+    int32_t root;
+};
+
+__device__ __forceinline__ RayCtx make_ray_ctx(const Scene& sc, const wrs_camera& cam, int x, int y) {
+    RayCtx r;
+    r.ray = wrs::primary_ray(cam, x, y);
+    const LbvhHeader h = *sc.hdr;
+    r.n = h.n;
+    r.leaf = h.leaf;
+    r.root = h.root;
+    r.br = wrs::make_box_ray(r.ray, wrs::traversal_eps(r.ray, h.maxabs));
+    return r;
+}
+
+// Forward trace of one ray (spec S6).  overflow_bits: status bits of a traversal failure.
+template <int K, bool COUNT>
+__device__ __forceinline__ float4 trace_ray(const Scene& sc, const Comp& cp, const RayCtx& rc,
+                                            uint32_t& overflow_bits, Counts& cnt) {
+    float T = 1.0f;
+    float3 C = make_float3(0.f, 0.f, 0.f);
+    overflow_bits = 0;
+    if (rc.n == 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+    int used = 0;
+    bool has_last = false;
+    float last_key = 0.0f;
+    uint32_t last_id = 0;
+    float kk[K];
+    uint32_t ki[K], kid[K];
+    while (true) {
+        const int count = gather<K, COUNT>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, has_last,
+                                           last_key, last_id, kk, ki, kid, cnt);
+        if (COUNT) cnt.passes++;
+        if (count < 0) { overflow_bits = count == -1 ? WRS_STATUS_STACK_OVERFLOW : WRS_STATUS_MALFORMED_TREE; break; }
+        bool done = false;
+#pragma unroll
+        for (int s = 0; s < K; s++) {
+            if (s >= count) break;
+            if ((cp.max_hits > 0 && used == cp.max_hits) || T <= cp.t_stop) { done = true; break; }
+            const HitTerms h = hit_terms(sc, cp, rc.ray, ki[s]);
+            const float tw = T * (h.op * h.w);
+            C.x = fmaf(tw, h.c.x, C.x);
+            C.y = fmaf(tw, h.c.y, C.y);
+            C.z = fmaf(tw, h.c.z, C.z);
+            T = T * (1.0f - h.a);
+            used++;
+            if (COUNT) cnt.composited++;
+        }
+        if (done || count < K) break;
+        if ((cp.max_hits > 0 && used == cp.max_hits) || T <= cp.t_stop) break;
+        has_last = true;
+        last_key = kk[K - 1];
+        last_id = kid[K - 1];
+    }
+    return make_float4(C.x, C.y, C.z, 1.0f - T);
+}
+
+// Pixel of thread t in a (16 x 4*warps/2) tile: warps are 8x4 pixel blocks, two across.
+__device__ __forceinline__ void tile_pixel(int t, int& px, int& py) {
+    const int warp = t >> 5, lane = t & 31;
+    px = (warp & 1) * 8 + (lane & 7);
+    py = (warp >> 1) * 4 + (lane >> 3);
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) k_trace(Scene sc, Comp cp, wrs_camera cam,
+                                               float4* __restrict__ out, int32_t* status) {
+    int px, py;
+    tile_pixel(threadIdx.x, px, py);
+    const int tile_h = (blockDim.x >> 6) * 4;
+    const int x = blockIdx.x * 16 + px, y = blockIdx.y * tile_h + py;
+    if (x >= cam.width || y >= cam.height) return;
+    const RayCtx rc = make_ray_ctx(sc, cam, x, y);
+    uint32_t overflow;
+    Counts cnt;
+    const float4 o = trace_ray<K, false>(sc, cp, rc, overflow, cnt);
+    if (overflow) wrs::set_status(status, overflow);
+    out[(size_t)y * cam.width + x] = o;
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) k_trace_count(Scene sc, Comp cp, wrs_camera cam,
+                                                     unsigned long long* counters, int32_t* status) {
+    int px, py;
+    tile_pixel(threadIdx.x, px, py);
+    const int tile_h = (blockDim.x >> 6) * 4;
+    const int x = blockIdx.x * 16 + px, y = blockIdx.y * tile_h + py;
+    Counts cnt = {0, 0, 0, 0, 0, 0};
+    if (x < cam.width && y < cam.height) {
+        const RayCtx rc = make_ray_ctx(sc, cam, x, y);
+        uint32_t overflow;
+        trace_ray<K, true>(sc, cp, rc, overflow, cnt);
+        if (overflow) wrs::set_status(status, overflow);
+    }
+    unsigned long long v[6] = {cnt.nodes, cnt.boxes, cnt.spheres, cnt.gathered, cnt.composited,
+                               cnt.passes};
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        unsigned long long s = v[k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(counters + k, s);
+    }
+}
+
+// Persistent multi-session trace: each block pops 16x16 tiles of any session.
+template <int K>
+__global__ void __launch_bounds__(256) k_trace_batched(const wrs_session* __restrict__ sess,
+                                                       int n_sessions, uint32_t total_tiles,
+                                                       Comp cp, uint32_t* work, int32_t* status) {
+    __shared__ uint32_t s_item;
+    __shared__ int s_sess;
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const uint32_t item = atomicAdd(work, 1u);
+            s_item = item;
+            int lo = 0, hi = n_sessions - 1;  // last session with tile_begin <= item
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (sess[mid].tile_begin <= item) lo = mid; else hi = mid - 1;
+            }
+            s_sess = lo;
+        }
+        __syncthreads();
+        const uint32_t item = s_item;
+        if (item >= total_tiles) break;
+        const wrs_session& S = sess[s_sess];
+        const uint32_t local = item - S.tile_begin;
+        const int tiles_x = (S.cam.width + 15) / 16;
+        const int tx = (int)(local % (uint32_t)tiles_x), ty = (int)(local / (uint32_t)tiles_x);
+        Scene sc;
+        sc.hdr = static_cast<const LbvhHeader*>(S.nodes);
+        sc.nodes = wrs::lbvh_nodes(S.nodes);
+        sc.pos_r = reinterpret_cast<const float4*>(S.pos_r);
+        sc.rgba = reinterpret_cast<const float4*>(S.rgba);
+        sc.id = S.id;
+        sc.src = S.src;
+        sc.opacity = S.opacity;
+        for (int t = threadIdx.x; t < 256; t += blockDim.x) {
+            // 16x16 tile: rows of 8x4 warp blocks, two across
+            int px, py;
+            tile_pixel(t, px, py);
+            const int x = tx * 16 + px, y = ty * 16 + py;
+            if (x >= S.cam.width || y >= S.cam.height) continue;
+            const RayCtx rc = make_ray_ctx(sc, S.cam, x, y);
+            uint32_t overflow;
+            Counts cnt;
+            const float4 o = trace_ray<K, false>(sc, cp, rc, overflow, cnt);
+            if (overflow) wrs::set_status(status, overflow);
+            reinterpret_cast<float4*>(S.rgba_out)[(size_t)y * S.cam.width + x] = o;
+        }
+    }
+}
+
+// ---- adjoint (spec S7) ---------------------------------------------------------------------
+// Pass A replays the forward pass chunk by chunk and records, per chunk, its lower bound and the
+// transmittance at its start.  Pass B walks the chunks back to front; each chunk is gathered
+// again (same bound, same K hits), its transmittances recomputed forward from the recorded
+// start, and the hits are then visited back to front with the suffix composite S and the suffix
+// transmittance P, so no division by (1 - alpha) is needed.
+template <int K>
+__global__ void __launch_bounds__(128) k_trace_bwd(Scene sc, Comp cp, wrs_camera cam,
+                                                   const float* __restrict__ scale, float gscale,
+                                                   const float4* __restrict__ dimg,
+                                                   float* __restrict__ g_rgba,
+                                                   float* __restrict__ g_op,
+                                                   float* __restrict__ g_sc, int32_t* status) {
+    int px, py;
+    tile_pixel(threadIdx.x, px, py);
+    const int tile_h = (blockDim.x >> 6) * 4;
+    const int x = blockIdx.x * 16 + px, y = blockIdx.y * tile_h + py;
+    if (x >= cam.width || y >= cam.height) return;
+    const float4 g = dimg[(size_t)y * cam.width + x];
+    if (g.x == 0.f && g.y == 0.f && g.z == 0.f && g.w == 0.f) return;
+    const RayCtx rc = make_ray_ctx(sc, cam, x, y);
+    if (rc.n == 0) return;
+    float b_key[wrs::kBwdChunks];
+    uint32_t b_id[wrs::kBwdChunks];
+    float b_T[wrs::kBwdChunks];
+    uint8_t b_used[wrs::kBwdChunks];
+    float kk[K];
+    uint32_t ki[K], kid[K];
+    Counts cnt;
+    // pass A
+    float T = 1.0f;
+    int used = 0, chunks = 0;
+    bool has_last = false;
+    float last_key = 0.f;
+    uint32_t last_id = 0;
+    while (true) {
+        if (chunks == wrs::kBwdChunks) { wrs::set_status(status, WRS_STATUS_CHUNK_OVERFLOW); return; }
+        const int count = gather<K, false>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, has_last,
+                                           last_key, last_id, kk, ki, kid, cnt);
+        if (count < 0) { wrs::set_status(status, count == -1 ? WRS_STATUS_STACK_OVERFLOW : WRS_STATUS_MALFORMED_TREE); return; }
+        b_key[chunks] = has_last ? last_key : -kInf;
+        b_id[chunks] = last_id;
+        b_T[chunks] = T;
+        int u = 0;
+        bool done = false;
+#pragma unroll
+        for (int s = 0; s < K; s++) {
+            if (s >= count) break;
+            if ((cp.max_hits > 0 && used == cp.max_hits) || T <= cp.t_stop) { done = true; break; }
+            const HitTerms h = hit_terms(sc, cp, rc.ray, ki[s]);
+            T = T * (1.0f - h.a);
+            used++;
+            u++;
+        }
+        b_used[chunks] = (uint8_t)u;
+        chunks++;
+        if (done || count < K) break;
+        if ((cp.max_hits > 0 && used == cp.max_hits) || T <= cp.t_stop) break;
+        has_last = true;
+        last_key = kk[K - 1];
+        last_id = kid[K - 1];
+    }
+    // pass B
+    float3 S = make_float3(0.f, 0.f, 0.f);
+    float P = 1.0f;
+    for (int c = chunks - 1; c >= 0; c--) {
+        const int u = b_used[c];
+        if (u == 0) continue;
+        const bool hl = b_key[c] != -kInf;
+        gather<K, false>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, hl, b_key[c], b_id[c], kk, ki,
+                         kid, cnt);
+        float Tk[K];
+        float t = b_T[c];
+#pragma unroll
+        for (int s = 0; s < K; s++) {
+            Tk[s] = t;
+            if (s < u) t = t * (1.0f - hit_terms(sc, cp, rc.ray, ki[s]).a);
+        }
+#pragma unroll
+        for (int s = K - 1; s >= 0; s--) {
+            if (s >= u) continue;
+            const uint32_t k = ki[s];
+            const HitTerms h = hit_terms(sc, cp, rc.ray, k);
+            const float Ti = Tk[s];
+            const float gC = g.x * h.c.x + g.y * h.c.y + g.z * h.c.z;
+            const float gS = g.x * S.x + g.y * S.y + g.z * S.z;
+            const float dLda = Ti * (g.w * P - gS);
+            const float pass = (h.x >= 0.0f && h.x <= 1.0f) ? 1.0f : 0.0f;
+            const uint32_t src = __ldg(sc.src + k);
+            const float tow = Ti * h.op * h.w;
+            atomicAdd(g_rgba + 4 * (size_t)src + 0, tow * g.x);
+            atomicAdd(g_rgba + 4 * (size_t)src + 1, tow * g.y);
+            atomicAdd(g_rgba + 4 * (size_t)src + 2, tow * g.z);
+            atomicAdd(g_rgba + 4 * (size_t)src + 3, dLda * pass * h.op * h.w);
+            if (g_op) atomicAdd(g_op + src, Ti * h.w * gC + dLda * pass * h.c.w * h.w);
+            if (g_sc && cp.beta > 0.0f) {
+                const float s_val = scale ? __ldg(scale + src) : gscale;
+                const float dw = wrs::soft_dw(h.rho, cp.beta);
+                if (s_val > 0.0f && dw != 0.0f) {
+                    const float dLdw = Ti * h.op * gC + dLda * pass * h.op * h.c.w;
+                    atomicAdd(g_sc + src, dLdw * dw * (-h.rho / s_val));
+                }
+            }
+            const float ow = h.op * h.w;
+            S.x = fmaf(1.0f - h.a, S.x, ow * h.c.x);
+            S.y = fmaf(1.0f - h.a, S.y, ow * h.c.y);
+            S.z = fmaf(1.0f - h.a, S.z, ow * h.c.z);
+            P = P * (1.0f - h.a);
+        }
+    }
+}
+
+// ---- host dispatch -------------------------------------------------------------------------
+int check_trace_args(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* cam,
+                     const wrs_trace_params* p, const char* fn) {
+    if (int rc = wrs::check_camera(cam, fn)) return rc;
+    if (!bvh || !bvh->nodes || !sorted || !p) return wrs::fail(WRS_ERR_ARG, "%s: NULL struct", fn);
+    if (!sorted->pos_r || !sorted->rgba || !sorted->id || !sorted->src)
+        return wrs::fail(WRS_ERR_ARG, "%s: sorted splats need pos_r, rgba, id and src", fn);
+    if ((reinterpret_cast<uintptr_t>(sorted->pos_r) | reinterpret_cast<uintptr_t>(sorted->rgba) |
+         reinterpret_cast<uintptr_t>(bvh->nodes)) & 15)
+        return wrs::fail(WRS_ERR_ARG, "%s: float4 arrays must be 16-byte aligned", fn);
+    const int K = p->k_chunk;
+    if (K != 1 && K != 2 && K != 4 && K != 8 && K != 16)
+        return wrs::fail(WRS_ERR_ARG, "%s: k_chunk %d not in {1,2,4,8,16}", fn, K);
+    if (p->block != 64 && p->block != 128 && p->block != 256)
+        return wrs::fail(WRS_ERR_ARG, "%s: block %d not in {64,128,256}", fn, p->block);
+    if (p->max_hits < 0) return wrs::fail(WRS_ERR_ARG, "%s: max_hits < 0", fn);
+    if (!(p->t_stop >= 0.0f && p->t_stop < 1.0f))
+        return wrs::fail(WRS_ERR_ARG, "%s: t_stop must be in [0, 1)", fn);
+    if (!(p->edge_softness >= 0.0f && p->edge_softness < 1.0f))
+        return wrs::fail(WRS_ERR_ARG, "%s: edge_softness must be in [0, 1)", fn);
+    return WRS_OK;
+}
+
+Scene make_scene(const wrs_lbvh* bvh, const wrs_splats* sorted, const float* opacity) {
+    Scene sc;
+    sc.hdr = static_cast<const LbvhHeader*>(bvh->nodes);
+    sc.nodes = wrs::lbvh_nodes(bvh->nodes);
+    sc.pos_r = reinterpret_cast<const float4*>(sorted->pos_r);
+    sc.rgba = reinterpret_cast<const float4*>(sorted->rgba);
+    sc.id = sorted->id;
+    sc.src = sorted->src;
+    sc.opacity = opacity;
+    return sc;
+}
+
+// A first-hit query (H small) needs no more than H hits per pass.
+int effective_k(const wrs_trace_params* p) {
+    int K = p->k_chunk;
+    if (p->max_hits > 0) {
+        int need = 1;
+        while (need < p->max_hits) need <<= 1;
+        if (need < K) K = need;
+    }
+    return K;
+}
+
+template <template <int> class Launch, typename... A>
+void dispatch_k(int K, A&&... a) {
+    switch (K) {
+        case 1: Launch<1>::run(a...); break;
+        case 2: Launch<2>::run(a...); break;
+        case 4: Launch<4>::run(a...); break;
+        case 8: Launch<8>::run(a...); break;
+        default: Launch<16>::run(a...); break;
+    }
+}
+
+template <int K> struct LaunchTrace {
+    static void run(dim3 g, int b, cudaStream_t s, Scene sc, Comp cp, wrs_camera cam, float4* o,
+                    int32_t* st) {
+        k_trace<K><<<g, b, 0, s>>>(sc, cp, cam, o, st);
+    }
+};
+template <int K> struct LaunchCount {
+    static void run(dim3 g, int b, cudaStream_t s, Scene sc, Comp cp, wrs_camera cam,
+                    unsigned long long* c, int32_t* st) {
+        k_trace_count<K><<<g, b, 0, s>>>(sc, cp, cam, c, st);
+    }
+};
+template <int K> struct LaunchBatched {
+    static void run(int g, int b, cudaStream_t s, const wrs_session* ss, int ns, uint32_t tt,
+                    Comp cp, uint32_t* w, int32_t* st) {
+        k_trace_batched<K><<<g, b, 0, s>>>(ss, ns, tt, cp, w, st);
+    }
+    static int blocks_per_sm(int b) {
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trace_batched<K>, b, 0);
+        return nb;
+    }
+};
+template <int K> struct LaunchBwd {
+    static void run(dim3 g, int b, cudaStream_t s, Scene sc, Comp cp, wrs_camera cam,
+                    const float* scale, float gs, const float4* d, float* gr, float* go, float* gsc,
+                    int32_t* st) {
+        k_trace_bwd<K><<<g, b, 0, s>>>(sc, cp, cam, scale, gs, d, gr, go, gsc, st);
+    }
+};
+
+dim3 grid_for(const wrs_camera* cam, int block) {
+    const int tile_h = (block / 64) * 4;
+    return dim3((cam->width + 15) / 16, (cam->height + tile_h - 1) / tile_h);
+}
+
+Comp comp_of(const wrs_trace_params* p) { return Comp{p->max_hits, p->t_stop, p->edge_softness}; }
+
+}  // namespace
+
+extern "C" {
+
+int wrs_trace(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* cam,
+              const wrs_trace_params* params, float* rgba_out, int32_t* status,
+              wrs_stream_t stream) {
+    const char* fn = "wrs_trace";
+    if (int rc = check_trace_args(bvh, sorted, cam, params, fn)) return rc;
+    if (!rgba_out || (reinterpret_cast<uintptr_t>(rgba_out) & 15))
+        return wrs::fail(WRS_ERR_ARG, "%s: rgba_out NULL or not 16-byte aligned", fn);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    dispatch_k<LaunchTrace>(effective_k(params), grid_for(cam, params->block), params->block, s,
+                            make_scene(bvh, sorted, params->opacity), comp_of(params), *cam,
+                            reinterpret_cast<float4*>(rgba_out), status);
+    WRS_LAUNCH_CHECK(fn);
+    return WRS_OK;
+}
+
+int wrs_trace_count(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* cam,
+                    const wrs_trace_params* params, unsigned long long* counters,
+                    int32_t* status, wrs_stream_t stream) {
+    const char* fn = "wrs_trace_count";
+    if (int rc = check_trace_args(bvh, sorted, cam, params, fn)) return rc;
+    if (!counters) return wrs::fail(WRS_ERR_ARG, "%s: counters is NULL", fn);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(counters, 0, 6 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return wrs::cuda_fail(e, fn);
+    dispatch_k<LaunchCount>(effective_k(params), grid_for(cam, params->block), params->block, s,
+                            make_scene(bvh, sorted, params->opacity), comp_of(params), *cam,
+                            counters, status);
+    WRS_LAUNCH_CHECK(fn);
+    return WRS_OK;
+}
+
+uint32_t wrs_session_tiles(int32_t width, int32_t height) {
+    if (width <= 0 || height <= 0) return 0;
+    return (uint32_t)((width + 15) / 16) * (uint32_t)((height + 15) / 16);
+}
+
+int wrs_trace_batched(const wrs_session* sessions, int32_t n_sessions, uint32_t total_tiles,
+                      const wrs_trace_params* params, uint32_t* work_counter, int32_t* status,
+                      wrs_stream_t stream) {
+    const char* fn = "wrs_trace_batched";
+    if (!sessions || !params || !work_counter)
+        return wrs::fail(WRS_ERR_ARG, "%s: NULL pointer", fn);
+    if (n_sessions <= 0) return wrs::fail(WRS_ERR_ARG, "%s: n_sessions must be > 0", fn);
+    const int K0 = params->k_chunk;
+    if (K0 != 1 && K0 != 2 && K0 != 4 && K0 != 8 && K0 != 16)
+        return wrs::fail(WRS_ERR_ARG, "%s: k_chunk %d not in {1,2,4,8,16}", fn, K0);
+    if (params->block != 64 && params->block != 128 && params->block != 256)
+        return wrs::fail(WRS_ERR_ARG, "%s: block %d not in {64,128,256}", fn, params->block);
+    if (params->max_hits < 0 || !(params->t_stop >= 0.0f && params->t_stop < 1.0f) ||
+        !(params->edge_softness >= 0.0f && params->edge_softness < 1.0f))
+        return wrs::fail(WRS_ERR_ARG, "%s: bad compositing parameters", fn);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(work_counter, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return wrs::cuda_fail(e, fn);
+    if (total_tiles == 0) return WRS_OK;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int K = effective_k(params);
+    int per_sm = 0;
+    switch (K) {
+        case 1: per_sm = LaunchBatched<1>::blocks_per_sm(params->block); break;
+        case 2: per_sm = LaunchBatched<2>::blocks_per_sm(params->block); break;
+        case 4: per_sm = LaunchBatched<4>::blocks_per_sm(params->block); break;
+        case 8: per_sm = LaunchBatched<8>::blocks_per_sm(params->block); break;
+        default: per_sm = LaunchBatched<16>::blocks_per_sm(params->block); break;
+    }
+    if (per_sm < 1) per_sm = 1;
+    int grid = sms * per_sm;
+    if ((uint32_t)grid > total_tiles) grid = (int)total_tiles;
+    dispatch_k<LaunchBatched>(K, grid, params->block, s, sessions, n_sessions, total_tiles,
+                              comp_of(params), work_counter, status);
+    WRS_LAUNCH_CHECK(fn);
+    return WRS_OK;
+}
+
+int wrs_trace_backward(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* cam,
+                       const wrs_trace_params* params, const float* radius_scale,
+                       float global_scale, const float* dL_drgba, float* g_rgba,
+                       float* g_opacity, float* g_scale, int32_t* status, wrs_stream_t stream) {
+    const char* fn = "wrs_trace_backward";
+    if (int rc = check_trace_args(bvh, sorted, cam, params, fn)) return rc;
+    if (!dL_drgba || !g_rgba || (reinterpret_cast<uintptr_t>(dL_drgba) & 15))
+        return wrs::fail(WRS_ERR_ARG, "%s: dL_drgba / g_rgba NULL or misaligned", fn);
+    const size_t cap = sorted->capacity;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(g_rgba, 0, 4 * sizeof(float) * cap, s);
+    if (e == cudaSuccess && g_opacity) e = cudaMemsetAsync(g_opacity, 0, sizeof(float) * cap, s);
+    if (e == cudaSuccess && g_scale) e = cudaMemsetAsync(g_scale, 0, sizeof(float) * cap, s);
+    if (e != cudaSuccess) return wrs::cuda_fail(e, fn);
+    int block = params->block > 128 ? 128 : params->block;  // local chunk table: keep occupancy
+    dispatch_k<LaunchBwd>(effective_k(params), grid_for(cam, block), block, s,
+                          make_scene(bvh, sorted, params->opacity), comp_of(params), *cam,
+                          radius_scale, global_scale, reinterpret_cast<const float4*>(dL_drgba),
+                          g_rgba, g_opacity, g_scale, status);
+    WRS_LAUNCH_CHECK(fn);
+    return WRS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,181 @@
+// unproject.cu -- object-space samples from a colour + depth image (Eq. 1, §4.1) with the
+// footprint or voxel radius and a stable compaction of the pixels that carry a sample (§4.1).
+//
+// Three launches: per-block counts of kept pixels, one-block exclusive scan of the counts (which
+// also writes the splat count), and the write pass that re-derives each pixel's rank inside its
+// block with warp ballots.  Every pass reads the image with coalesced 16-byte loads.
+#include "common.cuh"
+
+namespace wrs {
+int check_camera(const wrs_camera* c, const char* fn);
+}
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRounds = 4;
+constexpr int kTile = kThreads * kRounds;  // pixels per block
+
+__device__ __forceinline__ bool keep_pixel(const float4* __restrict__ rgba,
+                                           const float* __restrict__ depth, uint32_t i) {
+    const float t = __ldg(depth + i);
+    const float a = __ldg(&rgba[i].w);
+    return t >= 0.0f && t < __int_as_float(0x7f800000) && a > 0.0f;
+}
+
+__device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t* s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) s_warp[warp] = v;
+    __syncthreads();
+    uint32_t t = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kThreads / 32; w++) t += s_warp[w];
+    return t;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kThreads) k_unproject_count(const float4* __restrict__ rgba,
+                                                              const float* __restrict__ depth,
+                                                              uint32_t npix,
+                                                              uint32_t* __restrict__ counts) {
+    __shared__ uint32_t s_warp[kThreads / 32];
+    const uint32_t base = blockIdx.x * kTile;
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < kRounds; k++) {
+        const uint32_t i = base + k * kThreads + threadIdx.x;
+        if (i < npix && keep_pixel(rgba, depth, i)) c++;
+    }
+    const uint32_t t = block_sum(c, s_warp);
+    if (threadIdx.x == 0) counts[blockIdx.x] = t;
+}
+
+// Exclusive scan of nb block counts with one block of 1024 threads; writes *n_out = total.
+__global__ void __launch_bounds__(1024) k_scan_counts(const uint32_t* __restrict__ counts,
+                                                      uint32_t* __restrict__ offsets, uint32_t nb,
+                                                      uint32_t* __restrict__ n_out) {
+    __shared__ uint32_t s[1024];
+    const uint32_t per = (nb + 1023) / 1024;
+    const uint32_t lo = threadIdx.x * per, hi = min(lo + per, nb);
+    uint32_t sum = 0;
+    for (uint32_t i = lo; i < hi; i++) sum += counts[i];
+    s[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {  // Hillis-Steele inclusive scan
+        uint32_t v = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0;
+        __syncthreads();
+        s[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = s[threadIdx.x] - sum;
+    for (uint32_t i = lo; i < hi; i++) {
+        const uint32_t c = counts[i];
+        offsets[i] = run;
+        run += c;
+    }
+    if (threadIdx.x == 1023) *n_out = s[1023];
+}
+
+__global__ void __launch_bounds__(kThreads) k_unproject_write(
+    const float4* __restrict__ rgba, const float* __restrict__ depth, wrs_camera cam,
+    int32_t mode, float voxel_diag, const uint32_t* __restrict__ offsets, float4* __restrict__ pos_r,
+    float4* __restrict__ out_rgba, uint32_t* __restrict__ out_id) {
+    __shared__ uint32_t s_warp[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t npix = (uint32_t)cam.width * (uint32_t)cam.height;
+    const uint32_t base = blockIdx.x * kTile;
+    uint32_t run = offsets[blockIdx.x];
+    // pitch of one pixel at unit depth along the view axis (spec S3)
+    const float pitch = __fdiv_rn(__fmul_rn(2.0f, cam.tan_half_fovy), (float)cam.height);
+    const float r_vox = __fmul_rn(voxel_diag, 0.5f);
+    for (int k = 0; k < kRounds; k++) {
+        const uint32_t i = base + k * kThreads + threadIdx.x;
+        const bool keep = i < npix && keep_pixel(rgba, depth, i);
+        const uint32_t ball = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) s_warp[warp] = __popc(ball);
+        __syncthreads();
+        uint32_t before = 0, total = 0;
+        for (int w = 0; w < kThreads / 32; w++) {
+            const uint32_t c = s_warp[w];
+            before += (w < warp) ? c : 0;
+            total += c;
+        }
+        if (keep) {
+            const uint32_t slot = run + before + __popc(ball & ((1u << lane) - 1u));
+            const int x = (int)(i % (uint32_t)cam.width), y = (int)(i / (uint32_t)cam.width);
+            const wrs::Ray r = wrs::primary_ray(cam, x, y);
+            const float t = depth[i];
+            float r0;
+            if (mode == WRS_RADIUS_FOOTPRINT) {
+                const float dz = __fmaf_rn(r.d.z, cam.fwd[2],
+                                           __fmaf_rn(r.d.y, cam.fwd[1], __fmul_rn(r.d.x, cam.fwd[0])));
+                r0 = __fmul_rn(__fmul_rn(__fmul_rn(t, dz), pitch), 0.70710677f);
+            } else {
+                r0 = r_vox;
+            }
+            pos_r[slot] = make_float4(__fmaf_rn(r.d.x, t, r.o.x), __fmaf_rn(r.d.y, t, r.o.y),
+                                      __fmaf_rn(r.d.z, t, r.o.z), r0);
+            out_rgba[slot] = rgba[i];
+            out_id[slot] = i;
+        }
+        run += total;
+        __syncthreads();  // s_warp is reused by the next round
+    }
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" {
+
+size_t wrs_unproject_scratch_bytes(int32_t width, int32_t height) {
+    if (width <= 0 || height <= 0) return 0;
+    const size_t npix = (size_t)width * (size_t)height;
+    const size_t nb = (npix + kTile - 1) / kTile;
+    return 2 * align256(nb * sizeof(uint32_t));
+}
+
+int wrs_unproject(const float* rgba, const float* depth, const wrs_camera* cam,
+                  int32_t radius_mode, float voxel_diag, wrs_splats* out, void* scratch,
+                  size_t scratch_bytes, wrs_stream_t stream) {
+    const char* fn = "wrs_unproject";
+    if (int rc = wrs::check_camera(cam, fn)) return rc;
+    if (!rgba || !depth || !out || !out->pos_r || !out->rgba || !out->id || !out->n)
+        return wrs::fail(WRS_ERR_ARG, "%s: NULL input or output pointer", fn);
+    if ((reinterpret_cast<uintptr_t>(rgba) | reinterpret_cast<uintptr_t>(out->pos_r) |
+         reinterpret_cast<uintptr_t>(out->rgba)) & 15)
+        return wrs::fail(WRS_ERR_ARG, "%s: rgba / pos_r arrays must be 16-byte aligned", fn);
+    if (radius_mode != WRS_RADIUS_FOOTPRINT && radius_mode != WRS_RADIUS_VOXEL)
+        return wrs::fail(WRS_ERR_ARG, "%s: unknown radius_mode %d", fn, radius_mode);
+    if (radius_mode == WRS_RADIUS_VOXEL && !(voxel_diag > 0.0f && voxel_diag < 1e30f))
+        return wrs::fail(WRS_ERR_ARG, "%s: voxel_diag must be positive and finite", fn);
+    const size_t npix = (size_t)cam->width * (size_t)cam->height;
+    if (npix >= 0x80000000ull)
+        return wrs::fail(WRS_ERR_ARG, "%s: image of %zu pixels exceeds 2^31", fn, npix);
+    if (out->capacity < npix)
+        return wrs::fail(WRS_ERR_CAPACITY, "%s: splat capacity %u < %zu pixels", fn, out->capacity,
+                         npix);
+    const size_t need = wrs_unproject_scratch_bytes(cam->width, cam->height);
+    if (!scratch || scratch_bytes < need)
+        return wrs::fail(WRS_ERR_SCRATCH, "%s: scratch needs %zu bytes, got %zu", fn, need,
+                         scratch_bytes);
+    const uint32_t nb = (uint32_t)((npix + kTile - 1) / kTile);
+    uint32_t* counts = static_cast<uint32_t*>(scratch);
+    uint32_t* offsets = reinterpret_cast<uint32_t*>(static_cast<char*>(scratch) +
+                                                    align256(nb * sizeof(uint32_t)));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const float4* in4 = reinterpret_cast<const float4*>(rgba);
+    k_unproject_count<<<nb, kThreads, 0, s>>>(in4, depth, (uint32_t)npix, counts);
+    WRS_LAUNCH_CHECK("wrs_unproject count");
+    k_scan_counts<<<1, 1024, 0, s>>>(counts, offsets, nb, out->n);
+    WRS_LAUNCH_CHECK("wrs_unproject scan");
+    k_unproject_write<<<nb, kThreads, 0, s>>>(in4, depth, *cam, radius_mode, voxel_diag, offsets,
+                                              reinterpret_cast<float4*>(out->pos_r),
+                                              reinterpret_cast<float4*>(out->rgba), out->id);
+    WRS_LAUNCH_CHECK("wrs_unproject write");
+    return WRS_OK;
+}
+
+}  // extern "C"

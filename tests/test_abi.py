@@ -1,0 +1,118 @@
+"""The C ABI library loads on a machine without a GPU, exports every entry point that
+include/wrs.h declares, and rejects bad arguments on the host before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "wrs.h")
+
+
+@pytest.fixture(scope="module")
+def wrs():
+    from paper_2006_14726_b300 import _build
+    _build.build()
+    import paper_2006_14726_b300 as w
+    return w
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(wrs_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("wrs_unproject", "wrs_build_lbvh", "wrs_trace", "wrs_trace_batched",
+                     "wrs_trace_backward", "wrs_raycast_volume"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(wrs):
+    lib = ctypes.CDLL(wrs.LIB_PATH)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_struct_layouts_match(wrs):
+    assert wrs.lib.wrs_camera_size() == ctypes.sizeof(wrs.Camera) == 60
+    assert wrs.lib.wrs_session_size() == ctypes.sizeof(wrs.Session)
+
+
+def test_size_queries(wrs):
+    assert wrs.unproject_scratch_bytes(1920, 1080) >= 2 * 4 * ((1920 * 1080 + 1023) // 1024)
+    assert wrs.unproject_scratch_bytes(0, 5) == 0
+    assert wrs.lib.wrs_lbvh_bytes(1000, 1) == 64 + 64 * 999
+    assert wrs.lib.wrs_lbvh_bytes(1000, 4) == 64 + 64 * 249
+    assert wrs.lib.wrs_lbvh_bytes(10, 0) == 0 and wrs.lib.wrs_lbvh_bytes(10, 17) == 0
+    assert wrs.lbvh_scratch_bytes(2_073_600, 1) > 4 * 4 * 2_073_600
+    assert wrs.session_tiles(1024, 1024) == 4096 and wrs.session_tiles(17, 1) == 2
+
+
+def _cam(wrs, w=8, h=8, **kw):
+    c = wrs.Camera()
+    c.eye[:] = [0.5, 0.5, 2.0]
+    c.right[:] = [1, 0, 0]
+    c.up[:] = [0, 1, 0]
+    c.fwd[:] = [0, 0, -1]
+    c.tan_half_fovy = 0.4
+    c.width, c.height = w, h
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def test_host_validation_without_device(wrs):
+    """Argument errors are reported before any CUDA call (these run with no GPU present)."""
+    lib = wrs.lib
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: validation fails first
+    sp = wrs._Splats(fake.value, fake.value, fake.value, None, fake.value, 10)
+    # NULL image
+    assert lib.wrs_unproject(None, fake, ctypes.byref(_cam(wrs)), 0, 0.0, ctypes.byref(sp), fake, 1 << 20, None) == wrs.WRS_ERR_ARG
+    assert "NULL" in wrs.last_error()
+    # capacity below the pixel count
+    assert lib.wrs_unproject(fake, fake, ctypes.byref(_cam(wrs)), 0, 0.0, ctypes.byref(sp), fake, 1 << 20, None) == wrs.WRS_ERR_CAPACITY
+    # bad camera
+    assert lib.wrs_unproject(fake, fake, ctypes.byref(_cam(wrs, w=0)), 0, 0.0, ctypes.byref(sp), fake, 1 << 20, None) == wrs.WRS_ERR_ARG
+    bad = _cam(wrs)
+    bad.tan_half_fovy = float("nan")
+    assert lib.wrs_unproject(fake, fake, ctypes.byref(bad), 0, 0.0, ctypes.byref(sp), fake, 1 << 20, None) == wrs.WRS_ERR_ARG
+    # unknown radius mode, voxel mode without a voxel size
+    big = wrs._Splats(fake.value, fake.value, fake.value, None, fake.value, 64)
+    assert lib.wrs_unproject(fake, fake, ctypes.byref(_cam(wrs)), 7, 0.0, ctypes.byref(big), fake, 1 << 20, None) == wrs.WRS_ERR_ARG
+    assert lib.wrs_unproject(fake, fake, ctypes.byref(_cam(wrs)), 1, 0.0, ctypes.byref(big), fake, 1 << 20, None) == wrs.WRS_ERR_ARG
+    # scratch too small
+    assert lib.wrs_unproject(fake, fake, ctypes.byref(_cam(wrs)), 0, 0.0, ctypes.byref(big), fake, 1, None) == wrs.WRS_ERR_SCRATCH
+    # LBVH: bad leaf size, missing src, small capacity
+    bv = wrs._Lbvh(fake.value, 64, 0)
+    srt = wrs._Splats(fake.value, fake.value, fake.value, fake.value, fake.value, 64)
+    assert lib.wrs_build_lbvh(ctypes.byref(big), None, 1.0, ctypes.byref(bv), ctypes.byref(srt), fake, 1 << 30, None) == wrs.WRS_ERR_ARG
+    nosrc = wrs._Splats(fake.value, fake.value, fake.value, None, fake.value, 64)
+    bv1 = wrs._Lbvh(fake.value, 64, 1)
+    assert lib.wrs_build_lbvh(ctypes.byref(big), None, 1.0, ctypes.byref(bv1), ctypes.byref(nosrc), fake, 1 << 30, None) == wrs.WRS_ERR_ARG
+    small = wrs._Lbvh(fake.value, 8, 1)
+    assert lib.wrs_build_lbvh(ctypes.byref(big), None, 1.0, ctypes.byref(small), ctypes.byref(srt), fake, 1 << 30, None) == wrs.WRS_ERR_CAPACITY
+    assert lib.wrs_build_lbvh(ctypes.byref(big), None, 1.0, ctypes.byref(bv1), ctypes.byref(srt), fake, 16, None) == wrs.WRS_ERR_SCRATCH
+    # trace: bad k_chunk / block / t_stop / edge softness
+    for p in (wrs._Params(0, 1e-5, 0.0, None, 3, 128), wrs._Params(0, 1e-5, 0.0, None, 8, 96),
+              wrs._Params(0, 1.5, 0.0, None, 8, 128), wrs._Params(0, 1e-5, 1.0, None, 8, 128),
+              wrs._Params(-1, 1e-5, 0.0, None, 8, 128)):
+        assert lib.wrs_trace(ctypes.byref(bv1), ctypes.byref(srt), ctypes.byref(_cam(wrs)), ctypes.byref(p), fake, None, None) == wrs.WRS_ERR_ARG
+    # misaligned output
+    p = wrs._Params(0, 1e-5, 0.0, None, 8, 128)
+    assert lib.wrs_trace(ctypes.byref(bv1), ctypes.byref(srt), ctypes.byref(_cam(wrs)), ctypes.byref(p), ctypes.c_void_p(0x1004), None, None) == wrs.WRS_ERR_ARG
+    # batched: no sessions
+    assert lib.wrs_trace_batched(fake, 0, 0, ctypes.byref(p), fake, None, None) == wrs.WRS_ERR_ARG
+    # ray caster: bad dtype, bad size
+    assert lib.wrs_raycast_volume(fake, 5, 4, 4, 4, fake, ctypes.byref(_cam(wrs)), 0.5, 0.1, fake, fake, None) == wrs.WRS_ERR_ARG
+    assert lib.wrs_raycast_volume(fake, 0, 0, 4, 4, fake, ctypes.byref(_cam(wrs)), 0.5, 0.1, fake, fake, None) == wrs.WRS_ERR_ARG
+    assert lib.wrs_check_status(None, None) == wrs.WRS_ERR_ARG
+
+
+def test_cpu_tensors_are_rejected(wrs):
+    import torch
+    with pytest.raises(ValueError):
+        wrs._ptr(torch.zeros(4))

@@ -1,0 +1,399 @@
+"""GPU parity: every kernel of libwrs against the CPU oracle, through the C ABI.
+
+Integer and index outputs (splat count, ids, sort order, tree topology, boxes, depths decided by
+the binary32 spec) must match bitwise.  Floating-point images must match the binary64 oracle
+within the stated tolerance: per-pixel RGBA max abs <= 2e-3 and mean abs <= 1e-4.  Because every
+hit decision is taken in binary32 by the same operation sequence on both sides, no pixel is
+excluded; the binary64-decision diagnostic of the oracle is only reported.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MAX_ABS = 2e-3
+MEAN_ABS = 1e-4
+
+
+@pytest.fixture(scope="module")
+def wrs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2006_14726_b300 as w
+    oracle.build()
+    return w
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _assert_close(gpu, ref, what=""):
+    gpu = np.asarray(gpu, np.float64).reshape(-1, 4)
+    ref = np.asarray(ref, np.float64).reshape(-1, 4)
+    err = np.abs(gpu - ref)
+    assert err.max() <= MAX_ABS, f"{what}: max abs {err.max():.3g}"
+    assert err.mean() <= MEAN_ABS, f"{what}: mean abs {err.mean():.3g}"
+    return float(err.max())
+
+
+def _tiny_server():
+    W = synth.TINY
+    cam = W.server_cam()
+    vol = W.volume()
+    rgba, depth = oracle.raycast(vol, synth.tf_ramp(), cam)
+    return vol, cam, rgba.astype(np.float32), depth
+
+
+def _gpu_splats(wrs, rgba, depth, cam, mode=0, voxel_diag=0.0):
+    return wrs.unproject(_cuda(rgba), _cuda(depth), cam, mode, voxel_diag)
+
+
+# ---------------------------------------------------------------------------------------------
+# volume ray caster
+# ---------------------------------------------------------------------------------------------
+def test_raycast_tiny_full_image(wrs):
+    W = synth.TINY
+    cam = W.server_cam()
+    vol = W.volume()
+    tf = synth.tf_ramp()
+    ref_rgba, ref_depth = oracle.raycast(vol, tf, cam)
+    rgba, depth = wrs.raycast_volume(_cuda(vol), _cuda(tf), cam)
+    torch.cuda.synchronize()
+    d = depth.cpu().numpy()
+    assert np.array_equal(d, ref_depth)  # depth decided in binary32 on both sides
+    _assert_close(rgba.cpu().numpy(), ref_rgba, "raycast tiny")
+
+
+def test_raycast_u8_ragged_full_image(wrs):
+    vol = synth.fourier_volume(48, 32, 8, 11)
+    tf = synth.tf_ramp()
+    cam = synth.look_at((1.6, 1.1, 1.9), (0.5, 0.5, 0.5), (0, 1, 0), 40.0, 133, 97)
+    ref_rgba, ref_depth = oracle.raycast(vol, tf, cam)
+    rgba, depth = wrs.raycast_volume(_cuda(vol), _cuda(tf), cam)
+    assert np.array_equal(depth.cpu().numpy(), ref_depth)
+    _assert_close(rgba.cpu().numpy(), ref_rgba, "raycast u8")
+
+
+def test_raycast_mid_sampled(wrs):
+    W = synth.MID
+    cam = W.server_cam()
+    vol = W.volume()
+    tf = synth.tf_ramp()
+    rgba, depth = wrs.raycast_volume(_cuda(vol), _cuda(tf), cam)
+    pix = np.random.default_rng(1).choice(cam.width * cam.height, 3000, replace=False)
+    ref_rgba, ref_depth = oracle.raycast(vol, tf, cam, pixels=pix)
+    assert np.array_equal(depth.cpu().numpy().reshape(-1)[pix], ref_depth)
+    _assert_close(rgba.cpu().numpy().reshape(-1, 4)[pix], ref_rgba, "raycast mid")
+
+
+# ---------------------------------------------------------------------------------------------
+# unproject
+# ---------------------------------------------------------------------------------------------
+def _check_splats_equal(sp, ref):
+    k = sp.count()
+    assert k == ref.n
+    pos, rgba, ids = (t.cpu().numpy() for t in sp.view())
+    assert np.array_equal(ids.view(np.uint32), ref.id)
+    assert np.array_equal(pos.view(np.uint32), ref.pos_r.view(np.uint32))
+    assert np.array_equal(rgba.view(np.uint32), ref.rgba.view(np.uint32))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_unproject_tiny_bitwise(wrs, mode):
+    _, cam, rgba, depth = _tiny_server()
+    diag = synth.TINY.voxel_diag
+    sp = _gpu_splats(wrs, rgba, depth, cam, mode, diag)
+    _check_splats_equal(sp, oracle.unproject(rgba, depth, cam, mode, diag))
+
+
+def test_unproject_1080p_bitwise(wrs):
+    rgba, depth = synth.synthetic_server_image(1920, 1080, 21)
+    depth[0, :7] = -1.0
+    depth[5, 5] = np.nan
+    cam = synth.LARGE.server_cam()
+    sp = _gpu_splats(wrs, rgba, depth, cam)
+    _check_splats_equal(sp, oracle.unproject(rgba, depth, cam))
+
+
+def test_unproject_empty_and_one_pixel(wrs):
+    cam = synth.server_camera(1.4, 30.0, 7, 5)
+    sp = _gpu_splats(wrs, np.zeros((5, 7, 4), np.float32), np.full((5, 7), np.inf, np.float32), cam)
+    assert sp.count() == 0
+    cam1 = synth.server_camera(1.4, 30.0, 1, 1)
+    rgba = np.array([[[0.2, 0.2, 0.2, 0.5]]], np.float32)
+    sp1 = _gpu_splats(wrs, rgba, np.array([[1.2]], np.float32), cam1)
+    _check_splats_equal(sp1, oracle.unproject(rgba, np.array([[1.2]], np.float32), cam1))
+
+
+# ---------------------------------------------------------------------------------------------
+# LBVH
+# ---------------------------------------------------------------------------------------------
+def _check_lbvh(wrs, sp_gpu, ref_sp, leaf, scale=None):
+    sc_t = None if scale is None else _cuda(scale)
+    bvh, srt = wrs.build_lbvh(sp_gpu, leaf, radius_scale=sc_t)
+    ref = oracle.lbvh(ref_sp.pos_r, scale=scale, leaf=leaf)
+    h = bvh.header()
+    n = ref_sp.n
+    M = (n + leaf - 1) // leaf
+    assert h["n"] == n and h["m"] == M and h["leaf"] == leaf
+    assert np.array_equal(np.array(h["cmin"] + h["cmax"], np.float32), ref["cbounds"])
+    pos, rgba, ids, src = (t.cpu().numpy() for t in srt.view())
+    assert np.array_equal(src.view(np.uint32), ref["order"])
+    assert np.array_equal(ids.view(np.uint32), ref_sp.id[ref["order"]])
+    r0 = ref_sp.pos_r[ref["order"], 3]
+    s = np.ones(n, np.float32) if scale is None else np.maximum(scale[ref["order"]], 0).astype(np.float32)
+    assert np.array_equal(pos[:, 3], (s * r0).astype(np.float32))
+    assert np.array_equal(pos[:, :3], ref_sp.pos_r[ref["order"], :3])
+    if M >= 2:
+        assert h["root"] == 0
+        boxes, refs = bvh.node_table()
+        assert np.array_equal(refs.cpu().numpy(), ref["child"])
+        assert np.array_equal(boxes.cpu().numpy().view(np.uint32), ref["boxes"].view(np.uint32))
+    else:
+        assert h["root"] == -(2 ** 31)
+
+
+@pytest.mark.parametrize("leaf", [1, 4, 16])
+def test_lbvh_tiny_bitwise(wrs, leaf):
+    _, cam, rgba, depth = _tiny_server()
+    ref_sp = oracle.unproject(rgba, depth, cam)
+    _check_lbvh(wrs, _gpu_splats(wrs, rgba, depth, cam), ref_sp, leaf)
+
+
+def test_lbvh_large_bitwise_with_scales(wrs):
+    rgba, depth = synth.synthetic_server_image(640, 480, 31)
+    cam = synth.server_camera(1.4, 30.0, 640, 480)
+    ref_sp = oracle.unproject(rgba, depth, cam)
+    scale = np.random.default_rng(3).uniform(-0.2, 2.0, ref_sp.n).astype(np.float32)
+    sp = _gpu_splats(wrs, rgba, depth, cam)
+    _check_lbvh(wrs, sp, ref_sp, 1)
+    _check_lbvh(wrs, sp, ref_sp, 2, scale)
+
+
+def test_lbvh_duplicate_centres_and_tiny_counts(wrs):
+    """Equal Morton codes (duplicate centres) are ordered by index; 1, 2 and 3 splats."""
+    for n in (1, 2, 3, 300):
+        pos_r = np.zeros((n, 4), np.float32)
+        pos_r[:, :3] = 0.5
+        pos_r[: n // 2, 0] = 0.25
+        pos_r[:, 3] = 0.01
+        ref_sp = oracle.Splats(pos_r, np.full((n, 4), 0.5, np.float32), np.arange(n, dtype=np.uint32))
+        sp = wrs.SplatBuffers(n)
+        sp.pos_r.copy_(_cuda(pos_r))
+        sp.rgba.fill_(0.5)
+        sp.id.copy_(torch.arange(n, dtype=torch.int32))
+        sp.n.fill_(n)
+        for leaf in (1, 2):
+            _check_lbvh(wrs, sp, ref_sp, leaf)
+
+
+# ---------------------------------------------------------------------------------------------
+# trace
+# ---------------------------------------------------------------------------------------------
+def _trace_pair(wrs, rgba, depth, srv, cli, H=0, beta=0.0, opacity=None, scale=None, leaf=1,
+                k=8, block=128, pixels=None):
+    ref_sp = oracle.unproject(rgba, depth, srv)
+    sp = _gpu_splats(wrs, rgba, depth, srv)
+    bvh, srt = wrs.build_lbvh(sp, leaf, radius_scale=None if scale is None else _cuda(scale))
+    st = wrs.new_status()
+    params = wrs.TraceParams(max_hits=H, edge_softness=beta, k_chunk=k, block=block)
+    img = wrs.trace(bvh, srt, cli, params, opacity=None if opacity is None else _cuda(opacity),
+                    status=st)
+    wrs.check_status(st)
+    scene = oracle.Scene(ref_sp, scale=scale, opacity=opacity, max_hits=H, beta=beta)
+    ref = oracle.trace(scene, cli, pixels=pixels)
+    got = img.cpu().numpy().reshape(-1, 4)
+    if pixels is not None:
+        got = got[pixels]
+    return got, ref, (bvh, srt, params)
+
+
+@pytest.mark.parametrize("H,beta,k,block", [(0, 0.0, 8, 128), (1, 0.0, 8, 128), (0, 0.25, 4, 64),
+                                            (3, 0.0, 2, 256), (0, 0.0, 1, 128)])
+def test_trace_tiny_full_image(wrs, H, beta, k, block):
+    _, srv, rgba, depth = _tiny_server()
+    got, ref, _ = _trace_pair(wrs, rgba, depth, srv, synth.tiny_client_camera(), H=H, beta=beta,
+                              k=k, block=block)
+    m = _assert_close(got, ref["rgba"], f"tiny H={H} beta={beta}")
+    # identical hit lists: only compositing rounding remains.  With a soft edge the binary32
+    # distance of the ray from a centre (relative error ~1e-5 near the rim) enters W' <= 1.5/beta.
+    assert m < (1e-5 if beta == 0 else 2e-4)
+
+
+def test_trace_tiny_opacity_scale_ragged(wrs):
+    _, srv, rgba, depth = _tiny_server()
+    n = oracle.unproject(rgba, depth, srv).n
+    rng = np.random.default_rng(5)
+    op = rng.uniform(0.2, 1.5, n).astype(np.float32)
+    sc = rng.uniform(0.5, 3.0, n).astype(np.float32)
+    cli = synth.orbit(srv, (0.2, 1.0, 0.3), 9.0, 133, 97)
+    got, ref, _ = _trace_pair(wrs, rgba, depth, srv, cli, beta=0.3, opacity=op, scale=sc, leaf=4)
+    _assert_close(got, ref["rgba"], "tiny opacity/scale")
+
+
+def test_trace_invariant_to_tuning_bitwise(wrs):
+    rgba, depth = synth.synthetic_server_image(160, 120, 41)
+    srv = synth.server_camera(1.4, 30.0, 160, 120)
+    cli = synth.orbit(srv, (1.0, 0.3, 0.0), 14.0, 150, 110)
+    sp = _gpu_splats(wrs, rgba, depth, srv)
+    sc = _cuda(np.random.default_rng(2).uniform(1.0, 4.0, 160 * 120).astype(np.float32))
+    base = None
+    for leaf in (1, 4, 16):
+        bvh, srt = wrs.build_lbvh(sp, leaf, radius_scale=sc)
+        for k in (1, 2, 4, 8, 16):
+            for block in (64, 128, 256):
+                img = wrs.trace(bvh, srt, cli, wrs.TraceParams(k_chunk=k, block=block)).cpu().numpy()
+                if base is None:
+                    base = img
+                assert np.array_equal(img.view(np.uint32), base.view(np.uint32)), (leaf, k, block)
+
+
+def test_trace_mid_full_image(wrs):
+    """Mid workload: 256^3 Gaussian blobs, 512^2 server image from the oracle's ray caster,
+    1024^2 client at a pose within 15 degrees."""
+    W = synth.MID
+    srv = W.server_cam()
+    rgba, depth = oracle.raycast(W.volume(), synth.tf_ramp(), srv)
+    rgba = rgba.astype(np.float32)
+    cli = W.client_poses(3)[1]
+    got, ref, (bvh, srt, params) = _trace_pair(wrs, rgba, depth, srv, cli)
+    _assert_close(got, ref["rgba"], "mid")
+    cnt = wrs.trace_count(bvh, srt, cli, params)
+    assert cnt["composited"] == int(ref["nused"].sum())
+
+
+def test_trace_large_sampled(wrs):
+    """Full-size plain path: 1920x1080 server image (about 2 M splats), 1920x1080 client at 20
+    degrees, default launch configuration; sampled pixels against the oracle."""
+    rgba, depth = synth.synthetic_server_image(1920, 1080, 51)
+    srv = synth.LARGE.server_cam()
+    cli = synth.orbit(srv, (0.6, 0.8, 0.0), 20.0)
+    pix = np.random.default_rng(9).choice(1920 * 1080, 4096, replace=False)
+    for H in (0, 1):
+        got, ref, _ = _trace_pair(wrs, rgba, depth, srv, cli, H=H, pixels=pix)
+        _assert_close(got, ref["rgba"], f"large H={H}")
+
+
+def test_trace_empty_and_single(wrs):
+    cam = synth.server_camera(1.4, 30.0, 9, 9)
+    sp = _gpu_splats(wrs, np.zeros((9, 9, 4), np.float32), np.full((9, 9), np.inf, np.float32), cam)
+    bvh, srt = wrs.build_lbvh(sp, 1)
+    assert np.all(wrs.trace(bvh, srt, cam).cpu().numpy() == 0)
+    rgba = np.zeros((9, 9, 4), np.float32)
+    depth = np.full((9, 9), np.inf, np.float32)
+    rgba[4, 4] = [0.3, 0.2, 0.1, 0.6]
+    depth[4, 4] = 1.0
+    got, ref, _ = _trace_pair(wrs, rgba, depth, cam, synth.orbit(cam, (0, 1, 0), 3.0))
+    _assert_close(got, ref["rgba"], "single")
+
+
+def test_trace_many_layers_multi_pass(wrs):
+    """Deep stacks of translucent splats force many k-buffer passes (k_chunk = 1 and 2)."""
+    n = 40
+    W = H = 24
+    rgba = np.zeros((H, W, 4), np.float32)
+    depth = np.full((H, W), np.inf, np.float32)
+    rng = np.random.default_rng(4)
+    rgba[...] = 0.02
+    rgba[..., 3] = 0.05
+    depth[...] = rng.uniform(1.0, 1.2, (H, W)).astype(np.float32)
+    srv = synth.server_camera(1.4, 30.0, W, H)
+    cli = synth.orbit(srv, (1, 0, 0), 60.0)
+    sc = np.full(W * H, 8.0, np.float32)
+    for k in (1, 2, 16):
+        got, ref, _ = _trace_pair(wrs, rgba, depth, srv, cli, scale=sc, k=k)
+        assert ref["nhits"].max() > 20
+        _assert_close(got, ref["rgba"], f"layers k={k}")
+
+
+# ---------------------------------------------------------------------------------------------
+# batched
+# ---------------------------------------------------------------------------------------------
+def test_batched_equals_sequential_bitwise(wrs):
+    sessions = []
+    refs = []
+    for s, size in enumerate((64, 96, 160, 200, 128)):
+        rgba, depth = synth.synthetic_server_image(size, size, 60 + s)
+        srv = synth.server_camera(1.4, 30.0, size, size)
+        cli = synth.poses_in_cap(srv, 1, 15.0, 70 + s, 100 + 13 * s, 90 + 7 * s)[0]
+        sp = _gpu_splats(wrs, rgba, depth, srv)
+        bvh, srt = wrs.build_lbvh(sp, 1 + (s % 3))
+        sessions.append((bvh, srt, cli))
+        refs.append(wrs.trace(bvh, srt, cli).cpu().numpy())
+    batch = wrs.Batch(sessions)
+    st = wrs.new_status()
+    for k, block in ((8, 128), (4, 256), (16, 64)):
+        outs = wrs.trace_batched(batch, wrs.TraceParams(k_chunk=k, block=block), status=st)
+        wrs.check_status(st)
+        for o, r in zip(outs, refs):
+            assert np.array_equal(o.cpu().numpy().view(np.uint32), r.view(np.uint32))
+
+
+# ---------------------------------------------------------------------------------------------
+# backward
+# ---------------------------------------------------------------------------------------------
+def _bwd_instance(wrs, W=64, H=64, seed=0):
+    rgba, depth = synth.synthetic_server_image(W, H, seed, hole_frac=0.1)
+    srv = synth.server_camera(1.4, 30.0, W, H)
+    ref_sp = oracle.unproject(rgba, depth, srv)
+    n = ref_sp.n
+    rng = np.random.default_rng(seed)
+    op = rng.uniform(0.3, 1.0, n).astype(np.float32)
+    sc = rng.uniform(1.0, 2.5, n).astype(np.float32)
+    cli = synth.orbit(srv, (0.3, 1.0, 0.0), 10.0)
+    g = rng.normal(size=(cli.width * cli.height, 4))
+    return rgba, depth, srv, cli, ref_sp, op, sc, g
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+@pytest.mark.parametrize("beta,k", [(0.25, 8), (0.25, 1), (0.0, 4)])
+def test_backward_matches_oracle_adjoint(wrs, beta, k):
+    rgba, depth, srv, cli, ref_sp, op, sc, g = _bwd_instance(wrs)
+    n = ref_sp.n
+    sp = _gpu_splats(wrs, rgba, depth, srv)
+    bvh, srt = wrs.build_lbvh(sp, 1, radius_scale=_cuda(sc))
+    params = wrs.TraceParams(edge_softness=beta, k_chunk=k)
+    st = wrs.new_status()
+    gr, go, gs = wrs.trace_backward(bvh, srt, cli, _cuda(g.astype(np.float32).reshape(cli.height, cli.width, 4)),
+                                    params, opacity=_cuda(op), radius_scale=_cuda(sc), status=st)
+    wrs.check_status(st)
+    scene = oracle.Scene(ref_sp, scale=sc, opacity=op, beta=beta)
+    # the oracle adjoint takes the upstream gradient the GPU saw (rounded to binary32)
+    rr, ro, rs = oracle.trace_backward(scene, cli, g.astype(np.float32).astype(np.float64))
+    assert _rel(gr.cpu().numpy()[:n], rr) < 1e-3
+    assert _rel(go.cpu().numpy()[:n], ro) < 1e-3
+    if beta > 0:
+        assert np.abs(rs).max() > 0
+        assert _rel(gs.cpu().numpy()[:n], rs) < 1e-3
+    else:
+        assert np.all(gs.cpu().numpy()[:n] == 0)
+
+
+def test_autograd_function_matches_backward(wrs):
+    rgba, depth, srv, cli, ref_sp, op, sc, g = _bwd_instance(wrs, 48, 40, 3)
+    n = ref_sp.n
+    sp = _gpu_splats(wrs, rgba, depth, srv)
+    col = torch.tensor(ref_sp.rgba, device="cuda", requires_grad=True)
+    opt = torch.tensor(op, device="cuda", requires_grad=True)
+    sct = torch.tensor(sc, device="cuda", requires_grad=True)
+    params = wrs.TraceParams(edge_softness=0.25)
+    img = wrs.render(sp, cli, col, opt, sct, params)
+    gt = _cuda(g.astype(np.float32).reshape(cli.height, cli.width, 4))
+    (img * gt).sum().backward()
+    scene = oracle.Scene(ref_sp, scale=sc, opacity=op, beta=0.25)
+    ref_img = oracle.trace(scene, cli)["rgba"]
+    _assert_close(img.detach().cpu().numpy(), ref_img, "autograd forward")
+    rr, ro, rs = oracle.trace_backward(scene, cli, g.astype(np.float32).astype(np.float64))
+    assert _rel(col.grad.cpu().numpy(), rr) < 1e-3
+    assert _rel(opt.grad.cpu().numpy(), ro) < 1e-3
+    assert _rel(sct.grad.cpu().numpy(), rs) < 1e-3
