@@ -1,0 +1,567 @@
+#!/usr/bin/env python
+"""Benchmark of the sphere-splat warping hot path on B300.
+
+One step = one new server depth image of the large workload followed by its frames:
+unproject (Eq. 1, footprint radius, compaction) + LBVH rebuild + 4 client frames traced and
+composited (1920x1080 server image of a 512^3 u8 Fourier volume, about 2.07 M splats, 1920x1080
+client, poses within 20 degrees, a new depth image every 4 frames).  value = client primary rays
+per second over the whole job (all ranks), Mrays/s.
+
+Also reported on the same line: LBVH build and unproject ms, trace-only Mrays/s, the roofline of
+the trace kernel, the batched workload (64 sessions, one persistent launch in a CUDA graph vs 64
+sequential calls), forward and forward+backward throughput of the differentiable renderer, an
+end-to-end number through host buffers, and the CPU oracle timed on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl wrs|reference] [--no-extras]
+
+Multi-GPU (torchrun): every rank runs its own replica of the workload on its own poses (weak
+scaling, no collective on the data path); time = max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1080p/2M-splat Mrays/s & LBVH ms; batched and fwd+bwd vs plain, % roofline"
+UNIT = "Mrays/s"
+FRAMES_PER_IMAGE = 4
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="wrs", choices=["wrs", "reference"])
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip batched / fwd+bwd / e2e / cpu baseline (main line only)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_config(W, n_splats=None, extra=None):
+    cfg = {"workload": W.name, "volume": f"{W.vol_n}^3 u8, {W.vol_param} Fourier modes",
+           "server": [W.server_w, W.server_h], "client": [W.client_w, W.client_h],
+           "frames_per_depth_image": FRAMES_PER_IMAGE, "poses": f"{W.n_poses} within {W.cap_deg:g} deg",
+           "radius": "pixel footprint", "compositing": "all hits front to back, T_stop 1e-5"}
+    if n_splats is not None:
+        cfg["splats"] = int(n_splats)
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------------------------------
+# roofline helpers
+# ------------------------------------------------------------------------------------------------
+def trace_bytes_per_ray(c, rays):
+    """Algorithmic bytes per ray of the trace kernel: 64 per internal node visited (its two child
+    boxes and references), 16 per sphere tested (centre + radius), 4 per hit gathered (its id, for
+    the tie-break), 16 per hit composited (its RGBA), 16 for the output pixel."""
+    return (64 * c["nodes"] + 16 * c["spheres"] + 4 * c["gathered"] + 16 * c["composited"]) / rays + 16
+
+
+def trace_flops_per_ray(c, rays):
+    """22 flops per box test (6 FMA + 10 min/max), 24 per sphere test, 8 per composited hit."""
+    return (22 * c["boxes"] + 24 * c["spheres"] + 8 * c["composited"]) / rays
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+def kernel_digest():
+    h = hashlib.sha256()
+    for p in ("paper_2006_14726_b300/csrc/trace.cu", "paper_2006_14726_b300/csrc/common.cuh"):
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per trace launch from the committed ncu summary, if it was taken on the current
+    kernel source (the summary records the source digest); else None."""
+    path = os.path.join(ROOT, "profiles", "trace_large_1080p_2M.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_digest") != kernel_digest():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ------------------------------------------------------------------------------------------------
+def oracle_step_time(rgba_np, depth_np, srv, clis, ray_stride, threads=0):
+    """Time one step of the oracle: unproject + its BVH build over all splats + trace of every
+    ray_stride-th pixel of each client frame.  Returns (seconds for the full step extrapolated
+    from the sampled rays, rays of the full step, detail)."""
+    import oracle
+    t0 = time.perf_counter()
+    sp = oracle.unproject(rgba_np, depth_np, srv)
+    t1 = time.perf_counter()
+    scene = oracle.Scene(sp)
+    bvh = oracle.BVH(scene)
+    t2 = time.perf_counter()
+    t_trace = 0.0
+    rays_full = 0
+    for c in clis:
+        npix = c.width * c.height
+        pix = np.arange(0, npix, ray_stride, dtype=np.int32)
+        s = time.perf_counter()
+        oracle.trace(scene, c, pixels=pix, bvh=bvh, threads=threads)
+        t_trace += (time.perf_counter() - s) * (npix / pix.size)
+        rays_full += npix
+    total = (t1 - t0) + (t2 - t1) + t_trace
+    return total, rays_full, {"unproject_s": t1 - t0, "bvh_s": t2 - t1, "trace_s_extrapolated": t_trace,
+                              "splats": sp.n}
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, on the host cores, on a bounded sample of
+    the large workload per step (server and client downsampled per axis; same volume, cameras and
+    depth heuristic; every 4th ray traced), rank 0 only."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    oracle.build()
+    W = synth.LARGE
+    down = 4
+    vol = W.volume()
+    tf = synth.tf_ramp()
+    poses = W.client_poses()
+    groups = []
+    for g in range(2):
+        srv = poses[FRAMES_PER_IMAGE * g].with_size(W.server_w // down, W.server_h // down)
+        rgba, depth = oracle.raycast(vol, tf, srv)
+        clis = [poses[FRAMES_PER_IMAGE * g + f].with_size(W.client_w // down, W.client_h // down)
+                for f in range(FRAMES_PER_IMAGE)]
+        groups.append((rgba.astype(np.float32), depth, srv, clis))
+    threads = oracle.default_threads()
+    times = []
+    rays = 0
+    for s in range(args.warmup + args.steps):
+        rgba, depth, srv, clis = groups[s % len(groups)]
+        t, r, _ = oracle_step_time(rgba, depth, srv, clis, ray_stride=4, threads=threads)
+        if s >= args.warmup:
+            times.append(t)
+            rays += r
+    total = sum(times)
+    value = rays / total / 1e6
+    sample = (f"server and client {W.server_w // down}x{W.server_h // down} (1/{down} per axis of the "
+              f"1920x1080 workload), every 4th ray traced and the trace time scaled to all rays; "
+              f"unproject and BVH build over all splats")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": workload_config(W, extra={"sample": sample, "parallelism": "replicas"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, world, local = dist_env()
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU path)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2006_14726_b300 as wrs
+    from paper_2006_14726_b300 import autotune
+    import synth
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    W = synth.LARGE
+    dev = torch.device("cuda")
+    # ---------------- inputs (untimed): volume, poses, server images from the GPU ray caster ---
+    vol = torch.from_numpy(W.volume()).to(dev)
+    tf = torch.from_numpy(synth.tf_ramp()).to(dev)
+    poses = W.client_poses(seed_offset=97 * rank)
+    n_groups = len(poses) // FRAMES_PER_IMAGE
+    groups = []
+    for g in range(n_groups):
+        srv = poses[FRAMES_PER_IMAGE * g].with_size(W.server_w, W.server_h)
+        rgba, depth = wrs.raycast_volume(vol, tf, srv)
+        groups.append((rgba, depth, srv, [wrs.make_camera(poses[FRAMES_PER_IMAGE * g + f])
+                                           for f in range(FRAMES_PER_IMAGE)]))
+    torch.cuda.synchronize()
+    npix_s = W.server_w * W.server_h
+    npix_c = W.client_w * W.client_h
+    rays_per_step = FRAMES_PER_IMAGE * npix_c
+
+    # ---------------- autotune (untimed; the knobs do not change results) ----------------------
+    sp = wrs.unproject(groups[0][0], groups[0][1], groups[0][2])
+    tuned = autotune.tune_trace(sp, groups[0][3], use_cache=False)
+    leaf, kc, block = tuned["leaf"], tuned["k_chunk"], tuned["block"]
+    params = wrs.TraceParams(max_hits=0, t_stop=1e-5, k_chunk=kc, block=block)
+
+    # ---------------- buffers, allocated once -------------------------------------------------
+    splats = wrs.SplatBuffers(npix_s)
+    bvh = wrs.LBVH(npix_s, leaf)
+    srt = wrs.SplatBuffers(npix_s, sorted=True)
+    up_scratch = torch.empty(wrs.unproject_scratch_bytes(W.server_w, W.server_h), dtype=torch.uint8, device=dev)
+    bv_scratch = torch.empty(wrs.lbvh_scratch_bytes(npix_s, leaf), dtype=torch.uint8, device=dev)
+    outs = [torch.empty(W.client_h, W.client_w, 4, device=dev) for _ in range(FRAMES_PER_IMAGE)]
+    status = wrs.new_status()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    launches_per_step = 3 + 17 + FRAMES_PER_IMAGE  # unproject 3, LBVH 17 kernels, traces
+
+    def step(g, ev=None):
+        rgba, depth, srv, clis = groups[g % n_groups]
+        if ev:
+            ev[0].record(stream)
+        wrs.unproject(rgba, depth, srv, out=splats, scratch=up_scratch, stream=stream)
+        if ev:
+            ev[1].record(stream)
+        wrs.build_lbvh(splats, leaf, bvh=bvh, sorted=srt, scratch=bv_scratch, stream=stream)
+        if ev:
+            ev[2].record(stream)
+        for f in range(FRAMES_PER_IMAGE):
+            wrs.trace(bvh, srt, clis[f], params, out=outs[f], status=status, stream=stream)
+            if ev:
+                ev[3 + f].record(stream)
+
+    # roofline counts over every pose the timed loop visits (untimed)
+    cnt_tot = {k: 0 for k in wrs.COUNTER_NAMES}
+    rays_counted = 0
+    n_splats = []
+    for g in range(n_groups):
+        step(g)
+        n_splats.append(splats.count())
+        for c in groups[g][3]:
+            cc = wrs.trace_count(bvh, srt, c, params)
+            for k in cc:
+                cnt_tot[k] += cc[k]
+            rays_counted += npix_c
+    wrs.check_status(status)
+
+    for s in range(args.warmup):
+        step(s)
+    torch.cuda.synchronize()
+
+    nev = 3 + FRAMES_PER_IMAGE
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(nev)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("timed")
+    for s in range(args.steps):
+        flush.zero_()  # evict L2 before every step (outside the step's events)
+        step(s, events[s])
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    wrs.check_status(status)
+
+    step_ms = [ev[0].elapsed_time(ev[-1]) for ev in events]
+    up_ms = [ev[0].elapsed_time(ev[1]) for ev in events]
+    bv_ms = [ev[1].elapsed_time(ev[2]) for ev in events]
+    tr_ms = [ev[2 + f].elapsed_time(ev[3 + f]) for ev in events for f in range(FRAMES_PER_IMAGE)]
+    total_ms = max_over_ranks(sum(step_ms))
+    value = world * args.steps * rays_per_step / (total_ms * 1e-3) / 1e6
+    trace_ms = statistics.mean(tr_ms)
+
+    peaks, peak_src = measured_peaks()
+    bpr = trace_bytes_per_ray(cnt_tot, rays_counted)
+    fpr = trace_flops_per_ray(cnt_tot, rays_counted)
+    bytes_launch = bpr * npix_c
+    achieved = bytes_launch / (trace_ms * 1e-3) / 1e9
+    traffic = profiled_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "kernel": "k_trace", "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                "bytes_per_ray": bpr, "flops_per_ray": fpr,
+                "fp32_tflops_achieved": fpr * npix_c / (trace_ms * 1e-3) / 1e12,
+                "counts_per_ray": {k: v / rays_counted for k, v in cnt_tot.items()}}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(W, statistics.mean(n_splats), {
+                "leaf_size": leaf, "k_chunk": kc, "block": block, "autotuned": True,
+                "l2": "flushed before every step (256 MiB write outside the timed events)",
+                "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
+            "lbvh_ms": statistics.mean(bv_ms), "unproject_ms": statistics.mean(up_ms),
+            "trace_ms": trace_ms, "trace_mrays_s": npix_c / (trace_ms * 1e-3) / 1e6,
+            "wall_s_timed_region": wall,
+            "paper_context": {"hardware": "RTX 2080", "lbvh_ms_623k": 11, "compact_ms": 23,
+                              "mrays_s_1024sq_derived": [306, 289, 297, 240, 428]},
+            "roofline": roofline, "gpu_launches": launches_per_step * args.steps}
+    if clk:
+        line["clocks"] = clk
+
+    if not args.no_extras:
+        extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, world, barrier,
+               max_over_ranks)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def _time_ms(torch, fn, reps, warm=3):
+    for _ in range(warm):
+        fn()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s.record()
+    for _ in range(reps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / reps
+
+
+def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, world, barrier,
+           max_over_ranks):
+    dev = torch.device("cuda")
+    W = synth.LARGE
+    npix_s = W.server_w * W.server_h
+    npix_c = W.client_w * W.client_h
+    # ---------------- end to end through host buffers ------------------------------------------
+    rgba, depth, srv, clis = groups[0]
+    h_rgba = rgba.cpu().pin_memory()
+    h_depth = depth.cpu().pin_memory()
+    h_out = [torch.empty(W.client_h, W.client_w, 4).pin_memory() for _ in range(FRAMES_PER_IMAGE)]
+    d_rgba = torch.empty_like(rgba)
+    d_depth = torch.empty_like(depth)
+    splats = wrs.SplatBuffers(npix_s)
+    bvh = wrs.LBVH(npix_s, leaf)
+    srt = wrs.SplatBuffers(npix_s, sorted=True)
+    outs = [torch.empty(W.client_h, W.client_w, 4, device=dev) for _ in range(FRAMES_PER_IMAGE)]
+
+    def e2e_step():
+        d_rgba.copy_(h_rgba, non_blocking=True)
+        d_depth.copy_(h_depth, non_blocking=True)
+        wrs.unproject(d_rgba, d_depth, srv, out=splats)
+        wrs.build_lbvh(splats, leaf, bvh=bvh, sorted=srt)
+        for f in range(FRAMES_PER_IMAGE):
+            wrs.trace(bvh, srt, clis[f], params, out=outs[f])
+            h_out[f].copy_(outs[f], non_blocking=True)
+    steps = 30
+    barrier()
+    ms = max_over_ranks(_time_ms(torch, e2e_step, steps))
+    line["e2e"] = {"value": world * FRAMES_PER_IMAGE * npix_c / (ms * 1e-3) / 1e6, "unit": UNIT,
+                   "h2d_bytes_per_step": int(h_rgba.numel() * 4 + h_depth.numel() * 4),
+                   "d2h_bytes_per_step": int(sum(o.numel() * 4 for o in h_out)),
+                   "ms_per_step": ms, "path": "pinned host image -> device, unproject, LBVH, "
+                   "4 traces, 4 images -> pinned host"}
+    del splats, bvh, srt, outs
+
+    # ---------------- batched: 64 sessions, one persistent launch in a CUDA graph -------------
+    sessions = synth.batched_sessions(64, seed=4000 + 1000 * rank)
+    tfd = torch.from_numpy(synth.tf_ramp()).to(dev)
+    sess = []
+    n_total_splats = 0
+    for s, (size, srv_s, cli_s) in enumerate(sessions):
+        vol = synth.gaussian_volume_device(256, 64, 4000 + s + 1000 * rank)
+        rgba_s, depth_s = wrs.raycast_volume(vol, tfd, srv_s)
+        del vol
+        sp = wrs.unproject(rgba_s, depth_s, srv_s)
+        b, so = wrs.build_lbvh(sp, leaf)
+        n_total_splats += sp.count()
+        sess.append((b, so, cli_s))
+        del sp
+    batch = wrs.Batch(sess)
+    bt = autotune.tune_batched(batch, params)
+    bparams = wrs.TraceParams(0, 1e-5, 0.0, bt["k_chunk"], bt["block"])
+    outs = [torch.empty(c.height, c.width, 4, device=dev) for _, _, c in sess]
+    seq_cams = [wrs.make_camera(c) for _, _, c in sess]
+
+    def sequential():
+        for (b, so, _), c, o in zip(sess, seq_cams, outs):
+            wrs.trace(b, so, c, params, out=o)
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        wrs.trace_batched(batch, bparams)  # warm (caches the launch shape outside capture)
+        with torch.cuda.graph(g, stream=side):
+            wrs.trace_batched(batch, bparams)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    rays = sum(c.width * c.height for _, _, c in sess)
+    barrier()
+    ms_graph = max_over_ranks(_time_ms(torch, g.replay, 10))
+    ms_seq = max_over_ranks(_time_ms(torch, sequential, 10))
+    line["batched"] = {"sessions": len(sess), "rays_per_launch": rays,
+                       "splats_total": n_total_splats,
+                       "server_sizes": sorted({int(s[0]) for s in sessions}),
+                       "one_launch_graph_mrays_s": world * rays / (ms_graph * 1e-3) / 1e6,
+                       "sequential_mrays_s": world * rays / (ms_seq * 1e-3) / 1e6,
+                       "one_launch_ms": ms_graph, "sequential_ms": ms_seq,
+                       "k_chunk": bt["k_chunk"], "block": bt["block"], "leaf_size": leaf}
+    del sess, batch, outs, g
+
+    # ---------------- forward and forward+backward (differentiable renderer) -------------------
+    D = synth.DIFF
+    vol = synth.gaussian_volume_device(D.vol_n, D.vol_param, D.seed + rank)
+    srv_d = D.server_cam()
+    rgba_d, depth_d = wrs.raycast_volume(vol, tfd, srv_d)
+    views = D.client_poses(seed_offset=rank)
+    targets = [wrs.raycast_volume(vol, tfd, v)[0] for v in views]
+    sp = wrs.unproject(rgba_d, depth_d, srv_d)
+    n = sp.count()
+    col = sp.rgba[:n].clone().requires_grad_(True)
+    opa = torch.ones(n, device=dev, requires_grad=True)
+    scl = torch.ones(n, device=dev, requires_grad=True)
+    dparams = wrs.TraceParams(0, 1e-5, 0.25, params.k_chunk, params.block)
+
+    def fwd():
+        with torch.no_grad():
+            for v in views:
+                wrs.render(sp, v, col, opa, scl, dparams, leaf)
+
+    def fwd_bwd():
+        loss = 0.0
+        for v, t in zip(views, targets):
+            img = wrs.render(sp, v, col, opa, scl, dparams, leaf)
+            loss = loss + ((img - t) ** 2).mean()
+        loss.backward()
+    barrier()
+    ms_f = max_over_ranks(_time_ms(torch, fwd, 5))
+    ms_fb = max_over_ranks(_time_ms(torch, fwd_bwd, 5))
+    rays_d = sum(v.width * v.height for v in views)
+    line["fwd_bwd"] = {"views": len(views), "splats": n, "client": [D.client_w, D.client_h],
+                       "edge_softness": 0.25,
+                       "forward_mrays_s": world * rays_d / (ms_f * 1e-3) / 1e6,
+                       "forward_backward_mrays_s": world * rays_d / (ms_fb * 1e-3) / 1e6,
+                       "forward_ms_per_view": ms_f / len(views),
+                       "forward_backward_ms_per_view": ms_fb / len(views),
+                       "note": "forward = LBVH rebuild with the current radius scales + trace; "
+                               "backward = re-traversal adjoint; L2 loss vs GPU ray-cast views"}
+
+    # ---------------- CPU oracle on the host cores (rank 0, N = 1) ------------------------------
+    if rank == 0 and world == 1:
+        import oracle
+        oracle.build()
+        rgba, depth, srv, clis = groups[0]
+        cli_objs = W.client_poses()[:FRAMES_PER_IMAGE]
+        threads = oracle.default_threads()
+        t, r, det = oracle_step_time(rgba.cpu().numpy(), depth.cpu().numpy(), srv, cli_objs,
+                                     ray_stride=8, threads=threads)
+        line["cpu_baseline"] = {"value": r / t / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": "one step of the large workload: unproject and BVH build "
+                                          "over all splats, every 8th ray of the 4 frames traced and "
+                                          "the trace time scaled to all rays",
+                                "detail": det}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,109 @@
+"""Autotuner for the performance knobs of the trace: LBVH leaf size, k-buffer depth and block size.
+
+The knobs never change results (the hit set and order are fixed by the binary32 sphere test; the
+compositing visits hits in that order), so the tuner only measures time: it builds one LBVH per
+leaf size, times wrs_trace (or wrs_trace_batched) over the given cameras with CUDA events, and
+keeps the fastest combination.  Choices are cached per GPU model and workload signature in a
+small JSON file (``$WRS_AUTOTUNE_CACHE``, default ``~/.cache/wrs/autotune.json``).
+"""
+from __future__ import annotations
+
+import json
+import os
+from typing import Callable, Dict, Iterable, Optional, Sequence
+
+import torch
+
+from . import Batch, SplatBuffers, TraceParams, build_lbvh, trace, trace_batched
+
+LEAVES = (1, 2, 4, 8)
+KS = (1, 2, 4, 8, 16)
+BLOCKS = (64, 128, 256)
+
+
+def _cache_path() -> str:
+    return os.environ.get("WRS_AUTOTUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "wrs", "autotune.json"))
+
+
+def _load_cache() -> dict:
+    try:
+        with open(_cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(key: str, val: dict):
+    try:
+        c = _load_cache()
+        c[key] = val
+        os.makedirs(os.path.dirname(_cache_path()), exist_ok=True)
+        with open(_cache_path(), "w") as f:
+            json.dump(c, f, indent=1)
+    except OSError:
+        pass
+
+
+def _time_ms(fn: Callable[[], None], reps: int, warm: int = 2) -> float:
+    for _ in range(warm):
+        fn()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s.record()
+    for _ in range(reps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / reps
+
+
+def signature(kind: str, n_splats: int, width: int, height: int, base: TraceParams) -> str:
+    gpu = torch.cuda.get_device_name()
+    nb = 1 << max(0, int(n_splats).bit_length() - 1)  # power-of-two bucket of the splat count
+    return f"{gpu}|{kind}|n~{nb}|{width}x{height}|H{base.max_hits}|b{base.edge_softness:g}"
+
+
+def tune_trace(splats: SplatBuffers, cams: Sequence, base: TraceParams = TraceParams(),
+               leaves: Iterable[int] = LEAVES, ks: Iterable[int] = KS,
+               blocks: Iterable[int] = BLOCKS, reps: int = 3, use_cache: bool = True) -> Dict:
+    """Pick (leaf_size, k_chunk, block) minimising the mean wrs_trace time over ``cams``."""
+    c0 = cams[0]
+    key = signature("trace", splats.count(), c0.width, c0.height, base)
+    if use_cache:
+        hit = _load_cache().get(key)
+        if hit:
+            return hit
+    best = None
+    table = []
+    for leaf in leaves:
+        bvh, srt = build_lbvh(splats, leaf)
+        outs = [torch.empty(c.height, c.width, 4, device=splats.pos_r.device) for c in cams]
+        for k in ks:
+            for block in blocks:
+                p = TraceParams(base.max_hits, base.t_stop, base.edge_softness, k, block)
+
+                def run():
+                    for c, o in zip(cams, outs):
+                        trace(bvh, srt, c, p, out=o)
+                ms = _time_ms(run, reps) / len(cams)
+                table.append((leaf, k, block, ms))
+                if best is None or ms < best["ms"]:
+                    best = {"leaf": leaf, "k_chunk": k, "block": block, "ms": ms}
+    best["table"] = table
+    _store(key, best)
+    return best
+
+
+def tune_batched(batch: Batch, base: TraceParams = TraceParams(), ks: Iterable[int] = KS,
+                 blocks: Iterable[int] = BLOCKS, reps: int = 3) -> Dict:
+    """Pick (k_chunk, block) for one persistent multi-session launch (leaf sizes are fixed by the
+    sessions' LBVHs)."""
+    best = None
+    for k in ks:
+        for block in blocks:
+            p = TraceParams(base.max_hits, base.t_stop, base.edge_softness, k, block)
+            ms = _time_ms(lambda: trace_batched(batch, p), reps)
+            if best is None or ms < best["ms"]:
+                best = {"k_chunk": k, "block": block, "ms": ms}
+    return best

@@ -1,0 +1,71 @@
+"""Run one workload of the hot path once, with few launches, for profiling and inspection.
+
+    python -m paper_2006_14726_b300.cases large --frames 3 [--leaf 1 --k 1 --block 128]
+
+Sets up the server image with the GPU ray caster, frees the volume, then runs unproject, the
+LBVH build and ``frames`` client traces (each stage in its own NVTX range) and prints the CUDA
+event times.  Workloads: tiny, mid, large (see synth).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+import torch
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+import paper_2006_14726_b300 as wrs  # noqa: E402
+import synth  # noqa: E402
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("workload", choices=["tiny", "mid", "large"])
+    ap.add_argument("--frames", type=int, default=3)
+    ap.add_argument("--leaf", type=int, default=1)
+    ap.add_argument("--k", type=int, default=1)
+    ap.add_argument("--block", type=int, default=128)
+    ap.add_argument("--max-hits", type=int, default=0)
+    a = ap.parse_args()
+    W = {"tiny": synth.TINY, "mid": synth.MID, "large": synth.LARGE}[a.workload]
+    dev = torch.device("cuda")
+    srv = W.server_cam()
+    vol = torch.from_numpy(W.volume()).to(dev)
+    tf = torch.from_numpy(synth.tf_ramp()).to(dev)
+    rgba, depth = wrs.raycast_volume(vol, tf, srv)
+    del vol
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    cams = [wrs.make_camera(c) for c in W.client_poses(max(a.frames, 1))][: a.frames]
+    params = wrs.TraceParams(max_hits=a.max_hits, k_chunk=a.k, block=a.block)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 + a.frames)]
+    st = wrs.new_status()
+    ev[0].record()
+    torch.cuda.nvtx.range_push("unproject")
+    sp = wrs.unproject(rgba, depth, srv)
+    torch.cuda.nvtx.range_pop()
+    ev[1].record()
+    torch.cuda.nvtx.range_push("lbvh")
+    bvh, srt = wrs.build_lbvh(sp, a.leaf)
+    torch.cuda.nvtx.range_pop()
+    ev[2].record()
+    out = torch.empty(W.client_h, W.client_w, 4, device=dev)
+    for f, c in enumerate(cams):
+        torch.cuda.nvtx.range_push(f"trace{f}")
+        wrs.trace(bvh, srt, c, params, out=out, status=st)
+        torch.cuda.nvtx.range_pop()
+        ev[3 + f].record()
+    torch.cuda.synchronize()
+    wrs.check_status(st)
+    res = {"workload": a.workload, "splats": sp.count(), "unproject_ms": ev[0].elapsed_time(ev[1]),
+           "lbvh_ms": ev[1].elapsed_time(ev[2]),
+           "trace_ms": [ev[2 + f].elapsed_time(ev[3 + f]) for f in range(a.frames)],
+           "device_bytes_allocated": torch.cuda.memory_allocated()}
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -570,20 +570,28 @@ int wrs_trace_batched(const wrs_session* sessions, int32_t n_sessions, uint32_t 
     cudaError_t e = cudaMemsetAsync(work_counter, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return wrs::cuda_fail(e, fn);
     if (total_tiles == 0) return WRS_OK;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // occupancy and SM count are queried once per (K, block) and cached, so that a call made
+    // during stream capture issues nothing but the memset and the launch
+    static int cached_grid[5][3] = {{0}};
     const int K = effective_k(params);
+    const int ki = K == 1 ? 0 : K == 2 ? 1 : K == 4 ? 2 : K == 8 ? 3 : 4;
+    const int bi = params->block == 64 ? 0 : params->block == 128 ? 1 : 2;
     int per_sm = 0;
-    switch (K) {
-        case 1: per_sm = LaunchBatched<1>::blocks_per_sm(params->block); break;
-        case 2: per_sm = LaunchBatched<2>::blocks_per_sm(params->block); break;
-        case 4: per_sm = LaunchBatched<4>::blocks_per_sm(params->block); break;
-        case 8: per_sm = LaunchBatched<8>::blocks_per_sm(params->block); break;
-        default: per_sm = LaunchBatched<16>::blocks_per_sm(params->block); break;
+    if (cached_grid[ki][bi] == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        switch (K) {
+            case 1: per_sm = LaunchBatched<1>::blocks_per_sm(params->block); break;
+            case 2: per_sm = LaunchBatched<2>::blocks_per_sm(params->block); break;
+            case 4: per_sm = LaunchBatched<4>::blocks_per_sm(params->block); break;
+            case 8: per_sm = LaunchBatched<8>::blocks_per_sm(params->block); break;
+            default: per_sm = LaunchBatched<16>::blocks_per_sm(params->block); break;
+        }
+        if (per_sm < 1) per_sm = 1;
+        cached_grid[ki][bi] = sms * per_sm;
     }
-    if (per_sm < 1) per_sm = 1;
-    int grid = sms * per_sm;
+    int grid = cached_grid[ki][bi];
     if ((uint32_t)grid > total_tiles) grid = (int)total_tiles;
     dispatch_k<LaunchBatched>(K, grid, params->block, s, sessions, n_sessions, total_tiles,
                               comp_of(params), work_counter, status);

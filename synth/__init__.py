@@ -246,3 +246,24 @@ def batched_sessions(n: int = 64, seed: int = 4000):
                            BATCHED.client_h)[0]
         out.append((int(sizes[s]), srv, cli))
     return out
+
+
+def gaussian_volume_device(n: int, nblobs: int, seed: int, device="cuda"):
+    """The same Gaussian-blob law as :func:`gaussian_volume` (same seed -> same blobs), evaluated
+    with torch on ``device`` in float64 and stored as float32.  Used where many large volumes are
+    needed quickly (the batched workload); values may differ from the numpy version in the last
+    bit of float32."""
+    import torch
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(0.2, 0.8, size=(nblobs, 3))
+    sig = rng.uniform(0.08, 0.15, size=nblobs)
+    amp = rng.uniform(0.5, 1.0, size=nblobs)
+    g = (torch.arange(n, dtype=torch.float64, device=device) + 0.5) / n
+    vol = torch.zeros((n, n, n), dtype=torch.float64, device=device)
+    for b in range(nblobs):
+        ex = torch.exp(-((g - c[b, 0]) ** 2) / (2 * sig[b] ** 2))
+        ey = torch.exp(-((g - c[b, 1]) ** 2) / (2 * sig[b] ** 2))
+        ez = torch.exp(-((g - c[b, 2]) ** 2) / (2 * sig[b] ** 2))
+        vol += amp[b] * ez[:, None, None] * ey[None, :, None] * ex[None, None, :]
+    vol /= vol.max()
+    return vol.to(torch.float32)
