@@ -6,7 +6,7 @@ each pixel of a server-rendered colour + depth image becomes an object-space sph
 from the newer camera, compositing the hits front to back (Fig. 2 caption, §4).
 
 This module only marshals arguments: every step runs in the CUDA kernels of ``libwrs.so``
-(built from ``csrc/`` by ``python -m paper_2006_14726_b300._build``).  PyTorch provides device
+(built from ``csrc/`` by ``python paper_2006_14726_b300/_build.py``).  PyTorch provides device
 memory and streams.  There is no CPU fallback: importing this package without the built library
 raises ImportError, and every call needs CUDA tensors.
 
@@ -27,7 +27,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libwrs.so")
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2006_14726_b300._build` "
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2006_14726_b300/_build.py` "
                       "(there is no CPU fallback)")
 
 _lib = ctypes.CDLL(LIB_PATH)
@@ -83,6 +83,9 @@ class Session(ctypes.Structure):
 
 
 def _sig(name, res, *args):
+    if not hasattr(_lib, name):
+        raise ImportError(f"{LIB_PATH} lacks {name}: it is out of date; rebuild it with "
+                          "`python paper_2006_14726_b300/_build.py`")
     f = getattr(_lib, name)
     f.restype = res
     f.argtypes = list(args)

@@ -1,8 +1,9 @@
 """Compile the CUDA sources into the in-tree shared library ``libwrs.so`` (sm_103a only).
 
-    python -m paper_2006_14726_b300._build [--force]
+    python paper_2006_14726_b300/_build.py [--force] [--ptxas-v]
 
-nvcc cross-compiles without a GPU; the library travels with the source tree.
+Run it by path: importing the package would load the library being rebuilt.  nvcc
+cross-compiles without a GPU; the library travels with the source tree.
 """
 from __future__ import annotations
 

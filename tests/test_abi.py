@@ -12,8 +12,12 @@ HEADER = os.path.join(ROOT, "include", "wrs.h")
 
 @pytest.fixture(scope="module")
 def wrs():
-    from paper_2006_14726_b300 import _build
-    _build.build()
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "wrs_build", os.path.join(ROOT, "paper_2006_14726_b300", "_build.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    b.build()  # rebuilds only if a source is newer than the library
     import paper_2006_14726_b300 as w
     return w
 
