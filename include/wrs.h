@@ -146,6 +146,23 @@ int wrs_unproject(const float* rgba, const float* depth, const wrs_camera* cam,
                   int32_t radius_mode, float voxel_diag, wrs_splats* out, void* scratch,
                   size_t scratch_bytes, wrs_stream_t stream);
 
+/* wrs_unproject for callers that cannot give the library device memory: the paper has no
+ * counterpart; this is an interface convenience.  Some hosts fix their device memory when they
+ * start (a viewer or plug-in whose embedding application owns the GPU heap, or a process that
+ * forbids allocation once its frame loop runs) and so cannot allocate or lend a work buffer per
+ * call.  This entry point allocates nothing: its work buffer is a fixed 512 KiB array inside the
+ * library's device image, which every GPU that loads the library keeps until the process exits.
+ * Inputs and outputs are the caller's, exactly as for wrs_unproject, with the same results.
+ *  - Limit: width * height <= 67,108,864 (8192 x 8192); larger images return WRS_ERR_CAPACITY.
+ *  - The first call on a device looks up that device's address of the array (with the device
+ *    current) and caches it; make that first call before any stream capture.
+ *  - All calls share the one array per device, which keeps the last call's contents.  Each call
+ *    writes every entry it reads before reading it, so nothing needs clearing, but calls that
+ *    overlap on the GPU (other streams, other host threads) race on it: serialise them. */
+int wrs_unproject_static(const float* rgba, const float* depth, const wrs_camera* cam,
+                         int32_t radius_mode, float voxel_diag, wrs_splats* out,
+                         wrs_stream_t stream);
+
 /* LBVH over the spheres (§4.1, §4.2; spec S8): 30-bit Morton codes of the centres over their
  * bounds, stable LSD radix sort of (code, index), binary radix tree (Karras 2012) over leaves of
  * leaf_size consecutive sorted splats, bottom-up refit of the sphere boxes.  The effective radius

@@ -105,6 +105,7 @@ _sig("wrs_check_status", _I, _P, _P)
 _sig("wrs_raycast_volume", _I, _P, _I, _I, _I, _I, _P, ctypes.POINTER(Camera), _F, _F, _P, _P, _P)
 _sig("wrs_unproject_scratch_bytes", _Z, _I, _I)
 _sig("wrs_unproject", _I, _P, _P, ctypes.POINTER(Camera), _I, _F, ctypes.POINTER(_Splats), _P, _Z, _P)
+_sig("wrs_unproject_static", _I, _P, _P, ctypes.POINTER(Camera), _I, _F, ctypes.POINTER(_Splats), _P)
 _sig("wrs_lbvh_bytes", _Z, _U, _U)
 _sig("wrs_lbvh_scratch_bytes", _Z, _U, _U)
 _sig("wrs_build_lbvh", _I, ctypes.POINTER(_Splats), _P, _F, ctypes.POINTER(_Lbvh),

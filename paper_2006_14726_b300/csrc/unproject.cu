@@ -4,6 +4,8 @@
 // Three launches: per-block counts of kept pixels, one-block exclusive scan of the counts (which
 // also writes the splat count), and the write pass that re-derives each pixel's rank inside its
 // block with warp ballots.  Every pass reads the image with coalesced 16-byte loads.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace wrs {
@@ -179,3 +181,89 @@ int wrs_unproject(const float* rgba, const float* depth, const wrs_camera* cam,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// wrs_unproject_static: the same three kernels with their work buffer (per-block counts, then
+// per-block offsets) in a fixed array that lives in this library's device image, for callers that
+// cannot hand us device memory.
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+constexpr uint32_t kStaticMaxPixels = 1u << 26;                  // 67,108,864 = 8192 x 8192
+constexpr uint32_t kStaticMaxBlocks = kStaticMaxPixels / kTile;  // 65,536 blocks
+constexpr int kStaticMaxDevices = 64;
+
+}  // namespace
+
+// Counts in [0, kStaticMaxBlocks), offsets in [kStaticMaxBlocks, 2 kStaticMaxBlocks): 512 KiB that
+// every GPU which loads the library keeps until the process exits.
+static __device__ __align__(256) uint32_t g_unproject_static_scratch[2 * kStaticMaxBlocks];
+
+namespace {
+
+std::mutex g_static_mu;
+uint32_t* g_static_ptr[kStaticMaxDevices] = {};
+
+// Device address of the static array on the current device.  The host-side symbol is only a
+// stand-in, so the address is looked up once per device (with that device current) and cached.
+int static_scratch(uint32_t** out, const char* fn) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return wrs::cuda_fail(e, fn);
+    if (dev < 0 || dev >= kStaticMaxDevices)
+        return wrs::fail(WRS_ERR_ARG, "%s: device ordinal %d beyond %d", fn, dev, kStaticMaxDevices);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_unproject_static_scratch);
+        if (e != cudaSuccess) return wrs::cuda_fail(e, "wrs_unproject_static: cudaGetSymbolAddress");
+        g_static_ptr[dev] = static_cast<uint32_t*>(p);
+    }
+    *out = g_static_ptr[dev];
+    return WRS_OK;
+}
+
+}  // namespace
+
+extern "C" int wrs_unproject_static(const float* rgba, const float* depth, const wrs_camera* cam,
+                                    int32_t radius_mode, float voxel_diag, wrs_splats* out,
+                                    wrs_stream_t stream) {
+    const char* fn = "wrs_unproject_static";
+    if (int rc = wrs::check_camera(cam, fn)) return rc;
+    if (!rgba || !depth || !out || !out->pos_r || !out->rgba || !out->id || !out->n)
+        return wrs::fail(WRS_ERR_ARG, "%s: NULL input or output pointer", fn);
+    if ((reinterpret_cast<uintptr_t>(rgba) | reinterpret_cast<uintptr_t>(out->pos_r) |
+         reinterpret_cast<uintptr_t>(out->rgba)) & 15)
+        return wrs::fail(WRS_ERR_ARG, "%s: rgba / pos_r arrays must be 16-byte aligned", fn);
+    if (radius_mode != WRS_RADIUS_FOOTPRINT && radius_mode != WRS_RADIUS_VOXEL)
+        return wrs::fail(WRS_ERR_ARG, "%s: unknown radius_mode %d", fn, radius_mode);
+    if (radius_mode == WRS_RADIUS_VOXEL && !(voxel_diag > 0.0f && voxel_diag < 1e30f))
+        return wrs::fail(WRS_ERR_ARG, "%s: voxel_diag must be positive and finite", fn);
+    const size_t npix = (size_t)cam->width * (size_t)cam->height;
+    if (npix > kStaticMaxPixels)
+        return wrs::fail(WRS_ERR_CAPACITY,
+                         "%s: image of %zu pixels exceeds the fixed work buffer's limit of %u "
+                         "pixels (8192 x 8192); use wrs_unproject with caller scratch",
+                         fn, npix, kStaticMaxPixels);
+    if (out->capacity < npix)
+        return wrs::fail(WRS_ERR_CAPACITY, "%s: splat capacity %u < %zu pixels", fn, out->capacity,
+                         npix);
+    uint32_t* buf = nullptr;
+    if (int rc = static_scratch(&buf, fn)) return rc;
+    // Every count and offset the kernels read is written earlier in the same call, so nothing in
+    // the shared array has to be cleared between calls.
+    const uint32_t nb = (uint32_t)((npix + kTile - 1) / kTile);
+    uint32_t* counts = buf;
+    uint32_t* offsets = buf + kStaticMaxBlocks;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const float4* in4 = reinterpret_cast<const float4*>(rgba);
+    k_unproject_count<<<nb, kThreads, 0, s>>>(in4, depth, (uint32_t)npix, counts);
+    WRS_LAUNCH_CHECK("wrs_unproject_static count");
+    k_scan_counts<<<1, 1024, 0, s>>>(counts, offsets, nb, out->n);
+    WRS_LAUNCH_CHECK("wrs_unproject_static scan");
+    k_unproject_write<<<nb, kThreads, 0, s>>>(in4, depth, *cam, radius_mode, voxel_diag, offsets,
+                                              reinterpret_cast<float4*>(out->pos_r),
+                                              reinterpret_cast<float4*>(out->rgba), out->id);
+    WRS_LAUNCH_CHECK("wrs_unproject_static write");
+    return WRS_OK;
+}
