@@ -302,8 +302,8 @@ def main():
     # ---------------- autotune (untimed; the knobs do not change results) ----------------------
     sp = wrs.unproject(groups[0][0], groups[0][1], groups[0][2])
     tuned = autotune.tune_trace(sp, groups[0][3], use_cache=False)
-    leaf, kc, block = tuned["leaf"], tuned["k_chunk"], tuned["block"]
-    params = wrs.TraceParams(max_hits=0, t_stop=1e-5, k_chunk=kc, block=block)
+    leaf, kc, block, sched = tuned["leaf"], tuned["k_chunk"], tuned["block"], tuned["schedule"]
+    params = wrs.TraceParams(max_hits=0, t_stop=1e-5, k_chunk=kc, block=block, schedule=sched)
 
     # ---------------- buffers, allocated once -------------------------------------------------
     splats = wrs.SplatBuffers(npix_s)
@@ -395,6 +395,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(W, statistics.mean(n_splats), {
                 "leaf_size": leaf, "k_chunk": kc, "block": block, "autotuned": True,
+                "schedule": ["one thread per pixel", "persistent, lane refill"][sched],
                 "l2": "flushed before every step (256 MiB write outside the timed events)",
                 "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
             "lbvh_ms": statistics.mean(bv_ms), "unproject_ms": statistics.mean(up_ms),

@@ -90,15 +90,21 @@ typedef struct {
     uint32_t leaf_size; /* splats per leaf, 1..16 */
 } wrs_lbvh;
 
+/* Trace schedules (performance only; results are bitwise identical). */
+#define WRS_SCHEDULE_PER_PIXEL 0   /* one thread per pixel, grid over the image */
+#define WRS_SCHEDULE_PERSISTENT 1  /* one resident wave of 128-thread blocks; warps refill idle
+                                      lanes with new rays (block size fixed at 128) */
+
 /* Compositing (spec S6) and performance parameters of a trace.  Results do not depend on
- * k_chunk or block (bitwise). */
+ * k_chunk, block or schedule (bitwise). */
 typedef struct {
     int32_t max_hits;     /* H: hits composited at most; 1 = first hit (the paper), 0 = all */
     float t_stop;         /* stop once transmittance <= t_stop (default 1e-5) */
     float edge_softness;  /* beta in [0,1): soft sphere edge for differentiation; 0 = hard */
     const float* opacity; /* device [n] per-splat opacity in COMPACTED order, or NULL (= 1) */
     int32_t k_chunk;      /* hits gathered per traversal pass: 1, 2, 4, 8 or 16 */
-    int32_t block;        /* threads per block: 64, 128 or 256 */
+    int32_t block;        /* threads per block: 64, 128 or 256 (per-pixel schedule) */
+    int32_t schedule;     /* WRS_SCHEDULE_PER_PIXEL or WRS_SCHEDULE_PERSISTENT (wrs_trace only) */
 } wrs_trace_params;
 
 /* One client session of wrs_trace_batched (device array of these). */

@@ -44,6 +44,8 @@ F32 = 0
 U8 = 1
 RADIUS_FOOTPRINT = 0
 RADIUS_VOXEL = 1
+SCHEDULE_PER_PIXEL = 0
+SCHEDULE_PERSISTENT = 1
 
 
 class WrsError(RuntimeError):
@@ -72,7 +74,8 @@ class _Lbvh(ctypes.Structure):
 class _Params(ctypes.Structure):
     _fields_ = [("max_hits", ctypes.c_int32), ("t_stop", ctypes.c_float),
                 ("edge_softness", ctypes.c_float), ("opacity", ctypes.c_void_p),
-                ("k_chunk", ctypes.c_int32), ("block", ctypes.c_int32)]
+                ("k_chunk", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("schedule", ctypes.c_int32)]
 
 
 class Session(ctypes.Structure):
@@ -317,10 +320,11 @@ class TraceParams:
     edge_softness: float = 0.0
     k_chunk: int = 8
     block: int = 128
+    schedule: int = 0            # 0 = one thread per pixel, 1 = persistent with lane refill
 
     def c(self, opacity: Optional[torch.Tensor] = None) -> _Params:
         return _Params(int(self.max_hits), float(self.t_stop), float(self.edge_softness),
-                       _ptr(opacity), int(self.k_chunk), int(self.block))
+                       _ptr(opacity), int(self.k_chunk), int(self.block), int(self.schedule))
 
 
 def trace(bvh: LBVH, sorted: SplatBuffers, cam, params: TraceParams = TraceParams(),

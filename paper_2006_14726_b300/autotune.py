@@ -1,4 +1,5 @@
-"""Autotuner for the performance knobs of the trace: LBVH leaf size, k-buffer depth and block size.
+"""Autotuner for the performance knobs of the trace: LBVH leaf size, k-buffer depth, block size and
+schedule (one thread per pixel, or persistent blocks with lane refill).
 
 The knobs never change results (the hit set and order are fixed by the binary32 sphere test; the
 compositing visits hits in that order), so the tuner only measures time: it builds one LBVH per
@@ -14,7 +15,8 @@ from typing import Callable, Dict, Iterable, Optional, Sequence
 
 import torch
 
-from . import Batch, SplatBuffers, TraceParams, build_lbvh, trace, trace_batched
+from . import (SCHEDULE_PER_PIXEL, SCHEDULE_PERSISTENT, Batch, SplatBuffers, TraceParams,
+               build_lbvh, trace, trace_batched)
 
 LEAVES = (1, 2, 4, 8)
 KS = (1, 2, 4, 8, 16)
@@ -79,17 +81,18 @@ def tune_trace(splats: SplatBuffers, cams: Sequence, base: TraceParams = TracePa
     for leaf in leaves:
         bvh, srt = build_lbvh(splats, leaf)
         outs = [torch.empty(c.height, c.width, 4, device=splats.pos_r.device) for c in cams]
+        shapes = [(b, SCHEDULE_PER_PIXEL) for b in blocks] + [(128, SCHEDULE_PERSISTENT)]
         for k in ks:
-            for block in blocks:
-                p = TraceParams(base.max_hits, base.t_stop, base.edge_softness, k, block)
+            for block, sched in shapes:
+                p = TraceParams(base.max_hits, base.t_stop, base.edge_softness, k, block, sched)
 
                 def run():
                     for c, o in zip(cams, outs):
                         trace(bvh, srt, c, p, out=o)
                 ms = _time_ms(run, reps) / len(cams)
-                table.append((leaf, k, block, ms))
+                table.append((leaf, k, block, sched, ms))
                 if best is None or ms < best["ms"]:
-                    best = {"leaf": leaf, "k_chunk": k, "block": block, "ms": ms}
+                    best = {"leaf": leaf, "k_chunk": k, "block": block, "schedule": sched, "ms": ms}
     best["table"] = table
     _store(key, best)
     return best

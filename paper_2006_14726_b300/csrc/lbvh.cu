@@ -27,7 +27,7 @@ constexpr int kSortWarps = kSortThreads / 32;
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct Scratch {
-    uint32_t *keys0, *keys1, *vals0, *vals1, *hist, *leaf_parent, *node_parent, *visit;
+    uint32_t *keys0, *keys1, *vals0, *vals1, *hist, *totals, *leaf_parent, *node_parent, *visit;
     float* partials;
     uint32_t tiles;
 };
@@ -48,6 +48,7 @@ size_t scratch_layout(uint32_t cap, uint32_t leaf, char* base, Scratch* s) {
     char* v0 = take(sizeof(uint32_t) * cap);
     char* v1 = take(sizeof(uint32_t) * cap);
     char* h = take(sizeof(uint32_t) * 256 * (size_t)(tiles ? tiles : 1));
+    char* tt = take(sizeof(uint32_t) * 256);
     char* lp = take(sizeof(uint32_t) * m);
     char* np = take(sizeof(uint32_t) * m);
     char* vi = take(sizeof(uint32_t) * m);
@@ -55,7 +56,7 @@ size_t scratch_layout(uint32_t cap, uint32_t leaf, char* base, Scratch* s) {
     if (s) {
         s->keys0 = (uint32_t*)k0; s->keys1 = (uint32_t*)k1;
         s->vals0 = (uint32_t*)v0; s->vals1 = (uint32_t*)v1;
-        s->hist = (uint32_t*)h; s->leaf_parent = (uint32_t*)lp; s->node_parent = (uint32_t*)np;
+        s->hist = (uint32_t*)h; s->totals = (uint32_t*)tt; s->leaf_parent = (uint32_t*)lp; s->node_parent = (uint32_t*)np;
         s->visit = (uint32_t*)vi; s->partials = (float*)pa; s->tiles = tiles;
     }
     return off;
@@ -101,14 +102,29 @@ __global__ void __launch_bounds__(256) k_bounds_partial(const float4* __restrict
     }
 }
 
-__global__ void k_bounds_final(const float* __restrict__ partials, const uint32_t* __restrict__ n_in,
-                               uint32_t cap, uint32_t leaf, LbvhHeader* __restrict__ hdr,
-                               uint32_t* __restrict__ n_sorted) {
+__global__ void __launch_bounds__(kBoundsBlocks) k_bounds_final(
+    const float* __restrict__ partials, const uint32_t* __restrict__ n_in, uint32_t cap,
+    uint32_t leaf, LbvhHeader* __restrict__ hdr, uint32_t* __restrict__ n_sorted) {
+    __shared__ float s[7][kBoundsBlocks / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int b = threadIdx.x;  // one partial per thread
+#pragma unroll
+    for (int k = 0; k < 7; k++) {
+        float x = partials[b * 8 + k];
+        for (int o = 16; o > 0; o >>= 1) {
+            const float y = __shfl_xor_sync(0xffffffffu, x, o);
+            x = (k < 3) ? fminf(x, y) : fmaxf(x, y);
+        }
+        if (lane == 0) s[k][warp] = x;
+    }
+    __syncthreads();
     if (threadIdx.x != 0) return;
-    float v[7] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0f};
-    for (int b = 0; b < kBoundsBlocks; b++)
-        for (int k = 0; k < 7; k++)
-            v[k] = (k < 3) ? fminf(v[k], partials[b * 8 + k]) : fmaxf(v[k], partials[b * 8 + k]);
+    float v[7];
+    for (int k = 0; k < 7; k++) {
+        float x = s[k][0];
+        for (int w = 1; w < kBoundsBlocks / 32; w++) x = (k < 3) ? fminf(x, s[k][w]) : fmaxf(x, s[k][w]);
+        v[k] = x;
+    }
     const uint32_t n = min(*n_in, cap);  // a count beyond the capacity is clamped
     LbvhHeader h = {};
     h.n = n;
@@ -169,34 +185,61 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t* __rest
     __syncthreads();
     const uint32_t n = hdr->n;
     const uint32_t base = blockIdx.x * kSortTile;
+    const int lane = threadIdx.x & 31;
     for (int k = 0; k < kSortItems; k++) {
         const uint32_t i = base + k * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&s_cnt[(keys[i] >> shift) & 255u], 1u);
+        const bool valid = i < n;
+        const uint32_t d = valid ? (keys[i] >> shift) & 255u : 256u + lane;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);  // lanes with the same digit
+        if (valid && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&s_cnt[d], __popc(peers));
     }
     __syncthreads();
     hist[threadIdx.x * tiles + blockIdx.x] = s_cnt[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* __restrict__ hist, uint32_t total) {
-    __shared__ uint32_t s[1024];
-    const uint32_t per = (total + 1023) / 1024;
-    const uint32_t lo = min(threadIdx.x * per, total), hi = min(lo + per, total);
-    uint32_t sum = 0;
-    for (uint32_t i = lo; i < hi; i++) sum += hist[i];
-    s[threadIdx.x] = sum;
+// One block per digit: exclusive scan of that digit's per-tile counts (contiguous in the
+// digit-major layout) in place, and the digit's total.  The scatter adds the digit bases.
+__global__ void __launch_bounds__(256) k_rs_scan(uint32_t* __restrict__ hist, uint32_t tiles,
+                                                 uint32_t* __restrict__ totals) {
+    __shared__ uint32_t s_warp[8];
+    __shared__ uint32_t s_carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* h = hist + (size_t)blockIdx.x * tiles;
+    if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        const uint32_t v = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0;
+    for (uint32_t base = 0; base < tiles; base += 4 * 256) {
+        uint32_t v[4], sum = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {  // 4 consecutive tiles per thread
+            const uint32_t i = base + threadIdx.x * 4 + k;
+            v[k] = i < tiles ? h[i] : 0u;
+            sum += v[k];
+        }
+        uint32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) s_warp[warp] = inc;
         __syncthreads();
-        s[threadIdx.x] += v;
+        uint32_t wpre = 0, btot = 0;
+        for (int w = 0; w < 8; w++) {
+            wpre += (w < warp) ? s_warp[w] : 0u;
+            btot += s_warp[w];
+        }
+        uint32_t run = s_carry + wpre + inc - sum;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const uint32_t i = base + threadIdx.x * 4 + k;
+            if (i < tiles) h[i] = run;
+            run += v[k];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry += btot;
         __syncthreads();
     }
-    uint32_t run = s[threadIdx.x] - sum;
-    for (uint32_t i = lo; i < hi; i++) {
-        const uint32_t c = hist[i];
-        hist[i] = run;
-        run += c;
-    }
+    if (threadIdx.x == 0) totals[blockIdx.x] = s_carry;
 }
 
 // Rank every key of the tile stably by digit (warp match + per-warp digit counters), stage the
@@ -204,11 +247,12 @@ __global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* __restrict__ hist, u
 __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
-    const uint32_t* __restrict__ offsets, const LbvhHeader* __restrict__ hdr, int shift,
-    uint32_t tiles) {
+    const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ totals,
+    const LbvhHeader* __restrict__ hdr, int shift, uint32_t tiles) {
     __shared__ uint32_t s_wcnt[kSortWarps][256];
     __shared__ uint32_t s_start[256];
     __shared__ uint32_t s_glob[256];
+    __shared__ uint32_t s_base[256];
     __shared__ uint32_t s_keys[kSortTile];
     __shared__ uint32_t s_vals[kSortTile];
     const uint32_t n = hdr->n;
@@ -246,14 +290,16 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(
             s_wcnt[w][d] = run;
             run += c;
         }
-        s_start[d] = run;  // digit total, scanned below
-        s_glob[d] = offsets[d * tiles + blockIdx.x];
+        s_start[d] = run;  // digit total within the tile, scanned below
+        s_glob[d] = offsets[(size_t)d * tiles + blockIdx.x];
+        s_base[d] = totals[d];  // digit total over all tiles, scanned below
     }
     __syncthreads();
-    if (warp == 0) {  // exclusive scan of the 256 digit totals by one warp (8 per lane)
+    if (warp < 2) {  // exclusive scans of the 256 tile totals (warp 0) and global totals (warp 1)
+        uint32_t* arr = warp == 0 ? s_start : s_base;
         uint32_t t[8], sum = 0;
 #pragma unroll
-        for (int j = 0; j < 8; j++) { t[j] = s_start[lane * 8 + j]; sum += t[j]; }
+        for (int j = 0; j < 8; j++) { t[j] = arr[lane * 8 + j]; sum += t[j]; }
         uint32_t inc = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -262,8 +308,10 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(
         }
         uint32_t run = inc - sum;
 #pragma unroll
-        for (int j = 0; j < 8; j++) { const uint32_t c = t[j]; s_start[lane * 8 + j] = run; run += c; }
+        for (int j = 0; j < 8; j++) { const uint32_t c = t[j]; arr[lane * 8 + j] = run; run += c; }
     }
+    __syncthreads();
+    s_glob[threadIdx.x] += s_base[threadIdx.x];
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kSortItems; k++) {
@@ -328,6 +376,13 @@ __global__ void __launch_bounds__(256) k_karras(const uint32_t* __restrict__ cod
 }
 
 // ---- leaf gather + bottom-up refit ---------------------------------------------------------
+// Message passing between the two children of a node: the first child to finish stores its box,
+// then (release) increments the node's counter; the second child's increment observes it and,
+// after an acquire, reads both boxes from L2.  A fence.acq_rel on each side is sufficient for this
+// pattern; the sequentially consistent __threadfence() is not needed (and was the refit's main
+// stall).
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 __device__ __forceinline__ void store_box(float4* nodes, uint32_t node, uint32_t slot,
                                           const float lo[3], const float hi[3]) {
     float* f = reinterpret_cast<float*>(nodes + 4 * (size_t)node) + 6 * slot;
@@ -365,10 +420,10 @@ __global__ void __launch_bounds__(256) k_leaves_refit(
     uint32_t node = pp >> 1;
     if (node + 1 >= m) return;  // never taken for a well-formed tree
     store_box(nodes, node, pp & 1u, lo, hi);
-    __threadfence();
+    fence_acq_rel_gpu();
     uint32_t old = atomicAdd(visit + node, 1u);
     while (old == 1u) {  // second arrival: both children are final
-        __threadfence();
+        fence_acq_rel_gpu();
         const float* f = reinterpret_cast<const float*>(nodes + 4 * (size_t)node);
         float a[12];
 #pragma unroll
@@ -380,7 +435,7 @@ __global__ void __launch_bounds__(256) k_leaves_refit(
         node = pp >> 1;
         if (node + 1 >= m) break;  // never taken for a well-formed tree
         store_box(nodes, node, pp & 1u, lo, hi);
-        __threadfence();
+        fence_acq_rel_gpu();
         old = atomicAdd(visit + node, 1u);
     }
 }
@@ -443,7 +498,7 @@ int wrs_build_lbvh(const wrs_splats* in, const float* radius_scale, float global
     k_bounds_partial<<<kBoundsBlocks, 256, 0, s>>>(pos4, radius_scale, global_scale, in->n, cap,
                                                    S.partials);
     WRS_LAUNCH_CHECK("wrs_build_lbvh bounds");
-    k_bounds_final<<<1, 32, 0, s>>>(S.partials, in->n, cap, leaf, hdr, sorted->n);
+    k_bounds_final<<<1, kBoundsBlocks, 0, s>>>(S.partials, in->n, cap, leaf, hdr, sorted->n);
     WRS_LAUNCH_CHECK("wrs_build_lbvh bounds final");
     if (cap == 0) return WRS_OK;
     k_morton<<<g256, 256, 0, s>>>(pos4, hdr, S.keys0, S.vals0);
@@ -451,8 +506,9 @@ int wrs_build_lbvh(const wrs_splats* in, const float* radius_scale, float global
     uint32_t *ki = S.keys0, *vi = S.vals0, *ko = S.keys1, *vo = S.vals1;
     for (int shift = 0; shift < 32; shift += 8) {
         k_rs_hist<<<S.tiles, kSortThreads, 0, s>>>(ki, hdr, shift, S.tiles, S.hist);
-        k_rs_scan<<<1, 1024, 0, s>>>(S.hist, 256 * S.tiles);
-        k_rs_scatter<<<S.tiles, kSortThreads, 0, s>>>(ki, vi, ko, vo, S.hist, hdr, shift, S.tiles);
+        k_rs_scan<<<256, 256, 0, s>>>(S.hist, S.tiles, S.totals);
+        k_rs_scatter<<<S.tiles, kSortThreads, 0, s>>>(ki, vi, ko, vo, S.hist, S.totals, hdr, shift,
+                                                      S.tiles);
         WRS_LAUNCH_CHECK("wrs_build_lbvh radix sort");
         uint32_t* t = ki; ki = ko; ko = t;
         t = vi; vi = vo; vo = t;

@@ -165,6 +165,29 @@ __device__ __forceinline__ RayCtx make_ray_ctx(const Scene& sc, const wrs_camera
     return r;
 }
 
+// Composite the first `count` gathered hits front to back (spec S6).  Returns true when the ray
+// is finished (H hits used, transmittance at or below t_stop, or fewer than K hits were left).
+template <int K, bool COUNT>
+__device__ __forceinline__ bool composite_chunk(const Scene& sc, const Comp& cp, const Ray& ray,
+                                                const uint32_t (&ki)[K], int count, float& T,
+                                                float3& C, int& used, Counts& cnt) {
+#pragma unroll
+    for (int s = 0; s < K; s++) {
+        if (s >= count) break;
+        if ((cp.max_hits > 0 && used == cp.max_hits) || T <= cp.t_stop) return true;
+        const HitTerms h = hit_terms(sc, cp, ray, ki[s]);
+        const float tw = T * (h.op * h.w);
+        C.x = fmaf(tw, h.c.x, C.x);
+        C.y = fmaf(tw, h.c.y, C.y);
+        C.z = fmaf(tw, h.c.z, C.z);
+        T = T * (1.0f - h.a);
+        used++;
+        if (COUNT) cnt.composited++;
+    }
+    if (count < K) return true;
+    return (cp.max_hits > 0 && used == cp.max_hits) || T <= cp.t_stop;
+}
+
 // Forward trace of one ray (spec S6).  overflow_bits: status bits of a traversal failure.
 template <int K, bool COUNT>
 __device__ __forceinline__ float4 trace_ray(const Scene& sc, const Comp& cp, const RayCtx& rc,
@@ -184,27 +207,184 @@ __device__ __forceinline__ float4 trace_ray(const Scene& sc, const Comp& cp, con
                                            last_key, last_id, kk, ki, kid, cnt);
         if (COUNT) cnt.passes++;
         if (count < 0) { overflow_bits = count == -1 ? WRS_STATUS_STACK_OVERFLOW : WRS_STATUS_MALFORMED_TREE; break; }
-        bool done = false;
-#pragma unroll
-        for (int s = 0; s < K; s++) {
-            if (s >= count) break;
-            if ((cp.max_hits > 0 && used == cp.max_hits) || T <= cp.t_stop) { done = true; break; }
-            const HitTerms h = hit_terms(sc, cp, rc.ray, ki[s]);
-            const float tw = T * (h.op * h.w);
-            C.x = fmaf(tw, h.c.x, C.x);
-            C.y = fmaf(tw, h.c.y, C.y);
-            C.z = fmaf(tw, h.c.z, C.z);
-            T = T * (1.0f - h.a);
-            used++;
-            if (COUNT) cnt.composited++;
-        }
-        if (done || count < K) break;
-        if ((cp.max_hits > 0 && used == cp.max_hits) || T <= cp.t_stop) break;
+        if (composite_chunk<K, COUNT>(sc, cp, rc.ray, ki, count, T, C, used, cnt)) break;
         has_last = true;
         last_key = kk[K - 1];
         last_id = kid[K - 1];
     }
     return make_float4(C.x, C.y, C.z, 1.0f - T);
+}
+
+// ---- persistent schedule with lane refill ----------------------------------------------------
+// The same per-ray work as trace_ray, run as a per-lane state machine: every loop iteration a
+// lane advances its traversal by one node or one leaf; when a ray finishes its lane goes idle,
+// and as soon as kRefill lanes of a warp are idle the warp takes that many new rays (ballot +
+// one shared-memory atomic).  Each block owns the 8x4 ray tiles blockIdx.x, blockIdx.x + grid, ...
+// so that every block gets a mix of cheap and expensive parts of the image.
+constexpr int kRefill = 8;
+
+template <int K>
+struct Lane {
+    Ray ray;
+    wrs::BoxRay br;
+    uint32_t pix;
+    float T;
+    float3 C;
+    int used;
+    bool has_last;
+    float last_key;
+    uint32_t last_id;
+    float kk[K];
+    uint32_t ki[K], kid[K];
+    int count;
+    uint32_t ref;
+    int sp;
+    uint32_t budget;
+};
+
+template <int K>
+__device__ __forceinline__ void begin_pass(Lane<K>& L, int32_t root, uint32_t m) {
+#pragma unroll
+    for (int s = 0; s < K; s++) { L.kk[s] = kInf; L.ki[s] = 0xFFFFFFFFu; L.kid[s] = 0xFFFFFFFFu; }
+    L.count = 0;
+    L.ref = (uint32_t)root;
+    L.sp = 0;
+    L.budget = 2 * m + 2;
+}
+
+// One traversal step (the body of gather's loop).  0: continue; 1: pass finished; -1: stack
+// overflow; -2: malformed tree.
+template <int K>
+__device__ __forceinline__ int lane_step(const Scene& sc, Lane<K>& L, int* stack, uint32_t n,
+                                         uint32_t leaf, uint32_t m) {
+    if (L.budget-- == 0) return -2;
+    const float lower = L.has_last ? L.last_key : -kInf;
+    if (!(L.ref & kLeafBit)) {
+        if (L.ref + 1 >= m) return -2;
+        const float4* nd = sc.nodes + 4 * (size_t)L.ref;
+        const float4 a = __ldg(nd + 0), b = __ldg(nd + 1), c = __ldg(nd + 2), r = __ldg(nd + 3);
+        float tn0, tf0, tn1, tf1;
+        wrs::box_test(L.br, a.x, a.y, a.z, a.w, b.x, b.y, tn0, tf0);
+        wrs::box_test(L.br, b.z, b.w, c.x, c.y, c.z, c.w, tn1, tf1);
+        const float cut = L.kk[K - 1];
+        const bool h0 = tn0 <= tf0 && tn0 <= cut && tf0 >= lower;
+        const bool h1 = tn1 <= tf1 && tn1 <= cut && tf1 >= lower;
+        const uint32_t c0 = __float_as_uint(r.x), c1 = __float_as_uint(r.y);
+        if (h0 && h1) {
+            const bool first0 = tn0 <= tn1;
+            if (L.sp >= wrs::kStack) return -1;
+            stack[L.sp++] = (int)(first0 ? c1 : c0);
+            L.ref = first0 ? c0 : c1;
+            return 0;
+        }
+        if (h0) { L.ref = c0; return 0; }
+        if (h1) { L.ref = c1; return 0; }
+    } else {
+        const uint32_t first = (L.ref & ~kLeafBit) * leaf;
+        const uint32_t last = min(first + leaf, n);
+        for (uint32_t k = first; k < last; k++) {
+            const float4 s = __ldg(sc.pos_r + k);
+            float key, ff;
+            if (!wrs::sphere_hit(L.ray, s, key, ff)) continue;
+            if (key > L.kk[K - 1] || key < lower) continue;
+            const uint32_t hid = __ldg(sc.id + k);
+            if (L.has_last && !wrs::hit_less(L.last_key, L.last_id, key, hid)) continue;
+            if (!wrs::hit_less(key, hid, L.kk[K - 1], L.kid[K - 1])) continue;
+            float nk = key;
+            uint32_t ni = k, nid = hid;
+#pragma unroll
+            for (int s2 = 0; s2 < K; s2++) {
+                const bool lt = wrs::hit_less(nk, nid, L.kk[s2], L.kid[s2]);
+                const float tk = L.kk[s2];
+                const uint32_t ti = L.ki[s2], tid = L.kid[s2];
+                L.kk[s2] = lt ? nk : tk; L.ki[s2] = lt ? ni : ti; L.kid[s2] = lt ? nid : tid;
+                nk = lt ? tk : nk; ni = lt ? ti : ni; nid = lt ? tid : nid;
+            }
+            L.count = min(L.count + 1, K);
+        }
+    }
+    if (L.sp == 0) return 1;
+    L.ref = (uint32_t)stack[--L.sp];
+    return 0;
+}
+
+template <int K>
+__global__ void __launch_bounds__(128) k_trace_pr(Scene sc, Comp cp, wrs_camera cam,
+                                                  float4* __restrict__ out, int32_t* status) {
+    __shared__ uint32_t s_next;
+    if (threadIdx.x == 0) s_next = 0;
+    __syncthreads();
+    const uint32_t W = (uint32_t)cam.width, H = (uint32_t)cam.height;
+    const uint32_t tiles_x = (W + 7) / 8, n_tiles = tiles_x * ((H + 3) / 4);
+    const uint32_t G = gridDim.x;
+    const uint32_t my_rays = blockIdx.x < n_tiles ? ((n_tiles - 1 - blockIdx.x) / G + 1) * 32 : 0;
+    const LbvhHeader hd = *sc.hdr;
+    const uint32_t n = hd.n, leaf = hd.leaf;
+    const uint32_t m = n == 0 ? 0 : (n + leaf - 1) / leaf;
+    const int lane = threadIdx.x & 31;
+    Lane<K> L;
+    int stack[wrs::kStack];
+    Counts cnt;
+    bool active = false;
+    bool more = my_rays > 0;
+    while (true) {
+        const uint32_t idle = __ballot_sync(0xffffffffu, !active);
+        if (more && __popc(idle) >= kRefill) {
+            const uint32_t c = __popc(idle);
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(&s_next, c);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base + c >= my_rays) more = false;
+            if (!active) {
+                const uint32_t r = base + __popc(idle & ((1u << lane) - 1u));
+                if (r < my_rays) {
+                    const uint32_t tile = blockIdx.x + (r >> 5) * G, pos = r & 31;
+                    const uint32_t x = (tile % tiles_x) * 8 + (pos & 7);
+                    const uint32_t y = (tile / tiles_x) * 4 + (pos >> 3);
+                    if (x < W && y < H) {
+                        L.pix = y * W + x;
+                        if (n == 0) {
+                            out[L.pix] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        } else {
+                            L.ray = wrs::primary_ray(cam, (int)x, (int)y);
+                            L.br = wrs::make_box_ray(L.ray, wrs::traversal_eps(L.ray, hd.maxabs));
+                            L.T = 1.0f;
+                            L.C = make_float3(0.f, 0.f, 0.f);
+                            L.used = 0;
+                            L.has_last = false;
+                            L.last_key = 0.0f;
+                            L.last_id = 0;
+                            begin_pass(L, hd.root, m);
+                            active = true;
+                        }
+                    }
+                }
+            }
+        }
+        if (!__any_sync(0xffffffffu, active)) {
+            if (!more) break;
+            continue;
+        }
+        if (active) {
+            const int rc = lane_step<K>(sc, L, stack, n, leaf, m);
+            if (rc != 0) {
+                bool done = true;
+                if (rc < 0) {
+                    wrs::set_status(status, rc == -1 ? WRS_STATUS_STACK_OVERFLOW : WRS_STATUS_MALFORMED_TREE);
+                } else if (!composite_chunk<K, false>(sc, cp, L.ray, L.ki, L.count, L.T, L.C, L.used, cnt)) {
+                    done = false;
+                    L.has_last = true;
+                    L.last_key = L.kk[K - 1];
+                    L.last_id = L.kid[K - 1];
+                    begin_pass(L, hd.root, m);
+                }
+                if (done) {
+                    out[L.pix] = make_float4(L.C.x, L.C.y, L.C.z, 1.0f - L.T);
+                    active = false;
+                }
+            }
+        }
+    }
 }
 
 // Pixel of thread t in a (16 x 4*warps/2) tile: warps are 8x4 pixel blocks, two across.
@@ -432,6 +612,8 @@ int check_trace_args(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_ca
     if (p->block != 64 && p->block != 128 && p->block != 256)
         return wrs::fail(WRS_ERR_ARG, "%s: block %d not in {64,128,256}", fn, p->block);
     if (p->max_hits < 0) return wrs::fail(WRS_ERR_ARG, "%s: max_hits < 0", fn);
+    if (p->schedule != WRS_SCHEDULE_PER_PIXEL && p->schedule != WRS_SCHEDULE_PERSISTENT)
+        return wrs::fail(WRS_ERR_ARG, "%s: unknown schedule %d", fn, p->schedule);
     if (!(p->t_stop >= 0.0f && p->t_stop < 1.0f))
         return wrs::fail(WRS_ERR_ARG, "%s: t_stop must be in [0, 1)", fn);
     if (!(p->edge_softness >= 0.0f && p->edge_softness < 1.0f))
@@ -479,6 +661,17 @@ template <int K> struct LaunchTrace {
         k_trace<K><<<g, b, 0, s>>>(sc, cp, cam, o, st);
     }
 };
+template <int K> struct LaunchTracePr {
+    static void run(int g, int b, cudaStream_t s, Scene sc, Comp cp, wrs_camera cam, float4* o,
+                    int32_t* st) {
+        k_trace_pr<K><<<g, b, 0, s>>>(sc, cp, cam, o, st);
+    }
+    static int blocks_per_sm(int b) {
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trace_pr<K>, b, 0);
+        return nb;
+    }
+};
 template <int K> struct LaunchCount {
     static void run(dim3 g, int b, cudaStream_t s, Scene sc, Comp cp, wrs_camera cam,
                     unsigned long long* c, int32_t* st) {
@@ -523,9 +716,31 @@ int wrs_trace(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* c
     if (!rgba_out || (reinterpret_cast<uintptr_t>(rgba_out) & 15))
         return wrs::fail(WRS_ERR_ARG, "%s: rgba_out NULL or not 16-byte aligned", fn);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    dispatch_k<LaunchTrace>(effective_k(params), grid_for(cam, params->block), params->block, s,
-                            make_scene(bvh, sorted, params->opacity), comp_of(params), *cam,
-                            reinterpret_cast<float4*>(rgba_out), status);
+    const int K = effective_k(params);
+    if (params->schedule == WRS_SCHEDULE_PERSISTENT) {
+        // one resident wave of blocks (occupancy x SMs), queried once per K and cached
+        static int cached_grid[5] = {0};
+        const int ki = K == 1 ? 0 : K == 2 ? 1 : K == 4 ? 2 : K == 8 ? 3 : 4;
+        if (cached_grid[ki] == 0) {
+            int dev = 0, sms = 0, per_sm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            switch (K) {
+                case 1: per_sm = LaunchTracePr<1>::blocks_per_sm(128); break;
+                case 2: per_sm = LaunchTracePr<2>::blocks_per_sm(128); break;
+                case 4: per_sm = LaunchTracePr<4>::blocks_per_sm(128); break;
+                case 8: per_sm = LaunchTracePr<8>::blocks_per_sm(128); break;
+                default: per_sm = LaunchTracePr<16>::blocks_per_sm(128); break;
+            }
+            cached_grid[ki] = sms * (per_sm < 1 ? 1 : per_sm);
+        }
+        dispatch_k<LaunchTracePr>(K, cached_grid[ki], 128, s, make_scene(bvh, sorted, params->opacity),
+                                  comp_of(params), *cam, reinterpret_cast<float4*>(rgba_out), status);
+    } else {
+        dispatch_k<LaunchTrace>(K, grid_for(cam, params->block), params->block, s,
+                                make_scene(bvh, sorted, params->opacity), comp_of(params), *cam,
+                                reinterpret_cast<float4*>(rgba_out), status);
+    }
     WRS_LAUNCH_CHECK(fn);
     return WRS_OK;
 }

@@ -198,12 +198,13 @@ def test_lbvh_duplicate_centres_and_tiny_counts(wrs):
 # trace
 # ---------------------------------------------------------------------------------------------
 def _trace_pair(wrs, rgba, depth, srv, cli, H=0, beta=0.0, opacity=None, scale=None, leaf=1,
-                k=8, block=128, pixels=None):
+                k=8, block=128, pixels=None, schedule=0):
     ref_sp = oracle.unproject(rgba, depth, srv)
     sp = _gpu_splats(wrs, rgba, depth, srv)
     bvh, srt = wrs.build_lbvh(sp, leaf, radius_scale=None if scale is None else _cuda(scale))
     st = wrs.new_status()
-    params = wrs.TraceParams(max_hits=H, edge_softness=beta, k_chunk=k, block=block)
+    params = wrs.TraceParams(max_hits=H, edge_softness=beta, k_chunk=k, block=block,
+                             schedule=schedule)
     img = wrs.trace(bvh, srt, cli, params, opacity=None if opacity is None else _cuda(opacity),
                     status=st)
     wrs.check_status(st)
@@ -248,11 +249,12 @@ def test_trace_invariant_to_tuning_bitwise(wrs):
     for leaf in (1, 4, 16):
         bvh, srt = wrs.build_lbvh(sp, leaf, radius_scale=sc)
         for k in (1, 2, 4, 8, 16):
-            for block in (64, 128, 256):
-                img = wrs.trace(bvh, srt, cli, wrs.TraceParams(k_chunk=k, block=block)).cpu().numpy()
+            for block, sched in ((64, 0), (128, 0), (256, 0), (128, 1)):
+                p = wrs.TraceParams(k_chunk=k, block=block, schedule=sched)
+                img = wrs.trace(bvh, srt, cli, p).cpu().numpy()
                 if base is None:
                     base = img
-                assert np.array_equal(img.view(np.uint32), base.view(np.uint32)), (leaf, k, block)
+                assert np.array_equal(img.view(np.uint32), base.view(np.uint32)), (leaf, k, block, sched)
 
 
 def test_trace_mid_full_image(wrs):
@@ -276,9 +278,9 @@ def test_trace_large_sampled(wrs):
     srv = synth.LARGE.server_cam()
     cli = synth.orbit(srv, (0.6, 0.8, 0.0), 20.0)
     pix = np.random.default_rng(9).choice(1920 * 1080, 4096, replace=False)
-    for H in (0, 1):
-        got, ref, _ = _trace_pair(wrs, rgba, depth, srv, cli, H=H, pixels=pix)
-        _assert_close(got, ref["rgba"], f"large H={H}")
+    for H, k, sched in ((0, 1, 1), (0, 8, 0), (1, 1, 1)):
+        got, ref, _ = _trace_pair(wrs, rgba, depth, srv, cli, H=H, k=k, pixels=pix, schedule=sched)
+        _assert_close(got, ref["rgba"], f"large H={H} k={k} schedule={sched}")
 
 
 def test_trace_empty_and_single(wrs):
@@ -307,8 +309,8 @@ def test_trace_many_layers_multi_pass(wrs):
     srv = synth.server_camera(1.4, 30.0, W, H)
     cli = synth.orbit(srv, (1, 0, 0), 60.0)
     sc = np.full(W * H, 8.0, np.float32)
-    for k in (1, 2, 16):
-        got, ref, _ = _trace_pair(wrs, rgba, depth, srv, cli, scale=sc, k=k)
+    for k, sched in ((1, 0), (2, 1), (16, 0), (1, 1)):
+        got, ref, _ = _trace_pair(wrs, rgba, depth, srv, cli, scale=sc, k=k, schedule=sched)
         assert ref["nhits"].max() > 20
         _assert_close(got, ref["rgba"], f"layers k={k}")
 
