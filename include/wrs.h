@@ -198,14 +198,15 @@ int wrs_trace_count(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_cam
                     const wrs_trace_params* params, unsigned long long* counters,
                     int32_t* status, wrs_stream_t stream);
 
-/* Work items (16x16 pixel tiles) of one session with the given client size. */
+/* Work items (8x4 pixel ray tiles) of one session with the given client size. */
 uint32_t wrs_session_tiles(int32_t width, int32_t height);
 
 /* Many client sessions, each with its own LBVH, splats, camera and output, traced in ONE
- * persistent launch: blocks pop (session, tile) items from *work_counter (device uint32, reset by
- * this call).  sessions: device array of n_sessions descriptors whose tile_begin are the prefix
- * sums of wrs_session_tiles; total_tiles = their sum.  Each session's image equals wrs_trace's
- * bitwise. */
+ * persistent launch of 128-thread blocks (params->block is ignored): warps take chunks of four
+ * ray tiles of any session from *work_counter (device uint32, reset by this call) and refill their
+ * idle lanes from them.  sessions: device array of n_sessions descriptors whose tile_begin are the
+ * prefix sums of wrs_session_tiles; total_tiles = their sum.  Each session's image equals
+ * wrs_trace's bitwise. */
 int wrs_trace_batched(const wrs_session* sessions, int32_t n_sessions, uint32_t total_tiles,
                       const wrs_trace_params* params, uint32_t* work_counter, int32_t* status,
                       wrs_stream_t stream);

@@ -99,14 +99,13 @@ def tune_trace(splats: SplatBuffers, cams: Sequence, base: TraceParams = TracePa
 
 
 def tune_batched(batch: Batch, base: TraceParams = TraceParams(), ks: Iterable[int] = KS,
-                 blocks: Iterable[int] = BLOCKS, reps: int = 3) -> Dict:
-    """Pick (k_chunk, block) for one persistent multi-session launch (leaf sizes are fixed by the
-    sessions' LBVHs)."""
+                 reps: int = 3) -> Dict:
+    """Pick k_chunk for one persistent multi-session launch (leaf sizes are fixed by the sessions'
+    LBVHs; the launch shape is fixed: one resident wave of 128-thread blocks)."""
     best = None
     for k in ks:
-        for block in blocks:
-            p = TraceParams(base.max_hits, base.t_stop, base.edge_softness, k, block)
-            ms = _time_ms(lambda: trace_batched(batch, p), reps)
-            if best is None or ms < best["ms"]:
-                best = {"k_chunk": k, "block": block, "ms": ms}
+        p = TraceParams(base.max_hits, base.t_stop, base.edge_softness, k, 128)
+        ms = _time_ms(lambda: trace_batched(batch, p), reps)
+        if best is None or ms < best["ms"]:
+            best = {"k_chunk": k, "block": 128, "ms": ms}
     return best

@@ -434,52 +434,114 @@ __global__ void __launch_bounds__(256) k_trace_count(Scene sc, Comp cp, wrs_came
     }
 }
 
-// Persistent multi-session trace: each block pops 16x16 tiles of any session.
+// Persistent multi-session trace with lane refill.  Work is numbered in 8x4 ray tiles over all
+// sessions (session s owns tiles [tile_begin_s, tile_begin_s + tiles_s)); a warp grabs chunks of
+// kChunkTiles tiles from the global counter and refills its idle lanes from its chunk.  Each lane
+// carries the scene of the session its ray belongs to, so one warp may trace several sessions.
+constexpr uint32_t kChunkTiles = 4;
+
 template <int K>
-__global__ void __launch_bounds__(256) k_trace_batched(const wrs_session* __restrict__ sess,
+__global__ void __launch_bounds__(128) k_trace_batched(const wrs_session* __restrict__ sess,
                                                        int n_sessions, uint32_t total_tiles,
                                                        Comp cp, uint32_t* work, int32_t* status) {
-    __shared__ uint32_t s_item;
-    __shared__ int s_sess;
+    const int lane = threadIdx.x & 31;
+    Lane<K> L;
+    int stack[wrs::kStack];
+    Counts cnt;
+    Scene sc;
+    float4* out = nullptr;
+    uint32_t n = 0, leaf = 1, m = 0;
+    int32_t root = 0;
+    int si = -1;
+    bool active = false;
+    bool more = true;                          // warp-uniform
+    uint32_t next_ray = 0, end_ray = 0;        // warp-uniform: rays left in the warp's chunk
     while (true) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const uint32_t item = atomicAdd(work, 1u);
-            s_item = item;
-            int lo = 0, hi = n_sessions - 1;  // last session with tile_begin <= item
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (sess[mid].tile_begin <= item) lo = mid; else hi = mid - 1;
+        uint32_t idle = __ballot_sync(0xffffffffu, !active);
+        if (more && __popc(idle) >= kRefill) {
+            while (idle != 0u) {  // warp-uniform loop: hand rays of the chunk to idle lanes
+                if (next_ray == end_ray) {
+                    uint32_t c = 0;
+                    if (lane == 0) c = atomicAdd(work, 1u);
+                    c = __shfl_sync(0xffffffffu, c, 0);
+                    if ((uint64_t)c * kChunkTiles >= total_tiles) { more = false; break; }
+                    next_ray = c * kChunkTiles * 32u;
+                    end_ray = min(c * kChunkTiles + kChunkTiles, total_tiles) * 32u;
+                }
+                const uint32_t take = min(end_ray - next_ray, (uint32_t)__popc(idle));
+                const uint32_t rank = __popc(idle & ((1u << lane) - 1u));
+                if (((idle >> lane) & 1u) && rank < take) {
+                    const uint32_t r = next_ray + rank, tile = r >> 5, pos = r & 31u;
+                    int lo = 0, hi = n_sessions - 1;  // last session with tile_begin <= tile
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (sess[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+                    }
+                    const wrs_session& S = sess[lo];
+                    const uint32_t W = (uint32_t)S.cam.width, H = (uint32_t)S.cam.height;
+                    const uint32_t local = tile - S.tile_begin, tiles_x = (W + 7) / 8;
+                    const uint32_t x = (local % tiles_x) * 8 + (pos & 7);
+                    const uint32_t y = (local / tiles_x) * 4 + (pos >> 3);
+                    if (x < W && y < H) {
+                        if (lo != si) {
+                            si = lo;
+                            sc.hdr = static_cast<const LbvhHeader*>(S.nodes);
+                            sc.nodes = wrs::lbvh_nodes(S.nodes);
+                            sc.pos_r = reinterpret_cast<const float4*>(S.pos_r);
+                            sc.rgba = reinterpret_cast<const float4*>(S.rgba);
+                            sc.id = S.id;
+                            sc.src = S.src;
+                            sc.opacity = S.opacity;
+                            out = reinterpret_cast<float4*>(S.rgba_out);
+                            const LbvhHeader hd = *sc.hdr;
+                            n = hd.n;
+                            leaf = hd.leaf;
+                            root = hd.root;
+                            m = n == 0 ? 0 : (n + leaf - 1) / leaf;
+                        }
+                        L.pix = y * W + x;
+                        if (n == 0) {
+                            out[L.pix] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        } else {
+                            L.ray = wrs::primary_ray(S.cam, (int)x, (int)y);
+                            L.br = wrs::make_box_ray(L.ray, wrs::traversal_eps(L.ray, sc.hdr->maxabs));
+                            L.T = 1.0f;
+                            L.C = make_float3(0.f, 0.f, 0.f);
+                            L.used = 0;
+                            L.has_last = false;
+                            L.last_key = 0.0f;
+                            L.last_id = 0;
+                            begin_pass(L, root, m);
+                            active = true;
+                        }
+                    }
+                }
+                next_ray += take;
+                for (uint32_t t = 0; t < take; t++) idle &= idle - 1u;  // drop the served lanes
             }
-            s_sess = lo;
         }
-        __syncthreads();
-        const uint32_t item = s_item;
-        if (item >= total_tiles) break;
-        const wrs_session& S = sess[s_sess];
-        const uint32_t local = item - S.tile_begin;
-        const int tiles_x = (S.cam.width + 15) / 16;
-        const int tx = (int)(local % (uint32_t)tiles_x), ty = (int)(local / (uint32_t)tiles_x);
-        Scene sc;
-        sc.hdr = static_cast<const LbvhHeader*>(S.nodes);
-        sc.nodes = wrs::lbvh_nodes(S.nodes);
-        sc.pos_r = reinterpret_cast<const float4*>(S.pos_r);
-        sc.rgba = reinterpret_cast<const float4*>(S.rgba);
-        sc.id = S.id;
-        sc.src = S.src;
-        sc.opacity = S.opacity;
-        for (int t = threadIdx.x; t < 256; t += blockDim.x) {
-            // 16x16 tile: rows of 8x4 warp blocks, two across
-            int px, py;
-            tile_pixel(t, px, py);
-            const int x = tx * 16 + px, y = ty * 16 + py;
-            if (x >= S.cam.width || y >= S.cam.height) continue;
-            const RayCtx rc = make_ray_ctx(sc, S.cam, x, y);
-            uint32_t overflow;
-            Counts cnt;
-            const float4 o = trace_ray<K, false>(sc, cp, rc, overflow, cnt);
-            if (overflow) wrs::set_status(status, overflow);
-            reinterpret_cast<float4*>(S.rgba_out)[(size_t)y * S.cam.width + x] = o;
+        if (!__any_sync(0xffffffffu, active)) {
+            if (!more) break;
+            continue;
+        }
+        if (active) {
+            const int rc = lane_step<K>(sc, L, stack, n, leaf, m);
+            if (rc != 0) {
+                bool done = true;
+                if (rc < 0) {
+                    wrs::set_status(status, rc == -1 ? WRS_STATUS_STACK_OVERFLOW : WRS_STATUS_MALFORMED_TREE);
+                } else if (!composite_chunk<K, false>(sc, cp, L.ray, L.ki, L.count, L.T, L.C, L.used, cnt)) {
+                    done = false;
+                    L.has_last = true;
+                    L.last_key = L.kk[K - 1];
+                    L.last_id = L.kid[K - 1];
+                    begin_pass(L, root, m);
+                }
+                if (done) {
+                    out[L.pix] = make_float4(L.C.x, L.C.y, L.C.z, 1.0f - L.T);
+                    active = false;
+                }
+            }
         }
     }
 }
@@ -763,7 +825,7 @@ int wrs_trace_count(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_cam
 
 uint32_t wrs_session_tiles(int32_t width, int32_t height) {
     if (width <= 0 || height <= 0) return 0;
-    return (uint32_t)((width + 15) / 16) * (uint32_t)((height + 15) / 16);
+    return (uint32_t)((width + 7) / 8) * (uint32_t)((height + 3) / 4);
 }
 
 int wrs_trace_batched(const wrs_session* sessions, int32_t n_sessions, uint32_t total_tiles,
@@ -776,8 +838,6 @@ int wrs_trace_batched(const wrs_session* sessions, int32_t n_sessions, uint32_t 
     const int K0 = params->k_chunk;
     if (K0 != 1 && K0 != 2 && K0 != 4 && K0 != 8 && K0 != 16)
         return wrs::fail(WRS_ERR_ARG, "%s: k_chunk %d not in {1,2,4,8,16}", fn, K0);
-    if (params->block != 64 && params->block != 128 && params->block != 256)
-        return wrs::fail(WRS_ERR_ARG, "%s: block %d not in {64,128,256}", fn, params->block);
     if (params->max_hits < 0 || !(params->t_stop >= 0.0f && params->t_stop < 1.0f) ||
         !(params->edge_softness >= 0.0f && params->edge_softness < 1.0f))
         return wrs::fail(WRS_ERR_ARG, "%s: bad compositing parameters", fn);
@@ -785,30 +845,26 @@ int wrs_trace_batched(const wrs_session* sessions, int32_t n_sessions, uint32_t 
     cudaError_t e = cudaMemsetAsync(work_counter, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return wrs::cuda_fail(e, fn);
     if (total_tiles == 0) return WRS_OK;
-    // occupancy and SM count are queried once per (K, block) and cached, so that a call made
-    // during stream capture issues nothing but the memset and the launch
-    static int cached_grid[5][3] = {{0}};
+    // one resident wave of 128-thread blocks; occupancy and SM count are queried once per K and
+    // cached, so that a call made during stream capture issues nothing but the memset and launch
+    static int cached_grid[5] = {0};
     const int K = effective_k(params);
     const int ki = K == 1 ? 0 : K == 2 ? 1 : K == 4 ? 2 : K == 8 ? 3 : 4;
-    const int bi = params->block == 64 ? 0 : params->block == 128 ? 1 : 2;
-    int per_sm = 0;
-    if (cached_grid[ki][bi] == 0) {
-        int dev = 0, sms = 0;
+    if (cached_grid[ki] == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         switch (K) {
-            case 1: per_sm = LaunchBatched<1>::blocks_per_sm(params->block); break;
-            case 2: per_sm = LaunchBatched<2>::blocks_per_sm(params->block); break;
-            case 4: per_sm = LaunchBatched<4>::blocks_per_sm(params->block); break;
-            case 8: per_sm = LaunchBatched<8>::blocks_per_sm(params->block); break;
-            default: per_sm = LaunchBatched<16>::blocks_per_sm(params->block); break;
+            case 1: per_sm = LaunchBatched<1>::blocks_per_sm(128); break;
+            case 2: per_sm = LaunchBatched<2>::blocks_per_sm(128); break;
+            case 4: per_sm = LaunchBatched<4>::blocks_per_sm(128); break;
+            case 8: per_sm = LaunchBatched<8>::blocks_per_sm(128); break;
+            default: per_sm = LaunchBatched<16>::blocks_per_sm(128); break;
         }
-        if (per_sm < 1) per_sm = 1;
-        cached_grid[ki][bi] = sms * per_sm;
+        cached_grid[ki] = sms * (per_sm < 1 ? 1 : per_sm);
     }
-    int grid = cached_grid[ki][bi];
-    if ((uint32_t)grid > total_tiles) grid = (int)total_tiles;
-    dispatch_k<LaunchBatched>(K, grid, params->block, s, sessions, n_sessions, total_tiles,
+    const int grid = cached_grid[ki];
+    dispatch_k<LaunchBatched>(K, grid, 128, s, sessions, n_sessions, total_tiles,
                               comp_of(params), work_counter, status);
     WRS_LAUNCH_CHECK(fn);
     return WRS_OK;

@@ -53,7 +53,7 @@ def test_size_queries(wrs):
     assert wrs.lib.wrs_lbvh_bytes(1000, 4) == 64 + 64 * 249
     assert wrs.lib.wrs_lbvh_bytes(10, 0) == 0 and wrs.lib.wrs_lbvh_bytes(10, 17) == 0
     assert wrs.lbvh_scratch_bytes(2_073_600, 1) > 4 * 4 * 2_073_600
-    assert wrs.session_tiles(1024, 1024) == 4096 and wrs.session_tiles(17, 1) == 2
+    assert wrs.session_tiles(1024, 1024) == 128 * 256 and wrs.session_tiles(17, 1) == 3
 
 
 def _cam(wrs, w=8, h=8, **kw):

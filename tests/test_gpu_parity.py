@@ -321,8 +321,10 @@ def test_trace_many_layers_multi_pass(wrs):
 def test_batched_equals_sequential_bitwise(wrs):
     sessions = []
     refs = []
-    for s, size in enumerate((64, 96, 160, 200, 128)):
+    for s, size in enumerate((64, 96, 160, 200, 128, 8, 48)):
         rgba, depth = synth.synthetic_server_image(size, size, 60 + s)
+        if size == 8:  # a session without any splat
+            depth[...] = np.inf
         srv = synth.server_camera(1.4, 30.0, size, size)
         cli = synth.poses_in_cap(srv, 1, 15.0, 70 + s, 100 + 13 * s, 90 + 7 * s)[0]
         sp = _gpu_splats(wrs, rgba, depth, srv)
@@ -331,8 +333,8 @@ def test_batched_equals_sequential_bitwise(wrs):
         refs.append(wrs.trace(bvh, srt, cli).cpu().numpy())
     batch = wrs.Batch(sessions)
     st = wrs.new_status()
-    for k, block in ((8, 128), (4, 256), (16, 64)):
-        outs = wrs.trace_batched(batch, wrs.TraceParams(k_chunk=k, block=block), status=st)
+    for k in (8, 1, 4, 16):
+        outs = wrs.trace_batched(batch, wrs.TraceParams(k_chunk=k), status=st)
         wrs.check_status(st)
         for o, r in zip(outs, refs):
             assert np.array_equal(o.cpu().numpy().view(np.uint32), r.view(np.uint32))
