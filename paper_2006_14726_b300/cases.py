@@ -1,6 +1,6 @@
 """Run one workload of the hot path once, with few launches, for profiling and inspection.
 
-    python -m paper_2006_14726_b300.cases large --frames 3 [--leaf 1 --k 1 --block 128]
+    python -m paper_2006_14726_b300.cases large --frames 3 [--leaf 1 --k 1 --block 128 --schedule 1]
 
 Sets up the server image with the GPU ray caster, frees the volume, then runs unproject, the
 LBVH build and ``frames`` client traces (each stage in its own NVTX range) and prints the CUDA
@@ -29,6 +29,7 @@ def main():
     ap.add_argument("--k", type=int, default=1)
     ap.add_argument("--block", type=int, default=128)
     ap.add_argument("--max-hits", type=int, default=0)
+    ap.add_argument("--schedule", type=int, default=1, help="0 per pixel, 1 persistent")
     a = ap.parse_args()
     W = {"tiny": synth.TINY, "mid": synth.MID, "large": synth.LARGE}[a.workload]
     dev = torch.device("cuda")
@@ -40,7 +41,7 @@ def main():
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     cams = [wrs.make_camera(c) for c in W.client_poses(max(a.frames, 1))][: a.frames]
-    params = wrs.TraceParams(max_hits=a.max_hits, k_chunk=a.k, block=a.block)
+    params = wrs.TraceParams(max_hits=a.max_hits, k_chunk=a.k, block=a.block, schedule=a.schedule)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 + a.frames)]
     st = wrs.new_status()
     ev[0].record()

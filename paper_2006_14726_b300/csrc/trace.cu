@@ -44,6 +44,84 @@ struct Counts {
 
 constexpr float kInf = __builtin_huge_valf();
 
+// Test the splats of leaf `leafref` and insert qualifying hits into the sorted K-buffer: hits
+// strictly after (last_key, last_id) when has_last, keeping the K smallest (key, id).  The final
+// buffer does not depend on the order in which leaves are visited.
+template <int K, bool COUNT>
+__device__ __forceinline__ void leaf_hits(const Scene& sc, const Ray& ray, uint32_t leafref,
+                                          uint32_t n, uint32_t leaf, bool has_last, float last_key,
+                                          uint32_t last_id, float (&kk)[K], uint32_t (&ki)[K],
+                                          uint32_t (&kid)[K], int& count, Counts& cnt) {
+    const float lower = has_last ? last_key : -kInf;
+    const uint32_t first = (leafref & ~kLeafBit) * leaf;
+    const uint32_t last = min(first + leaf, n);  // empty if the reference is out of range
+    for (uint32_t k = first; k < last; k++) {
+        const float4 s = __ldg(sc.pos_r + k);
+        float key, ff;
+        if (COUNT) cnt.spheres++;
+        if (!wrs::sphere_hit(ray, s, key, ff)) continue;
+        if (key > kk[K - 1] || key < lower) continue;
+        const uint32_t hid = __ldg(sc.id + k);
+        if (has_last && !wrs::hit_less(last_key, last_id, key, hid)) continue;
+        if (!wrs::hit_less(key, hid, kk[K - 1], kid[K - 1])) continue;
+        // bubble the new hit into the sorted buffer; the old K-th entry drops out
+        float nk = key;
+        uint32_t ni = k, nid = hid;
+#pragma unroll
+        for (int s2 = 0; s2 < K; s2++) {
+            const bool lt = wrs::hit_less(nk, nid, kk[s2], kid[s2]);
+            const float tk = kk[s2];
+            const uint32_t ti = ki[s2], tid = kid[s2];
+            kk[s2] = lt ? nk : tk; ki[s2] = lt ? ni : ti; kid[s2] = lt ? nid : tid;
+            nk = lt ? tk : nk; ni = lt ? ti : ni; nid = lt ? tid : nid;
+        }
+        count = min(count + 1, K);
+        if (COUNT) cnt.gathered++;
+    }
+}
+
+// One visit of internal node `ref`: test both child boxes; the splats of a hit leaf child are
+// tested right away (so every traversal step is a node step and lanes do not diverge between
+// node and leaf code); hit internal children are descended into, nearer first, the other pushed.
+// Returns the next internal node, or kLeafBit when the pass must pop; -1 stack overflow,
+// -2 malformed reference.
+template <int K, bool COUNT>
+__device__ __forceinline__ int64_t visit_node(const Scene& sc, const Ray& ray,
+                                              const wrs::BoxRay& br, uint32_t ref, uint32_t n,
+                                              uint32_t leaf, uint32_t m, bool has_last,
+                                              float last_key, uint32_t last_id, float (&kk)[K],
+                                              uint32_t (&ki)[K], uint32_t (&kid)[K], int& count,
+                                              int* stack, int& sp, Counts& cnt) {
+    if (ref + 1 >= m) return -2;  // not an internal node of this tree
+    const float lower = has_last ? last_key : -kInf;
+    const float4* nd = sc.nodes + 4 * (size_t)ref;
+    const float4 a = __ldg(nd + 0), b = __ldg(nd + 1), c = __ldg(nd + 2), r = __ldg(nd + 3);
+    float tn0, tf0, tn1, tf1;
+    wrs::box_test(br, a.x, a.y, a.z, a.w, b.x, b.y, tn0, tf0);
+    wrs::box_test(br, b.z, b.w, c.x, c.y, c.z, c.w, tn1, tf1);
+    if (COUNT) { cnt.nodes++; cnt.boxes += 2; }
+    const uint32_t c0 = __float_as_uint(r.x), c1 = __float_as_uint(r.y);
+    bool h0 = tn0 <= tf0 && tn0 <= kk[K - 1] && tf0 >= lower;
+    bool h1 = tn1 <= tf1 && tn1 <= kk[K - 1] && tf1 >= lower;
+    if (h0 && (c0 & kLeafBit)) {
+        leaf_hits<K, COUNT>(sc, ray, c0, n, leaf, has_last, last_key, last_id, kk, ki, kid, count, cnt);
+        h0 = false;
+    }
+    if (h1 && (c1 & kLeafBit)) {
+        leaf_hits<K, COUNT>(sc, ray, c1, n, leaf, has_last, last_key, last_id, kk, ki, kid, count, cnt);
+        h1 = false;
+    }
+    if (h0 && h1) {
+        const bool first0 = tn0 <= tn1;
+        if (sp >= wrs::kStack) return -1;
+        stack[sp++] = (int)(first0 ? c1 : c0);
+        return first0 ? c0 : c1;
+    }
+    if (h0) return c0;
+    if (h1) return c1;
+    return kLeafBit;
+}
+
 // One traversal pass: the K smallest hits (key, id) strictly after (last_key, last_id).
 // Returns the number gathered (<= K); -1 if the stack overflowed; -2 if the pass met a reference
 // outside the tree or visited more nodes than the tree has (impossible for a well-formed tree; it
@@ -56,62 +134,22 @@ __device__ __forceinline__ int gather(const Scene& sc, const Ray& ray, const wrs
 #pragma unroll
     for (int s = 0; s < K; s++) { kk[s] = kInf; ki[s] = 0xFFFFFFFFu; kid[s] = 0xFFFFFFFFu; }
     int count = 0;
+    const uint32_t m = (n + leaf - 1) / leaf;  // leaves; internal nodes = m - 1
+    if ((uint32_t)root & kLeafBit) {           // a single leaf: no internal node
+        leaf_hits<K, COUNT>(sc, ray, (uint32_t)root, n, leaf, has_last, last_key, last_id, kk, ki,
+                            kid, count, cnt);
+        return count;
+    }
     int stack[wrs::kStack];
     int sp = 0;
     uint32_t ref = (uint32_t)root;
-    const float lower = has_last ? last_key : -kInf;
-    const uint32_t m = (n + leaf - 1) / leaf;  // leaves; internal nodes = m - 1
-    uint32_t budget = 2 * m + 2;              // node visits allowed in one pass
+    uint32_t budget = m + 1;  // internal node visits allowed in one pass
     while (true) {
         if (budget-- == 0) return -2;
-        if (!(ref & kLeafBit)) {
-            if (ref + 1 >= m) return -2;  // not an internal node of this tree
-            const float4* nd = sc.nodes + 4 * (size_t)ref;
-            const float4 a = __ldg(nd + 0), b = __ldg(nd + 1), c = __ldg(nd + 2), r = __ldg(nd + 3);
-            float tn0, tf0, tn1, tf1;
-            wrs::box_test(br, a.x, a.y, a.z, a.w, b.x, b.y, tn0, tf0);
-            wrs::box_test(br, b.z, b.w, c.x, c.y, c.z, c.w, tn1, tf1);
-            if (COUNT) { cnt.nodes++; cnt.boxes += 2; }
-            const float cut = kk[K - 1];
-            const bool h0 = tn0 <= tf0 && tn0 <= cut && tf0 >= lower;
-            const bool h1 = tn1 <= tf1 && tn1 <= cut && tf1 >= lower;
-            const uint32_t c0 = __float_as_uint(r.x), c1 = __float_as_uint(r.y);
-            if (h0 && h1) {
-                const bool first0 = tn0 <= tn1;
-                if (sp >= wrs::kStack) return -1;
-                stack[sp++] = (int)(first0 ? c1 : c0);
-                ref = first0 ? c0 : c1;
-                continue;
-            }
-            if (h0) { ref = c0; continue; }
-            if (h1) { ref = c1; continue; }
-        } else {
-            const uint32_t first = (ref & ~kLeafBit) * leaf;
-            const uint32_t last = min(first + leaf, n);  // empty if the reference is out of range
-            for (uint32_t k = first; k < last; k++) {
-                const float4 s = __ldg(sc.pos_r + k);
-                float key, ff;
-                if (COUNT) cnt.spheres++;
-                if (!wrs::sphere_hit(ray, s, key, ff)) continue;
-                if (key > kk[K - 1] || key < lower) continue;
-                const uint32_t hid = __ldg(sc.id + k);
-                if (has_last && !wrs::hit_less(last_key, last_id, key, hid)) continue;
-                if (!wrs::hit_less(key, hid, kk[K - 1], kid[K - 1])) continue;
-                // bubble the new hit into the sorted buffer; the old K-th entry drops out
-                float nk = key;
-                uint32_t ni = k, nid = hid;
-#pragma unroll
-                for (int s2 = 0; s2 < K; s2++) {
-                    const bool lt = wrs::hit_less(nk, nid, kk[s2], kid[s2]);
-                    const float tk = kk[s2];
-                    const uint32_t ti = ki[s2], tid = kid[s2];
-                    kk[s2] = lt ? nk : tk; ki[s2] = lt ? ni : ti; kid[s2] = lt ? nid : tid;
-                    nk = lt ? tk : nk; ni = lt ? ti : ni; nid = lt ? tid : nid;
-                }
-                count = min(count + 1, K);
-                if (COUNT) cnt.gathered++;
-            }
-        }
+        const int64_t next = visit_node<K, COUNT>(sc, ray, br, ref, n, leaf, m, has_last, last_key,
+                                                  last_id, kk, ki, kid, count, stack, sp, cnt);
+        if (next < 0) return (int)next;
+        if (next != kLeafBit) { ref = (uint32_t)next; continue; }
         if (sp == 0) break;
         ref = (uint32_t)stack[--sp];
     }
@@ -223,6 +261,17 @@ __device__ __forceinline__ float4 trace_ray(const Scene& sc, const Comp& cp, con
 // so that every block gets a mix of cheap and expensive parts of the image.
 constexpr int kRefill = 8;
 
+// Minimum resident 128-thread blocks per SM asked of the compiler for the single-view persistent
+// kernel with K <= 2 (it caps registers at 65536 / (128 * this)); larger K keep more state and
+// get no cap.  A build-time tuning knob (0 = no cap).
+#ifndef WRS_PERSISTENT_MIN_BLOCKS
+#define WRS_PERSISTENT_MIN_BLOCKS 10
+#endif
+template <int K>
+struct PersistentMinBlocks {
+    static constexpr int value = K <= 2 ? WRS_PERSISTENT_MIN_BLOCKS : 0;
+};
+
 template <int K>
 struct Lane {
     Ray ray;
@@ -249,67 +298,33 @@ __device__ __forceinline__ void begin_pass(Lane<K>& L, int32_t root, uint32_t m)
     L.count = 0;
     L.ref = (uint32_t)root;
     L.sp = 0;
-    L.budget = 2 * m + 2;
+    L.budget = m + 1;
 }
 
-// One traversal step (the body of gather's loop).  0: continue; 1: pass finished; -1: stack
-// overflow; -2: malformed tree.
+// One traversal step: one internal-node visit (its leaf children tested inline), as in gather's
+// loop.  0: continue; 1: pass finished; -1: stack overflow; -2: malformed tree.
 template <int K>
 __device__ __forceinline__ int lane_step(const Scene& sc, Lane<K>& L, int* stack, uint32_t n,
                                          uint32_t leaf, uint32_t m) {
-    if (L.budget-- == 0) return -2;
-    const float lower = L.has_last ? L.last_key : -kInf;
-    if (!(L.ref & kLeafBit)) {
-        if (L.ref + 1 >= m) return -2;
-        const float4* nd = sc.nodes + 4 * (size_t)L.ref;
-        const float4 a = __ldg(nd + 0), b = __ldg(nd + 1), c = __ldg(nd + 2), r = __ldg(nd + 3);
-        float tn0, tf0, tn1, tf1;
-        wrs::box_test(L.br, a.x, a.y, a.z, a.w, b.x, b.y, tn0, tf0);
-        wrs::box_test(L.br, b.z, b.w, c.x, c.y, c.z, c.w, tn1, tf1);
-        const float cut = L.kk[K - 1];
-        const bool h0 = tn0 <= tf0 && tn0 <= cut && tf0 >= lower;
-        const bool h1 = tn1 <= tf1 && tn1 <= cut && tf1 >= lower;
-        const uint32_t c0 = __float_as_uint(r.x), c1 = __float_as_uint(r.y);
-        if (h0 && h1) {
-            const bool first0 = tn0 <= tn1;
-            if (L.sp >= wrs::kStack) return -1;
-            stack[L.sp++] = (int)(first0 ? c1 : c0);
-            L.ref = first0 ? c0 : c1;
-            return 0;
-        }
-        if (h0) { L.ref = c0; return 0; }
-        if (h1) { L.ref = c1; return 0; }
-    } else {
-        const uint32_t first = (L.ref & ~kLeafBit) * leaf;
-        const uint32_t last = min(first + leaf, n);
-        for (uint32_t k = first; k < last; k++) {
-            const float4 s = __ldg(sc.pos_r + k);
-            float key, ff;
-            if (!wrs::sphere_hit(L.ray, s, key, ff)) continue;
-            if (key > L.kk[K - 1] || key < lower) continue;
-            const uint32_t hid = __ldg(sc.id + k);
-            if (L.has_last && !wrs::hit_less(L.last_key, L.last_id, key, hid)) continue;
-            if (!wrs::hit_less(key, hid, L.kk[K - 1], L.kid[K - 1])) continue;
-            float nk = key;
-            uint32_t ni = k, nid = hid;
-#pragma unroll
-            for (int s2 = 0; s2 < K; s2++) {
-                const bool lt = wrs::hit_less(nk, nid, L.kk[s2], L.kid[s2]);
-                const float tk = L.kk[s2];
-                const uint32_t ti = L.ki[s2], tid = L.kid[s2];
-                L.kk[s2] = lt ? nk : tk; L.ki[s2] = lt ? ni : ti; L.kid[s2] = lt ? nid : tid;
-                nk = lt ? tk : nk; ni = lt ? ti : ni; nid = lt ? tid : nid;
-            }
-            L.count = min(L.count + 1, K);
-        }
+    Counts cnt;
+    if (L.ref & kLeafBit) {  // a single leaf: no internal node
+        leaf_hits<K, false>(sc, L.ray, L.ref, n, leaf, L.has_last, L.last_key, L.last_id, L.kk,
+                            L.ki, L.kid, L.count, cnt);
+        return 1;
     }
+    if (L.budget-- == 0) return -2;
+    const int64_t next = visit_node<K, false>(sc, L.ray, L.br, L.ref, n, leaf, m, L.has_last,
+                                              L.last_key, L.last_id, L.kk, L.ki, L.kid, L.count,
+                                              stack, L.sp, cnt);
+    if (next < 0) return (int)next;
+    if (next != kLeafBit) { L.ref = (uint32_t)next; return 0; }
     if (L.sp == 0) return 1;
     L.ref = (uint32_t)stack[--L.sp];
     return 0;
 }
 
 template <int K>
-__global__ void __launch_bounds__(128) k_trace_pr(Scene sc, Comp cp, wrs_camera cam,
+__global__ void __launch_bounds__(128, PersistentMinBlocks<K>::value) k_trace_pr(Scene sc, Comp cp, wrs_camera cam,
                                                   float4* __restrict__ out, int32_t* status) {
     __shared__ uint32_t s_next;
     if (threadIdx.x == 0) s_next = 0;
