@@ -28,6 +28,7 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct Scratch {
     uint32_t *keys0, *keys1, *vals0, *vals1, *hist, *totals, *leaf_parent, *node_parent, *visit;
+    uint2* node_range;  // leaf range [lo, hi] of each internal node
     float* partials;
     uint32_t tiles;
 };
@@ -52,12 +53,13 @@ size_t scratch_layout(uint32_t cap, uint32_t leaf, char* base, Scratch* s) {
     char* lp = take(sizeof(uint32_t) * m);
     char* np = take(sizeof(uint32_t) * m);
     char* vi = take(sizeof(uint32_t) * m);
+    char* nr = take(sizeof(uint2) * m);
     char* pa = take(sizeof(float) * 8 * kBoundsBlocks);
     if (s) {
         s->keys0 = (uint32_t*)k0; s->keys1 = (uint32_t*)k1;
         s->vals0 = (uint32_t*)v0; s->vals1 = (uint32_t*)v1;
         s->hist = (uint32_t*)h; s->totals = (uint32_t*)tt; s->leaf_parent = (uint32_t*)lp; s->node_parent = (uint32_t*)np;
-        s->visit = (uint32_t*)vi; s->partials = (float*)pa; s->tiles = tiles;
+        s->visit = (uint32_t*)vi; s->node_range = (uint2*)nr; s->partials = (float*)pa; s->tiles = tiles;
     }
     return off;
 }
@@ -345,7 +347,8 @@ __global__ void __launch_bounds__(256) k_karras(const uint32_t* __restrict__ cod
                                                 const LbvhHeader* __restrict__ hdr,
                                                 float4* __restrict__ nodes,
                                                 uint32_t* __restrict__ leaf_parent,
-                                                uint32_t* __restrict__ node_parent) {
+                                                uint32_t* __restrict__ node_parent,
+                                                uint2* __restrict__ node_range) {
     const int m = (int)hdr->m;
     const uint32_t leaf = hdr->leaf;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -369,6 +372,7 @@ __global__ void __launch_bounds__(256) k_karras(const uint32_t* __restrict__ cod
     const uint32_t left = (lo == g) ? (kLeafBit | (uint32_t)g) : (uint32_t)g;
     const uint32_t right = (hi == g + 1) ? (kLeafBit | (uint32_t)(g + 1)) : (uint32_t)(g + 1);
     nodes[4 * i + 3] = make_float4(__uint_as_float(left), __uint_as_float(right), 0.0f, 0.0f);
+    node_range[i] = make_uint2((uint32_t)lo, (uint32_t)hi);
     if (lo == g) leaf_parent[g] = (uint32_t)i << 1;
     else node_parent[g] = (uint32_t)i << 1;
     if (hi == g + 1) leaf_parent[g + 1] = ((uint32_t)i << 1) | 1u;
@@ -378,9 +382,13 @@ __global__ void __launch_bounds__(256) k_karras(const uint32_t* __restrict__ cod
 // ---- leaf gather + bottom-up refit ---------------------------------------------------------
 // Message passing between the two children of a node: the first child to finish stores its box,
 // then (release) increments the node's counter; the second child's increment observes it and,
-// after an acquire, reads both boxes from L2.  A fence.acq_rel on each side is sufficient for this
-// pattern; the sequentially consistent __threadfence() is not needed (and was the refit's main
-// stall).
+// after an acquire, reads both boxes.  Each block owns kRefitBlock consecutive leaves.  A node
+// whose leaf range lies inside the block is finished inside the block: its counter and child boxes
+// live in shared memory and the fences are block-scope (cheap).  Only nodes whose range spans
+// blocks use global counters with device-scope fences -- a few per block boundary instead of one
+// per node, which was the refit's main stall.
+constexpr uint32_t kRefitBlock = 256;
+
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 __device__ __forceinline__ void store_box(float4* nodes, uint32_t node, uint32_t slot,
@@ -390,17 +398,23 @@ __device__ __forceinline__ void store_box(float4* nodes, uint32_t node, uint32_t
     __stcg(f + 3, hi[0]); __stcg(f + 4, hi[1]); __stcg(f + 5, hi[2]);
 }
 
-__global__ void __launch_bounds__(256) k_leaves_refit(
+__global__ void __launch_bounds__(kRefitBlock) k_leaves_refit(
     const uint32_t* __restrict__ order, const float4* __restrict__ pos_r,
     const float4* __restrict__ rgba, const uint32_t* __restrict__ id,
     const float* __restrict__ scale, float gscale, const LbvhHeader* __restrict__ hdr,
     float4* __restrict__ nodes, const uint32_t* __restrict__ leaf_parent,
-    const uint32_t* __restrict__ node_parent, uint32_t* __restrict__ visit,
-    float4* __restrict__ s_pos, float4* __restrict__ s_rgba, uint32_t* __restrict__ s_id,
-    uint32_t* __restrict__ s_src) {
+    const uint32_t* __restrict__ node_parent, const uint2* __restrict__ node_range,
+    uint32_t* __restrict__ visit, float4* __restrict__ s_pos, float4* __restrict__ s_rgba,
+    uint32_t* __restrict__ s_id, uint32_t* __restrict__ s_src) {
+    __shared__ uint32_t sh_cnt[kRefitBlock];
+    __shared__ float sh_box[kRefitBlock][12];  // child boxes of local internal node j0 + t
     const uint32_t n = hdr->n, m = hdr->m, leaf = hdr->leaf;
-    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t j0 = blockIdx.x * kRefitBlock;
+    sh_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t j = j0 + threadIdx.x;
     if (j >= m) return;
+    const uint32_t j1 = min(j0 + kRefitBlock, m) - 1;  // last leaf of this block
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     const uint32_t first = j * leaf, last = min(first + leaf, n);
     for (uint32_t k = first; k < last; k++) {
@@ -417,26 +431,35 @@ __global__ void __launch_bounds__(256) k_leaves_refit(
     }
     if (m < 2) return;
     uint32_t pp = leaf_parent[j];
-    uint32_t node = pp >> 1;
-    if (node + 1 >= m) return;  // never taken for a well-formed tree
-    store_box(nodes, node, pp & 1u, lo, hi);
-    fence_acq_rel_gpu();
-    uint32_t old = atomicAdd(visit + node, 1u);
-    while (old == 1u) {  // second arrival: both children are final
-        fence_acq_rel_gpu();
-        const float* f = reinterpret_cast<const float*>(nodes + 4 * (size_t)node);
+    bool local = true;  // ancestors of a node that spans blocks span blocks too
+    while (true) {
+        const uint32_t node = pp >> 1, slot = pp & 1u;
+        if (node + 1 >= m) return;  // never taken for a well-formed tree
+        store_box(nodes, node, slot, lo, hi);  // the traversal reads it after the kernel
+        const uint2 rg = node_range[node];
         float a[12];
+        if (local && rg.x >= j0 && rg.y <= j1 && node >= j0 && node <= j1) {
+            float* sb = sh_box[node - j0] + 6 * slot;
+            sb[0] = lo[0]; sb[1] = lo[1]; sb[2] = lo[2]; sb[3] = hi[0]; sb[4] = hi[1]; sb[5] = hi[2];
+            __threadfence_block();
+            if (atomicAdd(&sh_cnt[node - j0], 1u) == 0u) return;  // first child: done
+            __threadfence_block();
 #pragma unroll
-        for (int k = 0; k < 12; k++) a[k] = __ldcg(f + k);
+            for (int k = 0; k < 12; k++) a[k] = sh_box[node - j0][k];
+        } else {
+            local = false;
+            fence_acq_rel_gpu();
+            if (atomicAdd(visit + node, 1u) == 0u) return;  // first child: done
+            fence_acq_rel_gpu();
+            const float* f = reinterpret_cast<const float*>(nodes + 4 * (size_t)node);
+#pragma unroll
+            for (int k = 0; k < 12; k++) a[k] = __ldcg(f + k);
+        }
+        // second child: both boxes are final; this node's box goes to its parent
         lo[0] = fminf(a[0], a[6]); lo[1] = fminf(a[1], a[7]); lo[2] = fminf(a[2], a[8]);
         hi[0] = fmaxf(a[3], a[9]); hi[1] = fmaxf(a[4], a[10]); hi[2] = fmaxf(a[5], a[11]);
-        if (node == 0) break;
+        if (node == 0) return;
         pp = node_parent[node];
-        node = pp >> 1;
-        if (node + 1 >= m) break;  // never taken for a well-formed tree
-        store_box(nodes, node, pp & 1u, lo, hi);
-        fence_acq_rel_gpu();
-        old = atomicAdd(visit + node, 1u);
     }
 }
 
@@ -514,13 +537,14 @@ int wrs_build_lbvh(const wrs_splats* in, const float* radius_scale, float global
         t = vi; vi = vo; vo = t;
     }
     // four passes: the sorted keys / values are back in keys0 / vals0
-    k_karras<<<gm, 256, 0, s>>>(ki, hdr, nodes, S.leaf_parent, S.node_parent);
+    k_karras<<<gm, 256, 0, s>>>(ki, hdr, nodes, S.leaf_parent, S.node_parent, S.node_range);
     WRS_LAUNCH_CHECK("wrs_build_lbvh karras");
     cudaError_t e = cudaMemsetAsync(S.visit, 0, sizeof(uint32_t) * m_cap, s);
     if (e != cudaSuccess) return wrs::cuda_fail(e, "wrs_build_lbvh memset");
-    k_leaves_refit<<<gm, 256, 0, s>>>(vi, pos4, reinterpret_cast<const float4*>(in->rgba), in->id,
-                                      radius_scale, global_scale, hdr, nodes, S.leaf_parent,
-                                      S.node_parent, S.visit,
+    const uint32_t grefit = (m_cap + kRefitBlock - 1) / kRefitBlock;
+    k_leaves_refit<<<grefit, kRefitBlock, 0, s>>>(vi, pos4, reinterpret_cast<const float4*>(in->rgba),
+                                      in->id, radius_scale, global_scale, hdr, nodes, S.leaf_parent,
+                                      S.node_parent, S.node_range, S.visit,
                                       reinterpret_cast<float4*>(sorted->pos_r),
                                       reinterpret_cast<float4*>(sorted->rgba), sorted->id,
                                       sorted->src);
