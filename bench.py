@@ -262,31 +262,21 @@ def main():
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device (there is no CPU path)")
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
     import paper_2006_14726_b300 as wrs
     from paper_2006_14726_b300 import autotune
+    from paper_2006_14726_b300.replicas import Replicas
     import synth
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    reps = Replicas.from_env("nccl")
+    barrier = reps.barrier
+    max_over_ranks = reps.max_over_ranks
 
     W = synth.LARGE
     dev = torch.device("cuda")
     # ---------------- inputs (untimed): volume, poses, server images from the GPU ray caster ---
     vol = torch.from_numpy(W.volume()).to(dev)
     tf = torch.from_numpy(synth.tf_ramp()).to(dev)
-    poses = W.client_poses(seed_offset=97 * rank)
+    poses = W.client_poses(seed_offset=reps.pose_seed_offset())
     n_groups = len(poses) // FRAMES_PER_IMAGE
     groups = []
     for g in range(n_groups):
@@ -374,7 +364,7 @@ def main():
     bv_ms = [ev[1].elapsed_time(ev[2]) for ev in events]
     tr_ms = [ev[2 + f].elapsed_time(ev[3 + f]) for ev in events for f in range(FRAMES_PER_IMAGE)]
     total_ms = max_over_ranks(sum(step_ms))
-    value = world * args.steps * rays_per_step / (total_ms * 1e-3) / 1e6
+    value = reps.whole_job_rate(args.steps * rays_per_step, total_ms * 1e-3) / 1e6
     trace_ms = statistics.mean(tr_ms)
 
     peaks, peak_src = measured_peaks()
@@ -412,8 +402,7 @@ def main():
                max_over_ranks)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    reps.close()
 
 
 def _time_ms(torch, fn, reps, warm=3):
