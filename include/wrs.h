@@ -104,7 +104,8 @@ typedef struct {
     const float* opacity; /* device [n] per-splat opacity in COMPACTED order, or NULL (= 1) */
     int32_t k_chunk;      /* hits gathered per traversal pass: 1, 2, 4, 8 or 16 */
     int32_t block;        /* threads per block: 64, 128 or 256 (per-pixel schedule) */
-    int32_t schedule;     /* WRS_SCHEDULE_PER_PIXEL or WRS_SCHEDULE_PERSISTENT (wrs_trace only) */
+    int32_t schedule;     /* WRS_SCHEDULE_PER_PIXEL or WRS_SCHEDULE_PERSISTENT (wrs_trace and
+                             wrs_trace_backward; the batched launch is always persistent) */
 } wrs_trace_params;
 
 /* One client session of wrs_trace_batched (device array of these). */

@@ -567,13 +567,86 @@ __global__ void __launch_bounds__(128) k_trace_batched(const wrs_session* __rest
 // again (same bound, same K hits), its transmittances recomputed forward from the recorded
 // start, and the hits are then visited back to front with the suffix composite S and the suffix
 // transmittance P, so no division by (1 - alpha) is needed.
+// Pass A for one gathered chunk: advance the transmittance over its used hits exactly as the
+// forward compositing does; *u = hits used in this chunk.  Returns true when the ray is finished.
+template <int K>
+__device__ __forceinline__ bool chunk_forward_T(const Scene& sc, const Comp& cp, const Ray& ray,
+                                                const uint32_t (&ki)[K], int count, float& T,
+                                                int& used, int& u) {
+    u = 0;
+#pragma unroll
+    for (int s = 0; s < K; s++) {
+        if (s >= count) break;
+        if ((cp.max_hits > 0 && used == cp.max_hits) || T <= cp.t_stop) return true;
+        const HitTerms h = hit_terms(sc, cp, ray, ki[s]);
+        T = T * (1.0f - h.a);
+        used++;
+        u++;
+    }
+    if (count < K) return true;
+    return (cp.max_hits > 0 && used == cp.max_hits) || T <= cp.t_stop;
+}
+
+struct GradOut {
+    const float* scale;
+    float gscale;
+    float* g_rgba;
+    float* g_op;
+    float* g_sc;
+};
+
+// Pass B for one re-gathered chunk: transmittances forward from the chunk's recorded start T0,
+// then the adjoint of its u used hits back to front with the suffix composite S and suffix
+// transmittance P of the later chunks (spec S7); gradients go to the compacted splat order.
+template <int K>
+__device__ __forceinline__ void chunk_adjoint(const Scene& sc, const Comp& cp, const Ray& ray,
+                                              const uint32_t (&ki)[K], int u, float T0,
+                                              const float4 g, float3& S, float& P,
+                                              const GradOut& go) {
+    float Tk[K];
+    float t = T0;
+#pragma unroll
+    for (int s = 0; s < K; s++) {
+        Tk[s] = t;
+        if (s < u) t = t * (1.0f - hit_terms(sc, cp, ray, ki[s]).a);
+    }
+#pragma unroll
+    for (int s = K - 1; s >= 0; s--) {
+        if (s >= u) continue;
+        const uint32_t k = ki[s];
+        const HitTerms h = hit_terms(sc, cp, ray, k);
+        const float Ti = Tk[s];
+        const float gC = g.x * h.c.x + g.y * h.c.y + g.z * h.c.z;
+        const float gS = g.x * S.x + g.y * S.y + g.z * S.z;
+        const float dLda = Ti * (g.w * P - gS);
+        const float pass = (h.x >= 0.0f && h.x <= 1.0f) ? 1.0f : 0.0f;
+        const uint32_t src = __ldg(sc.src + k);
+        const float tow = Ti * h.op * h.w;
+        atomicAdd(go.g_rgba + 4 * (size_t)src + 0, tow * g.x);
+        atomicAdd(go.g_rgba + 4 * (size_t)src + 1, tow * g.y);
+        atomicAdd(go.g_rgba + 4 * (size_t)src + 2, tow * g.z);
+        atomicAdd(go.g_rgba + 4 * (size_t)src + 3, dLda * pass * h.op * h.w);
+        if (go.g_op) atomicAdd(go.g_op + src, Ti * h.w * gC + dLda * pass * h.c.w * h.w);
+        if (go.g_sc && cp.beta > 0.0f) {
+            const float s_val = go.scale ? __ldg(go.scale + src) : go.gscale;
+            const float dw = wrs::soft_dw(h.rho, cp.beta);
+            if (s_val > 0.0f && dw != 0.0f) {
+                const float dLdw = Ti * h.op * gC + dLda * pass * h.op * h.c.w;
+                atomicAdd(go.g_sc + src, dLdw * dw * (-h.rho / s_val));
+            }
+        }
+        const float ow = h.op * h.w;
+        S.x = fmaf(1.0f - h.a, S.x, ow * h.c.x);
+        S.y = fmaf(1.0f - h.a, S.y, ow * h.c.y);
+        S.z = fmaf(1.0f - h.a, S.z, ow * h.c.z);
+        P = P * (1.0f - h.a);
+    }
+}
+
 template <int K>
 __global__ void __launch_bounds__(128) k_trace_bwd(Scene sc, Comp cp, wrs_camera cam,
-                                                   const float* __restrict__ scale, float gscale,
-                                                   const float4* __restrict__ dimg,
-                                                   float* __restrict__ g_rgba,
-                                                   float* __restrict__ g_op,
-                                                   float* __restrict__ g_sc, int32_t* status) {
+                                                   const float4* __restrict__ dimg, GradOut go,
+                                                   int32_t* status) {
     int px, py;
     tile_pixel(threadIdx.x, px, py);
     const int tile_h = (blockDim.x >> 6) * 4;
@@ -604,21 +677,11 @@ __global__ void __launch_bounds__(128) k_trace_bwd(Scene sc, Comp cp, wrs_camera
         b_key[chunks] = has_last ? last_key : -kInf;
         b_id[chunks] = last_id;
         b_T[chunks] = T;
-        int u = 0;
-        bool done = false;
-#pragma unroll
-        for (int s = 0; s < K; s++) {
-            if (s >= count) break;
-            if ((cp.max_hits > 0 && used == cp.max_hits) || T <= cp.t_stop) { done = true; break; }
-            const HitTerms h = hit_terms(sc, cp, rc.ray, ki[s]);
-            T = T * (1.0f - h.a);
-            used++;
-            u++;
-        }
+        int u;
+        const bool done = chunk_forward_T<K>(sc, cp, rc.ray, ki, count, T, used, u);
         b_used[chunks] = (uint8_t)u;
         chunks++;
-        if (done || count < K) break;
-        if ((cp.max_hits > 0 && used == cp.max_hits) || T <= cp.t_stop) break;
+        if (done) break;
         has_last = true;
         last_key = kk[K - 1];
         last_id = kid[K - 1];
@@ -632,44 +695,125 @@ __global__ void __launch_bounds__(128) k_trace_bwd(Scene sc, Comp cp, wrs_camera
         const bool hl = b_key[c] != -kInf;
         gather<K, false>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, hl, b_key[c], b_id[c], kk, ki,
                          kid, cnt);
-        float Tk[K];
-        float t = b_T[c];
-#pragma unroll
-        for (int s = 0; s < K; s++) {
-            Tk[s] = t;
-            if (s < u) t = t * (1.0f - hit_terms(sc, cp, rc.ray, ki[s]).a);
-        }
-#pragma unroll
-        for (int s = K - 1; s >= 0; s--) {
-            if (s >= u) continue;
-            const uint32_t k = ki[s];
-            const HitTerms h = hit_terms(sc, cp, rc.ray, k);
-            const float Ti = Tk[s];
-            const float gC = g.x * h.c.x + g.y * h.c.y + g.z * h.c.z;
-            const float gS = g.x * S.x + g.y * S.y + g.z * S.z;
-            const float dLda = Ti * (g.w * P - gS);
-            const float pass = (h.x >= 0.0f && h.x <= 1.0f) ? 1.0f : 0.0f;
-            const uint32_t src = __ldg(sc.src + k);
-            const float tow = Ti * h.op * h.w;
-            atomicAdd(g_rgba + 4 * (size_t)src + 0, tow * g.x);
-            atomicAdd(g_rgba + 4 * (size_t)src + 1, tow * g.y);
-            atomicAdd(g_rgba + 4 * (size_t)src + 2, tow * g.z);
-            atomicAdd(g_rgba + 4 * (size_t)src + 3, dLda * pass * h.op * h.w);
-            if (g_op) atomicAdd(g_op + src, Ti * h.w * gC + dLda * pass * h.c.w * h.w);
-            if (g_sc && cp.beta > 0.0f) {
-                const float s_val = scale ? __ldg(scale + src) : gscale;
-                const float dw = wrs::soft_dw(h.rho, cp.beta);
-                if (s_val > 0.0f && dw != 0.0f) {
-                    const float dLdw = Ti * h.op * gC + dLda * pass * h.op * h.c.w;
-                    atomicAdd(g_sc + src, dLdw * dw * (-h.rho / s_val));
+        chunk_adjoint<K>(sc, cp, rc.ray, ki, u, b_T[c], g, S, P, go);
+    }
+}
+
+// Persistent backward with lane refill: the per-pixel backward's two phases run as a per-lane
+// state machine over the same traversal steps as k_trace_pr.  Phase A replays the forward passes
+// and records each chunk's bound and starting transmittance; phase B re-gathers the chunks back
+// to front and applies chunk_adjoint.
+template <int K>
+__global__ void __launch_bounds__(128) k_trace_bwd_pr(Scene sc, Comp cp, wrs_camera cam,
+                                                      const float4* __restrict__ dimg, GradOut go,
+                                                      int32_t* status) {
+    __shared__ uint32_t s_next;
+    if (threadIdx.x == 0) s_next = 0;
+    __syncthreads();
+    const uint32_t W = (uint32_t)cam.width, H = (uint32_t)cam.height;
+    const uint32_t tiles_x = (W + 7) / 8, n_tiles = tiles_x * ((H + 3) / 4);
+    const uint32_t G = gridDim.x;
+    const uint32_t my_rays = blockIdx.x < n_tiles ? ((n_tiles - 1 - blockIdx.x) / G + 1) * 32 : 0;
+    const LbvhHeader hd = *sc.hdr;
+    const uint32_t n = hd.n, leaf = hd.leaf;
+    const uint32_t m = n == 0 ? 0 : (n + leaf - 1) / leaf;
+    const int lane = threadIdx.x & 31;
+    Lane<K> L;
+    int stack[wrs::kStack];
+    float b_key[wrs::kBwdChunks];
+    uint32_t b_id[wrs::kBwdChunks];
+    float b_T[wrs::kBwdChunks];
+    uint8_t b_used[wrs::kBwdChunks];
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+    float3 S = make_float3(0.f, 0.f, 0.f);
+    float P = 1.0f;
+    int phase = 0, chunks = 0, cur = 0;
+    bool active = false;
+    bool more = my_rays > 0 && n > 0;
+    while (true) {
+        const uint32_t idle = __ballot_sync(0xffffffffu, !active);
+        if (more && __popc(idle) >= kRefill) {
+            const uint32_t c = __popc(idle);
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(&s_next, c);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base + c >= my_rays) more = false;
+            if (!active) {
+                const uint32_t r = base + __popc(idle & ((1u << lane) - 1u));
+                if (r < my_rays) {
+                    const uint32_t tile = blockIdx.x + (r >> 5) * G, pos = r & 31;
+                    const uint32_t x = (tile % tiles_x) * 8 + (pos & 7);
+                    const uint32_t y = (tile / tiles_x) * 4 + (pos >> 3);
+                    if (x < W && y < H) {
+                        g = dimg[(size_t)y * W + x];
+                        if (g.x != 0.f || g.y != 0.f || g.z != 0.f || g.w != 0.f) {
+                            L.ray = wrs::primary_ray(cam, (int)x, (int)y);
+                            L.br = wrs::make_box_ray(L.ray, wrs::traversal_eps(L.ray, hd.maxabs));
+                            L.T = 1.0f;
+                            L.used = 0;
+                            L.has_last = false;
+                            L.last_key = 0.0f;
+                            L.last_id = 0;
+                            phase = 0;
+                            chunks = 0;
+                            b_key[0] = -kInf;
+                            b_id[0] = 0;
+                            b_T[0] = 1.0f;
+                            begin_pass(L, hd.root, m);
+                            active = true;
+                        }
+                    }
                 }
             }
-            const float ow = h.op * h.w;
-            S.x = fmaf(1.0f - h.a, S.x, ow * h.c.x);
-            S.y = fmaf(1.0f - h.a, S.y, ow * h.c.y);
-            S.z = fmaf(1.0f - h.a, S.z, ow * h.c.z);
-            P = P * (1.0f - h.a);
         }
+        if (!__any_sync(0xffffffffu, active)) {
+            if (!more) break;
+            continue;
+        }
+        if (!active) continue;
+        const int rc = lane_step<K>(sc, L, stack, n, leaf, m);
+        if (rc == 0) continue;
+        if (rc < 0) {
+            wrs::set_status(status, rc == -1 ? WRS_STATUS_STACK_OVERFLOW : WRS_STATUS_MALFORMED_TREE);
+            active = false;
+            continue;
+        }
+        if (phase == 0) {  // a forward replay pass finished
+            int u;
+            const bool done = chunk_forward_T<K>(sc, cp, L.ray, L.ki, L.count, L.T, L.used, u);
+            b_used[chunks] = (uint8_t)u;
+            chunks++;
+            if (!done) {
+                if (chunks == wrs::kBwdChunks) {
+                    wrs::set_status(status, WRS_STATUS_CHUNK_OVERFLOW);
+                    active = false;
+                    continue;
+                }
+                L.has_last = true;
+                L.last_key = L.kk[K - 1];
+                L.last_id = L.kid[K - 1];
+                b_key[chunks] = L.last_key;
+                b_id[chunks] = L.last_id;
+                b_T[chunks] = L.T;
+                begin_pass(L, hd.root, m);
+                continue;
+            }
+            phase = 1;
+            S = make_float3(0.f, 0.f, 0.f);
+            P = 1.0f;
+            cur = chunks;
+        } else {  // chunk `cur` re-gathered: its adjoint
+            chunk_adjoint<K>(sc, cp, L.ray, L.ki, b_used[cur], b_T[cur], g, S, P, go);
+        }
+        do { cur--; } while (cur >= 0 && b_used[cur] == 0);  // next chunk with used hits
+        if (cur < 0) {
+            active = false;
+            continue;
+        }
+        L.has_last = b_key[cur] != -kInf;
+        L.last_key = b_key[cur];
+        L.last_id = b_id[cur];
+        begin_pass(L, hd.root, m);
     }
 }
 
@@ -768,9 +912,19 @@ template <int K> struct LaunchBatched {
 };
 template <int K> struct LaunchBwd {
     static void run(dim3 g, int b, cudaStream_t s, Scene sc, Comp cp, wrs_camera cam,
-                    const float* scale, float gs, const float4* d, float* gr, float* go, float* gsc,
-                    int32_t* st) {
-        k_trace_bwd<K><<<g, b, 0, s>>>(sc, cp, cam, scale, gs, d, gr, go, gsc, st);
+                    const float4* d, GradOut go, int32_t* st) {
+        k_trace_bwd<K><<<g, b, 0, s>>>(sc, cp, cam, d, go, st);
+    }
+};
+template <int K> struct LaunchBwdPr {
+    static void run(int g, int b, cudaStream_t s, Scene sc, Comp cp, wrs_camera cam,
+                    const float4* d, GradOut go, int32_t* st) {
+        k_trace_bwd_pr<K><<<g, b, 0, s>>>(sc, cp, cam, d, go, st);
+    }
+    static int blocks_per_sm(int b) {
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trace_bwd_pr<K>, b, 0);
+        return nb;
     }
 };
 
@@ -899,11 +1053,34 @@ int wrs_trace_backward(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_
     if (e == cudaSuccess && g_opacity) e = cudaMemsetAsync(g_opacity, 0, sizeof(float) * cap, s);
     if (e == cudaSuccess && g_scale) e = cudaMemsetAsync(g_scale, 0, sizeof(float) * cap, s);
     if (e != cudaSuccess) return wrs::cuda_fail(e, fn);
-    int block = params->block > 128 ? 128 : params->block;  // local chunk table: keep occupancy
-    dispatch_k<LaunchBwd>(effective_k(params), grid_for(cam, block), block, s,
-                          make_scene(bvh, sorted, params->opacity), comp_of(params), *cam,
-                          radius_scale, global_scale, reinterpret_cast<const float4*>(dL_drgba),
-                          g_rgba, g_opacity, g_scale, status);
+    const GradOut go = {radius_scale, global_scale, g_rgba, g_opacity, g_scale};
+    const int K = effective_k(params);
+    const float4* d4 = reinterpret_cast<const float4*>(dL_drgba);
+    if (params->schedule == WRS_SCHEDULE_PERSISTENT) {
+        static int cached_grid[5] = {0};  // one resident wave, cached per K
+        const int ki = K == 1 ? 0 : K == 2 ? 1 : K == 4 ? 2 : K == 8 ? 3 : 4;
+        if (cached_grid[ki] == 0) {
+            int dev = 0, sms = 0, per_sm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            switch (K) {
+                case 1: per_sm = LaunchBwdPr<1>::blocks_per_sm(128); break;
+                case 2: per_sm = LaunchBwdPr<2>::blocks_per_sm(128); break;
+                case 4: per_sm = LaunchBwdPr<4>::blocks_per_sm(128); break;
+                case 8: per_sm = LaunchBwdPr<8>::blocks_per_sm(128); break;
+                default: per_sm = LaunchBwdPr<16>::blocks_per_sm(128); break;
+            }
+            cached_grid[ki] = sms * (per_sm < 1 ? 1 : per_sm);
+        }
+        dispatch_k<LaunchBwdPr>(K, cached_grid[ki], 128, s,
+                                make_scene(bvh, sorted, params->opacity), comp_of(params), *cam,
+                                d4, go, status);
+    } else {
+        const int block = params->block > 128 ? 128 : params->block;  // keep occupancy
+        dispatch_k<LaunchBwd>(K, grid_for(cam, block), block, s,
+                              make_scene(bvh, sorted, params->opacity), comp_of(params), *cam, d4,
+                              go, status);
+    }
     WRS_LAUNCH_CHECK(fn);
     return WRS_OK;
 }

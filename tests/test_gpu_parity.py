@@ -360,13 +360,14 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
-@pytest.mark.parametrize("beta,k", [(0.25, 8), (0.25, 1), (0.0, 4)])
-def test_backward_matches_oracle_adjoint(wrs, beta, k):
+@pytest.mark.parametrize("beta,k,sched", [(0.25, 8, 0), (0.25, 1, 0), (0.0, 4, 0), (0.25, 1, 1),
+                                          (0.25, 4, 1), (0.0, 2, 1)])
+def test_backward_matches_oracle_adjoint(wrs, beta, k, sched):
     rgba, depth, srv, cli, ref_sp, op, sc, g = _bwd_instance(wrs)
     n = ref_sp.n
     sp = _gpu_splats(wrs, rgba, depth, srv)
     bvh, srt = wrs.build_lbvh(sp, 1, radius_scale=_cuda(sc))
-    params = wrs.TraceParams(edge_softness=beta, k_chunk=k)
+    params = wrs.TraceParams(edge_softness=beta, k_chunk=k, schedule=sched)
     st = wrs.new_status()
     gr, go, gs = wrs.trace_backward(bvh, srt, cli, _cuda(g.astype(np.float32).reshape(cli.height, cli.width, 4)),
                                     params, opacity=_cuda(op), radius_scale=_cuda(sc), status=st)

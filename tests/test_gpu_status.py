@@ -84,10 +84,11 @@ def test_backward_chunk_table_overflow_is_reported(wrs):
     wrs.check_status(st)
     assert float(img[..., 3].max()) > 0.05  # many layers composited
     g = torch.ones(H, W, 4, device="cuda")
-    wrs.trace_backward(bvh, srt, srv, g, wrs.TraceParams(k_chunk=1), status=st)
-    with pytest.raises(wrs.WrsError) as e:
+    for sched in (0, 1):
+        wrs.trace_backward(bvh, srt, srv, g, wrs.TraceParams(k_chunk=1, schedule=sched), status=st)
+        with pytest.raises(wrs.WrsError) as e:
+            wrs.check_status(st)
+        assert "chunk" in str(e.value)
+        # with k_chunk = 16 the same rays fit (80 hits = 5 chunks)
+        wrs.trace_backward(bvh, srt, srv, g, wrs.TraceParams(k_chunk=16, schedule=sched), status=st)
         wrs.check_status(st)
-    assert "chunk" in str(e.value)
-    # with k_chunk = 16 the same rays fit (80 hits = 5 chunks)
-    wrs.trace_backward(bvh, srt, srv, g, wrs.TraceParams(k_chunk=16), status=st)
-    wrs.check_status(st)
