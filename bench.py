@@ -125,11 +125,13 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------------
 # roofline helpers
 # ------------------------------------------------------------------------------------------------
-def trace_bytes_per_ray(c, rays):
-    """Algorithmic bytes per ray of the trace kernel: 64 per internal node visited (its two child
-    boxes and references), 16 per sphere tested (centre + radius), 4 per hit gathered (its id, for
-    the tie-break), 16 per hit composited (its RGBA), 16 for the output pixel."""
-    return (64 * c["nodes"] + 16 * c["spheres"] + 4 * c["gathered"] + 16 * c["composited"]) / rays + 16
+def trace_bytes_per_ray(c, rays, width=2):
+    """Algorithmic bytes per ray of the trace kernel: per node visited 64 (binary: two child boxes
+    and references) or 112 (4-wide: four boxes and references), 16 per sphere tested (centre +
+    radius), 4 per hit gathered (its id, for the tie-break), 16 per hit composited (its RGBA), 16
+    for the output pixel."""
+    node = 112 if width == 4 else 64
+    return (node * c["nodes"] + 16 * c["spheres"] + 4 * c["gathered"] + 16 * c["composited"]) / rays + 16
 
 
 def trace_flops_per_ray(c, rays):
@@ -293,7 +295,9 @@ def main():
     sp = wrs.unproject(groups[0][0], groups[0][1], groups[0][2])
     tuned = autotune.tune_trace(sp, groups[0][3], use_cache=False)
     leaf, kc, block, sched = tuned["leaf"], tuned["k_chunk"], tuned["block"], tuned["schedule"]
-    params = wrs.TraceParams(max_hits=0, t_stop=1e-5, k_chunk=kc, block=block, schedule=sched)
+    width = tuned["width"]
+    params = wrs.TraceParams(max_hits=0, t_stop=1e-5, k_chunk=kc, block=block, schedule=sched,
+                             width=width)
 
     # ---------------- buffers, allocated once -------------------------------------------------
     splats = wrs.SplatBuffers(npix_s)
@@ -368,14 +372,15 @@ def main():
     trace_ms = statistics.mean(tr_ms)
 
     peaks, peak_src = measured_peaks()
-    bpr = trace_bytes_per_ray(cnt_tot, rays_counted)
+    bpr = trace_bytes_per_ray(cnt_tot, rays_counted, width)
     fpr = trace_flops_per_ray(cnt_tot, rays_counted)
     bytes_launch = bpr * npix_c
     achieved = bytes_launch / (trace_ms * 1e-3) / 1e9
     traffic = profiled_traffic()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "kernel": "k_trace", "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                "kernel": "k_trace_pr" if sched == 1 else "k_trace",
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                 "bytes_per_ray": bpr, "flops_per_ray": fpr,
                 "fp32_tflops_achieved": fpr * npix_c / (trace_ms * 1e-3) / 1e12,
                 "counts_per_ray": {k: v / rays_counted for k, v in cnt_tot.items()}}
@@ -386,6 +391,7 @@ def main():
             "config": workload_config(W, statistics.mean(n_splats), {
                 "leaf_size": leaf, "k_chunk": kc, "block": block, "autotuned": True,
                 "schedule": ["one thread per pixel", "persistent, lane refill"][sched],
+                "bvh_width": width,
                 "l2": "flushed before every step (256 MiB write outside the timed events)",
                 "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
             "lbvh_ms": statistics.mean(bv_ms), "unproject_ms": statistics.mean(up_ms),
@@ -470,7 +476,7 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
         del sp
     batch = wrs.Batch(sess)
     bt = autotune.tune_batched(batch, params)
-    bparams = wrs.TraceParams(0, 1e-5, 0.0, bt["k_chunk"], bt["block"])
+    bparams = wrs.TraceParams(0, 1e-5, 0.0, bt["k_chunk"], bt["block"], 1, bt["width"])
     outs = [torch.empty(c.height, c.width, 4, device=dev) for _, _, c in sess]
     seq_cams = [wrs.make_camera(c) for _, _, c in sess]
 
@@ -496,7 +502,8 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
                        "one_launch_graph_mrays_s": world * rays / (ms_graph * 1e-3) / 1e6,
                        "sequential_mrays_s": world * rays / (ms_seq * 1e-3) / 1e6,
                        "one_launch_ms": ms_graph, "sequential_ms": ms_seq,
-                       "k_chunk": bt["k_chunk"], "block": bt["block"], "leaf_size": leaf}
+                       "k_chunk": bt["k_chunk"], "block": bt["block"], "bvh_width": bt["width"],
+                       "leaf_size": leaf}
     del sess, batch, outs, g
 
     # ---------------- forward and forward+backward (differentiable renderer) -------------------
@@ -511,7 +518,8 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
     col = sp.rgba[:n].clone().requires_grad_(True)
     opa = torch.ones(n, device=dev, requires_grad=True)
     scl = torch.ones(n, device=dev, requires_grad=True)
-    dparams = wrs.TraceParams(0, 1e-5, 0.25, params.k_chunk, params.block, params.schedule)
+    dparams = wrs.TraceParams(0, 1e-5, 0.25, params.k_chunk, params.block, params.schedule,
+                              params.width)
 
     def fwd():
         with torch.no_grad():

@@ -83,7 +83,8 @@ typedef struct {
 } wrs_splats;
 
 /* An LBVH: one device buffer of wrs_lbvh_bytes(capacity, leaf_size) bytes holding a 64-byte
- * header and the internal nodes (64 B each: both children's boxes and references). */
+ * header, the binary internal nodes (64 B each: both children's boxes and references) and, for
+ * every binary internal node, a 4-wide node over its grandchildren (128 B). */
 typedef struct {
     void* nodes;
     uint32_t capacity;  /* maximum splats */
@@ -106,6 +107,7 @@ typedef struct {
     int32_t block;        /* threads per block: 64, 128 or 256 (per-pixel schedule) */
     int32_t schedule;     /* WRS_SCHEDULE_PER_PIXEL or WRS_SCHEDULE_PERSISTENT (wrs_trace and
                              wrs_trace_backward; the batched launch is always persistent) */
+    int32_t width;        /* traversal: 2 (or 0) = binary nodes, 4 = the LBVH's 4-wide nodes */
 } wrs_trace_params;
 
 /* One client session of wrs_trace_batched (device array of these). */

@@ -75,7 +75,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("max_hits", ctypes.c_int32), ("t_stop", ctypes.c_float),
                 ("edge_softness", ctypes.c_float), ("opacity", ctypes.c_void_p),
                 ("k_chunk", ctypes.c_int32), ("block", ctypes.c_int32),
-                ("schedule", ctypes.c_int32)]
+                ("schedule", ctypes.c_int32), ("width", ctypes.c_int32)]
 
 
 class Session(ctypes.Structure):
@@ -237,6 +237,17 @@ class LBVH:
         refs = raw[:, 12:14].contiguous().view(torch.int32)
         return boxes, refs
 
+    def wide_table(self) -> Tuple[torch.Tensor, torch.Tensor]:
+        """(boxes [M-1, 4, 6] float32 as lo xyz, hi xyz; refs [M-1, 4] int32) of the 4-wide nodes
+        (unused entries have reference -1)."""
+        m = self.header()["m"]
+        k = max(m - 1, 0)
+        start = 64 + 64 * int(self.nodes[48:52].view(torch.int32).item())
+        raw = self.nodes[start:start + 128 * k].view(torch.float32).view(k, 8, 4)
+        boxes = raw[:, :6, :].permute(0, 2, 1).contiguous()  # [k, entry, coord]
+        refs = raw[:, 6, :].contiguous().view(torch.int32)
+        return boxes, refs
+
 
 def _scratch(nbytes: int, device=None) -> torch.Tensor:
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device or torch.device("cuda"))
@@ -321,10 +332,12 @@ class TraceParams:
     k_chunk: int = 8
     block: int = 128
     schedule: int = 0            # 0 = one thread per pixel, 1 = persistent with lane refill
+    width: int = 2               # 2 = binary traversal, 4 = 4-wide nodes
 
     def c(self, opacity: Optional[torch.Tensor] = None) -> _Params:
         return _Params(int(self.max_hits), float(self.t_stop), float(self.edge_softness),
-                       _ptr(opacity), int(self.k_chunk), int(self.block), int(self.schedule))
+                       _ptr(opacity), int(self.k_chunk), int(self.block), int(self.schedule),
+                       int(self.width))
 
 
 def trace(bvh: LBVH, sorted: SplatBuffers, cam, params: TraceParams = TraceParams(),

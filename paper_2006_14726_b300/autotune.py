@@ -18,9 +18,10 @@ import torch
 from . import (SCHEDULE_PER_PIXEL, SCHEDULE_PERSISTENT, Batch, SplatBuffers, TraceParams,
                build_lbvh, trace, trace_batched)
 
-LEAVES = (1, 2, 4, 8)
-KS = (1, 2, 4, 8, 16)
+LEAVES = (1, 2, 4)
+KS = (1, 2, 4, 8)
 BLOCKS = (64, 128, 256)
+WIDTHS = (2, 4)
 
 
 def _cache_path() -> str:
@@ -68,8 +69,10 @@ def signature(kind: str, n_splats: int, width: int, height: int, base: TracePara
 
 def tune_trace(splats: SplatBuffers, cams: Sequence, base: TraceParams = TraceParams(),
                leaves: Iterable[int] = LEAVES, ks: Iterable[int] = KS,
-               blocks: Iterable[int] = BLOCKS, reps: int = 3, use_cache: bool = True) -> Dict:
-    """Pick (leaf_size, k_chunk, block) minimising the mean wrs_trace time over ``cams``."""
+               blocks: Iterable[int] = BLOCKS, widths: Iterable[int] = WIDTHS, reps: int = 3,
+               use_cache: bool = True) -> Dict:
+    """Pick (leaf_size, k_chunk, block, schedule, width) minimising the mean wrs_trace time over
+    ``cams``."""
     c0 = cams[0]
     key = signature("trace", splats.count(), c0.width, c0.height, base)
     if use_cache:
@@ -84,28 +87,32 @@ def tune_trace(splats: SplatBuffers, cams: Sequence, base: TraceParams = TracePa
         shapes = [(b, SCHEDULE_PER_PIXEL) for b in blocks] + [(128, SCHEDULE_PERSISTENT)]
         for k in ks:
             for block, sched in shapes:
-                p = TraceParams(base.max_hits, base.t_stop, base.edge_softness, k, block, sched)
+                for width in widths:
+                    p = TraceParams(base.max_hits, base.t_stop, base.edge_softness, k, block, sched,
+                                    width)
 
-                def run():
-                    for c, o in zip(cams, outs):
-                        trace(bvh, srt, c, p, out=o)
-                ms = _time_ms(run, reps) / len(cams)
-                table.append((leaf, k, block, sched, ms))
-                if best is None or ms < best["ms"]:
-                    best = {"leaf": leaf, "k_chunk": k, "block": block, "schedule": sched, "ms": ms}
+                    def run():
+                        for c, o in zip(cams, outs):
+                            trace(bvh, srt, c, p, out=o)
+                    ms = _time_ms(run, reps) / len(cams)
+                    table.append((leaf, k, block, sched, width, ms))
+                    if best is None or ms < best["ms"]:
+                        best = {"leaf": leaf, "k_chunk": k, "block": block, "schedule": sched,
+                                "width": width, "ms": ms}
     best["table"] = table
     _store(key, best)
     return best
 
 
 def tune_batched(batch: Batch, base: TraceParams = TraceParams(), ks: Iterable[int] = KS,
-                 reps: int = 3) -> Dict:
-    """Pick k_chunk for one persistent multi-session launch (leaf sizes are fixed by the sessions'
-    LBVHs; the launch shape is fixed: one resident wave of 128-thread blocks)."""
+                 widths: Iterable[int] = WIDTHS, reps: int = 3) -> Dict:
+    """Pick (k_chunk, width) for one persistent multi-session launch (leaf sizes are fixed by the
+    sessions' LBVHs; the launch shape is fixed: one resident wave of 128-thread blocks)."""
     best = None
     for k in ks:
-        p = TraceParams(base.max_hits, base.t_stop, base.edge_softness, k, 128)
-        ms = _time_ms(lambda: trace_batched(batch, p), reps)
-        if best is None or ms < best["ms"]:
-            best = {"k_chunk": k, "block": 128, "ms": ms}
+        for width in widths:
+            p = TraceParams(base.max_hits, base.t_stop, base.edge_softness, k, 128, 1, width)
+            ms = _time_ms(lambda: trace_batched(batch, p), reps)
+            if best is None or ms < best["ms"]:
+                best = {"k_chunk": k, "block": 128, "width": width, "ms": ms}
     return best

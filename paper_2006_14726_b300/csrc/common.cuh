@@ -15,7 +15,8 @@
 namespace wrs {
 
 constexpr uint32_t kLeafBit = 0x80000000u;
-constexpr int kStack = 64;         // traversal stack entries (tree depth <= 30 + log2(leaves) + 1)
+constexpr uint32_t kNoChild = 0xFFFFFFFFu;  // unused entry of a 4-wide node
+constexpr int kStack = 96;         // traversal stack entries (binary: <= depth; 4-wide: <= 1.5 depth)
 constexpr int kMaxLeaf = 16;
 constexpr int kBwdChunks = 64;     // backward: traversal passes per ray it can replay
 
@@ -29,20 +30,32 @@ struct LbvhHeader {
     float cmax[3];
     float maxabs;      // largest |coordinate| of any sphere bound (traversal epsilon scale)
     float rmax;        // largest effective radius
-    uint32_t pad[4];
+    uint32_t wide_start;  // 64-byte slots of binary nodes before the 4-wide nodes
+    uint32_t pad[3];
 };
 static_assert(sizeof(LbvhHeader) == 64, "header must be 64 bytes");
 
-// Internal node = 4 x float4 = 64 B:
+// Binary internal node = 4 x float4 = 64 B:
 //   floats 0..5  : child 0 box (lo.xyz, hi.xyz)
 //   floats 6..11 : child 1 box
 //   floats 12,13 : child references (int bits; kLeafBit set = leaf index)
 //   floats 14,15 : unused
+// 4-wide node i (one per binary internal node i) = 8 x float4 = 128 B, structure of arrays over
+// the grandchildren of binary node i (a leaf child counts as its own grandchild):
+//   float4 0..2: lo.x, lo.y, lo.z of the 4 entries; 3..5: hi.x, hi.y, hi.z; 6: references
+//   (int bits; internal references name binary nodes, whose 4-wide node is visited next); 7: unused.
+//   Unused entries carry the reference kNoChild (and an inverted box, which a slab test would NOT
+//   reject, so the reference is what the traversal checks).
 __host__ __device__ inline float4* lbvh_nodes(void* buf) {
     return reinterpret_cast<float4*>(reinterpret_cast<char*>(buf) + sizeof(LbvhHeader));
 }
 __host__ __device__ inline const float4* lbvh_nodes(const void* buf) {
     return reinterpret_cast<const float4*>(reinterpret_cast<const char*>(buf) + sizeof(LbvhHeader));
+}
+// binary node slots reserved for a capacity (the 4-wide nodes start after them)
+__host__ __device__ inline uint32_t lbvh_binary_slots(uint32_t capacity, uint32_t leaf) {
+    const uint32_t m = capacity == 0 ? 1 : (capacity + leaf - 1) / leaf;
+    return m > 1 ? m - 1 : 1;
 }
 
 // ---------------------------------------------------------------------------------------------

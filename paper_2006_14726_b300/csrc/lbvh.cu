@@ -131,6 +131,7 @@ __global__ void __launch_bounds__(kBoundsBlocks) k_bounds_final(
     LbvhHeader h = {};
     h.n = n;
     h.leaf = leaf;
+    h.wide_start = wrs::lbvh_binary_slots(cap, leaf);
     h.m = n == 0 ? 0 : (n + leaf - 1) / leaf;
     h.root = h.m <= 1 ? (int32_t)kLeafBit : 0;
     float mx = 0.0f;
@@ -463,14 +464,77 @@ __global__ void __launch_bounds__(kRefitBlock) k_leaves_refit(
     }
 }
 
+// ---- 4-wide nodes ---------------------------------------------------------------------------
+// 4-wide node i lists the grandchildren of binary node i (a leaf child stands for itself), in
+// structure-of-arrays order so that a traversal step loads one coordinate of all four boxes per
+// float4.  Runs after the refit, when every binary node holds its final child boxes.
+__global__ void __launch_bounds__(256) k_widen(const LbvhHeader* __restrict__ hdr,
+                                               const float4* __restrict__ nodes,
+                                               float4* __restrict__ wide) {
+    const uint32_t m = hdr->m;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < 2 || i + 1 >= m) return;
+    float lo[3][4], hi[3][4];
+    uint32_t ref[4];
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        lo[0][e] = lo[1][e] = lo[2][e] = INFINITY;
+        hi[0][e] = hi[1][e] = hi[2][e] = -INFINITY;
+        ref[e] = wrs::kNoChild;  // unused entry: the traversal skips it by its reference
+    }
+    // one binary node as 16 floats, loaded with four 16-byte loads
+    auto load = [&](uint32_t k, float (&f)[16]) {
+        const float4* p = nodes + 4 * (size_t)k;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const float4 v = __ldg(p + q);
+            f[4 * q] = v.x; f[4 * q + 1] = v.y; f[4 * q + 2] = v.z; f[4 * q + 3] = v.w;
+        }
+    };
+    float f[16];
+    load(i, f);
+    // fixed slots: child c's entries go to slots 2c and 2c + 1 (a leaf child uses slot 2c only)
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        const uint32_t r = __float_as_uint(f[12 + c]);
+        if ((r & kLeafBit) || r + 1 >= m) {  // a leaf child: its own entry
+#pragma unroll
+            for (int a = 0; a < 3; a++) { lo[a][2 * c] = f[6 * c + a]; hi[a][2 * c] = f[6 * c + 3 + a]; }
+            ref[2 * c] = r;
+        } else {                             // an internal child: its two children
+            float g[16];
+            load(r, g);
+#pragma unroll
+            for (int gc = 0; gc < 2; gc++) {
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    lo[a][2 * c + gc] = g[6 * gc + a];
+                    hi[a][2 * c + gc] = g[6 * gc + 3 + a];
+                }
+                ref[2 * c + gc] = __float_as_uint(g[12 + gc]);
+            }
+        }
+    }
+    float4* w = wide + 8 * (size_t)i;
+    w[0] = make_float4(lo[0][0], lo[0][1], lo[0][2], lo[0][3]);
+    w[1] = make_float4(lo[1][0], lo[1][1], lo[1][2], lo[1][3]);
+    w[2] = make_float4(lo[2][0], lo[2][1], lo[2][2], lo[2][3]);
+    w[3] = make_float4(hi[0][0], hi[0][1], hi[0][2], hi[0][3]);
+    w[4] = make_float4(hi[1][0], hi[1][1], hi[1][2], hi[1][3]);
+    w[5] = make_float4(hi[2][0], hi[2][1], hi[2][2], hi[2][3]);
+    w[6] = make_float4(__uint_as_float(ref[0]), __uint_as_float(ref[1]), __uint_as_float(ref[2]),
+                       __uint_as_float(ref[3]));
+    w[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 }  // namespace
 
 extern "C" {
 
 size_t wrs_lbvh_bytes(uint32_t capacity, uint32_t leaf_size) {
     if (leaf_size < 1 || leaf_size > (uint32_t)wrs::kMaxLeaf) return 0;
-    const uint32_t m = leaves_for(capacity, leaf_size);
-    return sizeof(LbvhHeader) + 64 * (size_t)(m > 1 ? m - 1 : 1);
+    const size_t slots = wrs::lbvh_binary_slots(capacity, leaf_size);
+    return sizeof(LbvhHeader) + 64 * slots + 128 * slots;  // binary nodes, then 4-wide nodes
 }
 
 size_t wrs_lbvh_scratch_bytes(uint32_t capacity, uint32_t leaf_size) {
@@ -549,6 +613,9 @@ int wrs_build_lbvh(const wrs_splats* in, const float* radius_scale, float global
                                       reinterpret_cast<float4*>(sorted->rgba), sorted->id,
                                       sorted->src);
     WRS_LAUNCH_CHECK("wrs_build_lbvh refit");
+    float4* wide = nodes + 4 * (size_t)wrs::lbvh_binary_slots(cap, leaf);
+    k_widen<<<gm, 256, 0, s>>>(hdr, nodes, wide);
+    WRS_LAUNCH_CHECK("wrs_build_lbvh widen");
     return WRS_OK;
 }
 

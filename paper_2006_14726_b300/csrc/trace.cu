@@ -25,6 +25,7 @@ using wrs::Ray;
 struct Scene {
     const LbvhHeader* hdr;
     const float4* __restrict__ nodes;
+    const float4* __restrict__ wide;  // 4-wide nodes, or nullptr to traverse the binary nodes
     const float4* __restrict__ pos_r;
     const float4* __restrict__ rgba;
     const uint32_t* __restrict__ id;
@@ -36,6 +37,7 @@ struct Comp {
     int max_hits;
     float t_stop;
     float beta;
+    int width;  // 2: binary traversal; 4: 4-wide traversal
 };
 
 struct Counts {
@@ -53,8 +55,10 @@ __device__ __forceinline__ void leaf_hits(const Scene& sc, const Ray& ray, uint3
                                           uint32_t last_id, float (&kk)[K], uint32_t (&ki)[K],
                                           uint32_t (&kid)[K], int& count, Counts& cnt) {
     const float lower = has_last ? last_key : -kInf;
-    const uint32_t first = (leafref & ~kLeafBit) * leaf;
-    const uint32_t last = min(first + leaf, n);  // empty if the reference is out of range
+    const uint32_t j = leafref & ~kLeafBit;
+    if (j >= (n + leaf - 1) / leaf) return;  // not a leaf of this tree
+    const uint32_t first = j * leaf;
+    const uint32_t last = min(first + leaf, n);
     for (uint32_t k = first; k < last; k++) {
         const float4 s = __ldg(sc.pos_r + k);
         float key, ff;
@@ -122,11 +126,70 @@ __device__ __forceinline__ int64_t visit_node(const Scene& sc, const Ray& ray,
     return kLeafBit;
 }
 
+__device__ __forceinline__ void cswap(float& ka, uint32_t& ra, float& kb, uint32_t& rb) {
+    const bool s = kb < ka;
+    const float tk = s ? kb : ka;
+    const uint32_t tr = s ? rb : ra;
+    kb = s ? ka : kb;
+    rb = s ? ra : rb;
+    ka = tk;
+    ra = tr;
+}
+
+// One visit of the 4-wide node of binary node `ref` (its grandchildren): four box tests from
+// structure-of-arrays loads; hit leaf entries are tested right away; hit internal entries are
+// sorted by entry distance (5-comparator network), the nearest is returned and the others pushed
+// far to near.  Same return convention as visit_node.
+template <int K, bool COUNT>
+__device__ __forceinline__ int64_t visit_node4(const Scene& sc, const Ray& ray,
+                                               const wrs::BoxRay& br, uint32_t ref, uint32_t n,
+                                               uint32_t leaf, uint32_t m, bool has_last,
+                                               float last_key, uint32_t last_id, float (&kk)[K],
+                                               uint32_t (&ki)[K], uint32_t (&kid)[K], int& count,
+                                               int* stack, int& sp, Counts& cnt) {
+    if (ref + 1 >= m) return -2;  // not an internal node of this tree
+    const float lower = has_last ? last_key : -kInf;
+    const float4* w = sc.wide + 8 * (size_t)ref;
+    const float4 lx = __ldg(w + 0), ly = __ldg(w + 1), lz = __ldg(w + 2);
+    const float4 hx = __ldg(w + 3), hy = __ldg(w + 4), hz = __ldg(w + 5), rf = __ldg(w + 6);
+    if (COUNT) { cnt.nodes++; cnt.boxes += 4; }
+    float tn[4], tf[4];
+    wrs::box_test(br, lx.x, ly.x, lz.x, hx.x, hy.x, hz.x, tn[0], tf[0]);
+    wrs::box_test(br, lx.y, ly.y, lz.y, hx.y, hy.y, hz.y, tn[1], tf[1]);
+    wrs::box_test(br, lx.z, ly.z, lz.z, hx.z, hy.z, hz.z, tn[2], tf[2]);
+    wrs::box_test(br, lx.w, ly.w, lz.w, hx.w, hy.w, hz.w, tn[3], tf[3]);
+    uint32_t r[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
+                     __float_as_uint(rf.w)};
+    float key[4];
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        bool h = r[e] != wrs::kNoChild && tn[e] <= tf[e] && tn[e] <= kk[K - 1] && tf[e] >= lower;
+        if (h && (r[e] & kLeafBit)) {
+            leaf_hits<K, COUNT>(sc, ray, r[e], n, leaf, has_last, last_key, last_id, kk, ki, kid,
+                                count, cnt);
+            h = false;
+        }
+        key[e] = h ? tn[e] : kInf;
+    }
+    cswap(key[0], r[0], key[1], r[1]);
+    cswap(key[2], r[2], key[3], r[3]);
+    cswap(key[0], r[0], key[2], r[2]);
+    cswap(key[1], r[1], key[3], r[3]);
+    cswap(key[1], r[1], key[2], r[2]);
+    if (!(key[0] < kInf)) return kLeafBit;
+    const int extra = (key[1] < kInf) + (key[2] < kInf) + (key[3] < kInf);
+    if (sp + extra > wrs::kStack) return -1;
+    if (key[3] < kInf) stack[sp++] = (int)r[3];
+    if (key[2] < kInf) stack[sp++] = (int)r[2];
+    if (key[1] < kInf) stack[sp++] = (int)r[1];
+    return r[0];
+}
+
 // One traversal pass: the K smallest hits (key, id) strictly after (last_key, last_id).
 // Returns the number gathered (<= K); -1 if the stack overflowed; -2 if the pass met a reference
 // outside the tree or visited more nodes than the tree has (impossible for a well-formed tree; it
 // bounds the loop regardless).
-template <int K, bool COUNT>
+template <int K, bool COUNT, bool W4>
 __device__ __forceinline__ int gather(const Scene& sc, const Ray& ray, const wrs::BoxRay& br,
                                       uint32_t n, uint32_t leaf, int32_t root, bool has_last,
                                       float last_key, uint32_t last_id, float (&kk)[K],
@@ -146,8 +209,11 @@ __device__ __forceinline__ int gather(const Scene& sc, const Ray& ray, const wrs
     uint32_t budget = m + 1;  // internal node visits allowed in one pass
     while (true) {
         if (budget-- == 0) return -2;
-        const int64_t next = visit_node<K, COUNT>(sc, ray, br, ref, n, leaf, m, has_last, last_key,
-                                                  last_id, kk, ki, kid, count, stack, sp, cnt);
+        const int64_t next =
+            W4 ? visit_node4<K, COUNT>(sc, ray, br, ref, n, leaf, m, has_last, last_key, last_id,
+                                       kk, ki, kid, count, stack, sp, cnt)
+               : visit_node<K, COUNT>(sc, ray, br, ref, n, leaf, m, has_last, last_key, last_id,
+                                      kk, ki, kid, count, stack, sp, cnt);
         if (next < 0) return (int)next;
         if (next != kLeafBit) { ref = (uint32_t)next; continue; }
         if (sp == 0) break;
@@ -227,7 +293,7 @@ __device__ __forceinline__ bool composite_chunk(const Scene& sc, const Comp& cp,
 }
 
 // Forward trace of one ray (spec S6).  overflow_bits: status bits of a traversal failure.
-template <int K, bool COUNT>
+template <int K, bool COUNT, bool W4>
 __device__ __forceinline__ float4 trace_ray(const Scene& sc, const Comp& cp, const RayCtx& rc,
                                             uint32_t& overflow_bits, Counts& cnt) {
     float T = 1.0f;
@@ -241,8 +307,8 @@ __device__ __forceinline__ float4 trace_ray(const Scene& sc, const Comp& cp, con
     float kk[K];
     uint32_t ki[K], kid[K];
     while (true) {
-        const int count = gather<K, COUNT>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, has_last,
-                                           last_key, last_id, kk, ki, kid, cnt);
+        const int count = gather<K, COUNT, W4>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, has_last,
+                                               last_key, last_id, kk, ki, kid, cnt);
         if (COUNT) cnt.passes++;
         if (count < 0) { overflow_bits = count == -1 ? WRS_STATUS_STACK_OVERFLOW : WRS_STATUS_MALFORMED_TREE; break; }
         if (composite_chunk<K, COUNT>(sc, cp, rc.ray, ki, count, T, C, used, cnt)) break;
@@ -267,9 +333,9 @@ constexpr int kRefill = 8;
 #ifndef WRS_PERSISTENT_MIN_BLOCKS
 #define WRS_PERSISTENT_MIN_BLOCKS 10
 #endif
-template <int K>
+template <int K, bool W4>
 struct PersistentMinBlocks {
-    static constexpr int value = K <= 2 ? WRS_PERSISTENT_MIN_BLOCKS : 0;
+    static constexpr int value = (K <= 2 && !W4) ? WRS_PERSISTENT_MIN_BLOCKS : 0;
 };
 
 template <int K>
@@ -303,7 +369,7 @@ __device__ __forceinline__ void begin_pass(Lane<K>& L, int32_t root, uint32_t m)
 
 // One traversal step: one internal-node visit (its leaf children tested inline), as in gather's
 // loop.  0: continue; 1: pass finished; -1: stack overflow; -2: malformed tree.
-template <int K>
+template <int K, bool W4>
 __device__ __forceinline__ int lane_step(const Scene& sc, Lane<K>& L, int* stack, uint32_t n,
                                          uint32_t leaf, uint32_t m) {
     Counts cnt;
@@ -313,9 +379,11 @@ __device__ __forceinline__ int lane_step(const Scene& sc, Lane<K>& L, int* stack
         return 1;
     }
     if (L.budget-- == 0) return -2;
-    const int64_t next = visit_node<K, false>(sc, L.ray, L.br, L.ref, n, leaf, m, L.has_last,
-                                              L.last_key, L.last_id, L.kk, L.ki, L.kid, L.count,
-                                              stack, L.sp, cnt);
+    const int64_t next =
+        W4 ? visit_node4<K, false>(sc, L.ray, L.br, L.ref, n, leaf, m, L.has_last, L.last_key,
+                                   L.last_id, L.kk, L.ki, L.kid, L.count, stack, L.sp, cnt)
+           : visit_node<K, false>(sc, L.ray, L.br, L.ref, n, leaf, m, L.has_last, L.last_key,
+                                  L.last_id, L.kk, L.ki, L.kid, L.count, stack, L.sp, cnt);
     if (next < 0) return (int)next;
     if (next != kLeafBit) { L.ref = (uint32_t)next; return 0; }
     if (L.sp == 0) return 1;
@@ -323,8 +391,8 @@ __device__ __forceinline__ int lane_step(const Scene& sc, Lane<K>& L, int* stack
     return 0;
 }
 
-template <int K>
-__global__ void __launch_bounds__(128, PersistentMinBlocks<K>::value) k_trace_pr(Scene sc, Comp cp, wrs_camera cam,
+template <int K, bool W4>
+__global__ void __launch_bounds__(128, PersistentMinBlocks<K, W4>::value) k_trace_pr(Scene sc, Comp cp, wrs_camera cam,
                                                   float4* __restrict__ out, int32_t* status) {
     __shared__ uint32_t s_next;
     if (threadIdx.x == 0) s_next = 0;
@@ -381,7 +449,7 @@ __global__ void __launch_bounds__(128, PersistentMinBlocks<K>::value) k_trace_pr
             continue;
         }
         if (active) {
-            const int rc = lane_step<K>(sc, L, stack, n, leaf, m);
+            const int rc = lane_step<K, W4>(sc, L, stack, n, leaf, m);
             if (rc != 0) {
                 bool done = true;
                 if (rc < 0) {
@@ -409,7 +477,7 @@ __device__ __forceinline__ void tile_pixel(int t, int& px, int& py) {
     py = (warp >> 1) * 4 + (lane >> 3);
 }
 
-template <int K>
+template <int K, bool W4>
 __global__ void __launch_bounds__(256) k_trace(Scene sc, Comp cp, wrs_camera cam,
                                                float4* __restrict__ out, int32_t* status) {
     int px, py;
@@ -420,12 +488,12 @@ __global__ void __launch_bounds__(256) k_trace(Scene sc, Comp cp, wrs_camera cam
     const RayCtx rc = make_ray_ctx(sc, cam, x, y);
     uint32_t overflow;
     Counts cnt;
-    const float4 o = trace_ray<K, false>(sc, cp, rc, overflow, cnt);
+    const float4 o = trace_ray<K, false, W4>(sc, cp, rc, overflow, cnt);
     if (overflow) wrs::set_status(status, overflow);
     out[(size_t)y * cam.width + x] = o;
 }
 
-template <int K>
+template <int K, bool W4>
 __global__ void __launch_bounds__(256) k_trace_count(Scene sc, Comp cp, wrs_camera cam,
                                                      unsigned long long* counters, int32_t* status) {
     int px, py;
@@ -436,7 +504,7 @@ __global__ void __launch_bounds__(256) k_trace_count(Scene sc, Comp cp, wrs_came
     if (x < cam.width && y < cam.height) {
         const RayCtx rc = make_ray_ctx(sc, cam, x, y);
         uint32_t overflow;
-        trace_ray<K, true>(sc, cp, rc, overflow, cnt);
+        trace_ray<K, true, W4>(sc, cp, rc, overflow, cnt);
         if (overflow) wrs::set_status(status, overflow);
     }
     unsigned long long v[6] = {cnt.nodes, cnt.boxes, cnt.spheres, cnt.gathered, cnt.composited,
@@ -455,7 +523,7 @@ __global__ void __launch_bounds__(256) k_trace_count(Scene sc, Comp cp, wrs_came
 // carries the scene of the session its ray belongs to, so one warp may trace several sessions.
 constexpr uint32_t kChunkTiles = 4;
 
-template <int K>
+template <int K, bool W4>
 __global__ void __launch_bounds__(128) k_trace_batched(const wrs_session* __restrict__ sess,
                                                        int n_sessions, uint32_t total_tiles,
                                                        Comp cp, uint32_t* work, int32_t* status) {
@@ -502,6 +570,8 @@ __global__ void __launch_bounds__(128) k_trace_batched(const wrs_session* __rest
                             si = lo;
                             sc.hdr = static_cast<const LbvhHeader*>(S.nodes);
                             sc.nodes = wrs::lbvh_nodes(S.nodes);
+                            sc.wide = cp.width == 4 ? sc.nodes + 4 * (size_t)sc.hdr->wide_start
+                                                    : nullptr;
                             sc.pos_r = reinterpret_cast<const float4*>(S.pos_r);
                             sc.rgba = reinterpret_cast<const float4*>(S.rgba);
                             sc.id = S.id;
@@ -540,7 +610,7 @@ __global__ void __launch_bounds__(128) k_trace_batched(const wrs_session* __rest
             continue;
         }
         if (active) {
-            const int rc = lane_step<K>(sc, L, stack, n, leaf, m);
+            const int rc = lane_step<K, W4>(sc, L, stack, n, leaf, m);
             if (rc != 0) {
                 bool done = true;
                 if (rc < 0) {
@@ -643,7 +713,7 @@ __device__ __forceinline__ void chunk_adjoint(const Scene& sc, const Comp& cp, c
     }
 }
 
-template <int K>
+template <int K, bool W4>
 __global__ void __launch_bounds__(128) k_trace_bwd(Scene sc, Comp cp, wrs_camera cam,
                                                    const float4* __restrict__ dimg, GradOut go,
                                                    int32_t* status) {
@@ -671,7 +741,7 @@ __global__ void __launch_bounds__(128) k_trace_bwd(Scene sc, Comp cp, wrs_camera
     uint32_t last_id = 0;
     while (true) {
         if (chunks == wrs::kBwdChunks) { wrs::set_status(status, WRS_STATUS_CHUNK_OVERFLOW); return; }
-        const int count = gather<K, false>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, has_last,
+        const int count = gather<K, false, W4>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, has_last,
                                            last_key, last_id, kk, ki, kid, cnt);
         if (count < 0) { wrs::set_status(status, count == -1 ? WRS_STATUS_STACK_OVERFLOW : WRS_STATUS_MALFORMED_TREE); return; }
         b_key[chunks] = has_last ? last_key : -kInf;
@@ -693,7 +763,7 @@ __global__ void __launch_bounds__(128) k_trace_bwd(Scene sc, Comp cp, wrs_camera
         const int u = b_used[c];
         if (u == 0) continue;
         const bool hl = b_key[c] != -kInf;
-        gather<K, false>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, hl, b_key[c], b_id[c], kk, ki,
+        gather<K, false, W4>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, hl, b_key[c], b_id[c], kk, ki,
                          kid, cnt);
         chunk_adjoint<K>(sc, cp, rc.ray, ki, u, b_T[c], g, S, P, go);
     }
@@ -703,7 +773,7 @@ __global__ void __launch_bounds__(128) k_trace_bwd(Scene sc, Comp cp, wrs_camera
 // state machine over the same traversal steps as k_trace_pr.  Phase A replays the forward passes
 // and records each chunk's bound and starting transmittance; phase B re-gathers the chunks back
 // to front and applies chunk_adjoint.
-template <int K>
+template <int K, bool W4>
 __global__ void __launch_bounds__(128) k_trace_bwd_pr(Scene sc, Comp cp, wrs_camera cam,
                                                       const float4* __restrict__ dimg, GradOut go,
                                                       int32_t* status) {
@@ -771,7 +841,7 @@ __global__ void __launch_bounds__(128) k_trace_bwd_pr(Scene sc, Comp cp, wrs_cam
             continue;
         }
         if (!active) continue;
-        const int rc = lane_step<K>(sc, L, stack, n, leaf, m);
+        const int rc = lane_step<K, W4>(sc, L, stack, n, leaf, m);
         if (rc == 0) continue;
         if (rc < 0) {
             wrs::set_status(status, rc == -1 ? WRS_STATUS_STACK_OVERFLOW : WRS_STATUS_MALFORMED_TREE);
@@ -835,6 +905,8 @@ int check_trace_args(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_ca
     if (p->max_hits < 0) return wrs::fail(WRS_ERR_ARG, "%s: max_hits < 0", fn);
     if (p->schedule != WRS_SCHEDULE_PER_PIXEL && p->schedule != WRS_SCHEDULE_PERSISTENT)
         return wrs::fail(WRS_ERR_ARG, "%s: unknown schedule %d", fn, p->schedule);
+    if (p->width != 0 && p->width != 2 && p->width != 4)
+        return wrs::fail(WRS_ERR_ARG, "%s: width %d not 2 or 4 (0 = 2)", fn, p->width);
     if (!(p->t_stop >= 0.0f && p->t_stop < 1.0f))
         return wrs::fail(WRS_ERR_ARG, "%s: t_stop must be in [0, 1)", fn);
     if (!(p->edge_softness >= 0.0f && p->edge_softness < 1.0f))
@@ -842,10 +914,13 @@ int check_trace_args(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_ca
     return WRS_OK;
 }
 
-Scene make_scene(const wrs_lbvh* bvh, const wrs_splats* sorted, const float* opacity) {
+Scene make_scene(const wrs_lbvh* bvh, const wrs_splats* sorted, const float* opacity,
+                 int width = 2) {
     Scene sc;
     sc.hdr = static_cast<const LbvhHeader*>(bvh->nodes);
     sc.nodes = wrs::lbvh_nodes(bvh->nodes);
+    sc.wide = width == 4 ? sc.nodes + 4 * (size_t)wrs::lbvh_binary_slots(bvh->capacity, bvh->leaf_size)
+                         : nullptr;
     sc.pos_r = reinterpret_cast<const float4*>(sorted->pos_r);
     sc.rgba = reinterpret_cast<const float4*>(sorted->rgba);
     sc.id = sorted->id;
@@ -865,65 +940,84 @@ int effective_k(const wrs_trace_params* p) {
     return K;
 }
 
-template <template <int> class Launch, typename... A>
-void dispatch_k(int K, A&&... a) {
+template <template <int, bool> class Launch, bool W4, typename... A>
+void dispatch_k1(int K, A&&... a) {
     switch (K) {
-        case 1: Launch<1>::run(a...); break;
-        case 2: Launch<2>::run(a...); break;
-        case 4: Launch<4>::run(a...); break;
-        case 8: Launch<8>::run(a...); break;
-        default: Launch<16>::run(a...); break;
+        case 1: Launch<1, W4>::run(a...); break;
+        case 2: Launch<2, W4>::run(a...); break;
+        case 4: Launch<4, W4>::run(a...); break;
+        case 8: Launch<8, W4>::run(a...); break;
+        default: Launch<16, W4>::run(a...); break;
     }
 }
 
-template <int K> struct LaunchTrace {
+// launch Launch<K, W4>::run(a...) for the runtime K and traversal width
+template <template <int, bool> class Launch, typename... A>
+void dispatch_k(int K, int width, A&&... a) {
+    if (width == 4) dispatch_k1<Launch, true>(K, a...);
+    else dispatch_k1<Launch, false>(K, a...);
+}
+
+template <template <int, bool> class Launch>
+int blocks_per_sm_kw(int K, int width, int block) {
+    const bool w4 = width == 4;
+    switch (K) {
+        case 1: return w4 ? Launch<1, true>::blocks_per_sm(block) : Launch<1, false>::blocks_per_sm(block);
+        case 2: return w4 ? Launch<2, true>::blocks_per_sm(block) : Launch<2, false>::blocks_per_sm(block);
+        case 4: return w4 ? Launch<4, true>::blocks_per_sm(block) : Launch<4, false>::blocks_per_sm(block);
+        case 8: return w4 ? Launch<8, true>::blocks_per_sm(block) : Launch<8, false>::blocks_per_sm(block);
+        default: return w4 ? Launch<16, true>::blocks_per_sm(block) : Launch<16, false>::blocks_per_sm(block);
+    }
+}
+
+template <int K, bool W4> struct LaunchTrace {
     static void run(dim3 g, int b, cudaStream_t s, Scene sc, Comp cp, wrs_camera cam, float4* o,
                     int32_t* st) {
-        k_trace<K><<<g, b, 0, s>>>(sc, cp, cam, o, st);
+        k_trace<K, W4><<<g, b, 0, s>>>(sc, cp, cam, o, st);
     }
 };
-template <int K> struct LaunchTracePr {
+template <int K, bool W4> struct LaunchTracePr {
     static void run(int g, int b, cudaStream_t s, Scene sc, Comp cp, wrs_camera cam, float4* o,
                     int32_t* st) {
-        k_trace_pr<K><<<g, b, 0, s>>>(sc, cp, cam, o, st);
+        k_trace_pr<K, W4><<<g, b, 0, s>>>(sc, cp, cam, o, st);
     }
     static int blocks_per_sm(int b) {
         int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trace_pr<K>, b, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trace_pr<K, W4>, b, 0);
         return nb;
     }
 };
-template <int K> struct LaunchCount {
+template <int K, bool W4> struct LaunchCount {
     static void run(dim3 g, int b, cudaStream_t s, Scene sc, Comp cp, wrs_camera cam,
                     unsigned long long* c, int32_t* st) {
-        k_trace_count<K><<<g, b, 0, s>>>(sc, cp, cam, c, st);
+        k_trace_count<K, W4><<<g, b, 0, s>>>(sc, cp, cam, c, st);
     }
 };
-template <int K> struct LaunchBatched {
+template <int K, bool W4> struct LaunchBatched {
     static void run(int g, int b, cudaStream_t s, const wrs_session* ss, int ns, uint32_t tt,
                     Comp cp, uint32_t* w, int32_t* st) {
-        k_trace_batched<K><<<g, b, 0, s>>>(ss, ns, tt, cp, w, st);
+        k_trace_batched<K, W4><<<g, b, 0, s>>>(ss, ns, tt, cp, w, st);
     }
     static int blocks_per_sm(int b) {
         int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trace_batched<K>, b, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trace_batched<K, W4>, b, 0);
         return nb;
     }
 };
-template <int K> struct LaunchBwd {
+template <int K, bool W4> struct LaunchBwd {
     static void run(dim3 g, int b, cudaStream_t s, Scene sc, Comp cp, wrs_camera cam,
                     const float4* d, GradOut go, int32_t* st) {
-        k_trace_bwd<K><<<g, b, 0, s>>>(sc, cp, cam, d, go, st);
+        k_trace_bwd<K, W4><<<g, b, 0, s>>>(sc, cp, cam, d, go, st);
     }
 };
-template <int K> struct LaunchBwdPr {
+template <int K, bool W4> struct LaunchBwdPr {
     static void run(int g, int b, cudaStream_t s, Scene sc, Comp cp, wrs_camera cam,
                     const float4* d, GradOut go, int32_t* st) {
-        k_trace_bwd_pr<K><<<g, b, 0, s>>>(sc, cp, cam, d, go, st);
+        k_trace_bwd_pr<K, W4><<<g, b, 0, s>>>(sc, cp, cam, d, go, st);
     }
     static int blocks_per_sm(int b) {
         int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trace_bwd_pr<K>, b, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trace_bwd_pr<K, W4>, b, 0);
         return nb;
     }
 };
@@ -933,7 +1027,27 @@ dim3 grid_for(const wrs_camera* cam, int block) {
     return dim3((cam->width + 15) / 16, (cam->height + tile_h - 1) / tile_h);
 }
 
-Comp comp_of(const wrs_trace_params* p) { return Comp{p->max_hits, p->t_stop, p->edge_softness}; }
+Comp comp_of(const wrs_trace_params* p) {
+    return Comp{p->max_hits, p->t_stop, p->edge_softness, p->width};
+}
+
+// One resident wave of 128-thread blocks of a persistent kernel (occupancy x SMs).  Queried once
+// per (kernel, K, width) and cached, so that a call made during stream capture issues nothing but
+// its memsets and the launch.
+template <template <int, bool> class Launch>
+int resident_grid(int K, int width) {
+    static int cached[5][2] = {{0}};
+    const int ki = K == 1 ? 0 : K == 2 ? 1 : K == 4 ? 2 : K == 8 ? 3 : 4;
+    const int wi = width == 4 ? 1 : 0;
+    if (cached[ki][wi] == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int per_sm = blocks_per_sm_kw<Launch>(K, width, 128);
+        cached[ki][wi] = sms * (per_sm < 1 ? 1 : per_sm);
+    }
+    return cached[ki][wi];
+}
 
 }  // namespace
 
@@ -947,31 +1061,15 @@ int wrs_trace(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* c
     if (!rgba_out || (reinterpret_cast<uintptr_t>(rgba_out) & 15))
         return wrs::fail(WRS_ERR_ARG, "%s: rgba_out NULL or not 16-byte aligned", fn);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const int K = effective_k(params);
-    if (params->schedule == WRS_SCHEDULE_PERSISTENT) {
-        // one resident wave of blocks (occupancy x SMs), queried once per K and cached
-        static int cached_grid[5] = {0};
-        const int ki = K == 1 ? 0 : K == 2 ? 1 : K == 4 ? 2 : K == 8 ? 3 : 4;
-        if (cached_grid[ki] == 0) {
-            int dev = 0, sms = 0, per_sm = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            switch (K) {
-                case 1: per_sm = LaunchTracePr<1>::blocks_per_sm(128); break;
-                case 2: per_sm = LaunchTracePr<2>::blocks_per_sm(128); break;
-                case 4: per_sm = LaunchTracePr<4>::blocks_per_sm(128); break;
-                case 8: per_sm = LaunchTracePr<8>::blocks_per_sm(128); break;
-                default: per_sm = LaunchTracePr<16>::blocks_per_sm(128); break;
-            }
-            cached_grid[ki] = sms * (per_sm < 1 ? 1 : per_sm);
-        }
-        dispatch_k<LaunchTracePr>(K, cached_grid[ki], 128, s, make_scene(bvh, sorted, params->opacity),
-                                  comp_of(params), *cam, reinterpret_cast<float4*>(rgba_out), status);
-    } else {
-        dispatch_k<LaunchTrace>(K, grid_for(cam, params->block), params->block, s,
-                                make_scene(bvh, sorted, params->opacity), comp_of(params), *cam,
-                                reinterpret_cast<float4*>(rgba_out), status);
-    }
+    const int K = effective_k(params), W = params->width;
+    const Scene sc = make_scene(bvh, sorted, params->opacity, W);
+    float4* out = reinterpret_cast<float4*>(rgba_out);
+    if (params->schedule == WRS_SCHEDULE_PERSISTENT)
+        dispatch_k<LaunchTracePr>(K, W, resident_grid<LaunchTracePr>(K, W), 128, s, sc,
+                                  comp_of(params), *cam, out, status);
+    else
+        dispatch_k<LaunchTrace>(K, W, grid_for(cam, params->block), params->block, s, sc,
+                                comp_of(params), *cam, out, status);
     WRS_LAUNCH_CHECK(fn);
     return WRS_OK;
 }
@@ -985,9 +1083,9 @@ int wrs_trace_count(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_cam
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(counters, 0, 6 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return wrs::cuda_fail(e, fn);
-    dispatch_k<LaunchCount>(effective_k(params), grid_for(cam, params->block), params->block, s,
-                            make_scene(bvh, sorted, params->opacity), comp_of(params), *cam,
-                            counters, status);
+    dispatch_k<LaunchCount>(effective_k(params), params->width, grid_for(cam, params->block),
+                            params->block, s, make_scene(bvh, sorted, params->opacity, params->width),
+                            comp_of(params), *cam, counters, status);
     WRS_LAUNCH_CHECK(fn);
     return WRS_OK;
 }
@@ -1010,31 +1108,15 @@ int wrs_trace_batched(const wrs_session* sessions, int32_t n_sessions, uint32_t 
     if (params->max_hits < 0 || !(params->t_stop >= 0.0f && params->t_stop < 1.0f) ||
         !(params->edge_softness >= 0.0f && params->edge_softness < 1.0f))
         return wrs::fail(WRS_ERR_ARG, "%s: bad compositing parameters", fn);
+    if (params->width != 0 && params->width != 2 && params->width != 4)
+        return wrs::fail(WRS_ERR_ARG, "%s: width %d not 2 or 4 (0 = 2)", fn, params->width);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(work_counter, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return wrs::cuda_fail(e, fn);
     if (total_tiles == 0) return WRS_OK;
-    // one resident wave of 128-thread blocks; occupancy and SM count are queried once per K and
-    // cached, so that a call made during stream capture issues nothing but the memset and launch
-    static int cached_grid[5] = {0};
-    const int K = effective_k(params);
-    const int ki = K == 1 ? 0 : K == 2 ? 1 : K == 4 ? 2 : K == 8 ? 3 : 4;
-    if (cached_grid[ki] == 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        switch (K) {
-            case 1: per_sm = LaunchBatched<1>::blocks_per_sm(128); break;
-            case 2: per_sm = LaunchBatched<2>::blocks_per_sm(128); break;
-            case 4: per_sm = LaunchBatched<4>::blocks_per_sm(128); break;
-            case 8: per_sm = LaunchBatched<8>::blocks_per_sm(128); break;
-            default: per_sm = LaunchBatched<16>::blocks_per_sm(128); break;
-        }
-        cached_grid[ki] = sms * (per_sm < 1 ? 1 : per_sm);
-    }
-    const int grid = cached_grid[ki];
-    dispatch_k<LaunchBatched>(K, grid, 128, s, sessions, n_sessions, total_tiles,
-                              comp_of(params), work_counter, status);
+    const int K = effective_k(params), W = params->width;
+    dispatch_k<LaunchBatched>(K, W, resident_grid<LaunchBatched>(K, W), 128, s, sessions,
+                              n_sessions, total_tiles, comp_of(params), work_counter, status);
     WRS_LAUNCH_CHECK(fn);
     return WRS_OK;
 }
@@ -1054,31 +1136,15 @@ int wrs_trace_backward(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_
     if (e == cudaSuccess && g_scale) e = cudaMemsetAsync(g_scale, 0, sizeof(float) * cap, s);
     if (e != cudaSuccess) return wrs::cuda_fail(e, fn);
     const GradOut go = {radius_scale, global_scale, g_rgba, g_opacity, g_scale};
-    const int K = effective_k(params);
+    const int K = effective_k(params), W = params->width;
+    const Scene sc = make_scene(bvh, sorted, params->opacity, W);
     const float4* d4 = reinterpret_cast<const float4*>(dL_drgba);
     if (params->schedule == WRS_SCHEDULE_PERSISTENT) {
-        static int cached_grid[5] = {0};  // one resident wave, cached per K
-        const int ki = K == 1 ? 0 : K == 2 ? 1 : K == 4 ? 2 : K == 8 ? 3 : 4;
-        if (cached_grid[ki] == 0) {
-            int dev = 0, sms = 0, per_sm = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            switch (K) {
-                case 1: per_sm = LaunchBwdPr<1>::blocks_per_sm(128); break;
-                case 2: per_sm = LaunchBwdPr<2>::blocks_per_sm(128); break;
-                case 4: per_sm = LaunchBwdPr<4>::blocks_per_sm(128); break;
-                case 8: per_sm = LaunchBwdPr<8>::blocks_per_sm(128); break;
-                default: per_sm = LaunchBwdPr<16>::blocks_per_sm(128); break;
-            }
-            cached_grid[ki] = sms * (per_sm < 1 ? 1 : per_sm);
-        }
-        dispatch_k<LaunchBwdPr>(K, cached_grid[ki], 128, s,
-                                make_scene(bvh, sorted, params->opacity), comp_of(params), *cam,
-                                d4, go, status);
+        dispatch_k<LaunchBwdPr>(K, W, resident_grid<LaunchBwdPr>(K, W), 128, s, sc,
+                                comp_of(params), *cam, d4, go, status);
     } else {
         const int block = params->block > 128 ? 128 : params->block;  // keep occupancy
-        dispatch_k<LaunchBwd>(K, grid_for(cam, block), block, s,
-                              make_scene(bvh, sorted, params->opacity), comp_of(params), *cam, d4,
+        dispatch_k<LaunchBwd>(K, W, grid_for(cam, block), block, s, sc, comp_of(params), *cam, d4,
                               go, status);
     }
     WRS_LAUNCH_CHECK(fn);

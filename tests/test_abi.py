@@ -49,8 +49,8 @@ def test_struct_layouts_match(wrs):
 def test_size_queries(wrs):
     assert wrs.unproject_scratch_bytes(1920, 1080) >= 2 * 4 * ((1920 * 1080 + 1023) // 1024)
     assert wrs.unproject_scratch_bytes(0, 5) == 0
-    assert wrs.lib.wrs_lbvh_bytes(1000, 1) == 64 + 64 * 999
-    assert wrs.lib.wrs_lbvh_bytes(1000, 4) == 64 + 64 * 249
+    assert wrs.lib.wrs_lbvh_bytes(1000, 1) == 64 + (64 + 128) * 999
+    assert wrs.lib.wrs_lbvh_bytes(1000, 4) == 64 + (64 + 128) * 249
     assert wrs.lib.wrs_lbvh_bytes(10, 0) == 0 and wrs.lib.wrs_lbvh_bytes(10, 17) == 0
     assert wrs.lbvh_scratch_bytes(2_073_600, 1) > 4 * 4 * 2_073_600
     assert wrs.session_tiles(1024, 1024) == 128 * 256 and wrs.session_tiles(17, 1) == 3

@@ -156,6 +156,21 @@ def _check_lbvh(wrs, sp_gpu, ref_sp, leaf, scale=None):
         boxes, refs = bvh.node_table()
         assert np.array_equal(refs.cpu().numpy(), ref["child"])
         assert np.array_equal(boxes.cpu().numpy().view(np.uint32), ref["boxes"].view(np.uint32))
+        # 4-wide nodes: the grandchildren of each binary node in slots 2c, 2c + 1 for child c (a
+        # leaf child stands for itself in slot 2c; slot 2c + 1 is then unused, reference -1)
+        wb, wr = (t.cpu().numpy() for t in bvh.wide_table())
+        child, cbox = ref["child"], ref["boxes"]
+        for i in range(0, M - 1, max(1, (M - 1) // 500)):
+            for c in range(2):
+                r = int(child[i, c])
+                if r < 0:
+                    ents = [(cbox[i, c], r), (None, -1)]
+                else:
+                    ents = [(cbox[r, 0], int(child[r, 0])), (cbox[r, 1], int(child[r, 1]))]
+                for gc, (b, rr) in enumerate(ents):
+                    assert wr[i, 2 * c + gc] == rr
+                    if b is not None:
+                        assert np.array_equal(wb[i, 2 * c + gc].view(np.uint32), b.view(np.uint32))
     else:
         assert h["root"] == -(2 ** 31)
 
@@ -198,13 +213,13 @@ def test_lbvh_duplicate_centres_and_tiny_counts(wrs):
 # trace
 # ---------------------------------------------------------------------------------------------
 def _trace_pair(wrs, rgba, depth, srv, cli, H=0, beta=0.0, opacity=None, scale=None, leaf=1,
-                k=8, block=128, pixels=None, schedule=0):
+                k=8, block=128, pixels=None, schedule=0, width=2):
     ref_sp = oracle.unproject(rgba, depth, srv)
     sp = _gpu_splats(wrs, rgba, depth, srv)
     bvh, srt = wrs.build_lbvh(sp, leaf, radius_scale=None if scale is None else _cuda(scale))
     st = wrs.new_status()
     params = wrs.TraceParams(max_hits=H, edge_softness=beta, k_chunk=k, block=block,
-                             schedule=schedule)
+                             schedule=schedule, width=width)
     img = wrs.trace(bvh, srt, cli, params, opacity=None if opacity is None else _cuda(opacity),
                     status=st)
     wrs.check_status(st)
@@ -249,12 +264,14 @@ def test_trace_invariant_to_tuning_bitwise(wrs):
     for leaf in (1, 4, 16):
         bvh, srt = wrs.build_lbvh(sp, leaf, radius_scale=sc)
         for k in (1, 2, 4, 8, 16):
-            for block, sched in ((64, 0), (128, 0), (256, 0), (128, 1)):
-                p = wrs.TraceParams(k_chunk=k, block=block, schedule=sched)
+            for block, sched, width in ((64, 0, 2), (128, 0, 2), (256, 0, 4), (128, 1, 2),
+                                        (128, 1, 4)):
+                p = wrs.TraceParams(k_chunk=k, block=block, schedule=sched, width=width)
                 img = wrs.trace(bvh, srt, cli, p).cpu().numpy()
                 if base is None:
                     base = img
-                assert np.array_equal(img.view(np.uint32), base.view(np.uint32)), (leaf, k, block, sched)
+                assert np.array_equal(img.view(np.uint32), base.view(np.uint32)), \
+                    (leaf, k, block, sched, width)
 
 
 def test_trace_mid_full_image(wrs):
@@ -278,9 +295,10 @@ def test_trace_large_sampled(wrs):
     srv = synth.LARGE.server_cam()
     cli = synth.orbit(srv, (0.6, 0.8, 0.0), 20.0)
     pix = np.random.default_rng(9).choice(1920 * 1080, 4096, replace=False)
-    for H, k, sched in ((0, 1, 1), (0, 8, 0), (1, 1, 1)):
-        got, ref, _ = _trace_pair(wrs, rgba, depth, srv, cli, H=H, k=k, pixels=pix, schedule=sched)
-        _assert_close(got, ref["rgba"], f"large H={H} k={k} schedule={sched}")
+    for H, k, sched, width in ((0, 1, 1, 4), (0, 1, 1, 2), (0, 8, 0, 2), (1, 1, 1, 4)):
+        got, ref, _ = _trace_pair(wrs, rgba, depth, srv, cli, H=H, k=k, pixels=pix, schedule=sched,
+                                  width=width)
+        _assert_close(got, ref["rgba"], f"large H={H} k={k} schedule={sched} width={width}")
 
 
 def test_trace_empty_and_single(wrs):
@@ -309,8 +327,9 @@ def test_trace_many_layers_multi_pass(wrs):
     srv = synth.server_camera(1.4, 30.0, W, H)
     cli = synth.orbit(srv, (1, 0, 0), 60.0)
     sc = np.full(W * H, 8.0, np.float32)
-    for k, sched in ((1, 0), (2, 1), (16, 0), (1, 1)):
-        got, ref, _ = _trace_pair(wrs, rgba, depth, srv, cli, scale=sc, k=k, schedule=sched)
+    for k, sched, width in ((1, 0, 2), (2, 1, 4), (16, 0, 4), (1, 1, 2)):
+        got, ref, _ = _trace_pair(wrs, rgba, depth, srv, cli, scale=sc, k=k, schedule=sched,
+                                  width=width)
         assert ref["nhits"].max() > 20
         _assert_close(got, ref["rgba"], f"layers k={k}")
 
@@ -333,8 +352,8 @@ def test_batched_equals_sequential_bitwise(wrs):
         refs.append(wrs.trace(bvh, srt, cli).cpu().numpy())
     batch = wrs.Batch(sessions)
     st = wrs.new_status()
-    for k in (8, 1, 4, 16):
-        outs = wrs.trace_batched(batch, wrs.TraceParams(k_chunk=k), status=st)
+    for k, width in ((8, 2), (1, 4), (4, 2), (16, 4)):
+        outs = wrs.trace_batched(batch, wrs.TraceParams(k_chunk=k, width=width), status=st)
         wrs.check_status(st)
         for o, r in zip(outs, refs):
             assert np.array_equal(o.cpu().numpy().view(np.uint32), r.view(np.uint32))
@@ -360,14 +379,14 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
-@pytest.mark.parametrize("beta,k,sched", [(0.25, 8, 0), (0.25, 1, 0), (0.0, 4, 0), (0.25, 1, 1),
-                                          (0.25, 4, 1), (0.0, 2, 1)])
-def test_backward_matches_oracle_adjoint(wrs, beta, k, sched):
+@pytest.mark.parametrize("beta,k,sched,width", [(0.25, 8, 0, 2), (0.25, 1, 0, 4), (0.0, 4, 0, 2),
+                                                (0.25, 1, 1, 2), (0.25, 4, 1, 4), (0.0, 2, 1, 4)])
+def test_backward_matches_oracle_adjoint(wrs, beta, k, sched, width):
     rgba, depth, srv, cli, ref_sp, op, sc, g = _bwd_instance(wrs)
     n = ref_sp.n
     sp = _gpu_splats(wrs, rgba, depth, srv)
     bvh, srt = wrs.build_lbvh(sp, 1, radius_scale=_cuda(sc))
-    params = wrs.TraceParams(edge_softness=beta, k_chunk=k, schedule=sched)
+    params = wrs.TraceParams(edge_softness=beta, k_chunk=k, schedule=sched, width=width)
     st = wrs.new_status()
     gr, go, gs = wrs.trace_backward(bvh, srt, cli, _cuda(g.astype(np.float32).reshape(cli.height, cli.width, 4)),
                                     params, opacity=_cuda(op), radius_scale=_cuda(sc), status=st)
