@@ -29,7 +29,8 @@ def main():
     ap.add_argument("--k", type=int, default=1)
     ap.add_argument("--block", type=int, default=128)
     ap.add_argument("--max-hits", type=int, default=0)
-    ap.add_argument("--schedule", type=int, default=1, help="0 per pixel, 1 persistent")
+    ap.add_argument("--schedule", type=int, default=0, help="0 per pixel, 1 persistent")
+    ap.add_argument("--width", type=int, default=4, help="2 binary nodes, 4 four-wide nodes")
     a = ap.parse_args()
     W = {"tiny": synth.TINY, "mid": synth.MID, "large": synth.LARGE}[a.workload]
     dev = torch.device("cuda")
@@ -41,7 +42,8 @@ def main():
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     cams = [wrs.make_camera(c) for c in W.client_poses(max(a.frames, 1))][: a.frames]
-    params = wrs.TraceParams(max_hits=a.max_hits, k_chunk=a.k, block=a.block, schedule=a.schedule)
+    params = wrs.TraceParams(max_hits=a.max_hits, k_chunk=a.k, block=a.block, schedule=a.schedule,
+                             width=a.width)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 + a.frames)]
     st = wrs.new_status()
     ev[0].record()

@@ -328,14 +328,29 @@ __device__ __forceinline__ float4 trace_ray(const Scene& sc, const Comp& cp, con
 constexpr int kRefill = 8;
 
 // Minimum resident 128-thread blocks per SM asked of the compiler for the single-view persistent
-// kernel with K <= 2 (it caps registers at 65536 / (128 * this)); larger K keep more state and
-// get no cap.  A build-time tuning knob (0 = no cap).
+// kernel with K <= 2 (it caps registers at 65536 / (128 * this)): 10 (48 registers) for the binary
+// traversal, 9 (56 registers) for the 4-wide one, both measured faster than no cap on the 1080p,
+// 2 M splat workload; larger K keep more state and get no cap.  Build-time tuning knobs (0 = no cap).
 #ifndef WRS_PERSISTENT_MIN_BLOCKS
 #define WRS_PERSISTENT_MIN_BLOCKS 10
 #endif
+#ifndef WRS_PERSISTENT_W4_MIN_BLOCKS
+#define WRS_PERSISTENT_W4_MIN_BLOCKS 9
+#endif
 template <int K, bool W4>
 struct PersistentMinBlocks {
-    static constexpr int value = (K <= 2 && !W4) ? WRS_PERSISTENT_MIN_BLOCKS : 0;
+    static constexpr int value = K > 2 ? 0 : (W4 ? WRS_PERSISTENT_W4_MIN_BLOCKS : WRS_PERSISTENT_MIN_BLOCKS);
+};
+
+// Minimum resident 256-thread blocks per SM for the per-pixel kernel with the 4-wide traversal and
+// K <= 2 (caps registers at 65536 / (256 * this)); a build-time tuning knob.  Default 0 (no cap,
+// 64 registers): caps of 5 and 6 spill and measured slower on the 1080p, 2 M splat workload.
+#ifndef WRS_PIXEL_W4_MIN_BLOCKS
+#define WRS_PIXEL_W4_MIN_BLOCKS 0
+#endif
+template <int K, bool W4>
+struct PixelMinBlocks {
+    static constexpr int value = (K <= 2 && W4) ? WRS_PIXEL_W4_MIN_BLOCKS : 0;
 };
 
 template <int K>
@@ -478,7 +493,7 @@ __device__ __forceinline__ void tile_pixel(int t, int& px, int& py) {
 }
 
 template <int K, bool W4>
-__global__ void __launch_bounds__(256) k_trace(Scene sc, Comp cp, wrs_camera cam,
+__global__ void __launch_bounds__(256, PixelMinBlocks<K, W4>::value) k_trace(Scene sc, Comp cp, wrs_camera cam,
                                                float4* __restrict__ out, int32_t* status) {
     int px, py;
     tile_pixel(threadIdx.x, px, py);
