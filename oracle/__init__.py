@@ -12,6 +12,8 @@ marshals numpy arrays through ctypes.  Functions and the paper passage each one 
   (§4.1, §4.2, Fig. 2; the heuristic itself is cited from earlier work, §2).
 * :func:`unproject` -- object-space samples ``p = o + d t_i`` (Eq. 1), footprint radius (§4.1),
   zero-radius compaction (§4.1).
+* :func:`append_frame`, :func:`accumulate` -- splats of several server frames in one set, the
+  accumulation over frames named as future work in §6 (reading: spec S3a).
 * :func:`trace` -- first-hit / multi-hit ray tracing of the samples as semi-transparent spheres
   with constant colour (Fig. 2 caption, §4), front-to-back compositing (spec S6).
 * :func:`trace_backward` -- the adjoint of that compositing (spec S7; not in the paper).
@@ -184,6 +186,55 @@ def unproject(rgba: np.ndarray, depth: np.ndarray, cam, mode: int = RADIUS_FOOTP
     if n < 0:
         raise ValueError(f"orc_unproject failed ({n})")
     return Splats(pos_r[:n].copy(), out[:n].copy(), ids[:n].copy())
+
+
+STATUS_SPLAT_OVERFLOW = 8
+
+
+def append_frame(acc: Optional[Splats], rgba: np.ndarray, depth: np.ndarray, cam, weight: float = 1.0,
+                 id_base: int = 0, capacity: Optional[int] = None, mode: int = RADIUS_FOOTPRINT,
+                 voxel_diag: float = 0.0):
+    """Append one server frame's splats to ``acc`` (spec S3a; accumulation over frames, §6).
+
+    Steps in the reading's order: the frame's kept pixels by the unprojection rule (S3); ids
+    shifted by ``id_base``; colours scaled by ``weight`` in binary32; appended after the current
+    records; records beyond ``capacity`` dropped.  Returns ``(splats, overflow)``."""
+    new = unproject(rgba, depth, cam, mode, voxel_diag)
+    w = np.float32(weight)
+    col = new.rgba if w == np.float32(1.0) else (new.rgba * w).astype(np.float32)
+    ids = new.id.astype(np.uint64) + np.uint64(id_base)
+    if ids.size and int(ids.max()) >= 2**32:
+        raise ValueError("id_base + pixel index exceeds 32 bits")
+    if acc is None:
+        acc = Splats(np.zeros((0, 4), np.float32), np.zeros((0, 4), np.float32), np.zeros(0, np.uint32))
+    pos_r = np.concatenate([acc.pos_r, new.pos_r])
+    col = np.concatenate([acc.rgba, col])
+    ids = np.concatenate([acc.id, ids.astype(np.uint32)])
+    overflow = capacity is not None and ids.shape[0] > capacity
+    if overflow:
+        pos_r, col, ids = pos_r[:capacity], col[:capacity], ids[:capacity]
+    return Splats(pos_r.copy(), col.copy(), ids.copy()), overflow
+
+
+def window_weights(frames: int, decay: float = 1.0) -> np.ndarray:
+    """Weight of the frame of age g (0 = newest): decay^g by repeated binary32 multiplication."""
+    w = np.ones(frames, np.float32)
+    for g in range(1, frames):
+        w[g] = np.float32(w[g - 1] * np.float32(decay))
+    return w
+
+
+def accumulate(frames, decay: float = 1.0, mode: int = RADIUS_FOOTPRINT,
+               voxel_diag: float = 0.0) -> Splats:
+    """The splat set of a window of server frames (spec S3a).  ``frames`` = [(rgba, depth, cam)]
+    ordered newest first; the frame of age g is appended with weight decay^g and ids offset by
+    g * Ws * Hs, so that newer frames come first and win ties of equal hit distance."""
+    acc = None
+    w = window_weights(len(frames), decay)
+    for g, (rgba, depth, cam) in enumerate(frames):
+        npix = int(np.asarray(depth).size)
+        acc, _ = append_frame(acc, rgba, depth, cam, float(w[g]), g * npix, None, mode, voxel_diag)
+    return acc
 
 
 @dataclass
