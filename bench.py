@@ -9,8 +9,9 @@ per second over the whole job (all ranks), Mrays/s.
 
 Also reported on the same line: LBVH build and unproject ms, trace-only Mrays/s, the roofline of
 the trace kernel, the batched workload (64 sessions, one persistent launch in a CUDA graph vs 64
-sequential calls), forward and forward+backward throughput of the differentiable renderer, an
-end-to-end number through host buffers, and the CPU oracle timed on the host cores.
+sequential calls), accumulation over a window of the 4 newest server frames (one LBVH and one
+trace over their union), forward and forward+backward throughput of the differentiable renderer,
+an end-to-end number through host buffers, and the CPU oracle timed on the host cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl wrs|reference] [--no-extras]
 
@@ -505,6 +506,46 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
                        "k_chunk": bt["k_chunk"], "block": bt["block"], "bvh_width": bt["width"],
                        "leaf_size": leaf}
     del sess, batch, outs, g
+
+    # ---------------- accumulation over a window of server frames (one LBVH over all) -----------
+    # The union of several frames has several times the hits per ray of one frame, so the launch
+    # is tuned again on the window (untimed).
+    F_WIN = 4
+    probe = wrs.FrameWindow(F_WIN, W.server_w, W.server_h, decay=0.9)
+    for g_i in range(F_WIN):
+        probe.push(*groups[g_i][:3])
+    at = autotune.tune_trace(probe.splats, groups[F_WIN][3], use_cache=False)
+    del probe
+    aparams = wrs.TraceParams(max_hits=0, t_stop=1e-5, k_chunk=at["k_chunk"], block=at["block"],
+                              schedule=at["schedule"], width=at["width"])
+    win = wrs.FrameWindow(F_WIN, W.server_w, W.server_h, decay=0.9, leaf_size=at["leaf"])
+    for g_i in range(F_WIN):
+        win.push(*groups[g_i][:3])
+    outs = [torch.empty(W.client_h, W.client_w, 4, device=dev) for _ in range(FRAMES_PER_IMAGE)]
+    nxt = [F_WIN]
+
+    def acc_step():
+        rgba_a, depth_a, srv_a, clis_a = groups[nxt[0] % len(groups)]
+        nxt[0] += 1
+        win.push(rgba_a, depth_a, srv_a)
+        for f in range(FRAMES_PER_IMAGE):
+            win.trace(clis_a[f], aparams, out=outs[f])
+    barrier()
+    ms_acc = max_over_ranks(_time_ms(torch, acc_step, 10))
+    ms_rebuild = max_over_ranks(_time_ms(torch, win.rebuild, 10))
+    wrs.check_status(win.status)
+    line["accumulate"] = {"frames": F_WIN, "decay": 0.9, "splats": win.splats.count(),
+                          "client_frames_per_server_frame": FRAMES_PER_IMAGE,
+                          "mrays_s": world * FRAMES_PER_IMAGE * npix_c / (ms_acc * 1e-3) / 1e6,
+                          "ms_per_step": ms_acc, "rebuild_ms": ms_rebuild,
+                          "trace_ms": (ms_acc - ms_rebuild) / FRAMES_PER_IMAGE,
+                          "leaf_size": at["leaf"], "k_chunk": at["k_chunk"], "block": at["block"],
+                          "schedule": "persistent lane refill" if at["schedule"] else
+                                      "one thread per pixel", "bvh_width": at["width"],
+                          "note": "step = push one 1080p server frame into the window of the 4 "
+                                  "newest (4 unprojections into one set + LBVH over about 8 M "
+                                  "splats) + 4 client traces of the union"}
+    del win, outs
 
     # ---------------- forward and forward+backward (differentiable renderer) -------------------
     D = synth.DIFF

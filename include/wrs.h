@@ -51,6 +51,7 @@ typedef void* wrs_stream_t; /* cudaStream_t */
 #define WRS_STATUS_STACK_OVERFLOW 1u  /* BVH traversal stack exceeded; the ray was cut short */
 #define WRS_STATUS_CHUNK_OVERFLOW 2u  /* backward: more hit chunks than its table holds */
 #define WRS_STATUS_MALFORMED_TREE 4u  /* traversal met an impossible node reference or revisit */
+#define WRS_STATUS_SPLAT_OVERFLOW 8u  /* wrs_unproject_append: splats beyond capacity were dropped */
 
 /* volume scalar types */
 #define WRS_F32 0
@@ -154,6 +155,22 @@ size_t wrs_unproject_scratch_bytes(int32_t width, int32_t height);
 int wrs_unproject(const float* rgba, const float* depth, const wrs_camera* cam,
                   int32_t radius_mode, float voxel_diag, wrs_splats* out, void* scratch,
                   size_t scratch_bytes, wrs_stream_t stream);
+
+/* Accumulation over server frames (§6 names it as future work and gives no rule; spec S3a is
+ * this library's reading): wrs_unproject of one more frame, APPENDED to the splats already in out.
+ * With N0 = *out->n on entry (read on the device), the frame's kept pixels (same rule, radius and
+ * pixel order as wrs_unproject) are written at N0, N0+1, ... with id = id_base + pixel index and
+ * rgba = weight * rgba per channel (binary32; weight in (0, 1], 1 copies bit for bit); then
+ * *out->n = N0 + count.  Records whose slot is >= out->capacity are dropped, *out->n is clamped
+ * to the capacity and WRS_STATUS_SPLAT_OVERFLOW is OR-ed into *status (status may be NULL: then
+ * the overflow is silent).  Requires id_base + width * height <= 2^32 and capacity >= 1; any
+ * capacity is accepted (a window of F frames of one size needs F * width * height).  A window
+ * of frames is built by one wrs_unproject (newest frame) and one append per older frame; the
+ * trace and the LBVH need no change.  Scratch: wrs_unproject_scratch_bytes(w, h). */
+int wrs_unproject_append(const float* rgba, const float* depth, const wrs_camera* cam,
+                         int32_t radius_mode, float voxel_diag, float weight, uint32_t id_base,
+                         wrs_splats* out, void* scratch, size_t scratch_bytes, int32_t* status,
+                         wrs_stream_t stream);
 
 /* wrs_unproject for callers that cannot give the library device memory: the paper has no
  * counterpart; this is an interface convenience.  Some hosts fix their device memory when they

@@ -40,6 +40,8 @@ WRS_ERR_SCRATCH = -4
 WRS_ERR_DEVICE = -5
 STATUS_STACK_OVERFLOW = 1
 STATUS_CHUNK_OVERFLOW = 2
+STATUS_MALFORMED_TREE = 4
+STATUS_SPLAT_OVERFLOW = 8
 F32 = 0
 U8 = 1
 RADIUS_FOOTPRINT = 0
@@ -108,6 +110,8 @@ _sig("wrs_check_status", _I, _P, _P)
 _sig("wrs_raycast_volume", _I, _P, _I, _I, _I, _I, _P, ctypes.POINTER(Camera), _F, _F, _P, _P, _P)
 _sig("wrs_unproject_scratch_bytes", _Z, _I, _I)
 _sig("wrs_unproject", _I, _P, _P, ctypes.POINTER(Camera), _I, _F, ctypes.POINTER(_Splats), _P, _Z, _P)
+_sig("wrs_unproject_append", _I, _P, _P, ctypes.POINTER(Camera), _I, _F, _F, _U,
+     ctypes.POINTER(_Splats), _P, _Z, _P, _P)
 _sig("wrs_unproject_static", _I, _P, _P, ctypes.POINTER(Camera), _I, _F, ctypes.POINTER(_Splats), _P)
 _sig("wrs_lbvh_bytes", _Z, _U, _U)
 _sig("wrs_lbvh_scratch_bytes", _Z, _U, _U)
@@ -300,6 +304,27 @@ def unproject(rgba: torch.Tensor, depth: torch.Tensor, cam, radius_mode: int = R
     return out
 
 
+def unproject_append(rgba: torch.Tensor, depth: torch.Tensor, cam, out: SplatBuffers,
+                     weight: float = 1.0, id_base: int = 0, radius_mode: int = RADIUS_FOOTPRINT,
+                     voxel_diag: float = 0.0, status: Optional[torch.Tensor] = None,
+                     scratch: Optional[torch.Tensor] = None, stream=None) -> SplatBuffers:
+    """Append one more server frame's splats to ``out`` (accumulation over frames; see
+    wrs_unproject_append): ids offset by ``id_base``, colours scaled by ``weight``.  Splats beyond
+    the capacity are dropped and flag STATUS_SPLAT_OVERFLOW in ``status``."""
+    c = _cam(cam)
+    if int(id_base) + c.width * c.height > 2**31:
+        raise ValueError("id_base + pixels must stay below 2^31 (ids are held in int32 tensors)")
+    need = unproject_scratch_bytes(c.width, c.height)
+    if scratch is None:
+        scratch = _scratch(need, rgba.device)
+    sp = out.c()
+    _check(_lib.wrs_unproject_append(_ptr(rgba), _ptr(depth), ctypes.byref(c), int(radius_mode),
+                                     float(voxel_diag), float(weight), int(id_base),
+                                     ctypes.byref(sp), _ptr(scratch), scratch.numel(), _ptr(status),
+                                     _stream(stream)), "wrs_unproject_append")
+    return out
+
+
 def lbvh_scratch_bytes(capacity: int, leaf_size: int) -> int:
     return int(_lib.wrs_lbvh_scratch_bytes(int(capacity), int(leaf_size)))
 
@@ -440,3 +465,4 @@ def new_status(device=None) -> torch.Tensor:
 
 
 from .autograd import TraceFunction, render  # noqa: E402,F401
+from .accumulate import FrameWindow  # noqa: E402,F401

@@ -45,10 +45,11 @@ int wrs_check_status(int32_t* status, wrs_stream_t stream) {
         wrs::g_err[0] = 0;
         return WRS_OK;
     }
-    return wrs::fail(WRS_ERR_DEVICE, "device status 0x%x:%s%s%s", (unsigned)h,
+    return wrs::fail(WRS_ERR_DEVICE, "device status 0x%x:%s%s%s%s", (unsigned)h,
                      (h & WRS_STATUS_STACK_OVERFLOW) ? " traversal stack overflow" : "",
                      (h & WRS_STATUS_CHUNK_OVERFLOW) ? " backward chunk table overflow" : "",
-                     (h & WRS_STATUS_MALFORMED_TREE) ? " malformed tree" : "");
+                     (h & WRS_STATUS_MALFORMED_TREE) ? " malformed tree" : "",
+                     (h & WRS_STATUS_SPLAT_OVERFLOW) ? " splat capacity overflow" : "");
 }
 
 }  // extern "C"

@@ -53,15 +53,27 @@ __global__ void __launch_bounds__(kThreads) k_unproject_count(const float4* __re
     if (threadIdx.x == 0) counts[blockIdx.x] = t;
 }
 
-// Exclusive scan of nb block counts with one block of 1024 threads; writes *n_out = total.
+// Exclusive scan of nb block counts with one block of 1024 threads.  Plain mode: offsets start at
+// 0 and *n_out = total.  APPEND (accumulation over frames): offsets start at the current count
+// base = *n_out, and *n_out = min(base + total, capacity); a total above capacity (or a count that
+// was already above it) sets WRS_STATUS_SPLAT_OVERFLOW, and the write pass drops the records whose
+// slot is >= capacity.  Offsets saturate at 2^32 - 1 (>= capacity, so those records are dropped).
+template <bool APPEND>
 __global__ void __launch_bounds__(1024) k_scan_counts(const uint32_t* __restrict__ counts,
                                                       uint32_t* __restrict__ offsets, uint32_t nb,
-                                                      uint32_t* __restrict__ n_out) {
+                                                      uint32_t* __restrict__ n_out, uint32_t capacity,
+                                                      int32_t* __restrict__ status) {
     __shared__ uint32_t s[1024];
+    __shared__ uint32_t s_base;
     const uint32_t per = (nb + 1023) / 1024;
     const uint32_t lo = threadIdx.x * per, hi = min(lo + per, nb);
     uint32_t sum = 0;
     for (uint32_t i = lo; i < hi; i++) sum += counts[i];
+    if (APPEND && threadIdx.x == 0) {
+        const uint32_t b = *n_out;
+        if (b > capacity && status) atomicOr(status, (int32_t)WRS_STATUS_SPLAT_OVERFLOW);
+        s_base = min(b, capacity);
+    }
     s[threadIdx.x] = sum;
     __syncthreads();
     for (int o = 1; o < 1024; o <<= 1) {  // Hillis-Steele inclusive scan
@@ -70,24 +82,33 @@ __global__ void __launch_bounds__(1024) k_scan_counts(const uint32_t* __restrict
         s[threadIdx.x] += v;
         __syncthreads();
     }
-    uint32_t run = s[threadIdx.x] - sum;
+    const uint64_t base = APPEND ? s_base : 0;
+    uint64_t run = base + s[threadIdx.x] - sum;
     for (uint32_t i = lo; i < hi; i++) {
         const uint32_t c = counts[i];
-        offsets[i] = run;
+        offsets[i] = (uint32_t)min(run, (uint64_t)0xFFFFFFFFu);
         run += c;
     }
-    if (threadIdx.x == 1023) *n_out = s[1023];
+    if (threadIdx.x == 1023) {
+        const uint64_t total = base + s[1023];
+        if (APPEND && total > capacity && status) atomicOr(status, (int32_t)WRS_STATUS_SPLAT_OVERFLOW);
+        *n_out = APPEND ? (uint32_t)min(total, (uint64_t)capacity) : (uint32_t)total;
+    }
 }
 
+// APPEND: records go after the current count (offsets from the APPEND scan), slots >= capacity are
+// dropped, colours are scaled by weight (binary32 product per channel) and ids offset by id_base.
+template <bool APPEND>
 __global__ void __launch_bounds__(kThreads) k_unproject_write(
     const float4* __restrict__ rgba, const float* __restrict__ depth, wrs_camera cam,
     int32_t mode, float voxel_diag, const uint32_t* __restrict__ offsets, float4* __restrict__ pos_r,
-    float4* __restrict__ out_rgba, uint32_t* __restrict__ out_id) {
+    float4* __restrict__ out_rgba, uint32_t* __restrict__ out_id, float weight, uint32_t id_base,
+    uint32_t capacity) {
     __shared__ uint32_t s_warp[kThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t npix = (uint32_t)cam.width * (uint32_t)cam.height;
     const uint32_t base = blockIdx.x * kTile;
-    uint32_t run = offsets[blockIdx.x];
+    uint64_t run = offsets[blockIdx.x];
     // pitch of one pixel at unit depth along the view axis (spec S3)
     const float pitch = __fdiv_rn(__fmul_rn(2.0f, cam.tan_half_fovy), (float)cam.height);
     const float r_vox = __fmul_rn(voxel_diag, 0.5f);
@@ -103,8 +124,8 @@ __global__ void __launch_bounds__(kThreads) k_unproject_write(
             before += (w < warp) ? c : 0;
             total += c;
         }
-        if (keep) {
-            const uint32_t slot = run + before + __popc(ball & ((1u << lane) - 1u));
+        const uint64_t slot = run + before + __popc(ball & ((1u << lane) - 1u));
+        if (keep && (!APPEND || slot < capacity)) {
             const int x = (int)(i % (uint32_t)cam.width), y = (int)(i / (uint32_t)cam.width);
             const wrs::Ray r = wrs::primary_ray(cam, x, y);
             const float t = depth[i];
@@ -118,8 +139,13 @@ __global__ void __launch_bounds__(kThreads) k_unproject_write(
             }
             pos_r[slot] = make_float4(__fmaf_rn(r.d.x, t, r.o.x), __fmaf_rn(r.d.y, t, r.o.y),
                                       __fmaf_rn(r.d.z, t, r.o.z), r0);
-            out_rgba[slot] = rgba[i];
-            out_id[slot] = i;
+            float4 c = rgba[i];
+            if (APPEND) {
+                c = make_float4(__fmul_rn(weight, c.x), __fmul_rn(weight, c.y),
+                                __fmul_rn(weight, c.z), __fmul_rn(weight, c.w));
+            }
+            out_rgba[slot] = c;
+            out_id[slot] = APPEND ? id_base + i : i;
         }
         run += total;
         __syncthreads();  // s_warp is reused by the next round
@@ -171,12 +197,58 @@ int wrs_unproject(const float* rgba, const float* depth, const wrs_camera* cam,
     const float4* in4 = reinterpret_cast<const float4*>(rgba);
     k_unproject_count<<<nb, kThreads, 0, s>>>(in4, depth, (uint32_t)npix, counts);
     WRS_LAUNCH_CHECK("wrs_unproject count");
-    k_scan_counts<<<1, 1024, 0, s>>>(counts, offsets, nb, out->n);
+    k_scan_counts<false><<<1, 1024, 0, s>>>(counts, offsets, nb, out->n, out->capacity, nullptr);
     WRS_LAUNCH_CHECK("wrs_unproject scan");
-    k_unproject_write<<<nb, kThreads, 0, s>>>(in4, depth, *cam, radius_mode, voxel_diag, offsets,
-                                              reinterpret_cast<float4*>(out->pos_r),
-                                              reinterpret_cast<float4*>(out->rgba), out->id);
+    k_unproject_write<false><<<nb, kThreads, 0, s>>>(in4, depth, *cam, radius_mode, voxel_diag,
+                                                     offsets, reinterpret_cast<float4*>(out->pos_r),
+                                                     reinterpret_cast<float4*>(out->rgba), out->id,
+                                                     1.0f, 0u, out->capacity);
     WRS_LAUNCH_CHECK("wrs_unproject write");
+    return WRS_OK;
+}
+
+int wrs_unproject_append(const float* rgba, const float* depth, const wrs_camera* cam,
+                         int32_t radius_mode, float voxel_diag, float weight, uint32_t id_base,
+                         wrs_splats* out, void* scratch, size_t scratch_bytes, int32_t* status,
+                         wrs_stream_t stream) {
+    const char* fn = "wrs_unproject_append";
+    if (int rc = wrs::check_camera(cam, fn)) return rc;
+    if (!rgba || !depth || !out || !out->pos_r || !out->rgba || !out->id || !out->n)
+        return wrs::fail(WRS_ERR_ARG, "%s: NULL input or output pointer", fn);
+    if ((reinterpret_cast<uintptr_t>(rgba) | reinterpret_cast<uintptr_t>(out->pos_r) |
+         reinterpret_cast<uintptr_t>(out->rgba)) & 15)
+        return wrs::fail(WRS_ERR_ARG, "%s: rgba / pos_r arrays must be 16-byte aligned", fn);
+    if (radius_mode != WRS_RADIUS_FOOTPRINT && radius_mode != WRS_RADIUS_VOXEL)
+        return wrs::fail(WRS_ERR_ARG, "%s: unknown radius_mode %d", fn, radius_mode);
+    if (radius_mode == WRS_RADIUS_VOXEL && !(voxel_diag > 0.0f && voxel_diag < 1e30f))
+        return wrs::fail(WRS_ERR_ARG, "%s: voxel_diag must be positive and finite", fn);
+    if (!(weight > 0.0f && weight <= 1.0f))
+        return wrs::fail(WRS_ERR_ARG, "%s: weight must lie in (0, 1]", fn);
+    const size_t npix = (size_t)cam->width * (size_t)cam->height;
+    if (npix >= 0x80000000ull)
+        return wrs::fail(WRS_ERR_ARG, "%s: image of %zu pixels exceeds 2^31", fn, npix);
+    if ((uint64_t)id_base + npix > 0x100000000ull)
+        return wrs::fail(WRS_ERR_ARG, "%s: id_base %u + %zu pixels exceeds 2^32", fn, id_base, npix);
+    if (out->capacity == 0) return wrs::fail(WRS_ERR_CAPACITY, "%s: splat capacity is 0", fn);
+    const size_t need = wrs_unproject_scratch_bytes(cam->width, cam->height);
+    if (!scratch || scratch_bytes < need)
+        return wrs::fail(WRS_ERR_SCRATCH, "%s: scratch needs %zu bytes, got %zu", fn, need,
+                         scratch_bytes);
+    const uint32_t nb = (uint32_t)((npix + kTile - 1) / kTile);
+    uint32_t* counts = static_cast<uint32_t*>(scratch);
+    uint32_t* offsets = reinterpret_cast<uint32_t*>(static_cast<char*>(scratch) +
+                                                    align256(nb * sizeof(uint32_t)));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const float4* in4 = reinterpret_cast<const float4*>(rgba);
+    k_unproject_count<<<nb, kThreads, 0, s>>>(in4, depth, (uint32_t)npix, counts);
+    WRS_LAUNCH_CHECK("wrs_unproject_append count");
+    k_scan_counts<true><<<1, 1024, 0, s>>>(counts, offsets, nb, out->n, out->capacity, status);
+    WRS_LAUNCH_CHECK("wrs_unproject_append scan");
+    k_unproject_write<true><<<nb, kThreads, 0, s>>>(in4, depth, *cam, radius_mode, voxel_diag,
+                                                    offsets, reinterpret_cast<float4*>(out->pos_r),
+                                                    reinterpret_cast<float4*>(out->rgba), out->id,
+                                                    weight, id_base, out->capacity);
+    WRS_LAUNCH_CHECK("wrs_unproject_append write");
     return WRS_OK;
 }
 
@@ -259,11 +331,12 @@ extern "C" int wrs_unproject_static(const float* rgba, const float* depth, const
     const float4* in4 = reinterpret_cast<const float4*>(rgba);
     k_unproject_count<<<nb, kThreads, 0, s>>>(in4, depth, (uint32_t)npix, counts);
     WRS_LAUNCH_CHECK("wrs_unproject_static count");
-    k_scan_counts<<<1, 1024, 0, s>>>(counts, offsets, nb, out->n);
+    k_scan_counts<false><<<1, 1024, 0, s>>>(counts, offsets, nb, out->n, out->capacity, nullptr);
     WRS_LAUNCH_CHECK("wrs_unproject_static scan");
-    k_unproject_write<<<nb, kThreads, 0, s>>>(in4, depth, *cam, radius_mode, voxel_diag, offsets,
-                                              reinterpret_cast<float4*>(out->pos_r),
-                                              reinterpret_cast<float4*>(out->rgba), out->id);
+    k_unproject_write<false><<<nb, kThreads, 0, s>>>(in4, depth, *cam, radius_mode, voxel_diag,
+                                                     offsets, reinterpret_cast<float4*>(out->pos_r),
+                                                     reinterpret_cast<float4*>(out->rgba), out->id,
+                                                     1.0f, 0u, out->capacity);
     WRS_LAUNCH_CHECK("wrs_unproject_static write");
     return WRS_OK;
 }

@@ -90,6 +90,15 @@ def test_host_validation_without_device(wrs):
     assert lib.wrs_unproject(fake, fake, ctypes.byref(_cam(wrs)), 1, 0.0, ctypes.byref(big), fake, 1 << 20, None) == wrs.WRS_ERR_ARG
     # scratch too small
     assert lib.wrs_unproject(fake, fake, ctypes.byref(_cam(wrs)), 0, 0.0, ctypes.byref(big), fake, 1, None) == wrs.WRS_ERR_SCRATCH
+    # append: weight outside (0, 1], ids past 2^32, zero capacity (any other capacity is legal)
+    args = (fake, fake, ctypes.byref(_cam(wrs)), 0, 0.0)
+    assert lib.wrs_unproject_append(*args, 0.0, 0, ctypes.byref(sp), fake, 1 << 20, None, None) == wrs.WRS_ERR_ARG
+    assert lib.wrs_unproject_append(*args, 1.5, 0, ctypes.byref(sp), fake, 1 << 20, None, None) == wrs.WRS_ERR_ARG
+    assert lib.wrs_unproject_append(*args, 1.0, 2**32 - 63, ctypes.byref(sp), fake, 1 << 20, None, None) == wrs.WRS_ERR_ARG
+    assert "2^32" in wrs.last_error()
+    zero = wrs._Splats(fake.value, fake.value, fake.value, None, fake.value, 0)
+    assert lib.wrs_unproject_append(*args, 1.0, 0, ctypes.byref(zero), fake, 1 << 20, None, None) == wrs.WRS_ERR_CAPACITY
+    assert lib.wrs_unproject_append(*args, 1.0, 0, ctypes.byref(sp), fake, 1, None, None) == wrs.WRS_ERR_SCRATCH
     # LBVH: bad leaf size, missing src, small capacity
     bv = wrs._Lbvh(fake.value, 64, 0)
     srt = wrs._Splats(fake.value, fake.value, fake.value, fake.value, fake.value, 64)
