@@ -14,6 +14,9 @@ marshals numpy arrays through ctypes.  Functions and the paper passage each one 
   zero-radius compaction (§4.1).
 * :func:`append_frame`, :func:`accumulate` -- splats of several server frames in one set, the
   accumulation over frames named as future work in §6 (reading: spec S3a).
+* :func:`point_splat` -- the earlier warping the paper compares against (§2, §5, Fig. 3): each
+  sample drawn as a fixed-size pixel square with one depth per point (reading: spec S10).
+* :func:`psnr` -- the image-quality measure used to restate Fig. 3 numerically (spec S10).
 * :func:`trace` -- first-hit / multi-hit ray tracing of the samples as semi-transparent spheres
   with constant colour (Fig. 2 caption, §4), front-to-back compositing (spec S6).
 * :func:`trace_backward` -- the adjoint of that compositing (spec S7; not in the paper).
@@ -88,6 +91,7 @@ def _load():
                                            P, P, ctypes.c_int]
         lib.orc_lbvh.argtypes = [P, P, ctypes.c_float, ctypes.c_int64, ctypes.c_int32, P, P, P, P,
                                  P, P]
+        lib.orc_point_splat.argtypes = [P, P, ctypes.c_int64, ctypes.POINTER(_Cam), ctypes.c_int, P, P]
         lib.orc_default_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -235,6 +239,26 @@ def accumulate(frames, decay: float = 1.0, mode: int = RADIUS_FOOTPRINT,
         npix = int(np.asarray(depth).size)
         acc, _ = append_frame(acc, rgba, depth, cam, float(w[g]), g * npix, None, mode, voxel_diag)
     return acc
+
+
+def point_splat(splats: Splats, cam, size: int = 1):
+    """Point-splat warping of the splats into the client camera (spec S10): returns (rgba float32
+    [H, W, 4], index int64 [H, W] of the point each pixel shows, -1 where none)."""
+    pos_r = _c(splats.pos_r, np.float32)
+    rgba = _c(splats.rgba, np.float32)
+    out = np.zeros((cam.height, cam.width, 4), np.float32)
+    idx = np.zeros((cam.height, cam.width), np.int64)
+    rc = _load().orc_point_splat(pos_r.ctypes.data, rgba.ctypes.data, splats.n, ctypes.byref(_cam(cam)),
+                                 int(size), out.ctypes.data, idx.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"orc_point_splat failed ({rc})")
+    return out, idx
+
+
+def psnr(img: np.ndarray, ref: np.ndarray) -> float:
+    """10 log10(1 / MSE) over all channels of images with values in [0, 1] (binary64)."""
+    mse = float(np.mean((np.asarray(img, np.float64) - np.asarray(ref, np.float64)) ** 2))
+    return float("inf") if mse == 0.0 else 10.0 * np.log10(1.0 / mse)
 
 
 @dataclass

@@ -266,6 +266,60 @@ int64_t orc_unproject(const float* rgba, const float* depth, const orc_camera* c
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* S10: the earlier point-splat warping (§2; compared in §5, Fig. 3): every sample drawn as an    */
+/* s x s pixel square around its projection, one depth per point, nearest (z, k) kept, no blend.  */
+/* ------------------------------------------------------------------------------------------ */
+int orc_point_splat(const float* pos_r, const float* rgba, int64_t n, const orc_camera* cam,
+                    int size, float* rgba_out, int64_t* index_out) {
+    if (!cam || !rgba_out || !index_out || size < 1 || size > 64) return -1;
+    if (n > 0 && (!pos_r || !rgba)) return -1;
+    const int W = cam->width, H = cam->height;
+    if (W <= 0 || H <= 0) return -1;
+    float* zbest = (float*)malloc(sizeof(float) * (size_t)W * (size_t)H);
+    if (!zbest) return -2;
+    for (int64_t i = 0; i < (int64_t)W * H; i++) {
+        zbest[i] = INFINITY;
+        index_out[i] = -1;
+    }
+    const float aspect = (float)W / (float)H;
+    const float sx = cam->tan_half_fovy * aspect;
+    const float half = 0.5f * (float)size;
+    for (int64_t k = 0; k < n; k++) {
+        float q[3];
+        for (int a = 0; a < 3; a++) q[a] = pos_r[4 * k + a] - cam->eye[a];
+        /* depth along the view axis; points at or behind the eye plane are not drawn */
+        float z = fmaf(q[2], cam->fwd[2], fmaf(q[1], cam->fwd[1], q[0] * cam->fwd[0]));
+        if (!(z > 0.0f)) continue;
+        float xr = fmaf(q[2], cam->right[2], fmaf(q[1], cam->right[1], q[0] * cam->right[0]));
+        float yu = fmaf(q[2], cam->up[2], fmaf(q[1], cam->up[1], q[0] * cam->up[0]));
+        float nx = (xr / z) / sx;
+        float ny = (yu / z) / cam->tan_half_fovy;
+        /* pixel-centre coordinates: pixel x has its centre at x (camera convention of S1) */
+        float px = (nx + 1.0f) * (0.5f * (float)W) - 0.5f;
+        float py = (1.0f - ny) * (0.5f * (float)H) - 0.5f;
+        float x0f = ceilf(px - half), y0f = ceilf(py - half);
+        if (!(x0f > -(float)size && x0f < (float)W && y0f > -(float)size && y0f < (float)H)) continue;
+        int x0 = (int)x0f, y0 = (int)y0f;
+        for (int y = y0 < 0 ? 0 : y0; y < y0 + size && y < H; y++) {
+            for (int x = x0 < 0 ? 0 : x0; x < x0 + size && x < W; x++) {
+                int64_t i = (int64_t)y * W + x;
+                /* depth test on (z, k): the nearer point wins, equal depths go to the lower index */
+                if (z < zbest[i] || (z == zbest[i] && k < index_out[i])) {
+                    zbest[i] = z;
+                    index_out[i] = k;
+                }
+            }
+        }
+    }
+    for (int64_t i = 0; i < (int64_t)W * H; i++) {
+        int64_t k = index_out[i];
+        for (int c = 0; c < 4; c++) rgba_out[4 * i + c] = k >= 0 ? rgba[4 * k + c] : 0.0f;
+    }
+    free(zbest);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* S4/S5: sphere test.  Decision in binary32; the binary64 twin feeds only the diagnostic.      */
 /* ------------------------------------------------------------------------------------------ */
 static inline float eff_radius(const float* pos_r, const float* scale, float gscale, int64_t i) {
