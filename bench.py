@@ -406,7 +406,7 @@ def main():
 
     if not args.no_extras:
         extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, world, barrier,
-               max_over_ranks)
+               max_over_ranks, large_vol=vol)
     if rank == 0:
         print(json.dumps(line), flush=True)
     reps.close()
@@ -426,7 +426,7 @@ def _time_ms(torch, fn, reps, warm=3):
 
 
 def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, world, barrier,
-           max_over_ranks):
+           max_over_ranks, large_vol=None):
     dev = torch.device("cuda")
     W = synth.LARGE
     npix_s = W.server_w * W.server_h
@@ -546,6 +546,37 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
                                   "newest (4 unprojections into one set + LBVH over about 8 M "
                                   "splats) + 4 client traces of the union"}
     del win, outs
+
+    # ---------------- image quality, Fig. 3 as numbers: spheres vs fixed-size points ------------
+    from paper_2006_14726_b300.quality import warp_quality
+    if large_vol is not None:
+        srv_q = groups[0][2]
+        angles = (2.0, 5.0, 10.0, 20.0)
+        clis_q = [synth.orbit(srv_q, (0.6, 0.8, 0.0), a) for a in angles]
+        blobs = synth.gaussian_volume_device(256, 64, 2000)
+        scenes = {"fourier_512_ramp_tf": (large_vol, synth.tf_ramp()),
+                  "blobs_256_iso_tf": (blobs, synth.tf_iso())}
+        q = {"metric": "PSNR dB vs the ray caster at the client pose (all four premultiplied "
+                       "channels)", "server_and_client": [srv_q.width, srv_q.height],
+             "angles_deg": list(angles)}
+        for name, (v, tf_np) in scenes.items():
+            rows = warp_quality(v, torch.from_numpy(tf_np).to(dev), srv_q, clis_q)
+            q[name] = [{k: (round(x, 3) if x is not None else None) for k, x in r.items()}
+                       for r in rows]
+        del blobs
+        # cost of the two warps on the same 1080p frame (one client view)
+        sp_q = wrs.unproject(groups[0][0], groups[0][1], srv_q)
+        bvh_q, srt_q = wrs.build_lbvh(sp_q, leaf)
+        out_q = torch.empty(W.client_h, W.client_w, 4, device=dev)
+        psc = torch.empty(wrs.point_splat_scratch_bytes(W.client_w, W.client_h), dtype=torch.uint8,
+                          device=dev)
+        c_q = wrs.make_camera(clis_q[-1])
+        q["ms_per_view"] = {
+            "spheres_trace": _time_ms(torch, lambda: wrs.trace(bvh_q, srt_q, c_q, params, out=out_q), 20),
+            "points_1px": _time_ms(torch, lambda: wrs.point_splat(sp_q, c_q, 1, out=out_q, scratch=psc), 20),
+            "points_3px": _time_ms(torch, lambda: wrs.point_splat(sp_q, c_q, 3, out=out_q, scratch=psc), 20)}
+        line["quality"] = q
+        del sp_q, bvh_q, srt_q, out_q, psc
 
     # ---------------- forward and forward+backward (differentiable renderer) -------------------
     D = synth.DIFF

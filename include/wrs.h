@@ -243,6 +243,19 @@ int wrs_trace_backward(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_
                        float global_scale, const float* dL_drgba, float* g_rgba,
                        float* g_opacity, float* g_scale, int32_t* status, wrs_stream_t stream);
 
+/* The earlier 2.5D warping the paper compares against (§2, §5, Fig. 3): every splat of a set
+ * (compacted or sorted; index = its position in that set) drawn as a point_size x point_size pixel
+ * square around its projection into cam, one depth per point (the view-axis distance z, points
+ * with z <= 0 dropped), the nearest point kept per pixel (ties: lower index), no blending; spec S10
+ * gives the binary32 projection and the covering rule.  rgba_out: [H][W][4] premultiplied, the
+ * winner's colour or 0; index_out: [H][W] the winner's index or -1 (may be NULL).  point_size in
+ * 1..64.  Scratch: wrs_point_splat_scratch_bytes(W, H) (one 64-bit depth key per pixel), 8-byte
+ * aligned.  No OpenGL: the rasterisation is restated as a CUDA kernel. */
+size_t wrs_point_splat_scratch_bytes(int32_t width, int32_t height);
+int wrs_point_splat(const wrs_splats* splats, const wrs_camera* cam, int32_t point_size,
+                    float* rgba_out, int32_t* index_out, void* scratch, size_t scratch_bytes,
+                    wrs_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -112,6 +112,8 @@ _sig("wrs_unproject_scratch_bytes", _Z, _I, _I)
 _sig("wrs_unproject", _I, _P, _P, ctypes.POINTER(Camera), _I, _F, ctypes.POINTER(_Splats), _P, _Z, _P)
 _sig("wrs_unproject_append", _I, _P, _P, ctypes.POINTER(Camera), _I, _F, _F, _U,
      ctypes.POINTER(_Splats), _P, _Z, _P, _P)
+_sig("wrs_point_splat_scratch_bytes", _Z, _I, _I)
+_sig("wrs_point_splat", _I, ctypes.POINTER(_Splats), ctypes.POINTER(Camera), _I, _P, _P, _P, _Z, _P)
 _sig("wrs_unproject_static", _I, _P, _P, ctypes.POINTER(Camera), _I, _F, ctypes.POINTER(_Splats), _P)
 _sig("wrs_lbvh_bytes", _Z, _U, _U)
 _sig("wrs_lbvh_scratch_bytes", _Z, _U, _U)
@@ -322,6 +324,29 @@ def unproject_append(rgba: torch.Tensor, depth: torch.Tensor, cam, out: SplatBuf
                                      float(voxel_diag), float(weight), int(id_base),
                                      ctypes.byref(sp), _ptr(scratch), scratch.numel(), _ptr(status),
                                      _stream(stream)), "wrs_unproject_append")
+    return out
+
+
+def point_splat_scratch_bytes(width: int, height: int) -> int:
+    return int(_lib.wrs_point_splat_scratch_bytes(int(width), int(height)))
+
+
+def point_splat(splats: SplatBuffers, cam, point_size: int = 1, out: Optional[torch.Tensor] = None,
+                index: Optional[torch.Tensor] = None, scratch: Optional[torch.Tensor] = None,
+                stream=None) -> torch.Tensor:
+    """The earlier warping the paper compares against (§2, §5, Fig. 3): each splat drawn as a
+    point_size x point_size pixel square with one depth per point, nearest kept (wrs_point_splat).
+    Returns premultiplied RGBA [H,W,4]; ``index`` (int32 [H,W], optional) receives the winner."""
+    c = _cam(cam)
+    dev = splats.pos_r.device
+    if out is None:
+        out = torch.empty(c.height, c.width, 4, dtype=torch.float32, device=dev)
+    if scratch is None:
+        scratch = _scratch(point_splat_scratch_bytes(c.width, c.height), dev)
+    sp = splats.c()
+    _check(_lib.wrs_point_splat(ctypes.byref(sp), ctypes.byref(c), int(point_size), _ptr(out),
+                                _ptr(index), _ptr(scratch), scratch.numel(), _stream(stream)),
+           "wrs_point_splat")
     return out
 
 

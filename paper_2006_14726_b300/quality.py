@@ -1,0 +1,46 @@
+"""Image quality of the warped views, the paper's Fig. 3 comparison restated as numbers.
+
+Fig. 3 shows, for a sequence of client poses moving away from the server's, the view warped from
+one server image by (a) ray-traced sphere splats and (b) the earlier point rasterisation, next to
+the volume rendered directly at each pose.  Here each warped view is scored by its PSNR against the
+server ray caster run at the client pose (spec S10): all images come from this library's kernels
+(wrs_raycast_volume, wrs_unproject, wrs_build_lbvh, wrs_trace, wrs_point_splat); the PSNR itself is
+evaluation, computed with torch.
+"""
+from __future__ import annotations
+
+import math
+from typing import Dict, Iterable, List
+
+import torch
+
+from . import (TraceParams, build_lbvh, make_camera, point_splat, raycast_volume, trace,
+               unproject)
+
+
+def psnr(img: torch.Tensor, ref: torch.Tensor) -> float:
+    """10 log10(1 / MSE) over all channels (images in [0, 1])."""
+    mse = float(torch.mean((img.double() - ref.double()) ** 2))
+    return math.inf if mse == 0.0 else 10.0 * math.log10(1.0 / mse)
+
+
+def warp_quality(vol: torch.Tensor, tf: torch.Tensor, srv, clients: Iterable,
+                 point_sizes: Iterable[int] = (1, 2, 3), max_hits: Iterable[int] = (0, 1),
+                 step_vox: float = 0.5, tau: float = 0.1, leaf_size: int = 1) -> List[Dict]:
+    """PSNR of every warping method for each client pose; one dict per pose."""
+    rgba, depth = raycast_volume(vol, tf, srv, step_vox, tau)
+    sp = unproject(rgba, depth, srv)
+    bvh, srt = build_lbvh(sp, leaf_size)
+    rows = []
+    for cli in clients:
+        c = make_camera(cli)
+        truth, _ = raycast_volume(vol, tf, c, step_vox, tau)
+        row = {}
+        for h in max_hits:
+            img = trace(bvh, srt, c, TraceParams(max_hits=h, width=4))
+            row[f"spheres_H{h}"] = psnr(img, truth)
+        for s in point_sizes:
+            row[f"points_{s}px"] = psnr(point_splat(sp, c, s), truth)
+        row["server_view_unwarped"] = psnr(rgba, truth) if (c.width, c.height) == (srv.width, srv.height) else None
+        rows.append(row)
+    return rows

@@ -100,6 +100,16 @@ def tf_ramp() -> np.ndarray:
     return np.stack([x, 1 - np.abs(2 * x - 1), 1 - x, x], axis=1).astype(np.float32)
 
 
+def tf_iso(lo: float = 0.45, hi: float = 0.55, alpha: float = 0.9) -> np.ndarray:
+    """256-entry transfer function for iso-surface-like renderings (a narrow band of values mapped
+    to high opacity, the kind of transfer function the warping works best with, §2): colour as
+    tf_ramp, alpha = ``alpha`` for x in [lo, hi] and 0 elsewhere."""
+    t = tf_ramp()
+    x = np.arange(256, dtype=np.float64) / 255.0
+    t[:, 3] = np.where((x >= lo) & (x <= hi), alpha, 0.0).astype(np.float32)
+    return t
+
+
 def gaussian_volume(n: int, nblobs: int, seed: int) -> np.ndarray:
     """Sum of isotropic Gaussian blobs at the voxel centres, divided by its maximum, float32."""
     rng = np.random.default_rng(seed)
