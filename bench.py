@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--impl", default="wrs", choices=["wrs", "reference"])
     ap.add_argument("--no-extras", action="store_true",
                     help="skip batched / fwd+bwd / e2e / cpu baseline (main line only)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the launch the tuner picks on B300 (leaf 1, K 1, 128 threads per "
+                         "pixel, 4-wide nodes) instead of tuning; for profiler runs, where tuning "
+                         "times are distorted")
     return ap.parse_args()
 
 
@@ -294,7 +298,10 @@ def main():
 
     # ---------------- autotune (untimed; the knobs do not change results) ----------------------
     sp = wrs.unproject(groups[0][0], groups[0][1], groups[0][2])
-    tuned = autotune.tune_trace(sp, groups[0][3], use_cache=False)
+    if args.no_autotune:
+        tuned = {"leaf": 1, "k_chunk": 1, "block": 128, "schedule": 0, "width": 4}
+    else:
+        tuned = autotune.tune_trace(sp, groups[0][3], use_cache=False)
     leaf, kc, block, sched = tuned["leaf"], tuned["k_chunk"], tuned["block"], tuned["schedule"]
     width = tuned["width"]
     params = wrs.TraceParams(max_hits=0, t_stop=1e-5, k_chunk=kc, block=block, schedule=sched,
@@ -390,7 +397,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(W, statistics.mean(n_splats), {
-                "leaf_size": leaf, "k_chunk": kc, "block": block, "autotuned": True,
+                "leaf_size": leaf, "k_chunk": kc, "block": block, "autotuned": not args.no_autotune,
                 "schedule": ["one thread per pixel", "persistent, lane refill"][sched],
                 "bvh_width": width,
                 "l2": "flushed before every step (256 MiB write outside the timed events)",
@@ -554,13 +561,13 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
         angles = (2.0, 5.0, 10.0, 20.0)
         clis_q = [synth.orbit(srv_q, (0.6, 0.8, 0.0), a) for a in angles]
         blobs = synth.gaussian_volume_device(256, 64, 2000)
-        scenes = {"fourier_512_ramp_tf": (large_vol, synth.tf_ramp()),
-                  "blobs_256_iso_tf": (blobs, synth.tf_iso())}
+        scenes = {"fourier_512_ramp_tf": (large_vol, synth.tf_ramp(), 3 ** 0.5 / 512),
+                  "blobs_256_iso_tf": (blobs, synth.tf_iso(), 3 ** 0.5 / 256)}
         q = {"metric": "PSNR dB vs the ray caster at the client pose (all four premultiplied "
                        "channels)", "server_and_client": [srv_q.width, srv_q.height],
              "angles_deg": list(angles)}
-        for name, (v, tf_np) in scenes.items():
-            rows = warp_quality(v, torch.from_numpy(tf_np).to(dev), srv_q, clis_q)
+        for name, (v, tf_np, vd) in scenes.items():
+            rows = warp_quality(v, torch.from_numpy(tf_np).to(dev), srv_q, clis_q, voxel_diag=vd)
             q[name] = [{k: (round(x, 3) if x is not None else None) for k, x in r.items()}
                        for r in rows]
         del blobs

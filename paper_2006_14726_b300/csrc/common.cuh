@@ -118,6 +118,12 @@ struct BoxRay {
     float ix, iy, iz;      // 1 / d (guarded against zero components)
     float lx, ly, lz;      // -(o + eps) / d  : offset for the low planes
     float hx, hy, hz;      // -(o - eps) / d  : offset for the high planes
+    // the same planes ordered by the ray's direction: the near one of each axis is the low plane
+    // when 1/d >= 0, else the high one (used by the 4-wide nodes, whose low and high planes sit in
+    // separate float4s, so that the ordering costs an address offset instead of min/max pairs)
+    float nx, ny, nz;      // offset of the near plane per axis
+    float fx, fy, fz;      // offset of the far plane per axis
+    int sx, sy, sz;        // 0 if the near plane is the low one, 3 if it is the high one
 };
 
 __device__ __forceinline__ BoxRay make_box_ray(const Ray& r, float eps) {
@@ -132,16 +138,44 @@ __device__ __forceinline__ BoxRay make_box_ray(const Ray& r, float eps) {
     b.hx = -(r.o.x - eps) * b.ix;
     b.hy = -(r.o.y - eps) * b.iy;
     b.hz = -(r.o.z - eps) * b.iz;
+    const bool px = b.ix >= 0.0f, py = b.iy >= 0.0f, pz = b.iz >= 0.0f;
+    b.nx = px ? b.lx : b.hx;  b.fx = px ? b.hx : b.lx;  b.sx = px ? 0 : 3;
+    b.ny = py ? b.ly : b.hy;  b.fy = py ? b.hy : b.ly;  b.sy = py ? 0 : 3;
+    b.nz = pz ? b.lz : b.hz;  b.fz = pz ? b.hz : b.lz;  b.sz = pz ? 0 : 3;
     return b;
 }
 
+// Three-input minimum / maximum (one instruction on sm_100 and later).
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// Slab test of one box given by its low and high corners (either ray direction).
 __device__ __forceinline__ void box_test(const BoxRay& r, float lox, float loy, float loz,
                                          float hix, float hiy, float hiz, float& tn, float& tf) {
     const float ax = fmaf(lox, r.ix, r.lx), bx = fmaf(hix, r.ix, r.hx);
     const float ay = fmaf(loy, r.iy, r.ly), by = fmaf(hiy, r.iy, r.hy);
     const float az = fmaf(loz, r.iz, r.lz), bz = fmaf(hiz, r.iz, r.hz);
-    tn = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), 0.0f));
-    tf = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fmaxf(az, bz));
+    tn = max3f(fminf(ax, bx), fminf(ay, by), fmaxf(fminf(az, bz), 0.0f));
+    tf = min3f(fmaxf(ax, bx), fmaxf(ay, by), fmaxf(az, bz));
+}
+
+// The same test given the box's near and far plane coordinates for this ray (selected by the
+// sign of its direction): equal results for any box whose low corner is not above its high one.
+__device__ __forceinline__ void box_test_nf(const BoxRay& r, float nx, float ny, float nz,
+                                            float fx, float fy, float fz, float& tn, float& tf) {
+    const float ax = fmaf(nx, r.ix, r.nx), bx = fmaf(fx, r.ix, r.fx);
+    const float ay = fmaf(ny, r.iy, r.ny), by = fmaf(fy, r.iy, r.fy);
+    const float az = fmaf(nz, r.iz, r.nz), bz = fmaf(fz, r.iz, r.fz);
+    tn = fmaxf(max3f(ax, ay, az), 0.0f);
+    tf = min3f(bx, by, bz);
 }
 
 // Traversal epsilon: far above the binary32 error of the sphere test (a few units in the last

@@ -150,14 +150,17 @@ __device__ __forceinline__ int64_t visit_node4(const Scene& sc, const Ray& ray,
     if (ref + 1 >= m) return -2;  // not an internal node of this tree
     const float lower = has_last ? last_key : -kInf;
     const float4* w = sc.wide + 8 * (size_t)ref;
-    const float4 lx = __ldg(w + 0), ly = __ldg(w + 1), lz = __ldg(w + 2);
-    const float4 hx = __ldg(w + 3), hy = __ldg(w + 4), hz = __ldg(w + 5), rf = __ldg(w + 6);
+    // low planes at w[0..2], high planes at w[3..5]: the ray's near plane of each axis is picked
+    // by address (br.s* = 0 or 3), so no per-box min/max orders the slab distances
+    const float4 nx = __ldg(w + br.sx), ny = __ldg(w + 1 + br.sy), nz = __ldg(w + 2 + br.sz);
+    const float4 fx = __ldg(w + 3 - br.sx), fy = __ldg(w + 4 - br.sy), fz = __ldg(w + 5 - br.sz);
+    const float4 rf = __ldg(w + 6);
     if (COUNT) { cnt.nodes++; cnt.boxes += 4; }
     float tn[4], tf[4];
-    wrs::box_test(br, lx.x, ly.x, lz.x, hx.x, hy.x, hz.x, tn[0], tf[0]);
-    wrs::box_test(br, lx.y, ly.y, lz.y, hx.y, hy.y, hz.y, tn[1], tf[1]);
-    wrs::box_test(br, lx.z, ly.z, lz.z, hx.z, hy.z, hz.z, tn[2], tf[2]);
-    wrs::box_test(br, lx.w, ly.w, lz.w, hx.w, hy.w, hz.w, tn[3], tf[3]);
+    wrs::box_test_nf(br, nx.x, ny.x, nz.x, fx.x, fy.x, fz.x, tn[0], tf[0]);
+    wrs::box_test_nf(br, nx.y, ny.y, nz.y, fx.y, fy.y, fz.y, tn[1], tf[1]);
+    wrs::box_test_nf(br, nx.z, ny.z, nz.z, fx.z, fy.z, fz.z, tn[2], tf[2]);
+    wrs::box_test_nf(br, nx.w, ny.w, nz.w, fx.w, fy.w, fz.w, tn[3], tf[3]);
     uint32_t r[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
                      __float_as_uint(rf.w)};
     float key[4];

@@ -14,8 +14,8 @@ from typing import Dict, Iterable, List
 
 import torch
 
-from . import (TraceParams, build_lbvh, make_camera, point_splat, raycast_volume, trace,
-               unproject)
+from . import (RADIUS_VOXEL, TraceParams, build_lbvh, make_camera, point_splat, raycast_volume,
+               trace, unproject)
 
 
 def psnr(img: torch.Tensor, ref: torch.Tensor) -> float:
@@ -26,21 +26,32 @@ def psnr(img: torch.Tensor, ref: torch.Tensor) -> float:
 
 def warp_quality(vol: torch.Tensor, tf: torch.Tensor, srv, clients: Iterable,
                  point_sizes: Iterable[int] = (1, 2, 3), max_hits: Iterable[int] = (0, 1),
+                 sphere_scales: Iterable[float] = (1.0, 2.0), voxel_diag: float = 0.0,
                  step_vox: float = 0.5, tau: float = 0.1, leaf_size: int = 1) -> List[Dict]:
-    """PSNR of every warping method for each client pose; one dict per pose."""
+    """PSNR of every warping method for each client pose; one dict per pose.
+
+    Sphere variants: the footprint radius scaled by each of ``sphere_scales`` (composited with
+    each of ``max_hits``; 1 = the paper's first-hit query), and, if ``voxel_diag`` > 0, the
+    paper's own radius rule (half a voxel diagonal, §4.1) with first hit.  Point variants: each
+    of ``point_sizes`` pixels."""
     rgba, depth = raycast_volume(vol, tf, srv, step_vox, tau)
     sp = unproject(rgba, depth, srv)
-    bvh, srt = build_lbvh(sp, leaf_size)
+    trees = {f"spheres_x{g:g}": build_lbvh(sp, leaf_size, global_scale=g) for g in sphere_scales}
+    if voxel_diag > 0.0:
+        spv = unproject(rgba, depth, srv, RADIUS_VOXEL, voxel_diag)
+        trees["spheres_voxel"] = build_lbvh(spv, leaf_size)
     rows = []
     for cli in clients:
         c = make_camera(cli)
         truth, _ = raycast_volume(vol, tf, c, step_vox, tau)
         row = {}
-        for h in max_hits:
-            img = trace(bvh, srt, c, TraceParams(max_hits=h, width=4))
-            row[f"spheres_H{h}"] = psnr(img, truth)
+        for name, (bvh, srt) in trees.items():
+            for h in (max_hits if name != "spheres_voxel" else (1,)):
+                img = trace(bvh, srt, c, TraceParams(max_hits=h, width=4))
+                row[f"{name}_H{h}"] = psnr(img, truth)
         for s in point_sizes:
             row[f"points_{s}px"] = psnr(point_splat(sp, c, s), truth)
-        row["server_view_unwarped"] = psnr(rgba, truth) if (c.width, c.height) == (srv.width, srv.height) else None
+        same = (c.width, c.height) == (srv.width, srv.height)
+        row["server_view_unwarped"] = psnr(rgba, truth) if same else None
         rows.append(row)
     return rows
