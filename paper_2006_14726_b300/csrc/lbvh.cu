@@ -7,7 +7,8 @@
 //   k_karras                          : binary radix tree over leaf keys (Karras 2012)
 //   k_leaves_refit                    : gathers the splats into leaf order with their effective
 //                                       radius, computes leaf boxes and refits the internal nodes
-//                                       bottom-up (second thread to reach a node continues)
+//                                       bottom-up (second thread to reach a node continues); the
+//                                       same climb fills the 4-wide nodes
 //
 // The splat count is read on the device from the header, so the whole build runs without a host
 // synchronisation and can be captured into a CUDA graph.  No kernel waits on another block.
@@ -399,6 +400,22 @@ __device__ __forceinline__ void store_box(float4* nodes, uint32_t node, uint32_t
     __stcg(f + 3, hi[0]); __stcg(f + 4, hi[1]); __stcg(f + 5, hi[2]);
 }
 
+// ---- 4-wide nodes ---------------------------------------------------------------------------
+// 4-wide node i lists the grandchildren of binary node i in structure-of-arrays order (float4 q of
+// the node holds plane q -- low x, y, z, high x, y, z -- of all four entries; float4 6 holds the
+// four references), so that a traversal step loads one coordinate of all four boxes per float4.
+// Fixed slots: child c's children go to slots 2c and 2c + 1; a leaf child stands for itself in
+// slot 2c and slot 2c + 1 is unused (reference kNoChild).  The refit fills them: the thread that
+// holds the final box of a node or leaf X writes it into the 4-wide node of X's grandparent, and a
+// leaf also into its parent's.  These are plain stores off the climb's critical path.
+__device__ __forceinline__ void wide_entry(float4* __restrict__ wide, uint32_t i, uint32_t e,
+                                           const float lo[3], const float hi[3], uint32_t ref) {
+    float* w = reinterpret_cast<float*>(wide + 8 * (size_t)i) + e;
+    w[0] = lo[0]; w[4] = lo[1]; w[8] = lo[2];
+    w[12] = hi[0]; w[16] = hi[1]; w[20] = hi[2];
+    w[24] = __uint_as_float(ref);
+}
+
 __global__ void __launch_bounds__(kRefitBlock) k_leaves_refit(
     const uint32_t* __restrict__ order, const float4* __restrict__ pos_r,
     const float4* __restrict__ rgba, const uint32_t* __restrict__ id,
@@ -406,7 +423,7 @@ __global__ void __launch_bounds__(kRefitBlock) k_leaves_refit(
     float4* __restrict__ nodes, const uint32_t* __restrict__ leaf_parent,
     const uint32_t* __restrict__ node_parent, const uint2* __restrict__ node_range,
     uint32_t* __restrict__ visit, float4* __restrict__ s_pos, float4* __restrict__ s_rgba,
-    uint32_t* __restrict__ s_id, uint32_t* __restrict__ s_src) {
+    uint32_t* __restrict__ s_id, uint32_t* __restrict__ s_src, float4* __restrict__ wide) {
     __shared__ uint32_t sh_cnt[kRefitBlock];
     __shared__ float sh_box[kRefitBlock][12];  // child boxes of local internal node j0 + t
     const uint32_t n = hdr->n, m = hdr->m, leaf = hdr->leaf;
@@ -432,11 +449,20 @@ __global__ void __launch_bounds__(kRefitBlock) k_leaves_refit(
     }
     if (m < 2) return;
     uint32_t pp = leaf_parent[j];
+    uint32_t xref = kLeafBit | j;  // reference of the leaf or node whose box the thread holds
     bool local = true;  // ancestors of a node that spans blocks span blocks too
     while (true) {
         const uint32_t node = pp >> 1, slot = pp & 1u;
         if (node + 1 >= m) return;  // never taken for a well-formed tree
+        const uint32_t gp = node != 0 ? node_parent[node] : 0u;  // node's own link to its parent
         store_box(nodes, node, slot, lo, hi);  // the traversal reads it after the kernel
+        if (xref & kLeafBit) {  // a leaf child stands for itself in its parent's 4-wide node
+            wide_entry(wide, node, 2 * slot, lo, hi, xref);
+            reinterpret_cast<float*>(wide + 8 * (size_t)node)[24 + 2 * slot + 1] =
+                __uint_as_float(wrs::kNoChild);
+        }
+        if (node != 0 && (gp >> 1) + 1 < m)  // a grandchild of gp's node
+            wide_entry(wide, gp >> 1, 2 * (gp & 1u) + slot, lo, hi, xref);
         const uint2 rg = node_range[node];
         float a[12];
         if (local && rg.x >= j0 && rg.y <= j1 && node >= j0 && node <= j1) {
@@ -460,71 +486,9 @@ __global__ void __launch_bounds__(kRefitBlock) k_leaves_refit(
         lo[0] = fminf(a[0], a[6]); lo[1] = fminf(a[1], a[7]); lo[2] = fminf(a[2], a[8]);
         hi[0] = fmaxf(a[3], a[9]); hi[1] = fmaxf(a[4], a[10]); hi[2] = fmaxf(a[5], a[11]);
         if (node == 0) return;
-        pp = node_parent[node];
+        xref = node;
+        pp = gp;
     }
-}
-
-// ---- 4-wide nodes ---------------------------------------------------------------------------
-// 4-wide node i lists the grandchildren of binary node i (a leaf child stands for itself), in
-// structure-of-arrays order so that a traversal step loads one coordinate of all four boxes per
-// float4.  Runs after the refit, when every binary node holds its final child boxes.
-__global__ void __launch_bounds__(256) k_widen(const LbvhHeader* __restrict__ hdr,
-                                               const float4* __restrict__ nodes,
-                                               float4* __restrict__ wide) {
-    const uint32_t m = hdr->m;
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m < 2 || i + 1 >= m) return;
-    float lo[3][4], hi[3][4];
-    uint32_t ref[4];
-#pragma unroll
-    for (int e = 0; e < 4; e++) {
-        lo[0][e] = lo[1][e] = lo[2][e] = INFINITY;
-        hi[0][e] = hi[1][e] = hi[2][e] = -INFINITY;
-        ref[e] = wrs::kNoChild;  // unused entry: the traversal skips it by its reference
-    }
-    // one binary node as 16 floats, loaded with four 16-byte loads
-    auto load = [&](uint32_t k, float (&f)[16]) {
-        const float4* p = nodes + 4 * (size_t)k;
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const float4 v = __ldg(p + q);
-            f[4 * q] = v.x; f[4 * q + 1] = v.y; f[4 * q + 2] = v.z; f[4 * q + 3] = v.w;
-        }
-    };
-    float f[16];
-    load(i, f);
-    // fixed slots: child c's entries go to slots 2c and 2c + 1 (a leaf child uses slot 2c only)
-#pragma unroll
-    for (int c = 0; c < 2; c++) {
-        const uint32_t r = __float_as_uint(f[12 + c]);
-        if ((r & kLeafBit) || r + 1 >= m) {  // a leaf child: its own entry
-#pragma unroll
-            for (int a = 0; a < 3; a++) { lo[a][2 * c] = f[6 * c + a]; hi[a][2 * c] = f[6 * c + 3 + a]; }
-            ref[2 * c] = r;
-        } else {                             // an internal child: its two children
-            float g[16];
-            load(r, g);
-#pragma unroll
-            for (int gc = 0; gc < 2; gc++) {
-#pragma unroll
-                for (int a = 0; a < 3; a++) {
-                    lo[a][2 * c + gc] = g[6 * gc + a];
-                    hi[a][2 * c + gc] = g[6 * gc + 3 + a];
-                }
-                ref[2 * c + gc] = __float_as_uint(g[12 + gc]);
-            }
-        }
-    }
-    float4* w = wide + 8 * (size_t)i;
-    w[0] = make_float4(lo[0][0], lo[0][1], lo[0][2], lo[0][3]);
-    w[1] = make_float4(lo[1][0], lo[1][1], lo[1][2], lo[1][3]);
-    w[2] = make_float4(lo[2][0], lo[2][1], lo[2][2], lo[2][3]);
-    w[3] = make_float4(hi[0][0], hi[0][1], hi[0][2], hi[0][3]);
-    w[4] = make_float4(hi[1][0], hi[1][1], hi[1][2], hi[1][3]);
-    w[5] = make_float4(hi[2][0], hi[2][1], hi[2][2], hi[2][3]);
-    w[6] = make_float4(__uint_as_float(ref[0]), __uint_as_float(ref[1]), __uint_as_float(ref[2]),
-                       __uint_as_float(ref[3]));
-    w[7] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 }  // namespace
@@ -611,11 +575,9 @@ int wrs_build_lbvh(const wrs_splats* in, const float* radius_scale, float global
                                       S.node_parent, S.node_range, S.visit,
                                       reinterpret_cast<float4*>(sorted->pos_r),
                                       reinterpret_cast<float4*>(sorted->rgba), sorted->id,
-                                      sorted->src);
+                                      sorted->src,
+                                      nodes + 4 * (size_t)wrs::lbvh_binary_slots(cap, leaf));
     WRS_LAUNCH_CHECK("wrs_build_lbvh refit");
-    float4* wide = nodes + 4 * (size_t)wrs::lbvh_binary_slots(cap, leaf);
-    k_widen<<<gm, 256, 0, s>>>(hdr, nodes, wide);
-    WRS_LAUNCH_CHECK("wrs_build_lbvh widen");
     return WRS_OK;
 }
 
