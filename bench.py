@@ -554,6 +554,35 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
                                   "splats) + 4 client traces of the union"}
     del win, outs
 
+    # ---------------- mid workload: trace only, 1024^2 client, 262 k splats (median over poses) --
+    M = synth.MID
+    vol_m = synth.gaussian_volume_device(M.vol_n, M.vol_param, M.seed + rank)
+    srv_m = M.server_cam()
+    rgba_m, depth_m = wrs.raycast_volume(vol_m, torch.from_numpy(synth.tf_ramp()).to(dev), srv_m)
+    del vol_m
+    sp_m = wrs.unproject(rgba_m, depth_m, srv_m)
+    bvh_m, srt_m = wrs.build_lbvh(sp_m, leaf)
+    cams_m = [wrs.make_camera(c) for c in M.client_poses(seed_offset=rank)]
+    out_m = torch.empty(M.client_h, M.client_w, 4, device=dev)
+    per_pose = []
+    for c in cams_m:
+        per_pose.append(_time_ms(torch, lambda: wrs.trace(bvh_m, srt_m, c, params, out=out_m), 10))
+    ms_m = max_over_ranks(statistics.median(per_pose))
+    line["mid"] = {"splats": sp_m.count(), "client": [M.client_w, M.client_h], "poses": len(cams_m),
+                   "trace_ms_median": ms_m,
+                   "trace_mrays_s": world * M.client_w * M.client_h / (ms_m * 1e-3) / 1e6,
+                   "lbvh_ms": max_over_ranks(_time_ms(torch, lambda: wrs.build_lbvh(
+                       sp_m, leaf, bvh=bvh_m, sorted=srt_m), 10))}
+    if rank == 0 and world == 1:
+        import oracle
+        oracle.build()
+        t, r, det = oracle_step_time(rgba_m.cpu().numpy(), depth_m.cpu().numpy(), srv_m,
+                                     M.client_poses()[:2], ray_stride=8,
+                                     threads=oracle.default_threads())
+        line["mid"]["cpu_oracle_trace_mrays_s"] = r / det["trace_s_extrapolated"] / 1e6
+        line["mid"]["cpu_oracle_bvh_s"] = det["bvh_s"]
+    del sp_m, bvh_m, srt_m, out_m
+
     # ---------------- image quality, Fig. 3 as numbers: spheres vs fixed-size points ------------
     from paper_2006_14726_b300.quality import warp_quality
     if large_vol is not None:
