@@ -17,6 +17,8 @@ marshals numpy arrays through ctypes.  Functions and the paper passage each one 
 * :func:`point_splat` -- the earlier warping the paper compares against (§2, §5, Fig. 3): each
   sample drawn as a fixed-size pixel square with one depth per point (reading: spec S10).
 * :func:`psnr` -- the image-quality measure used to restate Fig. 3 numerically (spec S10).
+* :func:`encode`, :func:`decode` -- the 64-bit quantised position + radius word and the 32-bit
+  colour the server sends (§4.1, §6; bit layout: reading of spec S11).
 * :func:`trace` -- first-hit / multi-hit ray tracing of the samples as semi-transparent spheres
   with constant colour (Fig. 2 caption, §4), front-to-back compositing (spec S6).
 * :func:`trace_backward` -- the adjoint of that compositing (spec S7; not in the paper).
@@ -92,6 +94,8 @@ def _load():
         lib.orc_lbvh.argtypes = [P, P, ctypes.c_float, ctypes.c_int64, ctypes.c_int32, P, P, P, P,
                                  P, P]
         lib.orc_point_splat.argtypes = [P, P, ctypes.c_int64, ctypes.POINTER(_Cam), ctypes.c_int, P, P]
+        lib.orc_encode.argtypes = [P, P, ctypes.c_int64, P, P, ctypes.c_float, P, P]
+        lib.orc_decode.argtypes = [P, P, ctypes.c_int64, P, P, ctypes.c_float, P, P]
         lib.orc_default_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -259,6 +263,36 @@ def psnr(img: np.ndarray, ref: np.ndarray) -> float:
     """10 log10(1 / MSE) over all channels of images with values in [0, 1] (binary64)."""
     mse = float(np.mean((np.asarray(img, np.float64) - np.asarray(ref, np.float64)) ** 2))
     return float("inf") if mse == 0.0 else 10.0 * np.log10(1.0 / mse)
+
+
+def encode(splats: Splats, lo, hi, r_max: float):
+    """Quantise splats into 64-bit position + radius words and 32-bit colours (spec S11).
+    Returns (word uint64 [N], color uint32 [N])."""
+    pos_r = _c(splats.pos_r, np.float32)
+    rgba = _c(splats.rgba, np.float32)
+    lo = _c(lo, np.float32)
+    hi = _c(hi, np.float32)
+    word = np.zeros(splats.n, np.uint64)
+    color = np.zeros(splats.n, np.uint32)
+    if _load().orc_encode(pos_r.ctypes.data, rgba.ctypes.data, splats.n, lo.ctypes.data, hi.ctypes.data,
+                          float(r_max), word.ctypes.data, color.ctypes.data) != 0:
+        raise ValueError("orc_encode: bad box or radius bound")
+    return word, color
+
+
+def decode(word: np.ndarray, color: np.ndarray, lo, hi, r_max: float) -> Splats:
+    """Splats from the words and colours of :func:`encode` (spec S11); id = stream index."""
+    word = _c(word, np.uint64)
+    color = _c(color, np.uint32)
+    lo = _c(lo, np.float32)
+    hi = _c(hi, np.float32)
+    n = word.size
+    pos_r = np.zeros((n, 4), np.float32)
+    rgba = np.zeros((n, 4), np.float32)
+    if _load().orc_decode(word.ctypes.data, color.ctypes.data, n, lo.ctypes.data, hi.ctypes.data,
+                          float(r_max), pos_r.ctypes.data, rgba.ctypes.data) != 0:
+        raise ValueError("orc_decode failed")
+    return Splats(pos_r, rgba, np.arange(n, dtype=np.uint32))
 
 
 @dataclass

@@ -320,6 +320,68 @@ int orc_point_splat(const float* pos_r, const float* rgba, int64_t n, const orc_
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* S11: the 64-bit position + radius word and the 32-bit colour the server sends (§4.1, §6).      */
+/* ------------------------------------------------------------------------------------------ */
+static uint32_t quant_floor(float u, uint32_t top) {
+    if (!(u == u) || u == INFINITY || u == -INFINITY) return 0;
+    float f = floorf(u);
+    if (f < 0.0f) return 0;
+    if (f > (float)top) return top;
+    return (uint32_t)f;
+}
+
+int orc_encode(const float* pos_r, const float* rgba, int64_t n, const float lo[3],
+               const float hi[3], float r_max, uint64_t* word, uint32_t* color) {
+    if (n < 0 || (n > 0 && (!pos_r || !rgba || !word || !color))) return -1;
+    float inv[3];
+    for (int a = 0; a < 3; a++) {
+        float ext = hi[a] - lo[a];
+        if (!(ext > 0.0f) || ext == INFINITY) return -1;
+        inv[a] = 131072.0f / ext;
+    }
+    if (!(r_max > 0.0f) || r_max == INFINITY) return -1;
+    const float rinv = 8191.0f / r_max;
+    for (int64_t k = 0; k < n; k++) {
+        uint64_t q[3];
+        for (int a = 0; a < 3; a++) q[a] = quant_floor((pos_r[4 * k + a] - lo[a]) * inv[a], 131071u);
+        /* the radius is rounded up, so that a decoded sphere still covers its footprint */
+        float v = pos_r[4 * k + 3] * rinv;
+        uint64_t qr = 0;
+        if (v == v && v != INFINITY && v != -INFINITY) {
+            float c = ceilf(v);
+            qr = c < 0.0f ? 0 : (c > 8191.0f ? 8191 : (uint64_t)c);
+        }
+        word[k] = q[0] | (q[1] << 17) | (q[2] << 34) | (qr << 51);
+        uint32_t w = 0;
+        for (int ch = 0; ch < 4; ch++) {
+            float x = rgba[4 * k + ch] * 255.0f;
+            x = x + 0.5f;
+            w |= quant_floor(x, 255u) << (8 * ch);
+        }
+        color[k] = w;
+    }
+    return 0;
+}
+
+int orc_decode(const uint64_t* word, const uint32_t* color, int64_t n, const float lo[3],
+               const float hi[3], float r_max, float* pos_r, float* rgba) {
+    if (n < 0 || (n > 0 && (!word || !color || !pos_r || !rgba))) return -1;
+    float step[3];
+    for (int a = 0; a < 3; a++) step[a] = (hi[a] - lo[a]) * 0x1p-17f;
+    const float rstep = r_max / 8191.0f;
+    for (int64_t k = 0; k < n; k++) {
+        uint64_t w = word[k];
+        for (int a = 0; a < 3; a++) {
+            uint32_t q = (uint32_t)((w >> (17 * a)) & 0x1FFFFu);
+            pos_r[4 * k + a] = fmaf((float)q + 0.5f, step[a], lo[a]);  /* the cell's centre */
+        }
+        pos_r[4 * k + 3] = (float)(uint32_t)(w >> 51) * rstep;
+        for (int ch = 0; ch < 4; ch++) rgba[4 * k + ch] = (float)((color[k] >> (8 * ch)) & 255u) / 255.0f;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* S4/S5: sphere test.  Decision in binary32; the binary64 twin feeds only the diagnostic.      */
 /* ------------------------------------------------------------------------------------------ */
 static inline float eff_radius(const float* pos_r, const float* scale, float gscale, int64_t i) {
