@@ -612,7 +612,31 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
             "points_1px": _time_ms(torch, lambda: wrs.point_splat(sp_q, c_q, 1, out=out_q, scratch=psc), 20),
             "points_3px": _time_ms(torch, lambda: wrs.point_splat(sp_q, c_q, 3, out=out_q, scratch=psc), 20)}
         line["quality"] = q
-        del sp_q, bvh_q, srt_q, out_q, psc
+
+        # ---------------- 64-bit quantised splat stream (12 B per splat instead of 36) ----------
+        from paper_2006_14726_b300.quality import psnr
+        r_max = float(sp_q.pos_r[:sp_q.count(), 3].max())
+        codec = wrs.make_codec((0.0, 0.0, 0.0), (1.0, 1.0, 1.0), r_max)
+        rgba0, depth0 = groups[0][0], groups[0][1]
+        enc = wrs.unproject_encode(rgba0, depth0, srv_q, codec)
+        dec = wrs.decode_splats(enc, codec)
+        bvh_d, srt_d = wrs.build_lbvh(dec, leaf)
+        ref_img = wrs.trace(bvh_q, srt_q, c_q, params)
+        dec_img = wrs.trace(bvh_d, srt_d, c_q, params)
+        usc = torch.empty(wrs.unproject_scratch_bytes(W.server_w, W.server_h), dtype=torch.uint8,
+                          device=dev)
+        line["codec"] = {
+            "bytes_per_splat": 12, "float_bytes_per_splat": 36, "splats": enc.count(),
+            "stream_mb": enc.nbytes() / 1e6,
+            "unproject_encode_ms": _time_ms(torch, lambda: wrs.unproject_encode(
+                rgba0, depth0, srv_q, codec, out=enc, scratch=usc), 20),
+            "unproject_float_ms": _time_ms(torch, lambda: wrs.unproject(
+                rgba0, depth0, srv_q, out=sp_q, scratch=usc), 20),
+            "decode_ms": _time_ms(torch, lambda: wrs.decode_splats(enc, codec, out=dec), 20),
+            "psnr_decoded_vs_float_view_db": psnr(dec_img, ref_img),
+            "max_abs_decoded_vs_float_view": float((dec_img - ref_img).abs().max()),
+            "box": "unit cube (the volume's bounds)", "r_max": r_max}
+        del sp_q, bvh_q, srt_q, out_q, psc, enc, dec, bvh_d, srt_d
 
     # ---------------- forward and forward+backward (differentiable renderer) -------------------
     D = synth.DIFF

@@ -61,6 +61,14 @@ typedef void* wrs_stream_t; /* cudaStream_t */
 #define WRS_RADIUS_FOOTPRINT 0 /* half diagonal of the pixel footprint at the sample's depth */
 #define WRS_RADIUS_VOXEL 1     /* half a voxel's diagonal, the paper's rule (§4.1) */
 
+/* Quantisation box and radius bound of the 64-bit splat word (wrs_encode_splats and friends):
+ * positions are quantised to 2^17 cells per axis of [lo, hi] (hi > lo, finite), radii to 8192
+ * steps of [0, r_max] (r_max > 0, finite).  Passed by host pointer. */
+typedef struct {
+    float lo[3], hi[3];
+    float r_max;
+} wrs_codec;
+
 /* Pinhole camera.  right/up/fwd: orthonormal basis, view along +fwd.  Pixel (x, y), y = 0 top,
  * one ray through each pixel centre: u = ((2x+1)/W - 1) tan_half_fovy W/H,
  * v = (1 - (2y+1)/H) tan_half_fovy, d = normalize(fwd + u right + v up), origin eye (Eq. 1). */
@@ -155,6 +163,32 @@ size_t wrs_unproject_scratch_bytes(int32_t width, int32_t height);
 int wrs_unproject(const float* rgba, const float* depth, const wrs_camera* cam,
                   int32_t radius_mode, float voxel_diag, wrs_splats* out, void* scratch,
                   size_t scratch_bytes, wrs_stream_t stream);
+
+/* The server's record format (§4.1: the position is quantised and packed with the radius into
+ * 64 bits; §6: 32 bits of colour; the paper gives no layout -- spec S11 is this library's):
+ *   word[i]  = qx | qy << 17 | qz << 34 | qr << 51  (uint64; qa = floor((p_a - lo_a) * 2^17 / ext_a)
+ *              clamped to 0..2^17-1, qr = ceil(r * 8191 / r_max) clamped to 0..8191)
+ *   color[i] = r | g << 8 | b << 16 | a << 24       (uint32; floor(c * 255 + 0.5) per channel)
+ * 12 bytes per splat instead of 36.  Non-finite inputs quantise to 0.
+ *
+ * wrs_unproject_encode: wrs_unproject (same kept pixels, order, radius) writing the encoded stream
+ * directly: word/color [capacity], *n = count (device), capacity >= width * height.  Scratch:
+ * wrs_unproject_scratch_bytes(w, h).
+ * wrs_encode_splats: encode the first *in->n records of a float splat set (word/color hold
+ * in->capacity entries); *n_out (device, may be NULL) = that count.
+ * wrs_decode_splats: decode the first min(*n, capacity) records into float splats (position =
+ * the cell's centre, radius = qr * r_max / 8191, colour = c8 / 255, id = stream index, which keeps
+ * the tie order of pixel ids because the stream is in pixel order); *out->n = that count;
+ * out->capacity >= capacity.  The result feeds wrs_build_lbvh unchanged. */
+int wrs_unproject_encode(const float* rgba, const float* depth, const wrs_camera* cam,
+                         int32_t radius_mode, float voxel_diag, const wrs_codec* codec,
+                         uint64_t* word, uint32_t* color, uint32_t* n, uint32_t capacity,
+                         void* scratch, size_t scratch_bytes, wrs_stream_t stream);
+int wrs_encode_splats(const wrs_splats* in, const wrs_codec* codec, uint64_t* word,
+                      uint32_t* color, uint32_t* n_out, wrs_stream_t stream);
+int wrs_decode_splats(const uint64_t* word, const uint32_t* color, const uint32_t* n,
+                      uint32_t capacity, const wrs_codec* codec, wrs_splats* out,
+                      wrs_stream_t stream);
 
 /* Accumulation over server frames (§6 names it as future work and gives no rule; spec S3a is
  * this library's reading): wrs_unproject of one more frame, APPENDED to the splats already in out.

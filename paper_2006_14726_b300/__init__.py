@@ -80,6 +80,19 @@ class _Params(ctypes.Structure):
                 ("schedule", ctypes.c_int32), ("width", ctypes.c_int32)]
 
 
+class Codec(ctypes.Structure):
+    """wrs_codec: quantisation box and radius bound of the 64-bit splat word."""
+    _fields_ = [("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3), ("r_max", ctypes.c_float)]
+
+
+def make_codec(lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), r_max: float = 0.01) -> Codec:
+    c = Codec()
+    c.lo[:] = [float(x) for x in lo]
+    c.hi[:] = [float(x) for x in hi]
+    c.r_max = float(r_max)
+    return c
+
+
 class Session(ctypes.Structure):
     _fields_ = [("nodes", ctypes.c_void_p), ("pos_r", ctypes.c_void_p), ("rgba", ctypes.c_void_p),
                 ("id", ctypes.c_void_p), ("src", ctypes.c_void_p), ("opacity", ctypes.c_void_p),
@@ -112,6 +125,10 @@ _sig("wrs_unproject_scratch_bytes", _Z, _I, _I)
 _sig("wrs_unproject", _I, _P, _P, ctypes.POINTER(Camera), _I, _F, ctypes.POINTER(_Splats), _P, _Z, _P)
 _sig("wrs_unproject_append", _I, _P, _P, ctypes.POINTER(Camera), _I, _F, _F, _U,
      ctypes.POINTER(_Splats), _P, _Z, _P, _P)
+_sig("wrs_unproject_encode", _I, _P, _P, ctypes.POINTER(Camera), _I, _F, ctypes.POINTER(Codec), _P, _P,
+     _P, _U, _P, _Z, _P)
+_sig("wrs_encode_splats", _I, ctypes.POINTER(_Splats), ctypes.POINTER(Codec), _P, _P, _P, _P)
+_sig("wrs_decode_splats", _I, _P, _P, _P, _U, ctypes.POINTER(Codec), ctypes.POINTER(_Splats), _P)
 _sig("wrs_point_splat_scratch_bytes", _Z, _I, _I)
 _sig("wrs_point_splat", _I, ctypes.POINTER(_Splats), ctypes.POINTER(Camera), _I, _P, _P, _P, _Z, _P)
 _sig("wrs_unproject_static", _I, _P, _P, ctypes.POINTER(Camera), _I, _F, ctypes.POINTER(_Splats), _P)
@@ -324,6 +341,66 @@ def unproject_append(rgba: torch.Tensor, depth: torch.Tensor, cam, out: SplatBuf
                                      float(voxel_diag), float(weight), int(id_base),
                                      ctypes.byref(sp), _ptr(scratch), scratch.numel(), _ptr(status),
                                      _stream(stream)), "wrs_unproject_append")
+    return out
+
+
+class EncodedSplats:
+    """The server's stream of a splat set (see wrs_codec): word uint64 [cap] (held in an int64
+    tensor), color uint32 [cap] (held in an int32 tensor), n [1] on the device, 12 bytes a splat."""
+
+    def __init__(self, capacity: int, device=None):
+        device = device or torch.device("cuda")
+        cap = max(int(capacity), 1)
+        self.capacity = int(capacity)
+        self.word = torch.zeros(cap, dtype=torch.int64, device=device)
+        self.color = torch.zeros(cap, dtype=torch.int32, device=device)
+        self.n = torch.zeros(1, dtype=torch.int32, device=device)
+
+    def count(self) -> int:
+        return int(self.n.item())
+
+    def nbytes(self) -> int:
+        """Bytes of the valid records (what the server sends; synchronises)."""
+        return 12 * self.count()
+
+
+def unproject_encode(rgba: torch.Tensor, depth: torch.Tensor, cam, codec: Codec,
+                     radius_mode: int = RADIUS_FOOTPRINT, voxel_diag: float = 0.0,
+                     out: Optional[EncodedSplats] = None, scratch: Optional[torch.Tensor] = None,
+                     stream=None) -> EncodedSplats:
+    """Unprojection (Eq. 1, §4.1) writing the 64-bit word + 32-bit colour stream (§4.1, §6)."""
+    c = _cam(cam)
+    if out is None:
+        out = EncodedSplats(c.width * c.height, device=rgba.device)
+    if scratch is None:
+        scratch = _scratch(unproject_scratch_bytes(c.width, c.height), rgba.device)
+    _check(_lib.wrs_unproject_encode(_ptr(rgba), _ptr(depth), ctypes.byref(c), int(radius_mode),
+                                     float(voxel_diag), ctypes.byref(codec), _ptr(out.word),
+                                     _ptr(out.color), _ptr(out.n), out.capacity, _ptr(scratch),
+                                     scratch.numel(), _stream(stream)), "wrs_unproject_encode")
+    return out
+
+
+def encode_splats(splats: SplatBuffers, codec: Codec, out: Optional[EncodedSplats] = None,
+                  stream=None) -> EncodedSplats:
+    """Encode a float splat set into the 12-byte stream (the count is written on the device)."""
+    if out is None:
+        out = EncodedSplats(splats.capacity, device=splats.pos_r.device)
+    sp = splats.c()
+    _check(_lib.wrs_encode_splats(ctypes.byref(sp), ctypes.byref(codec), _ptr(out.word),
+                                  _ptr(out.color), _ptr(out.n), _stream(stream)), "wrs_encode_splats")
+    return out
+
+
+def decode_splats(enc: EncodedSplats, codec: Codec, out: Optional[SplatBuffers] = None,
+                  stream=None) -> SplatBuffers:
+    """Decode the stream into float splats (id = stream index) for wrs_build_lbvh."""
+    if out is None:
+        out = SplatBuffers(enc.capacity, device=enc.word.device)
+    sp = out.c()
+    _check(_lib.wrs_decode_splats(_ptr(enc.word), _ptr(enc.color), _ptr(enc.n), enc.capacity,
+                                  ctypes.byref(codec), ctypes.byref(sp), _stream(stream)),
+           "wrs_decode_splats")
     return out
 
 

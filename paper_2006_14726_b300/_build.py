@@ -16,8 +16,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libwrs.so")
-SOURCES = ["api.cu", "unproject.cu", "raycast.cu", "lbvh.cu", "trace.cu", "point_splat.cu"]
-HEADERS = [os.path.join(CSRC, "common.cuh"), os.path.join(INCLUDE, "wrs.h")]
+SOURCES = ["api.cu", "unproject.cu", "raycast.cu", "lbvh.cu", "trace.cu", "point_splat.cu", "codec.cu"]
+HEADERS = [os.path.join(CSRC, "common.cuh"), os.path.join(CSRC, "codec.cuh"), os.path.join(INCLUDE, "wrs.h")]
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",

@@ -6,7 +6,7 @@
 // block with warp ballots.  Every pass reads the image with coalesced 16-byte loads.
 #include <mutex>
 
-#include "common.cuh"
+#include "codec.cuh"
 
 namespace wrs {
 int check_camera(const wrs_camera* c, const char* fn);
@@ -96,14 +96,28 @@ __global__ void __launch_bounds__(1024) k_scan_counts(const uint32_t* __restrict
     }
 }
 
-// APPEND: records go after the current count (offsets from the APPEND scan), slots >= capacity are
-// dropped, colours are scaled by weight (binary32 product per channel) and ids offset by id_base.
-template <bool APPEND>
+// Output of the write pass.  kPlain: float records at their compacted slot.  kAppend: records go
+// after the current count (offsets from the APPEND scan), slots >= capacity are dropped, colours
+// are scaled by weight (binary32 product per channel) and ids offset by id_base.  kEncode: the
+// 64-bit position + radius word and the 32-bit colour (spec S11) instead of the float records.
+enum { kPlain = 0, kAppend = 1, kEncode = 2 };
+
+struct WriteOut {
+    float4* pos_r;
+    float4* rgba;
+    uint32_t* id;
+    uint64_t* word;
+    uint32_t* color;
+    float weight;
+    uint32_t id_base;
+    uint32_t capacity;
+    wrs::CodecConsts codec;
+};
+
+template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_unproject_write(
     const float4* __restrict__ rgba, const float* __restrict__ depth, wrs_camera cam,
-    int32_t mode, float voxel_diag, const uint32_t* __restrict__ offsets, float4* __restrict__ pos_r,
-    float4* __restrict__ out_rgba, uint32_t* __restrict__ out_id, float weight, uint32_t id_base,
-    uint32_t capacity) {
+    int32_t mode, float voxel_diag, const uint32_t* __restrict__ offsets, WriteOut out) {
     __shared__ uint32_t s_warp[kThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t npix = (uint32_t)cam.width * (uint32_t)cam.height;
@@ -125,7 +139,7 @@ __global__ void __launch_bounds__(kThreads) k_unproject_write(
             total += c;
         }
         const uint64_t slot = run + before + __popc(ball & ((1u << lane) - 1u));
-        if (keep && (!APPEND || slot < capacity)) {
+        if (keep && (MODE != kAppend || slot < out.capacity)) {
             const int x = (int)(i % (uint32_t)cam.width), y = (int)(i / (uint32_t)cam.width);
             const wrs::Ray r = wrs::primary_ray(cam, x, y);
             const float t = depth[i];
@@ -137,15 +151,22 @@ __global__ void __launch_bounds__(kThreads) k_unproject_write(
             } else {
                 r0 = r_vox;
             }
-            pos_r[slot] = make_float4(__fmaf_rn(r.d.x, t, r.o.x), __fmaf_rn(r.d.y, t, r.o.y),
-                                      __fmaf_rn(r.d.z, t, r.o.z), r0);
+            const float px = __fmaf_rn(r.d.x, t, r.o.x), py = __fmaf_rn(r.d.y, t, r.o.y),
+                        pz = __fmaf_rn(r.d.z, t, r.o.z);
             float4 c = rgba[i];
-            if (APPEND) {
-                c = make_float4(__fmul_rn(weight, c.x), __fmul_rn(weight, c.y),
-                                __fmul_rn(weight, c.z), __fmul_rn(weight, c.w));
+            if (MODE == kEncode) {
+                out.word[slot] = wrs::encode_word(out.codec, px, py, pz, r0);
+                out.color[slot] = wrs::encode_color(c);
+            } else {
+                out.pos_r[slot] = make_float4(px, py, pz, r0);
+                if (MODE == kAppend) {
+                    const float w = out.weight;
+                    c = make_float4(__fmul_rn(w, c.x), __fmul_rn(w, c.y), __fmul_rn(w, c.z),
+                                    __fmul_rn(w, c.w));
+                }
+                out.rgba[slot] = c;
+                out.id[slot] = MODE == kAppend ? out.id_base + i : i;
             }
-            out_rgba[slot] = c;
-            out_id[slot] = APPEND ? id_base + i : i;
         }
         run += total;
         __syncthreads();  // s_warp is reused by the next round
@@ -153,6 +174,17 @@ __global__ void __launch_bounds__(kThreads) k_unproject_write(
 }
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+WriteOut float_out(const wrs_splats* out, float weight, uint32_t id_base) {
+    WriteOut o{};
+    o.pos_r = reinterpret_cast<float4*>(out->pos_r);
+    o.rgba = reinterpret_cast<float4*>(out->rgba);
+    o.id = out->id;
+    o.weight = weight;
+    o.id_base = id_base;
+    o.capacity = out->capacity;
+    return o;
+}
 
 }  // namespace
 
@@ -199,11 +231,55 @@ int wrs_unproject(const float* rgba, const float* depth, const wrs_camera* cam,
     WRS_LAUNCH_CHECK("wrs_unproject count");
     k_scan_counts<false><<<1, 1024, 0, s>>>(counts, offsets, nb, out->n, out->capacity, nullptr);
     WRS_LAUNCH_CHECK("wrs_unproject scan");
-    k_unproject_write<false><<<nb, kThreads, 0, s>>>(in4, depth, *cam, radius_mode, voxel_diag,
-                                                     offsets, reinterpret_cast<float4*>(out->pos_r),
-                                                     reinterpret_cast<float4*>(out->rgba), out->id,
-                                                     1.0f, 0u, out->capacity);
+    k_unproject_write<kPlain><<<nb, kThreads, 0, s>>>(in4, depth, *cam, radius_mode, voxel_diag,
+                                                      offsets, float_out(out, 1.0f, 0u));
     WRS_LAUNCH_CHECK("wrs_unproject write");
+    return WRS_OK;
+}
+
+int wrs_unproject_encode(const float* rgba, const float* depth, const wrs_camera* cam,
+                         int32_t radius_mode, float voxel_diag, const wrs_codec* codec,
+                         uint64_t* word, uint32_t* color, uint32_t* n, uint32_t capacity,
+                         void* scratch, size_t scratch_bytes, wrs_stream_t stream) {
+    const char* fn = "wrs_unproject_encode";
+    if (int rc = wrs::check_camera(cam, fn)) return rc;
+    if (int rc = wrs::check_codec(codec, fn)) return rc;
+    if (!rgba || !depth || !word || !color || !n)
+        return wrs::fail(WRS_ERR_ARG, "%s: NULL input or output pointer", fn);
+    if ((reinterpret_cast<uintptr_t>(rgba) & 15) | (reinterpret_cast<uintptr_t>(word) & 7) |
+        (reinterpret_cast<uintptr_t>(color) & 3))
+        return wrs::fail(WRS_ERR_ARG, "%s: misaligned array", fn);
+    if (radius_mode != WRS_RADIUS_FOOTPRINT && radius_mode != WRS_RADIUS_VOXEL)
+        return wrs::fail(WRS_ERR_ARG, "%s: unknown radius_mode %d", fn, radius_mode);
+    if (radius_mode == WRS_RADIUS_VOXEL && !(voxel_diag > 0.0f && voxel_diag < 1e30f))
+        return wrs::fail(WRS_ERR_ARG, "%s: voxel_diag must be positive and finite", fn);
+    const size_t npix = (size_t)cam->width * (size_t)cam->height;
+    if (npix >= 0x80000000ull)
+        return wrs::fail(WRS_ERR_ARG, "%s: image of %zu pixels exceeds 2^31", fn, npix);
+    if (capacity < npix)
+        return wrs::fail(WRS_ERR_CAPACITY, "%s: capacity %u < %zu pixels", fn, capacity, npix);
+    const size_t need = wrs_unproject_scratch_bytes(cam->width, cam->height);
+    if (!scratch || scratch_bytes < need)
+        return wrs::fail(WRS_ERR_SCRATCH, "%s: scratch needs %zu bytes, got %zu", fn, need,
+                         scratch_bytes);
+    const uint32_t nb = (uint32_t)((npix + kTile - 1) / kTile);
+    uint32_t* counts = static_cast<uint32_t*>(scratch);
+    uint32_t* offsets = reinterpret_cast<uint32_t*>(static_cast<char*>(scratch) +
+                                                    align256(nb * sizeof(uint32_t)));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const float4* in4 = reinterpret_cast<const float4*>(rgba);
+    k_unproject_count<<<nb, kThreads, 0, s>>>(in4, depth, (uint32_t)npix, counts);
+    WRS_LAUNCH_CHECK("wrs_unproject_encode count");
+    k_scan_counts<false><<<1, 1024, 0, s>>>(counts, offsets, nb, n, capacity, nullptr);
+    WRS_LAUNCH_CHECK("wrs_unproject_encode scan");
+    WriteOut o{};
+    o.word = word;
+    o.color = color;
+    o.capacity = capacity;
+    o.codec = wrs::make_codec(*codec);
+    k_unproject_write<kEncode><<<nb, kThreads, 0, s>>>(in4, depth, *cam, radius_mode, voxel_diag,
+                                                       offsets, o);
+    WRS_LAUNCH_CHECK("wrs_unproject_encode write");
     return WRS_OK;
 }
 
@@ -244,10 +320,8 @@ int wrs_unproject_append(const float* rgba, const float* depth, const wrs_camera
     WRS_LAUNCH_CHECK("wrs_unproject_append count");
     k_scan_counts<true><<<1, 1024, 0, s>>>(counts, offsets, nb, out->n, out->capacity, status);
     WRS_LAUNCH_CHECK("wrs_unproject_append scan");
-    k_unproject_write<true><<<nb, kThreads, 0, s>>>(in4, depth, *cam, radius_mode, voxel_diag,
-                                                    offsets, reinterpret_cast<float4*>(out->pos_r),
-                                                    reinterpret_cast<float4*>(out->rgba), out->id,
-                                                    weight, id_base, out->capacity);
+    k_unproject_write<kAppend><<<nb, kThreads, 0, s>>>(in4, depth, *cam, radius_mode, voxel_diag,
+                                                       offsets, float_out(out, weight, id_base));
     WRS_LAUNCH_CHECK("wrs_unproject_append write");
     return WRS_OK;
 }
@@ -333,10 +407,8 @@ extern "C" int wrs_unproject_static(const float* rgba, const float* depth, const
     WRS_LAUNCH_CHECK("wrs_unproject_static count");
     k_scan_counts<false><<<1, 1024, 0, s>>>(counts, offsets, nb, out->n, out->capacity, nullptr);
     WRS_LAUNCH_CHECK("wrs_unproject_static scan");
-    k_unproject_write<false><<<nb, kThreads, 0, s>>>(in4, depth, *cam, radius_mode, voxel_diag,
-                                                     offsets, reinterpret_cast<float4*>(out->pos_r),
-                                                     reinterpret_cast<float4*>(out->rgba), out->id,
-                                                     1.0f, 0u, out->capacity);
+    k_unproject_write<kPlain><<<nb, kThreads, 0, s>>>(in4, depth, *cam, radius_mode, voxel_diag,
+                                                      offsets, float_out(out, 1.0f, 0u));
     WRS_LAUNCH_CHECK("wrs_unproject_static write");
     return WRS_OK;
 }

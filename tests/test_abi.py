@@ -99,6 +99,16 @@ def test_host_validation_without_device(wrs):
     zero = wrs._Splats(fake.value, fake.value, fake.value, None, fake.value, 0)
     assert lib.wrs_unproject_append(*args, 1.0, 0, ctypes.byref(zero), fake, 1 << 20, None, None) == wrs.WRS_ERR_CAPACITY
     assert lib.wrs_unproject_append(*args, 1.0, 0, ctypes.byref(sp), fake, 1, None, None) == wrs.WRS_ERR_SCRATCH
+    # codec: empty box axis, non-positive radius bound, capacity below the pixel count
+    good = wrs.make_codec((0, 0, 0), (1, 1, 1), 0.01)
+    flat = wrs.make_codec((0, 0, 0), (1, 1, 0), 0.01)
+    norad = wrs.make_codec((0, 0, 0), (1, 1, 1), 0.0)
+    for cd in (flat, norad):
+        assert lib.wrs_unproject_encode(fake, fake, ctypes.byref(_cam(wrs)), 0, 0.0, ctypes.byref(cd), fake, fake, fake, 64, fake, 1 << 20, None) == wrs.WRS_ERR_ARG
+    assert "codec" in wrs.last_error()
+    assert lib.wrs_unproject_encode(fake, fake, ctypes.byref(_cam(wrs)), 0, 0.0, ctypes.byref(good), fake, fake, fake, 10, fake, 1 << 20, None) == wrs.WRS_ERR_CAPACITY
+    assert lib.wrs_encode_splats(ctypes.byref(big), ctypes.byref(flat), fake, fake, None, None) == wrs.WRS_ERR_ARG
+    assert lib.wrs_decode_splats(fake, fake, fake, 65, ctypes.byref(good), ctypes.byref(big), None) == wrs.WRS_ERR_CAPACITY
     # LBVH: bad leaf size, missing src, small capacity
     bv = wrs._Lbvh(fake.value, 64, 0)
     srt = wrs._Splats(fake.value, fake.value, fake.value, fake.value, fake.value, 64)
