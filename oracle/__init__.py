@@ -9,7 +9,8 @@ marshals numpy arrays through ctypes.  Functions and the paper passage each one 
 
 * :func:`primary_ray` -- the ray ``r = o + d t`` of a pixel (Eq. 1, spec S1).
 * :func:`raycast` -- the server's volume ray marcher with the first-hit depth heuristic
-  (§4.1, §4.2, Fig. 2; the heuristic itself is cited from earlier work, §2).
+  (§4.1, §4.2, Fig. 2; the heuristic itself is cited from earlier work, §2) and the readings of
+  the other heuristics of §2 and §5 (max contribution, accumulated opacity, max gradient; S2a).
 * :func:`unproject` -- object-space samples ``p = o + d t_i`` (Eq. 1), footprint radius (§4.1),
   zero-radius compaction (§4.1).
 * :func:`append_frame`, :func:`accumulate` -- splats of several server frames in one set, the
@@ -81,6 +82,9 @@ def _load():
         lib.orc_raycast.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
                                     ctypes.POINTER(_Cam), ctypes.c_float, ctypes.c_float, P,
                                     ctypes.c_int64, P, P, ctypes.c_int]
+        lib.orc_raycast_heuristic.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              P, ctypes.POINTER(_Cam), ctypes.c_float, ctypes.c_int,
+                                              ctypes.c_float, P, ctypes.c_int64, P, P, ctypes.c_int]
         lib.orc_unproject.argtypes = [P, P, ctypes.POINTER(_Cam), ctypes.c_int, ctypes.c_float,
                                       P, P, P, ctypes.c_int64]
         lib.orc_unproject.restype = ctypes.c_int64
@@ -132,12 +136,21 @@ def primary_ray(cam, x: int, y: int):
     return o, d
 
 
-def raycast(vol: np.ndarray, tf: np.ndarray, cam, step_vox: float = 0.5, tau: float = 0.1,
-            pixels: Optional[np.ndarray] = None, threads: int = 0):
-    """Server volume ray caster + first-hit depth heuristic (spec S2).
+DEPTH_FIRST_HIT = 0
+DEPTH_MAX_CONTRIBUTION = 1
+DEPTH_ACCUMULATED = 2
+DEPTH_MAX_GRADIENT = 3
 
-    vol: [nz, ny, nx] float32 in [0,1] or uint8.  Returns (rgba float64 [npix,4] premultiplied,
-    depth float32 [npix]) for ``pixels`` (flat indices y*W+x), or images [H,W,4] / [H,W] if None.
+
+def raycast(vol: np.ndarray, tf: np.ndarray, cam, step_vox: float = 0.5, tau: float = 0.1,
+            pixels: Optional[np.ndarray] = None, threads: int = 0, heuristic: int = DEPTH_FIRST_HIT,
+            param: Optional[float] = None):
+    """Server volume ray caster + depth heuristic (spec S2; other heuristics: S2a).
+
+    vol: [nz, ny, nx] float32 in [0,1] or uint8.  ``param``: tau of the first-hit heuristic
+    (default ``tau``), theta of the accumulated-opacity heuristic (default 0.5), unused otherwise.
+    Returns (rgba float64 [npix,4] premultiplied, depth float32 [npix]) for ``pixels`` (flat
+    indices y*W+x), or images [H,W,4] / [H,W] if None.
     """
     lib = _load()
     if vol.dtype == np.uint8:
@@ -149,6 +162,8 @@ def raycast(vol: np.ndarray, tf: np.ndarray, cam, step_vox: float = 0.5, tau: fl
     nz, ny, nx = vol.shape
     tf = _c(tf, np.float32)
     assert tf.shape == (256, 4)
+    if param is None:
+        param = 0.5 if heuristic == DEPTH_ACCUMULATED else tau
     if pixels is None:
         npix = cam.width * cam.height
         pix = None
@@ -157,11 +172,12 @@ def raycast(vol: np.ndarray, tf: np.ndarray, cam, step_vox: float = 0.5, tau: fl
         npix = pix.size
     rgba = np.zeros((npix, 4), np.float64)
     depth = np.zeros(npix, np.float32)
-    rc = lib.orc_raycast(vol.ctypes.data, dtype, nx, ny, nz, tf.ctypes.data, ctypes.byref(_cam(cam)),
-                         float(step_vox), float(tau), _ptr(pix), int(npix), rgba.ctypes.data,
-                         depth.ctypes.data, int(threads))
+    rc = lib.orc_raycast_heuristic(vol.ctypes.data, dtype, nx, ny, nz, tf.ctypes.data,
+                                   ctypes.byref(_cam(cam)), float(step_vox), int(heuristic),
+                                   float(param), _ptr(pix), int(npix), rgba.ctypes.data,
+                                   depth.ctypes.data, int(threads))
     if rc != 0:
-        raise ValueError("orc_raycast: bad arguments")
+        raise ValueError("orc_raycast_heuristic: bad arguments")
     if pixels is None:
         return rgba.reshape(cam.height, cam.width, 4), depth.reshape(cam.height, cam.width)
     return rgba, depth

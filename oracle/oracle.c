@@ -94,6 +94,7 @@ typedef struct {
     const void* vol; int dtype; int nx, ny, nz;
     const float* tf; const orc_camera* cam; float step_vox; float tau;
     double* rgba_out; float* depth_out; const int32_t* pix;
+    int heur; /* S2a: 0 first hit (param tau), 1 max contribution, 2 accumulated (param theta), 3 max gradient */
 } rc_ctx;
 
 static float vox32(const rc_ctx* c, int i, int j, int k) {
@@ -199,6 +200,7 @@ static void rc_pixel(void* vctx, int64_t slot, int tid) {
     float dt = c->step_vox / (float)n;
 
     float t_first = INFINITY, t_any = INFINITY;
+    float A32 = 0.0f, best = -1.0f, t_best = INFINITY, t_acc = INFINITY;
     double C[3] = {0, 0, 0}, A = 0;
     for (int j = 0; j < (1 << 24); j++) { /* at most 2^24 samples per ray */
         float tj = fmaf((float)j + 0.5f, dt, lo);
@@ -209,6 +211,26 @@ static void rc_pixel(void* vctx, int64_t slot, int tid) {
         float a32 = tf_alpha32(c->tf, sample32(c, p32));
         if (a32 >= c->tau && t_first == INFINITY) t_first = tj;
         if (a32 > 0.0f && t_any == INFINITY) t_any = tj;
+        if (c->heur == 1 || c->heur == 2) {
+            /* S2a: contribution of this sample and opacity accumulated through it */
+            float w = (1.0f - A32) * a32;
+            A32 = A32 + w;
+            if (c->heur == 1 && w > 0.0f && w > best) { best = w; t_best = tj; }
+            if (c->heur == 2 && A32 >= c->tau && t_acc == INFINITY) t_acc = tj;
+        } else if (c->heur == 3 && a32 > 0.0f) {
+            /* S2a: squared gradient by central differences one voxel apart */
+            int n3[3] = {c->nx, c->ny, c->nz};
+            float g[3];
+            for (int a = 0; a < 3; a++) {
+                float h = 1.0f / (float)n3[a];
+                float pp[3] = {p32[0], p32[1], p32[2]}, pm[3] = {p32[0], p32[1], p32[2]};
+                pp[a] = p32[a] + h;
+                pm[a] = p32[a] - h;
+                g[a] = sample32(c, pp) - sample32(c, pm);
+            }
+            float m = fmaf(g[2], g[2], fmaf(g[1], g[1], g[0] * g[0]));
+            if (m > best) { best = m; t_best = tj; }
+        }
         /* compositing path, binary64 */
         double p64[3], rgba[4];
         for (int a = 0; a < 3; a++) p64[a] = (double)o[a] + (double)d[a] * (double)tj;
@@ -219,18 +241,31 @@ static void rc_pixel(void* vctx, int64_t slot, int tid) {
     }
     for (int k = 0; k < 3; k++) out[k] = C[k];
     out[3] = A;
-    c->depth_out[pix] = t_first < INFINITY ? t_first : t_any;
+    float depth;
+    if (c->heur == 1 || c->heur == 3) depth = t_best;
+    else if (c->heur == 2) depth = t_acc < INFINITY ? t_acc : t_any;
+    else depth = t_first < INFINITY ? t_first : t_any;
+    c->depth_out[pix] = depth;
+}
+
+int orc_raycast_heuristic(const void* vol, int dtype, int nx, int ny, int nz, const float* tf,
+                          const orc_camera* cam, float step_vox, int heuristic, float param,
+                          const int32_t* pix, int64_t npix, double* rgba_out, float* depth_out,
+                          int nthreads) {
+    if (!vol || !tf || !cam || !rgba_out || !depth_out || nx < 1 || ny < 1 || nz < 1) return -1;
+    if (dtype != 0 && dtype != 1) return -1;
+    if (heuristic < 0 || heuristic > 3) return -1;
+    if (!pix) npix = (int64_t)cam->width * cam->height;
+    rc_ctx c = {vol, dtype, nx, ny, nz, tf, cam, step_vox, param, rgba_out, depth_out, pix, heuristic};
+    orc_parallel(rc_pixel, &c, npix, nthreads);
+    return 0;
 }
 
 int orc_raycast(const void* vol, int dtype, int nx, int ny, int nz, const float* tf,
                 const orc_camera* cam, float step_vox, float tau, const int32_t* pix,
                 int64_t npix, double* rgba_out, float* depth_out, int nthreads) {
-    if (!vol || !tf || !cam || !rgba_out || !depth_out || nx < 1 || ny < 1 || nz < 1) return -1;
-    if (dtype != 0 && dtype != 1) return -1;
-    if (!pix) npix = (int64_t)cam->width * cam->height;
-    rc_ctx c = {vol, dtype, nx, ny, nz, tf, cam, step_vox, tau, rgba_out, depth_out, pix};
-    orc_parallel(rc_pixel, &c, npix, nthreads);
-    return 0;
+    return orc_raycast_heuristic(vol, dtype, nx, ny, nz, tf, cam, step_vox, 0, tau, pix, npix,
+                                 rgba_out, depth_out, nthreads);
 }
 
 /* ------------------------------------------------------------------------------------------ */
