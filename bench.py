@@ -599,6 +599,16 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
             rows = warp_quality(v, torch.from_numpy(tf_np).to(dev), srv_q, clis_q, voxel_diag=vd)
             q[name] = [{k: (round(x, 3) if x is not None else None) for k, x in r.items()}
                        for r in rows]
+        # the server's depth rule (first hit, max contribution, accumulated opacity, max
+        # gradient: Fig. 3 uses a gradient heuristic) on the iso scene, at 10 and 20 degrees
+        names = {0: "first_hit", 1: "max_contribution", 2: "accumulated_0.5", 3: "max_gradient"}
+        q["heuristics_blobs_256_iso_tf"] = {}
+        for hh, nm in names.items():
+            rows = warp_quality(blobs, torch.from_numpy(synth.tf_iso()).to(dev), srv_q, clis_q[2:],
+                                point_sizes=(2, 3), max_hits=(0,), voxel_diag=3 ** 0.5 / 256,
+                                heuristic=hh)
+            q["heuristics_blobs_256_iso_tf"][nm] = [
+                {k: (round(x, 3) if x is not None else None) for k, x in r.items()} for r in rows]
         del blobs
         # cost of the two warps on the same 1080p frame (one client view)
         sp_q = wrs.unproject(groups[0][0], groups[0][1], srv_q)

@@ -57,6 +57,14 @@ typedef void* wrs_stream_t; /* cudaStream_t */
 #define WRS_F32 0
 #define WRS_U8 1
 
+/* depth heuristics of wrs_raycast_volume_heuristic (spec S2a; §2 cites them, §5 uses a gradient
+ * heuristic, the paper defines none) */
+#define WRS_DEPTH_FIRST_HIT 0          /* first sample with alpha >= param (tau), else first alpha > 0 */
+#define WRS_DEPTH_MAX_CONTRIBUTION 1   /* sample with the largest (1 - A) alpha, A accumulated */
+#define WRS_DEPTH_ACCUMULATED 2        /* first sample where A reaches param (theta), else first alpha > 0 */
+#define WRS_DEPTH_MAX_GRADIENT 3       /* sample with alpha > 0 and the largest |grad s|^2 (central
+                                          differences one voxel apart) */
+
 /* radius rules for wrs_unproject */
 #define WRS_RADIUS_FOOTPRINT 0 /* half diagonal of the pixel footprint at the sample's depth */
 #define WRS_RADIUS_VOXEL 1     /* half a voxel's diagonal, the paper's rule (§4.1) */
@@ -153,6 +161,16 @@ int wrs_check_status(int32_t* status, wrs_stream_t stream);
 int wrs_raycast_volume(const void* vol, int32_t dtype, int32_t nx, int32_t ny, int32_t nz,
                        const float* tf, const wrs_camera* cam, float step_vox, float tau,
                        float* rgba_out, float* depth_out, wrs_stream_t stream);
+
+/* wrs_raycast_volume with another depth heuristic (WRS_DEPTH_*; readings of §2 and §5, spec
+ * S2a).  Decisions in binary32 on the same samples and uncorrected alphas; the colour composite
+ * is the same for every heuristic.  param: tau for WRS_DEPTH_FIRST_HIT, theta for
+ * WRS_DEPTH_ACCUMULATED, ignored otherwise.  wrs_raycast_volume(..., tau, ...) equals
+ * heuristic WRS_DEPTH_FIRST_HIT with param tau. */
+int wrs_raycast_volume_heuristic(const void* vol, int32_t dtype, int32_t nx, int32_t ny,
+                                 int32_t nz, const float* tf, const wrs_camera* cam,
+                                 float step_vox, int32_t heuristic, float param, float* rgba_out,
+                                 float* depth_out, wrs_stream_t stream);
 
 /* Unprojection with footprint radius and stable compaction (Eq. 1, §4.1).  For every server
  * pixel with finite depth t >= 0 and alpha > 0: p = eye + d t (d the pixel's ray of cam), radius

@@ -48,6 +48,10 @@ RADIUS_FOOTPRINT = 0
 RADIUS_VOXEL = 1
 SCHEDULE_PER_PIXEL = 0
 SCHEDULE_PERSISTENT = 1
+DEPTH_FIRST_HIT = 0
+DEPTH_MAX_CONTRIBUTION = 1
+DEPTH_ACCUMULATED = 2
+DEPTH_MAX_GRADIENT = 3
 
 
 class WrsError(RuntimeError):
@@ -121,6 +125,8 @@ _sig("wrs_session_size", _Z)
 _sig("wrs_camera_size", _Z)
 _sig("wrs_check_status", _I, _P, _P)
 _sig("wrs_raycast_volume", _I, _P, _I, _I, _I, _I, _P, ctypes.POINTER(Camera), _F, _F, _P, _P, _P)
+_sig("wrs_raycast_volume_heuristic", _I, _P, _I, _I, _I, _I, _P, ctypes.POINTER(Camera), _F, _I, _F,
+     _P, _P, _P)
 _sig("wrs_unproject_scratch_bytes", _Z, _I, _I)
 _sig("wrs_unproject", _I, _P, _P, ctypes.POINTER(Camera), _I, _F, ctypes.POINTER(_Splats), _P, _Z, _P)
 _sig("wrs_unproject_append", _I, _P, _P, ctypes.POINTER(Camera), _I, _F, _F, _U,
@@ -281,9 +287,12 @@ def _scratch(nbytes: int, device=None) -> torch.Tensor:
 # ----------------------------------------------------------------------------------------------
 def raycast_volume(vol: torch.Tensor, tf: torch.Tensor, cam, step_vox: float = 0.5,
                    tau: float = 0.1, rgba_out: Optional[torch.Tensor] = None,
-                   depth_out: Optional[torch.Tensor] = None, stream=None):
-    """Server volume ray caster + first-hit depth heuristic.  vol: CUDA [nz,ny,nx] float32 or
-    uint8; tf: CUDA [256,4] float32.  Returns (rgba [H,W,4], depth [H,W])."""
+                   depth_out: Optional[torch.Tensor] = None, stream=None,
+                   heuristic: int = 0, param: Optional[float] = None):
+    """Server volume ray caster + depth heuristic (DEPTH_*; default first hit with ``tau``).
+    vol: CUDA [nz,ny,nx] float32 or uint8; tf: CUDA [256,4] float32.  ``param``: theta of
+    DEPTH_ACCUMULATED (default 0.5), tau of DEPTH_FIRST_HIT (default ``tau``).  Returns
+    (rgba [H,W,4], depth [H,W])."""
     c = _cam(cam)
     if vol.dtype == torch.uint8:
         dt = U8
@@ -296,9 +305,12 @@ def raycast_volume(vol: torch.Tensor, tf: torch.Tensor, cam, step_vox: float = 0
         rgba_out = torch.empty(c.height, c.width, 4, dtype=torch.float32, device=vol.device)
     if depth_out is None:
         depth_out = torch.empty(c.height, c.width, dtype=torch.float32, device=vol.device)
-    _check(_lib.wrs_raycast_volume(_ptr(vol), dt, nx, ny, nz, _ptr(tf), ctypes.byref(c),
-                                   float(step_vox), float(tau), _ptr(rgba_out), _ptr(depth_out),
-                                   _stream(stream)), "wrs_raycast_volume")
+    if param is None:
+        param = 0.5 if heuristic == DEPTH_ACCUMULATED else tau
+    _check(_lib.wrs_raycast_volume_heuristic(_ptr(vol), dt, nx, ny, nz, _ptr(tf), ctypes.byref(c),
+                                             float(step_vox), int(heuristic), float(param),
+                                             _ptr(rgba_out), _ptr(depth_out), _stream(stream)),
+           "wrs_raycast_volume")
     return rgba_out, depth_out
 
 

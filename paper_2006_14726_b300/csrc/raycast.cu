@@ -1,5 +1,6 @@
 // raycast.cu -- the server's volume ray marcher with the first-hit depth heuristic (§4.1, §4.2,
-// Fig. 2; spec S2).  One thread per pixel.  Sample positions, trilinear reconstruction and the
+// Fig. 2; spec S2) and the readings of the other heuristics of §2 and §5 (spec S2a: max
+// contribution, accumulated opacity, max gradient).  One thread per pixel.  Sample positions, trilinear reconstruction and the
 // transfer-function alpha that drives the depth decision follow the spec's binary32 operation
 // order; the colour composite is ordinary binary32 arithmetic.  The transfer function is staged
 // in shared memory; volume reads go through the read-only cache.
@@ -53,10 +54,11 @@ __device__ __forceinline__ float sample(const void* __restrict__ vol, int nx, in
     return fminf(fmaxf(s, 0.0f), 1.0f);
 }
 
-template <int DT>
+// HEUR: WRS_DEPTH_* (spec S2a); param = tau (first hit) or theta (accumulated opacity).
+template <int DT, int HEUR>
 __global__ void __launch_bounds__(128) k_raycast(const void* __restrict__ vol, int nx, int ny,
                                                  int nz, const float4* __restrict__ tf,
-                                                 wrs_camera cam, float step_vox, float tau,
+                                                 wrs_camera cam, float step_vox, float param,
                                                  float4* __restrict__ rgba_out,
                                                  float* __restrict__ depth_out) {
     __shared__ float4 s_tf[256];
@@ -86,7 +88,9 @@ __global__ void __launch_bounds__(128) k_raycast(const void* __restrict__ vol, i
     }
     float3 C = make_float3(0.f, 0.f, 0.f);
     float A = 0.0f;
-    float t_first = __int_as_float(0x7f800000), t_any = t_first;
+    const float kInfF = __int_as_float(0x7f800000);
+    float t_first = kInfF, t_any = kInfF;
+    float Ad = 0.0f, best = -1.0f, t_best = kInfF, t_acc = kInfF;  // heuristic state (S2a)
     if (!miss && lo < hi) {
         const int n = max(nx, max(ny, nz));
         const float dt = __fdiv_rn(step_vox, (float)n);
@@ -103,8 +107,27 @@ __global__ void __launch_bounds__(128) k_raycast(const void* __restrict__ vol, i
             const float ph = __fsub_rn(X, (float)ti);
             const float4 e0 = s_tf[ti], e1 = s_tf[ti + 1];
             const float a = lerp_rn(e0.w, e1.w, ph);  // decision alpha (spec S2)
-            if (a >= tau && t_first == __int_as_float(0x7f800000)) t_first = tj;
-            if (a > 0.0f && t_any == __int_as_float(0x7f800000)) t_any = tj;
+            if (HEUR == WRS_DEPTH_FIRST_HIT && a >= param && t_first == kInfF) t_first = tj;
+            if (a > 0.0f && t_any == kInfF) t_any = tj;
+            if (HEUR == WRS_DEPTH_MAX_CONTRIBUTION || HEUR == WRS_DEPTH_ACCUMULATED) {
+                const float w = __fmul_rn(__fsub_rn(1.0f, Ad), a);  // this sample's contribution
+                Ad = __fadd_rn(Ad, w);
+                if (HEUR == WRS_DEPTH_MAX_CONTRIBUTION && w > 0.0f && w > best) { best = w; t_best = tj; }
+                if (HEUR == WRS_DEPTH_ACCUMULATED && Ad >= param && t_acc == kInfF) t_acc = tj;
+            }
+            if (HEUR == WRS_DEPTH_MAX_GRADIENT && a > 0.0f) {
+                // squared gradient by central differences one voxel apart
+                const float hx = __fdiv_rn(1.0f, (float)nx), hy = __fdiv_rn(1.0f, (float)ny),
+                            hz = __fdiv_rn(1.0f, (float)nz);
+                const float gx = __fsub_rn(sample<DT>(vol, nx, ny, nz, __fadd_rn(px, hx), py, pz),
+                                           sample<DT>(vol, nx, ny, nz, __fsub_rn(px, hx), py, pz));
+                const float gy = __fsub_rn(sample<DT>(vol, nx, ny, nz, px, __fadd_rn(py, hy), pz),
+                                           sample<DT>(vol, nx, ny, nz, px, __fsub_rn(py, hy), pz));
+                const float gz = __fsub_rn(sample<DT>(vol, nx, ny, nz, px, py, __fadd_rn(pz, hz)),
+                                           sample<DT>(vol, nx, ny, nz, px, py, __fsub_rn(pz, hz)));
+                const float m = __fmaf_rn(gz, gz, __fmaf_rn(gy, gy, __fmul_rn(gx, gx)));
+                if (m > best) { best = m; t_best = tj; }
+            }
             if (a > 0.0f) {
                 const float ac = half_step ? 1.0f - sqrtf(fmaxf(1.0f - a, 0.0f))
                                            : 1.0f - powf(fmaxf(1.0f - a, 0.0f), step_vox);
@@ -117,15 +140,43 @@ __global__ void __launch_bounds__(128) k_raycast(const void* __restrict__ vol, i
         }
     }
     rgba_out[pix] = make_float4(C.x, C.y, C.z, A);
-    depth_out[pix] = t_first < __int_as_float(0x7f800000) ? t_first : t_any;
+    float depth;
+    if (HEUR == WRS_DEPTH_MAX_CONTRIBUTION || HEUR == WRS_DEPTH_MAX_GRADIENT) depth = t_best;
+    else if (HEUR == WRS_DEPTH_ACCUMULATED) depth = t_acc < kInfF ? t_acc : t_any;
+    else depth = t_first < kInfF ? t_first : t_any;
+    depth_out[pix] = depth;
+}
+
+template <int DT>
+void launch_raycast(int heuristic, dim3 grid, cudaStream_t s, const void* vol, int nx, int ny,
+                    int nz, const float4* tf, const wrs_camera& cam, float step_vox, float param,
+                    float4* o4, float* depth_out) {
+    switch (heuristic) {
+        case WRS_DEPTH_MAX_CONTRIBUTION:
+            k_raycast<DT, WRS_DEPTH_MAX_CONTRIBUTION><<<grid, 128, 0, s>>>(vol, nx, ny, nz, tf, cam,
+                                                                            step_vox, param, o4, depth_out);
+            break;
+        case WRS_DEPTH_ACCUMULATED:
+            k_raycast<DT, WRS_DEPTH_ACCUMULATED><<<grid, 128, 0, s>>>(vol, nx, ny, nz, tf, cam,
+                                                                       step_vox, param, o4, depth_out);
+            break;
+        case WRS_DEPTH_MAX_GRADIENT:
+            k_raycast<DT, WRS_DEPTH_MAX_GRADIENT><<<grid, 128, 0, s>>>(vol, nx, ny, nz, tf, cam,
+                                                                        step_vox, param, o4, depth_out);
+            break;
+        default:
+            k_raycast<DT, WRS_DEPTH_FIRST_HIT><<<grid, 128, 0, s>>>(vol, nx, ny, nz, tf, cam,
+                                                                     step_vox, param, o4, depth_out);
+    }
 }
 
 }  // namespace
 
-extern "C" int wrs_raycast_volume(const void* vol, int32_t dtype, int32_t nx, int32_t ny,
-                                  int32_t nz, const float* tf, const wrs_camera* cam,
-                                  float step_vox, float tau, float* rgba_out, float* depth_out,
-                                  wrs_stream_t stream) {
+extern "C" int wrs_raycast_volume_heuristic(const void* vol, int32_t dtype, int32_t nx,
+                                            int32_t ny, int32_t nz, const float* tf,
+                                            const wrs_camera* cam, float step_vox,
+                                            int32_t heuristic, float param, float* rgba_out,
+                                            float* depth_out, wrs_stream_t stream) {
     const char* fn = "wrs_raycast_volume";
     if (int rc = wrs::check_camera(cam, fn)) return rc;
     if (!vol || !tf || !rgba_out || !depth_out)
@@ -136,7 +187,9 @@ extern "C" int wrs_raycast_volume(const void* vol, int32_t dtype, int32_t nx, in
         return wrs::fail(WRS_ERR_ARG, "%s: volume size %dx%dx%d out of range", fn, nx, ny, nz);
     if (!(step_vox >= 1e-3f && step_vox <= 1e3f))
         return wrs::fail(WRS_ERR_ARG, "%s: step_vox must be in [1e-3, 1e3] voxels", fn);
-    if (!(tau == tau)) return wrs::fail(WRS_ERR_ARG, "%s: tau is NaN", fn);
+    if (heuristic < WRS_DEPTH_FIRST_HIT || heuristic > WRS_DEPTH_MAX_GRADIENT)
+        return wrs::fail(WRS_ERR_ARG, "%s: unknown depth heuristic %d", fn, heuristic);
+    if (!(param == param)) return wrs::fail(WRS_ERR_ARG, "%s: heuristic parameter is NaN", fn);
     if ((reinterpret_cast<uintptr_t>(tf) | reinterpret_cast<uintptr_t>(rgba_out)) & 15)
         return wrs::fail(WRS_ERR_ARG, "%s: tf and rgba_out must be 16-byte aligned", fn);
     dim3 grid((cam->width + 15) / 16, (cam->height + 7) / 8);
@@ -144,9 +197,17 @@ extern "C" int wrs_raycast_volume(const void* vol, int32_t dtype, int32_t nx, in
     const float4* tf4 = reinterpret_cast<const float4*>(tf);
     float4* o4 = reinterpret_cast<float4*>(rgba_out);
     if (dtype == WRS_U8)
-        k_raycast<WRS_U8><<<grid, 128, 0, s>>>(vol, nx, ny, nz, tf4, *cam, step_vox, tau, o4, depth_out);
+        launch_raycast<WRS_U8>(heuristic, grid, s, vol, nx, ny, nz, tf4, *cam, step_vox, param, o4, depth_out);
     else
-        k_raycast<WRS_F32><<<grid, 128, 0, s>>>(vol, nx, ny, nz, tf4, *cam, step_vox, tau, o4, depth_out);
+        launch_raycast<WRS_F32>(heuristic, grid, s, vol, nx, ny, nz, tf4, *cam, step_vox, param, o4, depth_out);
     WRS_LAUNCH_CHECK(fn);
     return WRS_OK;
+}
+
+extern "C" int wrs_raycast_volume(const void* vol, int32_t dtype, int32_t nx, int32_t ny,
+                                  int32_t nz, const float* tf, const wrs_camera* cam,
+                                  float step_vox, float tau, float* rgba_out, float* depth_out,
+                                  wrs_stream_t stream) {
+    return wrs_raycast_volume_heuristic(vol, dtype, nx, ny, nz, tf, cam, step_vox,
+                                        WRS_DEPTH_FIRST_HIT, tau, rgba_out, depth_out, stream);
 }

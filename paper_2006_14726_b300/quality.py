@@ -27,14 +27,17 @@ def psnr(img: torch.Tensor, ref: torch.Tensor) -> float:
 def warp_quality(vol: torch.Tensor, tf: torch.Tensor, srv, clients: Iterable,
                  point_sizes: Iterable[int] = (1, 2, 3), max_hits: Iterable[int] = (0, 1),
                  sphere_scales: Iterable[float] = (1.0, 2.0), voxel_diag: float = 0.0,
-                 step_vox: float = 0.5, tau: float = 0.1, leaf_size: int = 1) -> List[Dict]:
+                 step_vox: float = 0.5, tau: float = 0.1, leaf_size: int = 1,
+                 heuristic: int = 0, heuristic_param=None) -> List[Dict]:
     """PSNR of every warping method for each client pose; one dict per pose.
 
     Sphere variants: the footprint radius scaled by each of ``sphere_scales`` (composited with
     each of ``max_hits``; 1 = the paper's first-hit query), and, if ``voxel_diag`` > 0, the
     paper's own radius rule (half a voxel diagonal, §4.1) with first hit.  Point variants: each
-    of ``point_sizes`` pixels."""
-    rgba, depth = raycast_volume(vol, tf, srv, step_vox, tau)
+    of ``point_sizes`` pixels.  ``heuristic`` picks the server's depth rule (DEPTH_*); the
+    ground truth's colours do not depend on it."""
+    rgba, depth = raycast_volume(vol, tf, srv, step_vox, tau, heuristic=heuristic,
+                                 param=heuristic_param)
     sp = unproject(rgba, depth, srv)
     trees = {f"spheres_x{g:g}": build_lbvh(sp, leaf_size, global_scale=g) for g in sphere_scales}
     if voxel_diag > 0.0:
