@@ -44,8 +44,9 @@ static_assert(sizeof(LbvhHeader) == 64, "header must be 64 bytes");
 // the grandchildren of binary node i (a leaf child counts as its own grandchild):
 //   float4 0..2: lo.x, lo.y, lo.z of the 4 entries; 3..5: hi.x, hi.y, hi.z; 6: references
 //   (int bits; internal references name binary nodes, whose 4-wide node is visited next); 7: unused.
-//   Unused entries carry the reference kNoChild (and an inverted box, which a slab test would NOT
-//   reject, so the reference is what the traversal checks).
+//   Unused entries carry the reference kNoChild and an empty box (low corner +inf, high corner
+//   -inf): the direction-ordered slab test (box_test_nf) gives it tn = +inf > tf = -inf, so no
+//   ray enters it.
 __host__ __device__ inline float4* lbvh_nodes(void* buf) {
     return reinterpret_cast<float4*>(reinterpret_cast<char*>(buf) + sizeof(LbvhHeader));
 }
@@ -168,13 +169,16 @@ __device__ __forceinline__ void box_test(const BoxRay& r, float lox, float loy, 
 }
 
 // The same test given the box's near and far plane coordinates for this ray (selected by the
-// sign of its direction): equal results for any box whose low corner is not above its high one.
+// sign of its direction), with a lower bound `low` >= 0 folded into the near distance: the ray
+// meets the box beyond `low` iff tn <= tf.  An empty box (low corner +inf, high corner -inf)
+// gives tn = +inf and tf = -inf, so it never passes.
 __device__ __forceinline__ void box_test_nf(const BoxRay& r, float nx, float ny, float nz,
-                                            float fx, float fy, float fz, float& tn, float& tf) {
+                                            float fx, float fy, float fz, float low, float& tn,
+                                            float& tf) {
     const float ax = fmaf(nx, r.ix, r.nx), bx = fmaf(fx, r.ix, r.fx);
     const float ay = fmaf(ny, r.iy, r.ny), by = fmaf(fy, r.iy, r.fy);
     const float az = fmaf(nz, r.iz, r.nz), bz = fmaf(fz, r.iz, r.fz);
-    tn = fmaxf(max3f(ax, ay, az), 0.0f);
+    tn = max3f(ax, ay, fmaxf(az, low));
     tf = min3f(bx, by, bz);
 }
 

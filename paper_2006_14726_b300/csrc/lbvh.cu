@@ -405,7 +405,8 @@ __device__ __forceinline__ void store_box(float4* nodes, uint32_t node, uint32_t
 // the node holds plane q -- low x, y, z, high x, y, z -- of all four entries; float4 6 holds the
 // four references), so that a traversal step loads one coordinate of all four boxes per float4.
 // Fixed slots: child c's children go to slots 2c and 2c + 1; a leaf child stands for itself in
-// slot 2c and slot 2c + 1 is unused (reference kNoChild).  The refit fills them: the thread that
+// slot 2c and slot 2c + 1 is unused (an empty box, low corner +inf and high corner -inf, which no
+// ray enters, and the reference kNoChild).  The refit fills them: the thread that
 // holds the final box of a node or leaf X writes it into the 4-wide node of X's grandparent, and a
 // leaf also into its parent's.  These are plain stores off the climb's critical path.
 __device__ __forceinline__ void wide_entry(float4* __restrict__ wide, uint32_t i, uint32_t e,
@@ -458,8 +459,10 @@ __global__ void __launch_bounds__(kRefitBlock) k_leaves_refit(
         store_box(nodes, node, slot, lo, hi);  // the traversal reads it after the kernel
         if (xref & kLeafBit) {  // a leaf child stands for itself in its parent's 4-wide node
             wide_entry(wide, node, 2 * slot, lo, hi, xref);
-            reinterpret_cast<float*>(wide + 8 * (size_t)node)[24 + 2 * slot + 1] =
-                __uint_as_float(wrs::kNoChild);
+            // the slot after it is unused: an empty box (never hit) and no reference
+            const float elo[3] = {INFINITY, INFINITY, INFINITY};
+            const float ehi[3] = {-INFINITY, -INFINITY, -INFINITY};
+            wide_entry(wide, node, 2 * slot + 1, elo, ehi, wrs::kNoChild);
         }
         if (node != 0 && (gp >> 1) + 1 < m)  // a grandchild of gp's node
             wide_entry(wide, gp >> 1, 2 * (gp & 1u) + slot, lo, hi, xref);

@@ -148,7 +148,8 @@ __device__ __forceinline__ int64_t visit_node4(const Scene& sc, const Ray& ray,
                                                uint32_t (&ki)[K], uint32_t (&kid)[K], int& count,
                                                int* stack, int& sp, Counts& cnt) {
     if (ref + 1 >= m) return -2;  // not an internal node of this tree
-    const float lower = has_last ? last_key : -kInf;
+    // hits of this pass lie at or beyond max(last key, 0): boxes ending before it are skipped
+    const float low = has_last ? fmaxf(last_key, 0.0f) : 0.0f;
     const float4* w = sc.wide + 8 * (size_t)ref;
     // low planes at w[0..2], high planes at w[3..5]: the ray's near plane of each axis is picked
     // by address (br.s* = 0 or 3), so no per-box min/max orders the slab distances
@@ -157,16 +158,18 @@ __device__ __forceinline__ int64_t visit_node4(const Scene& sc, const Ray& ray,
     const float4 rf = __ldg(w + 6);
     if (COUNT) { cnt.nodes++; cnt.boxes += 4; }
     float tn[4], tf[4];
-    wrs::box_test_nf(br, nx.x, ny.x, nz.x, fx.x, fy.x, fz.x, tn[0], tf[0]);
-    wrs::box_test_nf(br, nx.y, ny.y, nz.y, fx.y, fy.y, fz.y, tn[1], tf[1]);
-    wrs::box_test_nf(br, nx.z, ny.z, nz.z, fx.z, fy.z, fz.z, tn[2], tf[2]);
-    wrs::box_test_nf(br, nx.w, ny.w, nz.w, fx.w, fy.w, fz.w, tn[3], tf[3]);
+    wrs::box_test_nf(br, nx.x, ny.x, nz.x, fx.x, fy.x, fz.x, low, tn[0], tf[0]);
+    wrs::box_test_nf(br, nx.y, ny.y, nz.y, fx.y, fy.y, fz.y, low, tn[1], tf[1]);
+    wrs::box_test_nf(br, nx.z, ny.z, nz.z, fx.z, fy.z, fz.z, low, tn[2], tf[2]);
+    wrs::box_test_nf(br, nx.w, ny.w, nz.w, fx.w, fy.w, fz.w, low, tn[3], tf[3]);
     uint32_t r[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
                      __float_as_uint(rf.w)};
     float key[4];
 #pragma unroll
     for (int e = 0; e < 4; e++) {
-        bool h = r[e] != wrs::kNoChild && tn[e] <= tf[e] && tn[e] <= kk[K - 1] && tf[e] >= lower;
+        // an unused slot holds an empty box and never passes; the cut-off is the current K-th
+        // nearest hit of this pass (keys of this pass are >= low, so the cut-off is too)
+        bool h = tn[e] <= fminf(tf[e], kk[K - 1]);
         if (h && (r[e] & kLeafBit)) {
             leaf_hits<K, COUNT>(sc, ray, r[e], n, leaf, has_last, last_key, last_id, kk, ki, kid,
                                 count, cnt);
