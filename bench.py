@@ -28,6 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -86,7 +87,9 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the samples go to $WRS_CLOCKS_DIR (default: the system's temporary directory)
+        folder = os.environ.get("WRS_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(folder, f"wrs_clocks_rank{index}.csv")
 
     def start(self):
         try:
