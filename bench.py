@@ -39,6 +39,7 @@ sys.path.insert(0, ROOT)
 METRIC = "1080p/2M-splat Mrays/s & LBVH ms; batched and fwd+bwd vs plain, % roofline"
 UNIT = "Mrays/s"
 FRAMES_PER_IMAGE = 4
+SCHEDULE_NAMES = ["one thread per pixel", "persistent, lane refill", "packet, one traversal per warp"]
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -390,7 +391,7 @@ def main():
     traffic = profiled_traffic()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "kernel": "k_trace_pr" if sched == 1 else "k_trace",
+                "kernel": ["k_trace", "k_trace_pr", "k_trace_packet"][sched],
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                 "bytes_per_ray": bpr, "flops_per_ray": fpr,
                 "fp32_tflops_achieved": fpr * npix_c / (trace_ms * 1e-3) / 1e12,
@@ -401,7 +402,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(W, statistics.mean(n_splats), {
                 "leaf_size": leaf, "k_chunk": kc, "block": block, "autotuned": not args.no_autotune,
-                "schedule": ["one thread per pixel", "persistent, lane refill"][sched],
+                "schedule": SCHEDULE_NAMES[sched],
                 "bvh_width": width,
                 "l2": "flushed before every step (256 MiB write outside the timed events)",
                 "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
@@ -496,7 +497,7 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
         del sp
     batch = wrs.Batch(sess)
     bt = autotune.tune_batched(batch, params)
-    bparams = wrs.TraceParams(0, 1e-5, 0.0, bt["k_chunk"], bt["block"], 1, bt["width"])
+    bparams = wrs.TraceParams(0, 1e-5, 0.0, bt["k_chunk"], bt["block"], bt["schedule"], bt["width"])
     outs = [torch.empty(c.height, c.width, 4, device=dev) for _, _, c in sess]
     seq_cams = [wrs.make_camera(c) for _, _, c in sess]
 
@@ -523,6 +524,7 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
                        "sequential_mrays_s": world * rays / (ms_seq * 1e-3) / 1e6,
                        "one_launch_ms": ms_graph, "sequential_ms": ms_seq,
                        "k_chunk": bt["k_chunk"], "block": bt["block"], "bvh_width": bt["width"],
+                       "schedule": SCHEDULE_NAMES[bt["schedule"]],
                        "leaf_size": leaf}
     del sess, batch, outs, g
 
@@ -559,8 +561,7 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
                           "ms_per_step": ms_acc, "rebuild_ms": ms_rebuild,
                           "trace_ms": (ms_acc - ms_rebuild) / FRAMES_PER_IMAGE,
                           "leaf_size": at["leaf"], "k_chunk": at["k_chunk"], "block": at["block"],
-                          "schedule": "persistent lane refill" if at["schedule"] else
-                                      "one thread per pixel", "bvh_width": at["width"],
+                          "schedule": SCHEDULE_NAMES[at["schedule"]], "bvh_width": at["width"],
                           "note": "step = push one 1080p server frame into the window of the 4 "
                                   "newest (4 unprojections into one set + LBVH over about 8 M "
                                   "splats) + 4 client traces of the union"}

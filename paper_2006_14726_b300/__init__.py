@@ -48,6 +48,7 @@ RADIUS_FOOTPRINT = 0
 RADIUS_VOXEL = 1
 SCHEDULE_PER_PIXEL = 0
 SCHEDULE_PERSISTENT = 1
+SCHEDULE_PACKET = 2
 DEPTH_FIRST_HIT = 0
 DEPTH_MAX_CONTRIBUTION = 1
 DEPTH_ACCUMULATED = 2
@@ -540,7 +541,8 @@ class Batch:
 
 def trace_batched(batch: Batch, params: TraceParams = TraceParams(),
                   status: Optional[torch.Tensor] = None, stream=None) -> List[torch.Tensor]:
-    """All sessions of ``batch`` in one persistent launch; returns the per-session images."""
+    """All sessions of ``batch`` in one launch (params.schedule: per-pixel warps or persistent);
+    returns the per-session images."""
     p = params.c(None)
     _check(_lib.wrs_trace_batched(_ptr(batch.desc), batch.n_sessions, batch.total_tiles,
                                   ctypes.byref(p), _ptr(batch.work), _ptr(status), _stream(stream)),

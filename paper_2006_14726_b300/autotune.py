@@ -1,5 +1,6 @@
-"""Autotuner for the performance knobs of the trace: LBVH leaf size, k-buffer depth, block size and
-schedule (one thread per pixel, or persistent blocks with lane refill).
+"""Autotuner for the performance knobs of the trace: LBVH leaf size, k-buffer depth, block size,
+node width and schedule (one thread per pixel, persistent blocks with lane refill, or one
+warp-shared traversal per 8x4 tile).
 
 The knobs never change results (the hit set and order are fixed by the binary32 sphere test; the
 compositing visits hits in that order), so the tuner only measures time: it builds one LBVH per
@@ -15,7 +16,8 @@ from typing import Callable, Dict, Iterable, Optional, Sequence
 
 import torch
 
-from . import (SCHEDULE_PER_PIXEL, SCHEDULE_PERSISTENT, Batch, SplatBuffers, TraceParams,
+from . import (SCHEDULE_PACKET, SCHEDULE_PER_PIXEL, SCHEDULE_PERSISTENT, Batch, SplatBuffers,
+               TraceParams,
                build_lbvh, trace, trace_batched)
 
 LEAVES = (1, 2, 4)
@@ -84,10 +86,12 @@ def tune_trace(splats: SplatBuffers, cams: Sequence, base: TraceParams = TracePa
     for leaf in leaves:
         bvh, srt = build_lbvh(splats, leaf)
         outs = [torch.empty(c.height, c.width, 4, device=splats.pos_r.device) for c in cams]
-        shapes = [(b, SCHEDULE_PER_PIXEL) for b in blocks] + [(128, SCHEDULE_PERSISTENT)]
+        shapes = [(b, SCHEDULE_PER_PIXEL) for b in blocks] + [(128, SCHEDULE_PERSISTENT),
+                                                              (128, SCHEDULE_PACKET)]
         for k in ks:
             for block, sched in shapes:
-                for width in widths:
+                # the packet schedule always walks the 4-wide nodes
+                for width in (widths if sched != SCHEDULE_PACKET else (4,)):
                     p = TraceParams(base.max_hits, base.t_stop, base.edge_softness, k, block, sched,
                                     width)
 
@@ -106,13 +110,15 @@ def tune_trace(splats: SplatBuffers, cams: Sequence, base: TraceParams = TracePa
 
 def tune_batched(batch: Batch, base: TraceParams = TraceParams(), ks: Iterable[int] = KS,
                  widths: Iterable[int] = WIDTHS, reps: int = 3) -> Dict:
-    """Pick (k_chunk, width) for one persistent multi-session launch (leaf sizes are fixed by the
-    sessions' LBVHs; the launch shape is fixed: one resident wave of 128-thread blocks)."""
+    """Pick (k_chunk, width, schedule) for one multi-session launch (leaf sizes are fixed by the
+    sessions' LBVHs; blocks of 128 threads: one warp per tile, or one resident wave with lane
+    refill)."""
     best = None
-    for k in ks:
-        for width in widths:
-            p = TraceParams(base.max_hits, base.t_stop, base.edge_softness, k, 128, 1, width)
-            ms = _time_ms(lambda: trace_batched(batch, p), reps)
-            if best is None or ms < best["ms"]:
-                best = {"k_chunk": k, "block": 128, "width": width, "ms": ms}
+    for sched in (SCHEDULE_PER_PIXEL, SCHEDULE_PERSISTENT):
+        for k in ks:
+            for width in widths:
+                p = TraceParams(base.max_hits, base.t_stop, base.edge_softness, k, 128, sched, width)
+                ms = _time_ms(lambda: trace_batched(batch, p), reps)
+                if best is None or ms < best["ms"]:
+                    best = {"k_chunk": k, "block": 128, "width": width, "schedule": sched, "ms": ms}
     return best

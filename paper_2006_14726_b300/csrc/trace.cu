@@ -325,6 +325,133 @@ __device__ __forceinline__ float4 trace_ray(const Scene& sc, const Comp& cp, con
     return make_float4(C.x, C.y, C.z, 1.0f - T);
 }
 
+// ---- packet schedule: one traversal per warp ------------------------------------------------
+// The 32 rays of an 8x4 pixel tile share one traversal of the 4-wide nodes: every lane tests the
+// node's four boxes against its own ray (its own pass bound and k-buffer cut-off), a child is
+// entered if any lane enters it, and the children are ordered by the smallest entry distance over
+// the lanes.  Control flow and the stack are warp-uniform (every lane holds the same stack), so
+// the box tests run with all lanes active; a leaf is tested only by the lanes whose ray enters
+// it.  Each lane keeps its own k-buffer, so the hits a lane gathers -- and the image -- are those
+// of the per-ray traversal; only the set of visited nodes differs (the union over the warp).
+// All 32 lanes of a warp must call these functions together (lanes without a ray pass
+// part = false).
+template <int K>
+__device__ __forceinline__ int64_t visit_node4_packet(const Scene& sc, const Ray& ray,
+                                                      const wrs::BoxRay& br, uint32_t ref,
+                                                      uint32_t n, uint32_t leaf, uint32_t m,
+                                                      bool part, bool has_last, float last_key,
+                                                      uint32_t last_id, float (&kk)[K],
+                                                      uint32_t (&ki)[K], uint32_t (&kid)[K],
+                                                      int& count, int* stack, int& sp) {
+    if (ref + 1 >= m) return -2;  // not an internal node of this tree (ref is warp-uniform)
+    const float low = has_last ? fmaxf(last_key, 0.0f) : 0.0f;
+    const float4* w = sc.wide + 8 * (size_t)ref;
+    const float4 nx = __ldg(w + br.sx), ny = __ldg(w + 1 + br.sy), nz = __ldg(w + 2 + br.sz);
+    const float4 fx = __ldg(w + 3 - br.sx), fy = __ldg(w + 4 - br.sy), fz = __ldg(w + 5 - br.sz);
+    const float4 rf = __ldg(w + 6);
+    float tn[4], tf[4];
+    wrs::box_test_nf(br, nx.x, ny.x, nz.x, fx.x, fy.x, fz.x, low, tn[0], tf[0]);
+    wrs::box_test_nf(br, nx.y, ny.y, nz.y, fx.y, fy.y, fz.y, low, tn[1], tf[1]);
+    wrs::box_test_nf(br, nx.z, ny.z, nz.z, fx.z, fy.z, fz.z, low, tn[2], tf[2]);
+    wrs::box_test_nf(br, nx.w, ny.w, nz.w, fx.w, fy.w, fz.w, low, tn[3], tf[3]);
+    uint32_t r[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
+                     __float_as_uint(rf.w)};
+    float key[4];
+    Counts none;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        bool h = part && tn[e] <= fminf(tf[e], kk[K - 1]);
+        if (h && (r[e] & kLeafBit)) {
+            leaf_hits<K, false>(sc, ray, r[e], n, leaf, has_last, last_key, last_id, kk, ki, kid,
+                                count, none);
+            h = false;
+        }
+        // the warp's key of the entry: its smallest entry distance over the lanes that enter it
+        // (distances are >= 0, so their bit patterns order like the values; +inf = nobody)
+        key[e] = __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(h ? tn[e] : kInf)));
+    }
+    cswap(key[0], r[0], key[1], r[1]);
+    cswap(key[2], r[2], key[3], r[3]);
+    cswap(key[0], r[0], key[2], r[2]);
+    cswap(key[1], r[1], key[3], r[3]);
+    cswap(key[1], r[1], key[2], r[2]);
+    if (!(key[0] < kInf)) return kLeafBit;
+    const int extra = (key[1] < kInf) + (key[2] < kInf) + (key[3] < kInf);
+    if (sp + extra > wrs::kStack) return -1;
+    if (key[3] < kInf) stack[sp++] = (int)r[3];
+    if (key[2] < kInf) stack[sp++] = (int)r[2];
+    if (key[1] < kInf) stack[sp++] = (int)r[1];
+    return r[0];
+}
+
+template <int K>
+__device__ __forceinline__ int gather_packet(const Scene& sc, const Ray& ray,
+                                             const wrs::BoxRay& br, uint32_t n, uint32_t leaf,
+                                             int32_t root, bool part, bool has_last,
+                                             float last_key, uint32_t last_id, float (&kk)[K],
+                                             uint32_t (&ki)[K], uint32_t (&kid)[K]) {
+#pragma unroll
+    for (int s = 0; s < K; s++) { kk[s] = kInf; ki[s] = 0xFFFFFFFFu; kid[s] = 0xFFFFFFFFu; }
+    int count = 0;
+    Counts none;
+    const uint32_t m = (n + leaf - 1) / leaf;
+    if ((uint32_t)root & kLeafBit) {
+        if (part)
+            leaf_hits<K, false>(sc, ray, (uint32_t)root, n, leaf, has_last, last_key, last_id, kk,
+                                ki, kid, count, none);
+        return count;
+    }
+    int stack[wrs::kStack];
+    int sp = 0;
+    uint32_t ref = (uint32_t)root;
+    uint32_t budget = m + 1;
+    while (true) {
+        if (budget-- == 0) return -2;
+        const int64_t next = visit_node4_packet<K>(sc, ray, br, ref, n, leaf, m, part, has_last,
+                                                   last_key, last_id, kk, ki, kid, count, stack, sp);
+        if (next < 0) return (int)next;
+        if (next != kLeafBit) { ref = (uint32_t)next; continue; }
+        if (sp == 0) break;
+        ref = (uint32_t)stack[--sp];
+    }
+    return count;
+}
+
+// Forward trace of the warp's rays; lanes with active = false take part without a ray.
+template <int K>
+__device__ __forceinline__ float4 trace_ray_packet(const Scene& sc, const Comp& cp,
+                                                   const RayCtx& rc, bool active,
+                                                   uint32_t& overflow_bits) {
+    float T = 1.0f;
+    float3 C = make_float3(0.f, 0.f, 0.f);
+    overflow_bits = 0;
+    bool done = !active || rc.n == 0;
+    int used = 0;
+    bool has_last = false;
+    float last_key = 0.0f;
+    uint32_t last_id = 0;
+    float kk[K];
+    uint32_t ki[K], kid[K];
+    Counts none;
+    // passes continue while any lane of the warp still needs hits; each pass is one traversal
+    for (uint32_t pass = 0; __any_sync(0xffffffffu, !done); pass++) {
+        const int count = gather_packet<K>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, !done,
+                                           has_last, last_key, last_id, kk, ki, kid);
+        if (count < 0) {  // warp-uniform: the traversal failed for every lane
+            if (!done)
+                overflow_bits = count == -1 ? WRS_STATUS_STACK_OVERFLOW : WRS_STATUS_MALFORMED_TREE;
+            break;
+        }
+        if (!done) {
+            done = composite_chunk<K, false>(sc, cp, rc.ray, ki, count, T, C, used, none);
+            has_last = true;
+            last_key = kk[K - 1];
+            last_id = kid[K - 1];
+        }
+    }
+    return make_float4(C.x, C.y, C.z, 1.0f - T);
+}
+
 // ---- persistent schedule with lane refill ----------------------------------------------------
 // The same per-ray work as trace_ray, run as a per-lane state machine: every loop iteration a
 // lane advances its traversal by one node or one leaf; when a ray finishes its lane goes idle,
@@ -514,6 +641,23 @@ __global__ void __launch_bounds__(256, PixelMinBlocks<K, W4>::value) k_trace(Sce
     out[(size_t)y * cam.width + x] = o;
 }
 
+// Packet schedule (4-wide nodes only): every lane of the block stays to the end, lanes outside
+// the image take part in their warp's traversal without a ray.
+template <int K>
+__global__ void __launch_bounds__(256) k_trace_packet(Scene sc, Comp cp, wrs_camera cam,
+                                                      float4* __restrict__ out, int32_t* status) {
+    int px, py;
+    tile_pixel(threadIdx.x, px, py);
+    const int tile_h = (blockDim.x >> 6) * 4;
+    const int x = blockIdx.x * 16 + px, y = blockIdx.y * tile_h + py;
+    const bool active = x < cam.width && y < cam.height;
+    const RayCtx rc = make_ray_ctx(sc, cam, active ? x : 0, active ? y : 0);
+    uint32_t overflow;
+    const float4 o = trace_ray_packet<K>(sc, cp, rc, active, overflow);
+    if (overflow) wrs::set_status(status, overflow);
+    if (active) out[(size_t)y * cam.width + x] = o;
+}
+
 template <int K, bool W4>
 __global__ void __launch_bounds__(256) k_trace_count(Scene sc, Comp cp, wrs_camera cam,
                                                      unsigned long long* counters, int32_t* status) {
@@ -536,6 +680,43 @@ __global__ void __launch_bounds__(256) k_trace_count(Scene sc, Comp cp, wrs_came
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if ((threadIdx.x & 31) == 0) atomicAdd(counters + k, s);
     }
+}
+
+// Multi-session trace, one thread per pixel: warp w of the grid traces 8x4 tile w of the
+// concatenated tile space (session s owns tiles [tile_begin_s, tile_begin_s + tiles_s)); the
+// warp finds its session by binary search over the sessions' first tiles.
+template <int K, bool W4>
+__global__ void __launch_bounds__(128) k_trace_batched_pp(const wrs_session* __restrict__ sess,
+                                                          int n_sessions, uint32_t total_tiles,
+                                                          Comp cp, int32_t* status) {
+    const uint32_t tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (tile >= total_tiles) return;
+    const uint32_t pos = threadIdx.x & 31u;
+    int lo = 0, hi = n_sessions - 1;  // last session with tile_begin <= tile
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sess[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+    }
+    const wrs_session& S = sess[lo];
+    const uint32_t W = (uint32_t)S.cam.width, H = (uint32_t)S.cam.height;
+    const uint32_t local = tile - S.tile_begin, tiles_x = (W + 7) / 8;
+    const uint32_t x = (local % tiles_x) * 8 + (pos & 7), y = (local / tiles_x) * 4 + (pos >> 3);
+    if (x >= W || y >= H) return;
+    Scene sc;
+    sc.hdr = static_cast<const LbvhHeader*>(S.nodes);
+    sc.nodes = wrs::lbvh_nodes(S.nodes);
+    sc.wide = W4 ? sc.nodes + 4 * (size_t)sc.hdr->wide_start : nullptr;
+    sc.pos_r = reinterpret_cast<const float4*>(S.pos_r);
+    sc.rgba = reinterpret_cast<const float4*>(S.rgba);
+    sc.id = S.id;
+    sc.src = S.src;
+    sc.opacity = S.opacity;
+    const RayCtx rc = make_ray_ctx(sc, S.cam, (int)x, (int)y);
+    uint32_t overflow;
+    Counts cnt;
+    const float4 o = trace_ray<K, false, W4>(sc, cp, rc, overflow, cnt);
+    if (overflow) wrs::set_status(status, overflow);
+    reinterpret_cast<float4*>(S.rgba_out)[(size_t)y * W + x] = o;
 }
 
 // Persistent multi-session trace with lane refill.  Work is numbered in 8x4 ray tiles over all
@@ -924,7 +1105,8 @@ int check_trace_args(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_ca
     if (p->block != 64 && p->block != 128 && p->block != 256)
         return wrs::fail(WRS_ERR_ARG, "%s: block %d not in {64,128,256}", fn, p->block);
     if (p->max_hits < 0) return wrs::fail(WRS_ERR_ARG, "%s: max_hits < 0", fn);
-    if (p->schedule != WRS_SCHEDULE_PER_PIXEL && p->schedule != WRS_SCHEDULE_PERSISTENT)
+    if (p->schedule != WRS_SCHEDULE_PER_PIXEL && p->schedule != WRS_SCHEDULE_PERSISTENT &&
+        p->schedule != WRS_SCHEDULE_PACKET)
         return wrs::fail(WRS_ERR_ARG, "%s: unknown schedule %d", fn, p->schedule);
     if (p->width != 0 && p->width != 2 && p->width != 4)
         return wrs::fail(WRS_ERR_ARG, "%s: width %d not 2 or 4 (0 = 2)", fn, p->width);
@@ -995,6 +1177,18 @@ template <int K, bool W4> struct LaunchTrace {
     static void run(dim3 g, int b, cudaStream_t s, Scene sc, Comp cp, wrs_camera cam, float4* o,
                     int32_t* st) {
         k_trace<K, W4><<<g, b, 0, s>>>(sc, cp, cam, o, st);
+    }
+};
+template <int K, bool W4> struct LaunchBatchedPP {
+    static void run(uint32_t blocks, const wrs_session* ss, int ns, uint32_t tt, Comp cp,
+                    int32_t* st, cudaStream_t s) {
+        k_trace_batched_pp<K, W4><<<blocks, 128, 0, s>>>(ss, ns, tt, cp, st);
+    }
+};
+template <int K, bool W4> struct LaunchTracePacket {  // W4 is implied: the packet traversal is 4-wide
+    static void run(dim3 g, int b, cudaStream_t s, Scene sc, Comp cp, wrs_camera cam, float4* o,
+                    int32_t* st) {
+        k_trace_packet<K><<<g, b, 0, s>>>(sc, cp, cam, o, st);
     }
 };
 template <int K, bool W4> struct LaunchTracePr {
@@ -1088,6 +1282,10 @@ int wrs_trace(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* c
     if (params->schedule == WRS_SCHEDULE_PERSISTENT)
         dispatch_k<LaunchTracePr>(K, W, resident_grid<LaunchTracePr>(K, W), 128, s, sc,
                                   comp_of(params), *cam, out, status);
+    else if (params->schedule == WRS_SCHEDULE_PACKET)
+        dispatch_k1<LaunchTracePacket, true>(K, grid_for(cam, params->block), params->block, s,
+                                             make_scene(bvh, sorted, params->opacity, 4),
+                                             comp_of(params), *cam, out, status);
     else
         dispatch_k<LaunchTrace>(K, W, grid_for(cam, params->block), params->block, s, sc,
                                 comp_of(params), *cam, out, status);
@@ -1136,8 +1334,12 @@ int wrs_trace_batched(const wrs_session* sessions, int32_t n_sessions, uint32_t 
     if (e != cudaSuccess) return wrs::cuda_fail(e, fn);
     if (total_tiles == 0) return WRS_OK;
     const int K = effective_k(params), W = params->width;
-    dispatch_k<LaunchBatched>(K, W, resident_grid<LaunchBatched>(K, W), 128, s, sessions,
-                              n_sessions, total_tiles, comp_of(params), work_counter, status);
+    if (params->schedule == WRS_SCHEDULE_PER_PIXEL)
+        dispatch_k<LaunchBatchedPP>(K, W, (total_tiles + 3) / 4, sessions, n_sessions, total_tiles,
+                                    comp_of(params), status, s);
+    else
+        dispatch_k<LaunchBatched>(K, W, resident_grid<LaunchBatched>(K, W), 128, s, sessions,
+                                  n_sessions, total_tiles, comp_of(params), work_counter, status);
     WRS_LAUNCH_CHECK(fn);
     return WRS_OK;
 }

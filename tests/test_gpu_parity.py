@@ -353,11 +353,15 @@ def test_batched_equals_sequential_bitwise(wrs):
         refs.append(wrs.trace(bvh, srt, cli).cpu().numpy())
     batch = wrs.Batch(sessions)
     st = wrs.new_status()
-    for k, width in ((8, 2), (1, 4), (4, 2), (16, 4)):
-        outs = wrs.trace_batched(batch, wrs.TraceParams(k_chunk=k, width=width), status=st)
-        wrs.check_status(st)
-        for o, r in zip(outs, refs):
-            assert np.array_equal(o.cpu().numpy().view(np.uint32), r.view(np.uint32))
+    for sched in (wrs.SCHEDULE_PER_PIXEL, wrs.SCHEDULE_PERSISTENT):
+        for k, width in ((8, 2), (1, 4), (4, 2), (16, 4)):
+            for o in batch.outputs:
+                o.fill_(-1.0)
+            outs = wrs.trace_batched(batch, wrs.TraceParams(k_chunk=k, width=width, schedule=sched),
+                                     status=st)
+            wrs.check_status(st)
+            for o, r in zip(outs, refs):
+                assert np.array_equal(o.cpu().numpy().view(np.uint32), r.view(np.uint32)), (sched, k)
 
 
 # ---------------------------------------------------------------------------------------------
