@@ -44,9 +44,10 @@ static_assert(sizeof(LbvhHeader) == 64, "header must be 64 bytes");
 // the grandchildren of binary node i (a leaf child counts as its own grandchild):
 //   float4 0..2: lo.x, lo.y, lo.z of the 4 entries; 3..5: hi.x, hi.y, hi.z; 6: references
 //   (int bits; internal references name binary nodes, whose 4-wide node is visited next); 7: unused.
-//   Unused entries carry the reference kNoChild and an empty box (low corner +inf, high corner
-//   -inf): the direction-ordered slab test (box_test_nf) gives it tn = +inf > tf = -inf, so no
-//   ray enters it.
+//   Unused entries carry the reference kNoChild, low x = +inf and high x = -inf (their other
+//   planes are not written): the direction-ordered slab test (box_test_nf) gets tn = +inf from
+//   the x slab and tf = -inf (three-input min/max ignore a NaN in the other planes), so no ray
+//   enters them.
 __host__ __device__ inline float4* lbvh_nodes(void* buf) {
     return reinterpret_cast<float4*>(reinterpret_cast<char*>(buf) + sizeof(LbvhHeader));
 }

@@ -393,11 +393,18 @@ constexpr uint32_t kRefitBlock = 256;
 
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
+// Child box `slot` of binary node `node` (floats 6 slot .. 6 slot + 5 of its 64-byte record) in
+// two vector stores: slot 0 = 16 + 8 bytes, slot 1 = 8 + 16 bytes (all naturally aligned).
 __device__ __forceinline__ void store_box(float4* nodes, uint32_t node, uint32_t slot,
                                           const float lo[3], const float hi[3]) {
-    float* f = reinterpret_cast<float*>(nodes + 4 * (size_t)node) + 6 * slot;
-    __stcg(f + 0, lo[0]); __stcg(f + 1, lo[1]); __stcg(f + 2, lo[2]);
-    __stcg(f + 3, hi[0]); __stcg(f + 4, hi[1]); __stcg(f + 5, hi[2]);
+    float* f = reinterpret_cast<float*>(nodes + 4 * (size_t)node);
+    if (slot == 0) {
+        __stcg(reinterpret_cast<float4*>(f), make_float4(lo[0], lo[1], lo[2], hi[0]));
+        __stcg(reinterpret_cast<float2*>(f + 4), make_float2(hi[1], hi[2]));
+    } else {
+        __stcg(reinterpret_cast<float2*>(f + 6), make_float2(lo[0], lo[1]));
+        __stcg(reinterpret_cast<float4*>(f + 8), make_float4(lo[2], hi[0], hi[1], hi[2]));
+    }
 }
 
 // ---- 4-wide nodes ---------------------------------------------------------------------------
@@ -405,8 +412,9 @@ __device__ __forceinline__ void store_box(float4* nodes, uint32_t node, uint32_t
 // the node holds plane q -- low x, y, z, high x, y, z -- of all four entries; float4 6 holds the
 // four references), so that a traversal step loads one coordinate of all four boxes per float4.
 // Fixed slots: child c's children go to slots 2c and 2c + 1; a leaf child stands for itself in
-// slot 2c and slot 2c + 1 is unused (an empty box, low corner +inf and high corner -inf, which no
-// ray enters, and the reference kNoChild).  The refit fills them: the thread that
+// slot 2c and slot 2c + 1 is unused: low x = +inf and high x = -inf (whatever its other planes
+// hold, no ray enters it: its x slab is empty) and the reference kNoChild.  The refit fills them:
+// the thread that
 // holds the final box of a node or leaf X writes it into the 4-wide node of X's grandparent, and a
 // leaf also into its parent's.  These are plain stores off the climb's critical path.
 __device__ __forceinline__ void wide_entry(float4* __restrict__ wide, uint32_t i, uint32_t e,
@@ -415,6 +423,14 @@ __device__ __forceinline__ void wide_entry(float4* __restrict__ wide, uint32_t i
     w[0] = lo[0]; w[4] = lo[1]; w[8] = lo[2];
     w[12] = hi[0]; w[16] = hi[1]; w[20] = hi[2];
     w[24] = __uint_as_float(ref);
+}
+
+// An unused entry: three stores (its x slab empty, no reference) instead of a whole empty box.
+__device__ __forceinline__ void wide_unused(float4* __restrict__ wide, uint32_t i, uint32_t e) {
+    float* w = reinterpret_cast<float*>(wide + 8 * (size_t)i) + e;
+    w[0] = INFINITY;
+    w[12] = -INFINITY;
+    w[24] = __uint_as_float(wrs::kNoChild);
 }
 
 __global__ void __launch_bounds__(kRefitBlock) k_leaves_refit(
@@ -459,10 +475,7 @@ __global__ void __launch_bounds__(kRefitBlock) k_leaves_refit(
         store_box(nodes, node, slot, lo, hi);  // the traversal reads it after the kernel
         if (xref & kLeafBit) {  // a leaf child stands for itself in its parent's 4-wide node
             wide_entry(wide, node, 2 * slot, lo, hi, xref);
-            // the slot after it is unused: an empty box (never hit) and no reference
-            const float elo[3] = {INFINITY, INFINITY, INFINITY};
-            const float ehi[3] = {-INFINITY, -INFINITY, -INFINITY};
-            wide_entry(wide, node, 2 * slot + 1, elo, ehi, wrs::kNoChild);
+            wide_unused(wide, node, 2 * slot + 1);  // the slot after it is unused
         }
         if (node != 0 && (gp >> 1) + 1 < m)  // a grandchild of gp's node
             wide_entry(wide, gp >> 1, 2 * (gp & 1u) + slot, lo, hi, xref);

@@ -157,15 +157,16 @@ def _check_lbvh(wrs, sp_gpu, ref_sp, leaf, scale=None):
         assert np.array_equal(refs.cpu().numpy(), ref["child"])
         assert np.array_equal(boxes.cpu().numpy().view(np.uint32), ref["boxes"].view(np.uint32))
         # 4-wide nodes: the grandchildren of each binary node in slots 2c, 2c + 1 for child c (a
-        # leaf child stands for itself in slot 2c; slot 2c + 1 is then unused: reference -1 and
-        # an empty box, low corner +inf and high corner -inf, which no ray enters)
+        # leaf child stands for itself in slot 2c; slot 2c + 1 is then unused: reference -1, low
+        # x = +inf and high x = -inf, so that no ray enters it)
         wb, wr = (t.cpu().numpy() for t in bvh.wide_table())
         child, cbox = ref["child"], ref["boxes"]
         for i in range(0, M - 1, max(1, (M - 1) // 500)):
             for c in range(2):
                 r = int(child[i, c])
                 if r < 0:
-                    ents = [(cbox[i, c], r), (np.float32([np.inf] * 3 + [-np.inf] * 3), -1)]
+                    ents = [(cbox[i, c], r), (None, -1)]
+                    assert wb[i, 2 * c + 1, 0] == np.inf and wb[i, 2 * c + 1, 3] == -np.inf
                 else:
                     ents = [(cbox[r, 0], int(child[r, 0])), (cbox[r, 1], int(child[r, 1]))]
                 for gc, (b, rr) in enumerate(ents):
