@@ -676,17 +676,16 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
     dparams = wrs.TraceParams(0, 1e-5, 0.25, params.k_chunk, params.block, params.schedule,
                               params.width)
 
+    # all views of a step share one LBVH build (one radius scale per step); the backward pass
+    # accumulates every view's gradient in place
+    target = torch.stack(targets)
+
     def fwd():
         with torch.no_grad():
-            for v in views:
-                wrs.render(sp, v, col, opa, scl, dparams, leaf)
+            wrs.render_views(sp, views, col, opa, scl, dparams, leaf)
 
     def loss_fn():
-        loss = 0.0
-        for v, t in zip(views, targets):
-            img = wrs.render(sp, v, col, opa, scl, dparams, leaf)
-            loss = loss + ((img - t) ** 2).mean()
-        return loss / len(views)
+        return ((wrs.render_views(sp, views, col, opa, scl, dparams, leaf) - target) ** 2).mean()
 
     def fwd_bwd():
         loss_fn().backward()
@@ -718,9 +717,10 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
                        "fit": {"steps": 200, "optimizer": "Adam lr 1e-2 on per-splat radius scale",
                                "loss_curve": curve, "seconds": fit_s,
                                "scale_mean_after": float(scl.detach().mean())},
-                       "note": "forward = LBVH rebuild with the current radius scales + trace; "
-                               "backward = re-traversal adjoint; L2 loss vs the GPU ray-cast "
-                               "novel views (which match the binary64 oracle ray caster to 1e-5)"}
+                       "note": "forward = one LBVH rebuild with the current radius scales + a trace "
+                               "per view; backward = re-traversal adjoint per view, accumulated in "
+                               "place; L2 loss vs the GPU ray-cast novel views (which match the "
+                               "binary64 oracle ray caster to 1e-5)"}
 
     # ---------------- CPU oracle on the host cores (rank 0, N = 1) ------------------------------
     if rank == 0 and world == 1:

@@ -300,6 +300,15 @@ int wrs_trace_backward(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_
                        float global_scale, const float* dL_drgba, float* g_rgba,
                        float* g_opacity, float* g_scale, int32_t* status, wrs_stream_t stream);
 
+/* wrs_trace_backward without zeroing the outputs: the gradients of this view are added to what
+ * g_rgba / g_opacity / g_scale hold, so several views of one splat set (one LBVH) accumulate into
+ * one gradient.  Not in the paper; used for multi-view fitting. */
+int wrs_trace_backward_accumulate(const wrs_lbvh* bvh, const wrs_splats* sorted,
+                                  const wrs_camera* cam, const wrs_trace_params* params,
+                                  const float* radius_scale, float global_scale,
+                                  const float* dL_drgba, float* g_rgba, float* g_opacity,
+                                  float* g_scale, int32_t* status, wrs_stream_t stream);
+
 /* The earlier 2.5D warping the paper compares against (§2, §5, Fig. 3): every splat of a set
  * (compacted or sorted; index = its position in that set) drawn as a point_size x point_size pixel
  * square around its projection into cam, one depth per point (the view-axis distance z, points

@@ -151,6 +151,8 @@ _sig("wrs_session_tiles", _U, _I, _I)
 _sig("wrs_trace_batched", _I, _P, _I, _U, ctypes.POINTER(_Params), _P, _P, _P)
 _sig("wrs_trace_backward", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats), ctypes.POINTER(Camera),
      ctypes.POINTER(_Params), _P, _F, _P, _P, _P, _P, _P, _P)
+_sig("wrs_trace_backward_accumulate", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats),
+     ctypes.POINTER(Camera), ctypes.POINTER(_Params), _P, _F, _P, _P, _P, _P, _P, _P)
 
 lib = _lib
 assert _lib.wrs_session_size() == ctypes.sizeof(Session), "wrs_session layout mismatch"
@@ -471,8 +473,9 @@ class TraceParams:
     edge_softness: float = 0.0
     k_chunk: int = 8
     block: int = 128
-    schedule: int = 0            # 0 = one thread per pixel, 1 = persistent with lane refill
-    width: int = 2               # 2 = binary traversal, 4 = 4-wide nodes
+    schedule: int = 0            # 0 = one thread per pixel, 1 = persistent with lane refill,
+                                 # 2 = one warp-shared traversal per 8x4 tile (wrs_trace only)
+    width: int = 4               # 4 = 4-wide nodes (faster in every measured case), 2 = binary
 
     def c(self, opacity: Optional[torch.Tensor] = None) -> _Params:
         return _Params(int(self.max_hits), float(self.t_stop), float(self.edge_softness),
@@ -554,20 +557,25 @@ def trace_backward(bvh: LBVH, sorted: SplatBuffers, cam, dL_drgba: torch.Tensor,
                    params: TraceParams = TraceParams(), opacity: Optional[torch.Tensor] = None,
                    radius_scale: Optional[torch.Tensor] = None, global_scale: float = 1.0,
                    want_opacity: bool = True, want_scale: bool = True,
-                   status: Optional[torch.Tensor] = None, stream=None):
+                   status: Optional[torch.Tensor] = None, stream=None, accumulate_into=None):
     """Adjoint of :func:`trace`: returns (g_rgba [cap,4], g_opacity [cap] | None, g_scale [cap] | None)
-    in compacted splat order."""
+    in compacted splat order.  ``accumulate_into=(g_rgba, g_opacity, g_scale)`` adds this view's
+    gradients to those buffers instead (wrs_trace_backward_accumulate) and returns them."""
     c = _cam(cam)
     dev = sorted.pos_r.device
     cap = max(sorted.capacity, 1)
-    g_rgba = torch.empty(cap, 4, dtype=torch.float32, device=dev)
-    g_op = torch.empty(cap, dtype=torch.float32, device=dev) if want_opacity else None
-    g_sc = torch.empty(cap, dtype=torch.float32, device=dev) if want_scale else None
+    if accumulate_into is not None:
+        g_rgba, g_op, g_sc = accumulate_into
+        fn, name = _lib.wrs_trace_backward_accumulate, "wrs_trace_backward_accumulate"
+    else:
+        g_rgba = torch.empty(cap, 4, dtype=torch.float32, device=dev)
+        g_op = torch.empty(cap, dtype=torch.float32, device=dev) if want_opacity else None
+        g_sc = torch.empty(cap, dtype=torch.float32, device=dev) if want_scale else None
+        fn, name = _lib.wrs_trace_backward, "wrs_trace_backward"
     b, s, p = bvh.c(), sorted.c(), params.c(opacity)
-    _check(_lib.wrs_trace_backward(ctypes.byref(b), ctypes.byref(s), ctypes.byref(c), ctypes.byref(p),
-                                   _ptr(radius_scale), float(global_scale), _ptr(dL_drgba.contiguous()),
-                                   _ptr(g_rgba), _ptr(g_op), _ptr(g_sc), _ptr(status), _stream(stream)),
-           "wrs_trace_backward")
+    _check(fn(ctypes.byref(b), ctypes.byref(s), ctypes.byref(c), ctypes.byref(p),
+              _ptr(radius_scale), float(global_scale), _ptr(dL_drgba.contiguous()), _ptr(g_rgba),
+              _ptr(g_op), _ptr(g_sc), _ptr(status), _stream(stream)), name)
     return g_rgba, g_op, g_sc
 
 
@@ -580,5 +588,5 @@ def new_status(device=None) -> torch.Tensor:
     return torch.zeros(1, dtype=torch.int32, device=device or torch.device("cuda"))
 
 
-from .autograd import TraceFunction, render  # noqa: E402,F401
+from .autograd import MultiViewTraceFunction, TraceFunction, render, render_views  # noqa: E402,F401
 from .accumulate import FrameWindow  # noqa: E402,F401

@@ -4,11 +4,12 @@ backward: wrs_trace_backward).
 The differentiable quantities are the per-splat colour (premultiplied RGBA), opacity and radius
 scale, all in compacted splat order.  The forward pass stores no hit lists: the backward kernel
 re-traverses every ray (spec S7).  The radius scale changes the spheres, so every forward call
-rebuilds the LBVH with the current scales.
+rebuilds the LBVH with the current scales; :func:`render_views` renders several views from one
+build and accumulates their gradients in place (wrs_trace_backward_accumulate).
 """
 from __future__ import annotations
 
-from typing import Optional
+from typing import Optional, Sequence
 
 import torch
 
@@ -50,3 +51,57 @@ def render(splats: SplatBuffers, cam, rgba: torch.Tensor, opacity: Optional[torc
     """Differentiable client image [H,W,4] of the splats (geometry from ``splats``; colour,
     opacity and radius scale from the given per-splat tensors, compacted order)."""
     return TraceFunction.apply(rgba, opacity, radius_scale, splats, cam, params, leaf_size)
+
+
+class MultiViewTraceFunction(torch.autograd.Function):
+    """Several client views of one splat set: one LBVH build, one trace per view; the backward
+    pass accumulates every view's gradient into one buffer (no per-view buffers, no sums)."""
+
+    @staticmethod
+    def forward(ctx, rgba: torch.Tensor, opacity: Optional[torch.Tensor],
+                radius_scale: Optional[torch.Tensor], splats: SplatBuffers, cams,
+                params: TraceParams, leaf_size: int):
+        n = rgba.shape[0]
+        if n > splats.capacity:
+            raise ValueError("more colours than splats")
+        splats.rgba[:n].copy_(rgba.detach())
+        op = None if opacity is None else opacity.detach().contiguous()
+        sc = None if radius_scale is None else radius_scale.detach().contiguous()
+        bvh, sorted_ = build_lbvh(splats, leaf_size, radius_scale=sc)
+        c0 = cams[0]
+        out = torch.empty(len(cams), c0.height, c0.width, 4, dtype=torch.float32,
+                          device=rgba.device)
+        for v, cam in enumerate(cams):
+            if (cam.width, cam.height) != (c0.width, c0.height):
+                raise ValueError("all views must have the same size")
+            trace(bvh, sorted_, cam, params, opacity=op, out=out[v])
+        ctx.state = (bvh, sorted_, list(cams), params, op, sc, n)
+        return out
+
+    @staticmethod
+    def backward(ctx, g_img: torch.Tensor):
+        bvh, sorted_, cams, params, op, sc, n = ctx.state
+        need_rgba, need_op, need_sc = ctx.needs_input_grad[:3]
+        cap = max(sorted_.capacity, 1)
+        dev = g_img.device
+        acc = (torch.zeros(cap, 4, dtype=torch.float32, device=dev),
+               torch.zeros(cap, dtype=torch.float32, device=dev) if need_op else None,
+               torch.zeros(cap, dtype=torch.float32, device=dev) if need_sc else None)
+        g_img = g_img.contiguous()
+        for v, cam in enumerate(cams):
+            trace_backward(bvh, sorted_, cam, g_img[v], params, opacity=op, radius_scale=sc,
+                           accumulate_into=acc)
+        g_rgba, g_op, g_sc = acc
+        return (g_rgba[:n] if need_rgba else None,
+                g_op[:n] if need_op else None,
+                g_sc[:n] if need_sc else None,
+                None, None, None, None)
+
+
+def render_views(splats: SplatBuffers, cams: Sequence, rgba: torch.Tensor,
+                 opacity: Optional[torch.Tensor] = None,
+                 radius_scale: Optional[torch.Tensor] = None, params: TraceParams = TraceParams(),
+                 leaf_size: int = 1) -> torch.Tensor:
+    """Differentiable images [V,H,W,4] of several same-size client views of the splats."""
+    return MultiViewTraceFunction.apply(rgba, opacity, radius_scale, splats, list(cams), params,
+                                        leaf_size)

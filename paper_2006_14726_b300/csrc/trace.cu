@@ -1344,20 +1344,23 @@ int wrs_trace_batched(const wrs_session* sessions, int32_t n_sessions, uint32_t 
     return WRS_OK;
 }
 
-int wrs_trace_backward(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* cam,
-                       const wrs_trace_params* params, const float* radius_scale,
-                       float global_scale, const float* dL_drgba, float* g_rgba,
-                       float* g_opacity, float* g_scale, int32_t* status, wrs_stream_t stream) {
-    const char* fn = "wrs_trace_backward";
+static int trace_backward_impl(const wrs_lbvh* bvh, const wrs_splats* sorted,
+                               const wrs_camera* cam, const wrs_trace_params* params,
+                               const float* radius_scale, float global_scale,
+                               const float* dL_drgba, float* g_rgba, float* g_opacity,
+                               float* g_scale, int32_t* status, wrs_stream_t stream, bool zero,
+                               const char* fn) {
     if (int rc = check_trace_args(bvh, sorted, cam, params, fn)) return rc;
     if (!dL_drgba || !g_rgba || (reinterpret_cast<uintptr_t>(dL_drgba) & 15))
         return wrs::fail(WRS_ERR_ARG, "%s: dL_drgba / g_rgba NULL or misaligned", fn);
     const size_t cap = sorted->capacity;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemsetAsync(g_rgba, 0, 4 * sizeof(float) * cap, s);
-    if (e == cudaSuccess && g_opacity) e = cudaMemsetAsync(g_opacity, 0, sizeof(float) * cap, s);
-    if (e == cudaSuccess && g_scale) e = cudaMemsetAsync(g_scale, 0, sizeof(float) * cap, s);
-    if (e != cudaSuccess) return wrs::cuda_fail(e, fn);
+    if (zero) {
+        cudaError_t e = cudaMemsetAsync(g_rgba, 0, 4 * sizeof(float) * cap, s);
+        if (e == cudaSuccess && g_opacity) e = cudaMemsetAsync(g_opacity, 0, sizeof(float) * cap, s);
+        if (e == cudaSuccess && g_scale) e = cudaMemsetAsync(g_scale, 0, sizeof(float) * cap, s);
+        if (e != cudaSuccess) return wrs::cuda_fail(e, fn);
+    }
     const GradOut go = {radius_scale, global_scale, g_rgba, g_opacity, g_scale};
     const int K = effective_k(params), W = params->width;
     const Scene sc = make_scene(bvh, sorted, params->opacity, W);
@@ -1372,6 +1375,25 @@ int wrs_trace_backward(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_
     }
     WRS_LAUNCH_CHECK(fn);
     return WRS_OK;
+}
+
+int wrs_trace_backward(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* cam,
+                       const wrs_trace_params* params, const float* radius_scale,
+                       float global_scale, const float* dL_drgba, float* g_rgba,
+                       float* g_opacity, float* g_scale, int32_t* status, wrs_stream_t stream) {
+    return trace_backward_impl(bvh, sorted, cam, params, radius_scale, global_scale, dL_drgba,
+                               g_rgba, g_opacity, g_scale, status, stream, true,
+                               "wrs_trace_backward");
+}
+
+int wrs_trace_backward_accumulate(const wrs_lbvh* bvh, const wrs_splats* sorted,
+                                  const wrs_camera* cam, const wrs_trace_params* params,
+                                  const float* radius_scale, float global_scale,
+                                  const float* dL_drgba, float* g_rgba, float* g_opacity,
+                                  float* g_scale, int32_t* status, wrs_stream_t stream) {
+    return trace_backward_impl(bvh, sorted, cam, params, radius_scale, global_scale, dL_drgba,
+                               g_rgba, g_opacity, g_scale, status, stream, false,
+                               "wrs_trace_backward_accumulate");
 }
 
 }  // extern "C"

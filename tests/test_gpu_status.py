@@ -30,27 +30,35 @@ def _scene(wrs, W=40, H=30, seed=2):
     return bvh, srt, synth.orbit(srv, (0, 1, 0), 5.0)
 
 
-@pytest.mark.parametrize("schedule", [0, 1])
-def test_corrupted_child_reference_sets_malformed_bit(wrs, schedule):
+def _child_refs(bvh, width):
+    """The root's child references (int32 view): in its binary node (2), or its 4-wide node (4)."""
+    if width == 2:
+        return bvh.nodes[64 + 48:64 + 56].view(torch.int32)
+    start = 64 + 64 * int(bvh.nodes[48:52].view(torch.int32).item())
+    return bvh.nodes[start + 96:start + 112].view(torch.int32)
+
+
+@pytest.mark.parametrize("schedule,width", [(0, 2), (1, 2), (0, 4), (1, 4), (2, 4)])
+def test_corrupted_child_reference_sets_malformed_bit(wrs, schedule, width):
     bvh, srt, cam = _scene(wrs)
-    good = wrs.trace(bvh, srt, cam, wrs.TraceParams(schedule=schedule)).clone()
+    params = wrs.TraceParams(schedule=schedule, width=width)
+    good = wrs.trace(bvh, srt, cam, params).clone()
     bad = wrs.LBVH(bvh.capacity, 1)
     bad.nodes.copy_(bvh.nodes)
-    refs = bad.nodes[64 + 48:64 + 56].view(torch.int32)  # root node: child references
-    refs[0] = 0x7FFFFFF0                                  # an internal node far beyond the tree
+    _child_refs(bad, width)[0] = 0x7FFFFFF0  # an internal node far beyond the tree
     st = wrs.new_status()
-    wrs.trace(bad, srt, cam, wrs.TraceParams(schedule=schedule), status=st)
+    wrs.trace(bad, srt, cam, params, status=st)
     with pytest.raises(wrs.WrsError) as e:
         wrs.check_status(st)
     assert e.value.code == wrs.WRS_ERR_DEVICE and "malformed" in str(e.value)
     # a reference cycle (the root's child is the root) exhausts the visit budget
     bad.nodes.copy_(bvh.nodes)
-    bad.nodes[64 + 48:64 + 52].view(torch.int32)[0] = 0
-    wrs.trace(bad, srt, cam, wrs.TraceParams(schedule=schedule), status=st)
+    _child_refs(bad, width)[0] = 0
+    wrs.trace(bad, srt, cam, params, status=st)
     with pytest.raises(wrs.WrsError):
         wrs.check_status(st)
     # the context is still usable and the good tree still gives the same image
-    again = wrs.trace(bvh, srt, cam, wrs.TraceParams(schedule=schedule), status=st)
+    again = wrs.trace(bvh, srt, cam, params, status=st)
     wrs.check_status(st)
     assert torch.equal(again, good)
 
