@@ -164,9 +164,9 @@ def kernel_digest():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per trace launch from the committed ncu summary, if it was taken on the current
-    kernel source (the summary records the source digest); else None."""
+def profiled(key):
+    """A figure of the committed ncu summary of the trace kernel (``- key: value`` lines), if the
+    summary was taken on the current kernel source (it records the source digest); else None."""
     path = os.path.join(ROOT, "profiles", "trace_large_1080p_2M.md")
     try:
         txt = open(path).read()
@@ -180,9 +180,14 @@ def profiled_traffic():
     if vals.get("kernel_digest") != kernel_digest():
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
+
+
+def profiled_traffic():
+    """DRAM bytes per trace launch (dram__bytes_read.sum + dram__bytes_write.sum) or None."""
+    return profiled("dram_bytes_per_launch")
 
 
 # ------------------------------------------------------------------------------------------------
@@ -414,6 +419,21 @@ def main():
             "roofline": roofline, "gpu_launches": launches_per_step * args.steps}
     if clk:
         line["clocks"] = clk
+    # the bound the profile shows: instruction issue.  Warp instructions per launch (ncu, same
+    # kernel source) over the live launch time, against 148 SMs x 4 schedulers x 1 instruction
+    # per cycle at the sampled SM clock
+    winst = profiled("warp_instructions_per_launch")
+    profiled_launch = sched == 0 and width == 4 and kc == 1 and leaf == 1  # the captured launch
+    if winst is not None and profiled_launch and clk and clk.get("sm_mhz"):
+        peak_gi = 148 * 4 * clk["sm_mhz"] * 1e6 / 1e9
+        ach_gi = winst / (trace_ms * 1e-3) / 1e9
+        line["roofline"]["issue"] = {"warp_instructions_per_launch": winst,
+                                     "achieved_ginst_s": ach_gi, "peak_ginst_s": peak_gi,
+                                     "frac": ach_gi / peak_gi,
+                                     "note": "the kernel's binding limit (ALU pipe 65 %, issue "
+                                             "68 % under ncu); instructions counted on one "
+                                             "1080p frame of the same workload; the hbm entry "
+                                             "is the counted-bytes roofline"}
 
     if not args.no_extras:
         extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, world, barrier,
