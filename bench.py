@@ -310,7 +310,9 @@ def main():
     if args.no_autotune:
         tuned = {"leaf": 1, "k_chunk": 1, "block": 128, "schedule": 0, "width": 4}
     else:
-        tuned = autotune.tune_trace(sp, groups[0][3], use_cache=False)
+        # the step builds one LBVH per 4 traced views: tune the whole step, not the trace alone
+        tuned = autotune.tune_trace(sp, groups[0][3], use_cache=False,
+                                    build_weight=1.0 / FRAMES_PER_IMAGE)
     leaf, kc, block, sched = tuned["leaf"], tuned["k_chunk"], tuned["block"], tuned["schedule"]
     width = tuned["width"]
     params = wrs.TraceParams(max_hits=0, t_stop=1e-5, k_chunk=kc, block=block, schedule=sched,
@@ -555,7 +557,8 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
     probe = wrs.FrameWindow(F_WIN, W.server_w, W.server_h, decay=0.9)
     for g_i in range(F_WIN):
         probe.push(*groups[g_i][:3])
-    at = autotune.tune_trace(probe.splats, groups[F_WIN][3], use_cache=False)
+    at = autotune.tune_trace(probe.splats, groups[F_WIN][3], use_cache=False,
+                             build_weight=1.0 / FRAMES_PER_IMAGE)
     del probe
     aparams = wrs.TraceParams(max_hits=0, t_stop=1e-5, k_chunk=at["k_chunk"], block=at["block"],
                               schedule=at["schedule"], width=at["width"])

@@ -72,11 +72,12 @@ def signature(kind: str, n_splats: int, width: int, height: int, base: TracePara
 def tune_trace(splats: SplatBuffers, cams: Sequence, base: TraceParams = TraceParams(),
                leaves: Iterable[int] = LEAVES, ks: Iterable[int] = KS,
                blocks: Iterable[int] = BLOCKS, widths: Iterable[int] = WIDTHS, reps: int = 3,
-               use_cache: bool = True) -> Dict:
+               use_cache: bool = True, build_weight: float = 0.0) -> Dict:
     """Pick (leaf_size, k_chunk, block, schedule, width) minimising the mean wrs_trace time over
-    ``cams``."""
+    ``cams`` plus ``build_weight`` times the LBVH build time of the leaf size (the share of a
+    build per traced view, e.g. 1/4 when a server frame serves four client views)."""
     c0 = cams[0]
-    key = signature("trace", splats.count(), c0.width, c0.height, base)
+    key = signature("trace", splats.count(), c0.width, c0.height, base) + f"|w{build_weight:g}"
     if use_cache:
         hit = _load_cache().get(key)
         if hit:
@@ -85,6 +86,7 @@ def tune_trace(splats: SplatBuffers, cams: Sequence, base: TraceParams = TracePa
     table = []
     for leaf in leaves:
         bvh, srt = build_lbvh(splats, leaf)
+        build_ms = _time_ms(lambda: build_lbvh(splats, leaf, bvh=bvh, sorted=srt), reps)
         outs = [torch.empty(c.height, c.width, 4, device=splats.pos_r.device) for c in cams]
         shapes = [(b, SCHEDULE_PER_PIXEL) for b in blocks] + [(128, SCHEDULE_PERSISTENT),
                                                               (128, SCHEDULE_PACKET)]
@@ -99,10 +101,11 @@ def tune_trace(splats: SplatBuffers, cams: Sequence, base: TraceParams = TracePa
                         for c, o in zip(cams, outs):
                             trace(bvh, srt, c, p, out=o)
                     ms = _time_ms(run, reps) / len(cams)
-                    table.append((leaf, k, block, sched, width, ms))
-                    if best is None or ms < best["ms"]:
+                    score = ms + build_weight * build_ms
+                    table.append((leaf, k, block, sched, width, ms, build_ms))
+                    if best is None or score < best["score"]:
                         best = {"leaf": leaf, "k_chunk": k, "block": block, "schedule": sched,
-                                "width": width, "ms": ms}
+                                "width": width, "ms": ms, "build_ms": build_ms, "score": score}
     best["table"] = table
     _store(key, best)
     return best
