@@ -13,6 +13,8 @@ marshals numpy arrays through ctypes.  Functions and the paper passage each one 
   the other heuristics of §2 and §5 (max contribution, accumulated opacity, max gradient; S2a).
 * :func:`unproject` -- object-space samples ``p = o + d t_i`` (Eq. 1), footprint radius (§4.1),
   zero-radius compaction (§4.1).
+* :func:`unproject_interval` -- samples smeared along their viewing ray over the depth interval
+  of growing opacity, as chains of touching spheres (future work, §6; reading: spec S3b).
 * :func:`append_frame`, :func:`accumulate` -- splats of several server frames in one set, the
   accumulation over frames named as future work in §6 (reading: spec S3a).
 * :func:`point_splat` -- the earlier warping the paper compares against (§2, §5, Fig. 3): each
@@ -98,6 +100,9 @@ def _load():
         lib.orc_lbvh.argtypes = [P, P, ctypes.c_float, ctypes.c_int64, ctypes.c_int32, P, P, P, P,
                                  P, P]
         lib.orc_point_splat.argtypes = [P, P, ctypes.c_int64, ctypes.POINTER(_Cam), ctypes.c_int, P, P]
+        lib.orc_unproject_interval.argtypes = [P, P, P, ctypes.POINTER(_Cam), ctypes.c_int,
+                                               ctypes.c_float, ctypes.c_int, P, P, P, ctypes.c_int64]
+        lib.orc_unproject_interval.restype = ctypes.c_int64
         lib.orc_encode.argtypes = [P, P, ctypes.c_int64, P, P, ctypes.c_float, P, P]
         lib.orc_decode.argtypes = [P, P, ctypes.c_int64, P, P, ctypes.c_float, P, P]
         lib.orc_default_threads.restype = ctypes.c_int
@@ -209,6 +214,27 @@ def unproject(rgba: np.ndarray, depth: np.ndarray, cam, mode: int = RADIUS_FOOTP
                               cap)
     if n < 0:
         raise ValueError(f"orc_unproject failed ({n})")
+    return Splats(pos_r[:n].copy(), out[:n].copy(), ids[:n].copy())
+
+
+def unproject_interval(rgba: np.ndarray, depth_lo: np.ndarray, depth_hi: np.ndarray, cam,
+                       mode: int = RADIUS_FOOTPRINT, voxel_diag: float = 0.0,
+                       max_chain: int = 8) -> Splats:
+    """Each kept pixel as a chain of spheres along its server ray over [depth_lo, depth_hi]
+    (spec S3b); ids = pixel * max_chain + position in the chain."""
+    rgba = _c(rgba, np.float32).reshape(-1, 4)
+    lo = _c(depth_lo, np.float32).reshape(-1)
+    hi = _c(depth_hi, np.float32).reshape(-1)
+    cap = lo.size * int(max_chain)
+    pos_r = np.zeros((cap, 4), np.float32)
+    out = np.zeros((cap, 4), np.float32)
+    ids = np.zeros(cap, np.uint32)
+    n = _load().orc_unproject_interval(rgba.ctypes.data, lo.ctypes.data, hi.ctypes.data,
+                                       ctypes.byref(_cam(cam)), int(mode), float(voxel_diag),
+                                       int(max_chain), pos_r.ctypes.data, out.ctypes.data,
+                                       ids.ctypes.data, cap)
+    if n < 0:
+        raise ValueError(f"orc_unproject_interval failed ({n})")
     return Splats(pos_r[:n].copy(), out[:n].copy(), ids[:n].copy())
 
 

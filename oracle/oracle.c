@@ -301,6 +301,60 @@ int64_t orc_unproject(const float* rgba, const float* depth, const orc_camera* c
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* S3b: samples smeared along the viewing ray over their depth interval (future work, §6): each */
+/* kept pixel becomes a chain of touching spheres whose opacities compose to the pixel's alpha.  */
+/* ------------------------------------------------------------------------------------------ */
+int64_t orc_unproject_interval(const float* rgba, const float* depth_lo, const float* depth_hi,
+                               const orc_camera* cam, int mode, float voxel_diag, int max_chain,
+                               float* pos_r, float* rgba_out, uint32_t* id, int64_t capacity) {
+    if (!rgba || !depth_lo || !depth_hi || !cam || !pos_r || !rgba_out || !id) return -1;
+    if (max_chain < 1 || max_chain > 64) return -1;
+    int W = cam->width, H = cam->height;
+    int64_t n_out = 0;
+    float pitch = (2.0f * cam->tan_half_fovy) / (float)H;
+    for (int64_t i = 0; i < (int64_t)W * H; i++) {
+        float tlo = depth_lo[i], thi = depth_hi[i];
+        float a = rgba[4 * i + 3];
+        if (!(tlo >= 0.0f && tlo < INFINITY && a > 0.0f)) continue;
+        if (!(thi < INFINITY) || !(thi >= tlo)) thi = tlo;
+        float dt = thi - tlo;
+        float tm = fmaf(dt, 0.5f, tlo);
+        float o[3], d[3];
+        orc_primary_ray(cam, (int)(i % W), (int)(i / W), o, d);
+        float r0;
+        if (mode == 0) {
+            float dz = fmaf(d[2], cam->fwd[2], fmaf(d[1], cam->fwd[1], d[0] * cam->fwd[0]));
+            r0 = ((tm * dz) * pitch) * 0.70710677f;
+        } else {
+            r0 = voxel_diag * 0.5f;
+        }
+        int n = 1;
+        if (r0 > 0.0f) {
+            float c = ceilf(dt / (2.0f * r0));
+            n = c < 1.0f ? 1 : (c > (float)max_chain ? max_chain : (int)c);
+        }
+        /* per-sphere opacity so that n of them compose to a along the ray */
+        double scale = 1.0;
+        if (n > 1) {
+            double ap = -expm1(log1p(-(double)a) / (double)n);
+            scale = ap / (double)a;
+        }
+        for (int k = 0; k < n; k++) {
+            if (n_out >= capacity) return -3;
+            float u = (float)(2 * k + 1) / (float)(2 * n);
+            float tk = fmaf(u, dt, tlo);
+            for (int q = 0; q < 3; q++) pos_r[4 * n_out + q] = fmaf(d[q], tk, o[q]);
+            pos_r[4 * n_out + 3] = r0;
+            for (int ch = 0; ch < 4; ch++)
+                rgba_out[4 * n_out + ch] = n == 1 ? rgba[4 * i + ch] : (float)((double)rgba[4 * i + ch] * scale);
+            id[n_out] = (uint32_t)(i * max_chain + k);
+            n_out++;
+        }
+    }
+    return n_out;
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* S10: the earlier point-splat warping (§2; compared in §5, Fig. 3): every sample drawn as an    */
 /* s x s pixel square around its projection, one depth per point, nearest (z, k) kept, no blend.  */
 /* ------------------------------------------------------------------------------------------ */
