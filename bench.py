@@ -632,7 +632,8 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
                        "channels)", "server_and_client": [srv_q.width, srv_q.height],
              "angles_deg": list(angles)}
         for name, (v, tf_np, vd) in scenes.items():
-            rows = warp_quality(v, torch.from_numpy(tf_np).to(dev), srv_q, clis_q, voxel_diag=vd)
+            rows = warp_quality(v, torch.from_numpy(tf_np).to(dev), srv_q, clis_q, voxel_diag=vd,
+                                interval_chain=8)
             q[name] = [{k: (round(x, 3) if x is not None else None) for k, x in r.items()}
                        for r in rows]
         # the server's depth rule (first hit, max contribution, accumulated opacity, max

@@ -211,6 +211,23 @@ int wrs_decode_splats(const uint64_t* word, const uint32_t* color, const uint32_
                       uint32_t capacity, const wrs_codec* codec, wrs_splats* out,
                       wrs_stream_t stream);
 
+/* Samples smeared along the viewing ray by depth uncertainty (§6 proposes it as future work and
+ * gives no rule; spec S3b is this library's reading).  depth_lo / depth_hi: [H][W] the depths at
+ * which the accumulated opacity reaches 0.25 and 0.75 (wrs_raycast_volume_heuristic with
+ * WRS_DEPTH_ACCUMULATED and those thresholds).  Every pixel kept by the wrs_unproject rule (on
+ * depth_lo) becomes a chain of n = clamp(ceil((t_hi - t_lo) / 2 r0), 1, max_chain) spheres of
+ * radius r0 (the radius rule at the interval's middle) centred at t_lo + (2k+1)(t_hi - t_lo)/2n on
+ * its ray, each with opacity a' = 1 - (1 - a)^(1/n) (colour scaled by a'/a) so that the chain
+ * composites back to the pixel along its own ray; id = pixel * max_chain + k; records in pixel
+ * order.  max_chain in 1..64, width * height * max_chain <= 2^32.  *out->n = the number of
+ * records, clamped to out->capacity (then WRS_STATUS_SPLAT_OVERFLOW is OR-ed into *status, which
+ * may be NULL).  With t_hi = t_lo the output equals wrs_unproject's, ids times max_chain.
+ * Scratch: wrs_unproject_scratch_bytes(w, h). */
+int wrs_unproject_interval(const float* rgba, const float* depth_lo, const float* depth_hi,
+                           const wrs_camera* cam, int32_t radius_mode, float voxel_diag,
+                           int32_t max_chain, wrs_splats* out, void* scratch,
+                           size_t scratch_bytes, int32_t* status, wrs_stream_t stream);
+
 /* Accumulation over server frames (§6 names it as future work and gives no rule; spec S3a is
  * this library's reading): wrs_unproject of one more frame, APPENDED to the splats already in out.
  * With N0 = *out->n on entry (read on the device), the frame's kept pixels (same rule, radius and

@@ -138,6 +138,8 @@ _sig("wrs_encode_splats", _I, ctypes.POINTER(_Splats), ctypes.POINTER(Codec), _P
 _sig("wrs_decode_splats", _I, _P, _P, _P, _U, ctypes.POINTER(Codec), ctypes.POINTER(_Splats), _P)
 _sig("wrs_point_splat_scratch_bytes", _Z, _I, _I)
 _sig("wrs_point_splat", _I, ctypes.POINTER(_Splats), ctypes.POINTER(Camera), _I, _P, _P, _P, _Z, _P)
+_sig("wrs_unproject_interval", _I, _P, _P, _P, ctypes.POINTER(Camera), _I, _F, _I,
+     ctypes.POINTER(_Splats), _P, _Z, _P, _P)
 _sig("wrs_unproject_static", _I, _P, _P, ctypes.POINTER(Camera), _I, _F, ctypes.POINTER(_Splats), _P)
 _sig("wrs_lbvh_bytes", _Z, _U, _U)
 _sig("wrs_lbvh_scratch_bytes", _Z, _U, _U)
@@ -416,6 +418,27 @@ def decode_splats(enc: EncodedSplats, codec: Codec, out: Optional[SplatBuffers] 
     _check(_lib.wrs_decode_splats(_ptr(enc.word), _ptr(enc.color), _ptr(enc.n), enc.capacity,
                                   ctypes.byref(codec), ctypes.byref(sp), _stream(stream)),
            "wrs_decode_splats")
+    return out
+
+
+def unproject_interval(rgba: torch.Tensor, depth_lo: torch.Tensor, depth_hi: torch.Tensor, cam,
+                       max_chain: int = 8, radius_mode: int = RADIUS_FOOTPRINT,
+                       voxel_diag: float = 0.0, out: Optional[SplatBuffers] = None,
+                       status: Optional[torch.Tensor] = None, scratch: Optional[torch.Tensor] = None,
+                       stream=None) -> SplatBuffers:
+    """Each kept pixel as a chain of spheres along its server ray over [depth_lo, depth_hi], the
+    depth interval of growing opacity (depth uncertainty; see wrs_unproject_interval).  The default
+    output holds width * height * max_chain records."""
+    c = _cam(cam)
+    if out is None:
+        out = SplatBuffers(c.width * c.height * int(max_chain), device=rgba.device)
+    if scratch is None:
+        scratch = _scratch(unproject_scratch_bytes(c.width, c.height), rgba.device)
+    sp = out.c()
+    _check(_lib.wrs_unproject_interval(_ptr(rgba), _ptr(depth_lo), _ptr(depth_hi), ctypes.byref(c),
+                                       int(radius_mode), float(voxel_diag), int(max_chain),
+                                       ctypes.byref(sp), _ptr(scratch), scratch.numel(),
+                                       _ptr(status), _stream(stream)), "wrs_unproject_interval")
     return out
 
 

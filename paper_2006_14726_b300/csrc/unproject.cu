@@ -173,6 +173,121 @@ __global__ void __launch_bounds__(kThreads) k_unproject_write(
     }
 }
 
+// ---- samples smeared along the viewing ray (spec S3b) ------------------------------------------
+// Pixel i's chain: its depth interval, radius, chain length n (0 = not a sample) and the colour
+// scale of one chain sphere.  Both passes evaluate it the same way.
+struct Chain {
+    float t_lo, dt, r0, scale;
+    int n;
+};
+
+__device__ __forceinline__ Chain chain_of(const float4* __restrict__ rgba,
+                                          const float* __restrict__ depth_lo,
+                                          const float* __restrict__ depth_hi, const wrs_camera& cam,
+                                          int32_t mode, float voxel_diag, int max_chain, uint32_t i,
+                                          wrs::Ray& ray) {
+    Chain c{0.f, 0.f, 0.f, 1.f, 0};
+    const float t_lo = __ldg(depth_lo + i);
+    const float a = __ldg(&rgba[i].w);
+    if (!(t_lo >= 0.0f && t_lo < __int_as_float(0x7f800000) && a > 0.0f)) return c;
+    float t_hi = __ldg(depth_hi + i);
+    if (!(t_hi < __int_as_float(0x7f800000)) || !(t_hi >= t_lo)) t_hi = t_lo;
+    const float dt = __fsub_rn(t_hi, t_lo);
+    const float tm = __fmaf_rn(dt, 0.5f, t_lo);
+    const int x = (int)(i % (uint32_t)cam.width), y = (int)(i / (uint32_t)cam.width);
+    ray = wrs::primary_ray(cam, x, y);
+    float r0;
+    if (mode == WRS_RADIUS_FOOTPRINT) {
+        const float pitch = __fdiv_rn(__fmul_rn(2.0f, cam.tan_half_fovy), (float)cam.height);
+        const float dz = __fmaf_rn(ray.d.z, cam.fwd[2],
+                                   __fmaf_rn(ray.d.y, cam.fwd[1], __fmul_rn(ray.d.x, cam.fwd[0])));
+        r0 = __fmul_rn(__fmul_rn(__fmul_rn(tm, dz), pitch), 0.70710677f);
+    } else {
+        r0 = __fmul_rn(voxel_diag, 0.5f);
+    }
+    int n = 1;
+    if (r0 > 0.0f) {
+        const float q = ceilf(__fdiv_rn(dt, __fmul_rn(2.0f, r0)));
+        n = q < 1.0f ? 1 : (q > (float)max_chain ? max_chain : (int)q);
+    }
+    c.t_lo = t_lo;
+    c.dt = dt;
+    c.r0 = r0;
+    c.n = n;
+    if (n > 1) c.scale = __fdiv_rn(-expm1f(__fdiv_rn(log1pf(-a), (float)n)), a);
+    return c;
+}
+
+__global__ void __launch_bounds__(kThreads) k_interval_count(
+    const float4* __restrict__ rgba, const float* __restrict__ depth_lo,
+    const float* __restrict__ depth_hi, wrs_camera cam, int32_t mode, float voxel_diag,
+    int max_chain, uint32_t* __restrict__ counts) {
+    __shared__ uint32_t s_warp[kThreads / 32];
+    const uint32_t npix = (uint32_t)cam.width * (uint32_t)cam.height;
+    const uint32_t base = blockIdx.x * kTile;
+    uint32_t c = 0;
+    for (int k = 0; k < kRounds; k++) {
+        const uint32_t i = base + k * kThreads + threadIdx.x;
+        wrs::Ray ray;
+        if (i < npix) c += chain_of(rgba, depth_lo, depth_hi, cam, mode, voxel_diag, max_chain, i, ray).n;
+    }
+    const uint32_t t = block_sum(c, s_warp);
+    if (threadIdx.x == 0) counts[blockIdx.x] = t;
+}
+
+// Write pass: a block-wide exclusive scan of the chain lengths gives each pixel's first slot.
+__global__ void __launch_bounds__(kThreads) k_interval_write(
+    const float4* __restrict__ rgba, const float* __restrict__ depth_lo,
+    const float* __restrict__ depth_hi, wrs_camera cam, int32_t mode, float voxel_diag,
+    int max_chain, const uint32_t* __restrict__ offsets, float4* __restrict__ pos_r,
+    float4* __restrict__ out_rgba, uint32_t* __restrict__ out_id, uint32_t capacity) {
+    __shared__ uint32_t s_warp[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t npix = (uint32_t)cam.width * (uint32_t)cam.height;
+    const uint32_t base = blockIdx.x * kTile;
+    uint64_t run = offsets[blockIdx.x];
+    for (int k = 0; k < kRounds; k++) {
+        const uint32_t i = base + k * kThreads + threadIdx.x;
+        wrs::Ray ray;
+        Chain ch{0.f, 0.f, 0.f, 1.f, 0};
+        if (i < npix) ch = chain_of(rgba, depth_lo, depth_hi, cam, mode, voxel_diag, max_chain, i, ray);
+        // inclusive warp scan of the lengths, then the warps' totals
+        uint32_t incl = (uint32_t)ch.n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        uint32_t before = 0, total = 0;
+        for (int w = 0; w < kThreads / 32; w++) {
+            const uint32_t c = s_warp[w];
+            before += (w < warp) ? c : 0;
+            total += c;
+        }
+        const uint64_t first = run + before + incl - (uint32_t)ch.n;
+        if (ch.n > 0) {
+            const float4 c = __ldg(rgba + i);
+            const float4 cs = ch.n == 1 ? c
+                                        : make_float4(__fmul_rn(c.x, ch.scale), __fmul_rn(c.y, ch.scale),
+                                                      __fmul_rn(c.z, ch.scale), __fmul_rn(c.w, ch.scale));
+            for (int q = 0; q < ch.n; q++) {
+                const uint64_t slot = first + (uint64_t)q;
+                if (slot >= capacity) break;
+                const float u = __fdiv_rn((float)(2 * q + 1), (float)(2 * ch.n));
+                const float tk = __fmaf_rn(u, ch.dt, ch.t_lo);
+                pos_r[slot] = make_float4(__fmaf_rn(ray.d.x, tk, ray.o.x), __fmaf_rn(ray.d.y, tk, ray.o.y),
+                                          __fmaf_rn(ray.d.z, tk, ray.o.z), ch.r0);
+                out_rgba[slot] = cs;
+                out_id[slot] = i * (uint32_t)max_chain + (uint32_t)q;
+            }
+        }
+        run += total;
+        __syncthreads();  // s_warp is reused by the next round
+    }
+}
+
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 WriteOut float_out(const wrs_splats* out, float weight, uint32_t id_base) {
@@ -280,6 +395,55 @@ int wrs_unproject_encode(const float* rgba, const float* depth, const wrs_camera
     k_unproject_write<kEncode><<<nb, kThreads, 0, s>>>(in4, depth, *cam, radius_mode, voxel_diag,
                                                        offsets, o);
     WRS_LAUNCH_CHECK("wrs_unproject_encode write");
+    return WRS_OK;
+}
+
+int wrs_unproject_interval(const float* rgba, const float* depth_lo, const float* depth_hi,
+                           const wrs_camera* cam, int32_t radius_mode, float voxel_diag,
+                           int32_t max_chain, wrs_splats* out, void* scratch,
+                           size_t scratch_bytes, int32_t* status, wrs_stream_t stream) {
+    const char* fn = "wrs_unproject_interval";
+    if (int rc = wrs::check_camera(cam, fn)) return rc;
+    if (!rgba || !depth_lo || !depth_hi || !out || !out->pos_r || !out->rgba || !out->id || !out->n)
+        return wrs::fail(WRS_ERR_ARG, "%s: NULL input or output pointer", fn);
+    if ((reinterpret_cast<uintptr_t>(rgba) | reinterpret_cast<uintptr_t>(out->pos_r) |
+         reinterpret_cast<uintptr_t>(out->rgba)) & 15)
+        return wrs::fail(WRS_ERR_ARG, "%s: rgba / pos_r arrays must be 16-byte aligned", fn);
+    if (radius_mode != WRS_RADIUS_FOOTPRINT && radius_mode != WRS_RADIUS_VOXEL)
+        return wrs::fail(WRS_ERR_ARG, "%s: unknown radius_mode %d", fn, radius_mode);
+    if (radius_mode == WRS_RADIUS_VOXEL && !(voxel_diag > 0.0f && voxel_diag < 1e30f))
+        return wrs::fail(WRS_ERR_ARG, "%s: voxel_diag must be positive and finite", fn);
+    if (max_chain < 1 || max_chain > 64)
+        return wrs::fail(WRS_ERR_ARG, "%s: max_chain %d not in 1..64", fn, max_chain);
+    const size_t npix = (size_t)cam->width * (size_t)cam->height;
+    if (npix >= 0x80000000ull || npix * (size_t)max_chain > 0x100000000ull)
+        return wrs::fail(WRS_ERR_ARG, "%s: %zu pixels x %d exceeds the 32-bit ids", fn, npix,
+                         max_chain);
+    if (out->capacity == 0) return wrs::fail(WRS_ERR_CAPACITY, "%s: splat capacity is 0", fn);
+    const size_t need = wrs_unproject_scratch_bytes(cam->width, cam->height);
+    if (!scratch || scratch_bytes < need)
+        return wrs::fail(WRS_ERR_SCRATCH, "%s: scratch needs %zu bytes, got %zu", fn, need,
+                         scratch_bytes);
+    const uint32_t nb = (uint32_t)((npix + kTile - 1) / kTile);
+    uint32_t* counts = static_cast<uint32_t*>(scratch);
+    uint32_t* offsets = reinterpret_cast<uint32_t*>(static_cast<char*>(scratch) +
+                                                    align256(nb * sizeof(uint32_t)));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const float4* in4 = reinterpret_cast<const float4*>(rgba);
+    k_interval_count<<<nb, kThreads, 0, s>>>(in4, depth_lo, depth_hi, *cam, radius_mode, voxel_diag,
+                                             max_chain, counts);
+    WRS_LAUNCH_CHECK("wrs_unproject_interval count");
+    // the count starts at 0; the append form of the scan clamps it to the capacity and flags
+    // SPLAT_OVERFLOW when the chains need more records than that
+    cudaError_t e = cudaMemsetAsync(out->n, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return wrs::cuda_fail(e, fn);
+    k_scan_counts<true><<<1, 1024, 0, s>>>(counts, offsets, nb, out->n, out->capacity, status);
+    WRS_LAUNCH_CHECK("wrs_unproject_interval scan");
+    k_interval_write<<<nb, kThreads, 0, s>>>(in4, depth_lo, depth_hi, *cam, radius_mode, voxel_diag,
+                                             max_chain, offsets, reinterpret_cast<float4*>(out->pos_r),
+                                             reinterpret_cast<float4*>(out->rgba), out->id,
+                                             out->capacity);
+    WRS_LAUNCH_CHECK("wrs_unproject_interval write");
     return WRS_OK;
 }
 

@@ -14,8 +14,8 @@ from typing import Dict, Iterable, List
 
 import torch
 
-from . import (RADIUS_VOXEL, TraceParams, build_lbvh, make_camera, point_splat, raycast_volume,
-               trace, unproject)
+from . import (DEPTH_ACCUMULATED, RADIUS_VOXEL, TraceParams, build_lbvh, make_camera, point_splat,
+               raycast_volume, trace, unproject, unproject_interval)
 
 
 def psnr(img: torch.Tensor, ref: torch.Tensor) -> float:
@@ -28,14 +28,15 @@ def warp_quality(vol: torch.Tensor, tf: torch.Tensor, srv, clients: Iterable,
                  point_sizes: Iterable[int] = (1, 2, 3), max_hits: Iterable[int] = (0, 1),
                  sphere_scales: Iterable[float] = (1.0, 2.0), voxel_diag: float = 0.0,
                  step_vox: float = 0.5, tau: float = 0.1, leaf_size: int = 1,
-                 heuristic: int = 0, heuristic_param=None) -> List[Dict]:
+                 heuristic: int = 0, heuristic_param=None, interval_chain: int = 0) -> List[Dict]:
     """PSNR of every warping method for each client pose; one dict per pose.
 
     Sphere variants: the footprint radius scaled by each of ``sphere_scales`` (composited with
     each of ``max_hits``; 1 = the paper's first-hit query), and, if ``voxel_diag`` > 0, the
     paper's own radius rule (half a voxel diagonal, §4.1) with first hit.  Point variants: each
     of ``point_sizes`` pixels.  ``heuristic`` picks the server's depth rule (DEPTH_*); the
-    ground truth's colours do not depend on it."""
+    ground truth's colours do not depend on it.  ``interval_chain`` > 0 adds samples smeared along
+    their rays over the depth interval of growing opacity (chains of up to that many spheres)."""
     rgba, depth = raycast_volume(vol, tf, srv, step_vox, tau, heuristic=heuristic,
                                  param=heuristic_param)
     sp = unproject(rgba, depth, srv)
@@ -43,13 +44,19 @@ def warp_quality(vol: torch.Tensor, tf: torch.Tensor, srv, clients: Iterable,
     if voxel_diag > 0.0:
         spv = unproject(rgba, depth, srv, RADIUS_VOXEL, voxel_diag)
         trees["spheres_voxel"] = build_lbvh(spv, leaf_size)
+    if interval_chain > 0:
+        _, d_lo = raycast_volume(vol, tf, srv, step_vox, heuristic=DEPTH_ACCUMULATED, param=0.25)
+        _, d_hi = raycast_volume(vol, tf, srv, step_vox, heuristic=DEPTH_ACCUMULATED, param=0.75)
+        spi = unproject_interval(rgba, d_lo, d_hi, srv, interval_chain)
+        trees["spheres_interval"] = build_lbvh(spi, leaf_size)
     rows = []
     for cli in clients:
         c = make_camera(cli)
         truth, _ = raycast_volume(vol, tf, c, step_vox, tau)
         row = {}
         for name, (bvh, srt) in trees.items():
-            for h in (max_hits if name != "spheres_voxel" else (1,)):
+            for h in ((1,) if name == "spheres_voxel" else (0,) if name == "spheres_interval"
+                      else max_hits):
                 img = trace(bvh, srt, c, TraceParams(max_hits=h, width=4))
                 row[f"{name}_H{h}"] = psnr(img, truth)
         for s in point_sizes:
