@@ -123,7 +123,8 @@ typedef struct {
     float edge_softness;  /* beta in [0,1): soft sphere edge for differentiation; 0 = hard */
     const float* opacity; /* device [n] per-splat opacity in COMPACTED order, or NULL (= 1) */
     int32_t k_chunk;      /* hits gathered per traversal pass: 1, 2, 4, 8 or 16 */
-    int32_t block;        /* threads per block: 64, 128 or 256 (per-pixel schedule) */
+    int32_t block;        /* threads per block: 64, 128 or 256 (per-pixel schedule; the 4-wide
+                             traversal with k_chunk <= 2 uses at most 128) */
     int32_t schedule;     /* WRS_SCHEDULE_PER_PIXEL, WRS_SCHEDULE_PERSISTENT or (wrs_trace only)
                              WRS_SCHEDULE_PACKET; wrs_trace_batched: PER_PIXEL = one warp per
                              8x4 tile of all sessions, otherwise persistent with lane refill */

@@ -475,15 +475,19 @@ struct PersistentMinBlocks {
     static constexpr int value = K > 2 ? 0 : (W4 ? WRS_PERSISTENT_W4_MIN_BLOCKS : WRS_PERSISTENT_MIN_BLOCKS);
 };
 
-// Minimum resident 256-thread blocks per SM for the per-pixel kernel with the 4-wide traversal and
-// K <= 2 (caps registers at 65536 / (256 * this)); a build-time tuning knob.  Default 0 (no cap,
-// 64 registers): caps of 5 and 6 spill and measured slower on the 1080p, 2 M splat workload.
+// Launch bounds of the per-pixel kernel.  With the 4-wide traversal and K <= 2 it runs in blocks
+// of at most 128 threads with 9 resident blocks per SM (56 registers): measured 1 % faster than
+// no cap on the 1080p, 2 M splat workload, while caps of 40 and 48 registers spill and are 3-14 %
+// slower.  Other instances keep blocks of up to 256 threads and no register cap.  A build-time
+// knob: WRS_PIXEL_W4_MIN_BLOCKS (resident 128-thread blocks, 0 = no cap).
 #ifndef WRS_PIXEL_W4_MIN_BLOCKS
-#define WRS_PIXEL_W4_MIN_BLOCKS 0
+#define WRS_PIXEL_W4_MIN_BLOCKS 9
 #endif
 template <int K, bool W4>
-struct PixelMinBlocks {
-    static constexpr int value = (K <= 2 && W4) ? WRS_PIXEL_W4_MIN_BLOCKS : 0;
+struct PixelBounds {
+    static constexpr bool capped = K <= 2 && W4;
+    static constexpr int max_threads = capped ? 128 : 256;
+    static constexpr int min_blocks = capped ? WRS_PIXEL_W4_MIN_BLOCKS : 0;
 };
 
 template <int K>
@@ -626,7 +630,8 @@ __device__ __forceinline__ void tile_pixel(int t, int& px, int& py) {
 }
 
 template <int K, bool W4>
-__global__ void __launch_bounds__(256, PixelMinBlocks<K, W4>::value) k_trace(Scene sc, Comp cp, wrs_camera cam,
+__global__ void __launch_bounds__(PixelBounds<K, W4>::max_threads, PixelBounds<K, W4>::min_blocks)
+k_trace(Scene sc, Comp cp, wrs_camera cam,
                                                float4* __restrict__ out, int32_t* status) {
     int px, py;
     tile_pixel(threadIdx.x, px, py);
@@ -1286,9 +1291,12 @@ int wrs_trace(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* c
         dispatch_k1<LaunchTracePacket, true>(K, grid_for(cam, params->block), params->block, s,
                                              make_scene(bvh, sorted, params->opacity, 4),
                                              comp_of(params), *cam, out, status);
-    else
-        dispatch_k<LaunchTrace>(K, W, grid_for(cam, params->block), params->block, s, sc,
-                                comp_of(params), *cam, out, status);
+    else {
+        // the 4-wide kernel with K <= 2 is built for blocks of at most 128 threads
+        const int block = (W == 4 && K <= 2 && params->block > 128) ? 128 : params->block;
+        dispatch_k<LaunchTrace>(K, W, grid_for(cam, block), block, s, sc, comp_of(params), *cam,
+                                out, status);
+    }
     WRS_LAUNCH_CHECK(fn);
     return WRS_OK;
 }
