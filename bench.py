@@ -8,7 +8,7 @@ client, poses within 20 degrees, a new depth image every 4 frames).  value = cli
 per second over the whole job (all ranks), Mrays/s.
 
 Also reported on the same line: LBVH build and unproject ms, trace-only Mrays/s, the roofline of
-the trace kernel, the batched workload (64 sessions, one persistent launch in a CUDA graph vs 64
+the trace kernel, the batched workload (64 sessions, one launch replayed from a CUDA graph vs 64
 sequential calls), accumulation over a window of the 4 newest server frames (one LBVH and one
 trace over their union), forward and forward+backward throughput of the differentiable renderer,
 an end-to-end number through host buffers, and the CPU oracle timed on the host cores.
@@ -503,7 +503,7 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
                            "stream); copies overlap neighbouring frames' compute; host clock"}
     del client
 
-    # ---------------- batched: 64 sessions, one persistent launch in a CUDA graph -------------
+    # ---------------- batched: 64 sessions, one launch in a CUDA graph ------------------------
     sessions = synth.batched_sessions(64, seed=4000 + 1000 * rank)
     tfd = torch.from_numpy(synth.tf_ramp()).to(dev)
     sess = []
