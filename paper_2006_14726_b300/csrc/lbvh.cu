@@ -433,6 +433,22 @@ __device__ __forceinline__ void wide_unused(float4* __restrict__ wide, uint32_t 
     w[24] = __uint_as_float(wrs::kNoChild);
 }
 
+// The whole 4-wide node of a binary node whose two children are the leaves l0 (slot 0) and l1
+// (slot 1), from their boxes a[0..5] and a[6..11], in seven 16-byte stores: the leaves stand for
+// themselves in slots 0 and 2, slots 1 and 3 are unused (empty x slab, no reference).
+__device__ __forceinline__ void write_cherry(float4* __restrict__ wide, uint32_t i,
+                                             const float (&a)[12], uint32_t l0, uint32_t l1) {
+    float4* w = wide + 8 * (size_t)i;
+    w[0] = make_float4(a[0], INFINITY, a[6], INFINITY);
+    w[1] = make_float4(a[1], 0.0f, a[7], 0.0f);
+    w[2] = make_float4(a[2], 0.0f, a[8], 0.0f);
+    w[3] = make_float4(a[3], -INFINITY, a[9], -INFINITY);
+    w[4] = make_float4(a[4], 0.0f, a[10], 0.0f);
+    w[5] = make_float4(a[5], 0.0f, a[11], 0.0f);
+    w[6] = make_float4(__uint_as_float(kLeafBit | l0), __uint_as_float(wrs::kNoChild),
+                       __uint_as_float(kLeafBit | l1), __uint_as_float(wrs::kNoChild));
+}
+
 __global__ void __launch_bounds__(kRefitBlock) k_leaves_refit(
     const uint32_t* __restrict__ order, const float4* __restrict__ pos_r,
     const float4* __restrict__ rgba, const uint32_t* __restrict__ id,
@@ -472,14 +488,16 @@ __global__ void __launch_bounds__(kRefitBlock) k_leaves_refit(
         const uint32_t node = pp >> 1, slot = pp & 1u;
         if (node + 1 >= m) return;  // never taken for a well-formed tree
         const uint32_t gp = node != 0 ? node_parent[node] : 0u;  // node's own link to its parent
+        const uint2 rg = node_range[node];
+        // a node over two leaves: its 4-wide node is written whole by its second arrival
+        const bool cherry = rg.y == rg.x + 1;
         store_box(nodes, node, slot, lo, hi);  // the traversal reads it after the kernel
-        if (xref & kLeafBit) {  // a leaf child stands for itself in its parent's 4-wide node
+        if ((xref & kLeafBit) && !cherry) {  // a leaf child stands for itself in its parent's
             wide_entry(wide, node, 2 * slot, lo, hi, xref);
-            wide_unused(wide, node, 2 * slot + 1);  // the slot after it is unused
+            wide_unused(wide, node, 2 * slot + 1);  // 4-wide node; the slot after it is unused
         }
         if (node != 0 && (gp >> 1) + 1 < m)  // a grandchild of gp's node
             wide_entry(wide, gp >> 1, 2 * (gp & 1u) + slot, lo, hi, xref);
-        const uint2 rg = node_range[node];
         float a[12];
         if (local && rg.x >= j0 && rg.y <= j1 && node >= j0 && node <= j1) {
             float* sb = sh_box[node - j0] + 6 * slot;
@@ -499,6 +517,7 @@ __global__ void __launch_bounds__(kRefitBlock) k_leaves_refit(
             for (int k = 0; k < 12; k++) a[k] = __ldcg(f + k);
         }
         // second child: both boxes are final; this node's box goes to its parent
+        if (cherry) write_cherry(wide, node, a, rg.x, rg.y);
         lo[0] = fminf(a[0], a[6]); lo[1] = fminf(a[1], a[7]); lo[2] = fminf(a[2], a[8]);
         hi[0] = fmaxf(a[3], a[9]); hi[1] = fmaxf(a[4], a[10]); hi[2] = fmaxf(a[5], a[11]);
         if (node == 0) return;
