@@ -29,7 +29,7 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct Scratch {
     uint32_t *keys0, *keys1, *vals0, *vals1, *hist, *totals, *leaf_parent, *node_parent, *visit;
-    uint2* node_range;  // leaf range [lo, hi] of each internal node
+    uint4* node_range;  // leaf range [lo, hi] and split of each internal node
     float* partials;
     uint32_t tiles;
 };
@@ -54,13 +54,13 @@ size_t scratch_layout(uint32_t cap, uint32_t leaf, char* base, Scratch* s) {
     char* lp = take(sizeof(uint32_t) * m);
     char* np = take(sizeof(uint32_t) * m);
     char* vi = take(sizeof(uint32_t) * m);
-    char* nr = take(sizeof(uint2) * m);
+    char* nr = take(sizeof(uint4) * m);
     char* pa = take(sizeof(float) * 8 * kBoundsBlocks);
     if (s) {
         s->keys0 = (uint32_t*)k0; s->keys1 = (uint32_t*)k1;
         s->vals0 = (uint32_t*)v0; s->vals1 = (uint32_t*)v1;
         s->hist = (uint32_t*)h; s->totals = (uint32_t*)tt; s->leaf_parent = (uint32_t*)lp; s->node_parent = (uint32_t*)np;
-        s->visit = (uint32_t*)vi; s->node_range = (uint2*)nr; s->partials = (float*)pa; s->tiles = tiles;
+        s->visit = (uint32_t*)vi; s->node_range = (uint4*)nr; s->partials = (float*)pa; s->tiles = tiles;
     }
     return off;
 }
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(256) k_karras(const uint32_t* __restrict__ cod
                                                 float4* __restrict__ nodes,
                                                 uint32_t* __restrict__ leaf_parent,
                                                 uint32_t* __restrict__ node_parent,
-                                                uint2* __restrict__ node_range) {
+                                                uint4* __restrict__ node_range) {
     const int m = (int)hdr->m;
     const uint32_t leaf = hdr->leaf;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(256) k_karras(const uint32_t* __restrict__ cod
     const uint32_t left = (lo == g) ? (kLeafBit | (uint32_t)g) : (uint32_t)g;
     const uint32_t right = (hi == g + 1) ? (kLeafBit | (uint32_t)(g + 1)) : (uint32_t)(g + 1);
     nodes[4 * i + 3] = make_float4(__uint_as_float(left), __uint_as_float(right), 0.0f, 0.0f);
-    node_range[i] = make_uint2((uint32_t)lo, (uint32_t)hi);
+    node_range[i] = make_uint4((uint32_t)lo, (uint32_t)hi, (uint32_t)g, 0u);
     if (lo == g) leaf_parent[g] = (uint32_t)i << 1;
     else node_parent[g] = (uint32_t)i << 1;
     if (hi == g + 1) leaf_parent[g + 1] = ((uint32_t)i << 1) | 1u;
@@ -413,24 +413,32 @@ __device__ __forceinline__ void store_box(float4* nodes, uint32_t node, uint32_t
 // four references), so that a traversal step loads one coordinate of all four boxes per float4.
 // Fixed slots: child c's children go to slots 2c and 2c + 1; a leaf child stands for itself in
 // slot 2c and slot 2c + 1 is unused: low x = +inf and high x = -inf (whatever its other planes
-// hold, no ray enters it: its x slab is empty) and the reference kNoChild.  The refit fills them:
-// the thread that
-// holds the final box of a node or leaf X writes it into the 4-wide node of X's grandparent, and a
-// leaf also into its parent's.  These are plain stores off the climb's critical path.
-__device__ __forceinline__ void wide_entry(float4* __restrict__ wide, uint32_t i, uint32_t e,
-                                           const float lo[3], const float hi[3], uint32_t ref) {
-    float* w = reinterpret_cast<float*>(wide + 8 * (size_t)i) + e;
-    w[0] = lo[0]; w[4] = lo[1]; w[8] = lo[2];
-    w[12] = hi[0]; w[16] = hi[1]; w[20] = hi[2];
-    w[24] = __uint_as_float(ref);
+// hold, no ray enters it: its x slab is empty) and the reference kNoChild.  The refit fills them
+// when a node is finished (by the thread that arrives second): the node's two children as a pair
+// of slots of its parent's 4-wide node, a leaf child also as itself in the node's own 4-wide node
+// (both slots of a node over two leaves at once).  These are vector stores off the loads of the
+// climb.
+
+// Slots 2c and 2c + 1 of 4-wide node i: the boxes b[0..5], b[6..11] with references r0, r1, one
+// 8-byte store per plane (the two slots are adjacent in every plane's float4).
+__device__ __forceinline__ void write_pair(float4* __restrict__ wide, uint32_t i, uint32_t c,
+                                           const float* b, uint32_t r0, uint32_t r1) {
+    float* w = reinterpret_cast<float*>(wide + 8 * (size_t)i) + 2 * c;
+#pragma unroll
+    for (int q = 0; q < 6; q++) *reinterpret_cast<float2*>(w + 4 * q) = make_float2(b[q], b[6 + q]);
+    *reinterpret_cast<float2*>(w + 24) = make_float2(__uint_as_float(r0), __uint_as_float(r1));
 }
 
-// An unused entry: three stores (its x slab empty, no reference) instead of a whole empty box.
-__device__ __forceinline__ void wide_unused(float4* __restrict__ wide, uint32_t i, uint32_t e) {
-    float* w = reinterpret_cast<float*>(wide + 8 * (size_t)i) + e;
-    w[0] = INFINITY;
-    w[12] = -INFINITY;
-    w[24] = __uint_as_float(wrs::kNoChild);
+// Slots 2c and 2c + 1 of 4-wide node i for a leaf child c: the leaf (box b[0..5], reference r)
+// stands for itself, the slot after it is unused (empty x slab, no reference).
+__device__ __forceinline__ void write_leaf_pair(float4* __restrict__ wide, uint32_t i, uint32_t c,
+                                                const float* b, uint32_t r) {
+    float* w = reinterpret_cast<float*>(wide + 8 * (size_t)i) + 2 * c;
+#pragma unroll
+    for (int q = 0; q < 6; q++)
+        *reinterpret_cast<float2*>(w + 4 * q) =
+            make_float2(b[q], q == 0 ? INFINITY : (q == 3 ? -INFINITY : 0.0f));
+    *reinterpret_cast<float2*>(w + 24) = make_float2(__uint_as_float(r), __uint_as_float(wrs::kNoChild));
 }
 
 // The whole 4-wide node of a binary node whose two children are the leaves l0 (slot 0) and l1
@@ -454,7 +462,7 @@ __global__ void __launch_bounds__(kRefitBlock) k_leaves_refit(
     const float4* __restrict__ rgba, const uint32_t* __restrict__ id,
     const float* __restrict__ scale, float gscale, const LbvhHeader* __restrict__ hdr,
     float4* __restrict__ nodes, const uint32_t* __restrict__ leaf_parent,
-    const uint32_t* __restrict__ node_parent, const uint2* __restrict__ node_range,
+    const uint32_t* __restrict__ node_parent, const uint4* __restrict__ node_range,
     uint32_t* __restrict__ visit, float4* __restrict__ s_pos, float4* __restrict__ s_rgba,
     uint32_t* __restrict__ s_id, uint32_t* __restrict__ s_src, float4* __restrict__ wide) {
     __shared__ uint32_t sh_cnt[kRefitBlock];
@@ -488,16 +496,8 @@ __global__ void __launch_bounds__(kRefitBlock) k_leaves_refit(
         const uint32_t node = pp >> 1, slot = pp & 1u;
         if (node + 1 >= m) return;  // never taken for a well-formed tree
         const uint32_t gp = node != 0 ? node_parent[node] : 0u;  // node's own link to its parent
-        const uint2 rg = node_range[node];
-        // a node over two leaves: its 4-wide node is written whole by its second arrival
-        const bool cherry = rg.y == rg.x + 1;
+        const uint4 rg = node_range[node];
         store_box(nodes, node, slot, lo, hi);  // the traversal reads it after the kernel
-        if ((xref & kLeafBit) && !cherry) {  // a leaf child stands for itself in its parent's
-            wide_entry(wide, node, 2 * slot, lo, hi, xref);
-            wide_unused(wide, node, 2 * slot + 1);  // 4-wide node; the slot after it is unused
-        }
-        if (node != 0 && (gp >> 1) + 1 < m)  // a grandchild of gp's node
-            wide_entry(wide, gp >> 1, 2 * (gp & 1u) + slot, lo, hi, xref);
         float a[12];
         if (local && rg.x >= j0 && rg.y <= j1 && node >= j0 && node <= j1) {
             float* sb = sh_box[node - j0] + 6 * slot;
@@ -516,8 +516,16 @@ __global__ void __launch_bounds__(kRefitBlock) k_leaves_refit(
 #pragma unroll
             for (int k = 0; k < 12; k++) a[k] = __ldcg(f + k);
         }
-        // second child: both boxes are final; this node's box goes to its parent
-        if (cherry) write_cherry(wide, node, a, rg.x, rg.y);
+        // second child: both boxes are final.  The node's children enter the 4-wide nodes here:
+        // as grandchildren of its parent (a pair of slots), and a leaf child also as itself in the
+        // node's own 4-wide node; then the node's box goes to its parent
+        const uint32_t g = rg.z;
+        const bool leaf0 = rg.x == g, leaf1 = rg.y == g + 1;
+        const uint32_t ref0 = leaf0 ? (kLeafBit | g) : g, ref1 = leaf1 ? (kLeafBit | (g + 1)) : g + 1;
+        if (leaf0 && leaf1) write_cherry(wide, node, a, g, g + 1);
+        else if (leaf0) write_leaf_pair(wide, node, 0, a, ref0);
+        else if (leaf1) write_leaf_pair(wide, node, 1, a + 6, ref1);
+        if (node != 0 && (gp >> 1) + 1 < m) write_pair(wide, gp >> 1, gp & 1u, a, ref0, ref1);
         lo[0] = fminf(a[0], a[6]); lo[1] = fminf(a[1], a[7]); lo[2] = fminf(a[2], a[8]);
         hi[0] = fmaxf(a[3], a[9]); hi[1] = fmaxf(a[4], a[10]); hi[2] = fmaxf(a[5], a[11]);
         if (node == 0) return;
