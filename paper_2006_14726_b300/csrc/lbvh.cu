@@ -490,14 +490,12 @@ __global__ void __launch_bounds__(kRefitBlock) k_leaves_refit(
     }
     if (m < 2) return;
     uint32_t pp = leaf_parent[j];
-    uint32_t xref = kLeafBit | j;  // reference of the leaf or node whose box the thread holds
     bool local = true;  // ancestors of a node that spans blocks span blocks too
     while (true) {
         const uint32_t node = pp >> 1, slot = pp & 1u;
         if (node + 1 >= m) return;  // never taken for a well-formed tree
         const uint32_t gp = node != 0 ? node_parent[node] : 0u;  // node's own link to its parent
         const uint4 rg = node_range[node];
-        store_box(nodes, node, slot, lo, hi);  // the traversal reads it after the kernel
         float a[12];
         if (local && rg.x >= j0 && rg.y <= j1 && node >= j0 && node <= j1) {
             float* sb = sh_box[node - j0] + 6 * slot;
@@ -507,7 +505,16 @@ __global__ void __launch_bounds__(kRefitBlock) k_leaves_refit(
             __threadfence_block();
 #pragma unroll
             for (int k = 0; k < 12; k++) a[k] = sh_box[node - j0][k];
+            // the node's binary record (both child boxes) in three 16-byte stores; the traversal
+            // reads it after the kernel
+            float4* rec = nodes + 4 * (size_t)node;
+            __stcg(rec + 0, make_float4(a[0], a[1], a[2], a[3]));
+            __stcg(rec + 1, make_float4(a[4], a[5], a[6], a[7]));
+            __stcg(rec + 2, make_float4(a[8], a[9], a[10], a[11]));
         } else {
+            // a node spanning blocks: each child's box goes to the record before the release, the
+            // second child reads the other one from there
+            store_box(nodes, node, slot, lo, hi);
             local = false;
             fence_acq_rel_gpu();
             if (atomicAdd(visit + node, 1u) == 0u) return;  // first child: done
@@ -529,7 +536,6 @@ __global__ void __launch_bounds__(kRefitBlock) k_leaves_refit(
         lo[0] = fminf(a[0], a[6]); lo[1] = fminf(a[1], a[7]); lo[2] = fminf(a[2], a[8]);
         hi[0] = fmaxf(a[3], a[9]); hi[1] = fmaxf(a[4], a[10]); hi[2] = fmaxf(a[5], a[11]);
         if (node == 0) return;
-        xref = node;
         pp = gp;
     }
 }
