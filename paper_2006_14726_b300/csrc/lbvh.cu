@@ -391,7 +391,20 @@ __global__ void __launch_bounds__(256) k_karras(const uint32_t* __restrict__ cod
 // per node, which was the refit's main stall.
 constexpr uint32_t kRefitBlock = 256;
 
-__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+// Counter increments with acquire-release semantics on the atomic itself (one ordered operation
+// instead of a fence on each side of a relaxed atomic): the release publishes this child's box,
+// the acquire makes the sibling's box visible to the second arrival.
+__device__ __forceinline__ uint32_t add_acq_rel_gpu(uint32_t* p) {
+    uint32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
+    return old;
+}
+__device__ __forceinline__ uint32_t add_acq_rel_cta_shared(uint32_t* p) {
+    uint32_t old;
+    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+    asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], 1;" : "=r"(old) : "r"(a) : "memory");
+    return old;
+}
 
 // Child box `slot` of binary node `node` (floats 6 slot .. 6 slot + 5 of its 64-byte record) in
 // two vector stores: slot 0 = 16 + 8 bytes, slot 1 = 8 + 16 bytes (all naturally aligned).
@@ -500,9 +513,7 @@ __global__ void __launch_bounds__(kRefitBlock) k_leaves_refit(
         if (local && rg.x >= j0 && rg.y <= j1 && node >= j0 && node <= j1) {
             float* sb = sh_box[node - j0] + 6 * slot;
             sb[0] = lo[0]; sb[1] = lo[1]; sb[2] = lo[2]; sb[3] = hi[0]; sb[4] = hi[1]; sb[5] = hi[2];
-            __threadfence_block();
-            if (atomicAdd(&sh_cnt[node - j0], 1u) == 0u) return;  // first child: done
-            __threadfence_block();
+            if (add_acq_rel_cta_shared(&sh_cnt[node - j0]) == 0u) return;  // first child: done
 #pragma unroll
             for (int k = 0; k < 12; k++) a[k] = sh_box[node - j0][k];
             // the node's binary record (both child boxes) in three 16-byte stores; the traversal
@@ -516,9 +527,7 @@ __global__ void __launch_bounds__(kRefitBlock) k_leaves_refit(
             // second child reads the other one from there
             store_box(nodes, node, slot, lo, hi);
             local = false;
-            fence_acq_rel_gpu();
-            if (atomicAdd(visit + node, 1u) == 0u) return;  // first child: done
-            fence_acq_rel_gpu();
+            if (add_acq_rel_gpu(visit + node) == 0u) return;  // first child: done
             const float* f = reinterpret_cast<const float*>(nodes + 4 * (size_t)node);
 #pragma unroll
             for (int k = 0; k < 12; k++) a[k] = __ldcg(f + k);
