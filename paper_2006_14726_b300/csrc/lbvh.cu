@@ -383,12 +383,12 @@ __global__ void __launch_bounds__(256) k_karras(const uint32_t* __restrict__ cod
 
 // ---- leaf gather + bottom-up refit ---------------------------------------------------------
 // Message passing between the two children of a node: the first child to finish stores its box,
-// then (release) increments the node's counter; the second child's increment observes it and,
-// after an acquire, reads both boxes.  Each block owns kRefitBlock consecutive leaves.  A node
-// whose leaf range lies inside the block is finished inside the block: its counter and child boxes
-// live in shared memory and the fences are block-scope (cheap).  Only nodes whose range spans
-// blocks use global counters with device-scope fences -- a few per block boundary instead of one
-// per node, which was the refit's main stall.
+// then increments the node's counter with release semantics; the second child's increment (with
+// acquire semantics) observes it and reads both boxes.  Each block owns kRefitBlock consecutive
+// leaves.  A node whose leaf range lies inside the block is finished inside the block: its counter
+// and child boxes live in shared memory and the ordering is block-scope (cheap).  Only nodes whose
+// range spans blocks use global counters with device-scope ordering -- a few per block boundary
+// instead of one per node.
 constexpr uint32_t kRefitBlock = 256;
 
 // Counter increments with acquire-release semantics on the atomic itself (one ordered operation
