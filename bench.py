@@ -165,9 +165,10 @@ def kernel_digest():
 
 
 def profiled(key):
-    """A figure of the committed ncu summary of the trace kernel (``- key: value`` lines), if the
-    summary was taken on the current kernel source (it records the source digest); else None."""
-    path = os.path.join(ROOT, "profiles", "trace_large_1080p_2M.md")
+    """A figure of the committed ncu summary of the trace kernel over the timed loop's 60 client
+    poses (``- key: value`` lines, means per launch), if the summary was taken on the current
+    kernel source (it records the source digest); else None."""
+    path = os.path.join(ROOT, "profiles", "trace_large_1080p_bench_poses.md")
     try:
         txt = open(path).read()
     except OSError:
@@ -432,10 +433,11 @@ def main():
         line["roofline"]["issue"] = {"warp_instructions_per_launch": winst,
                                      "achieved_ginst_s": ach_gi, "peak_ginst_s": peak_gi,
                                      "frac": ach_gi / peak_gi,
-                                     "note": "the kernel's binding limit (ALU pipe 65 %, issue "
-                                             "68 % under ncu); instructions counted on one "
-                                             "1080p frame of the same workload; the hbm entry "
-                                             "is the counted-bytes roofline"}
+                                     "note": "the kernel's binding limit (ALU pipe 66 %, issue "
+                                             "70 % under ncu on one frame); warp instructions "
+                                             "per launch counted by ncu over the 60 poses the "
+                                             "timed loop visits; the hbm entry is the "
+                                             "counted-bytes roofline"}
 
     if not args.no_extras:
         extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, world, barrier,
