@@ -447,6 +447,27 @@ def main():
     reps.close()
 
 
+def link_rates(torch, nbytes, reps=5):
+    """Pinned host <-> device copy rates in GB/s (CUDA events, median of reps, one direction at
+    a time)."""
+    host = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    dev = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    out = {}
+    for name, dst, src in (("h2d_gbs", dev, host), ("d2h_gbs", host, dev)):
+        dst.copy_(src, non_blocking=True)
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            dst.copy_(src, non_blocking=True)
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        out[name] = nbytes / (statistics.median(ts) * 1e-3) / 1e9
+    del host, dev
+    return out
+
+
 def _time_ms(torch, fn, reps, warm=3):
     for _ in range(warm):
         fn()
@@ -496,14 +517,23 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
     ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / steps)
     wrs.check_status(client.status)
     hr0, hd0 = h_groups[0][0], h_groups[0][1]
+    h2d_bytes = int(hr0.numel() * 4 + hd0.numel() * 4)
+    d2h_bytes = int(FRAMES_PER_IMAGE * W.client_w * W.client_h * 16)
+    del client
+    # the host link's own copy rates (pinned, one direction at a time): with the step's device
+    # time they bound the end-to-end step from below
+    link = link_rates(torch, 128 << 20)
+    bound_ms = max(line["ms_per_step"], h2d_bytes / (link["h2d_gbs"] * 1e6),
+                   d2h_bytes / (link["d2h_gbs"] * 1e6))
     line["e2e"] = {"value": world * FRAMES_PER_IMAGE * npix_c / (ms * 1e-3) / 1e6, "unit": UNIT,
-                   "h2d_bytes_per_step": int(hr0.numel() * 4 + hd0.numel() * 4),
-                   "d2h_bytes_per_step": int(FRAMES_PER_IMAGE * W.client_w * W.client_h * 16),
+                   "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes,
                    "ms_per_step": ms, "steps": steps,
+                   "link_gbs": link, "bound_ms_per_step": bound_ms,
+                   "frac_of_bound": bound_ms / ms,
+                   "bound": "max(device step, h2d bytes / h2d rate, d2h bytes / d2h rate)",
                    "path": "WarpingClient: pinned host frame -> device (copy stream), unproject, "
                            "LBVH, 4 traces (compute stream), 4 images -> pinned host (copy "
                            "stream); copies overlap neighbouring frames' compute; host clock"}
-    del client
 
     # ---------------- batched: 64 sessions, one launch in a CUDA graph ------------------------
     sessions = synth.batched_sessions(64, seed=4000 + 1000 * rank)
