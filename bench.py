@@ -157,10 +157,17 @@ def measured_peaks():
 
 
 def kernel_digest():
+    """Digest of the trace kernel's code (trace.cu and common.cuh with comments, blank lines and
+    trailing spaces removed), so that a profile stays attached to the code it measured."""
+    import re
     h = hashlib.sha256()
     for p in ("paper_2006_14726_b300/csrc/trace.cu", "paper_2006_14726_b300/csrc/common.cuh"):
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, p), encoding="utf-8") as f:
+            src = f.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        lines = [ln.rstrip() for ln in src.splitlines()]
+        h.update("\n".join(ln for ln in lines if ln).encode())
     return h.hexdigest()[:16]
 
 

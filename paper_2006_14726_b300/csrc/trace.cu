@@ -5,8 +5,10 @@
 // are kept sorted by (key, id) in registers; nodes whose entry lies beyond the K-th key (or whose
 // exit lies before the previous pass's last key) are culled; after each pass the K hits are
 // composited front to back.  A ray stops once its transmittance reaches t_stop, H hits are used,
-// or a pass finds fewer than K hits.  Node records are 64 B (four float4 loads through the
-// read-only path); a splat is one float4 for the test and one float4 for its colour.
+// or a pass finds fewer than K hits.  The 4-wide traversal (the default) reads seven float4 of a
+// 128-B node per visit (the near and far planes of the ray's direction, and the references); the
+// binary traversal reads a 64-B node (four float4); both through the read-only path.  A splat is
+// one float4 for the test and one float4 for its colour.
 //
 // Results do not depend on K, the block shape or the LBVH leaf size: the hit set and order are
 // fixed by the binary32 sphere test, and the compositing visits them in the same order.
