@@ -736,22 +736,35 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
     col = sp.rgba[:n].clone().requires_grad_(True)
     opa = torch.ones(n, device=dev, requires_grad=True)
     scl = torch.ones(n, device=dev, requires_grad=True)
-    dparams = wrs.TraceParams(0, 1e-5, 0.25, params.k_chunk, params.block, params.schedule,
-                              params.width)
-
-    # all views of a step share one LBVH build (one radius scale per step); the backward pass
-    # accumulates every view's gradient in place
+    # all views of a step share one LBVH build (one radius scale per step) and run in one launch;
+    # the backward pass, also one launch, accumulates every view's gradient in place
     target = torch.stack(targets)
+    cfg = {}
 
     def fwd():
         with torch.no_grad():
-            wrs.render_views(sp, views, col, opa, scl, dparams, leaf)
+            wrs.render_views(sp, views, col, opa, scl, cfg["p"], cfg["leaf"])
 
     def loss_fn():
-        return ((wrs.render_views(sp, views, col, opa, scl, dparams, leaf) - target) ** 2).mean()
+        return ((wrs.render_views(sp, views, col, opa, scl, cfg["p"], cfg["leaf"]) - target) ** 2).mean()
 
     def fwd_bwd():
         loss_fn().backward()
+
+    # the launch of this workload (soft edges, several hits per ray, 512^2 views) is tuned on the
+    # forward + backward step itself: leaf size, K, and the per-pixel or packet schedule
+    d_table = []
+    for d_leaf in (1, 2):
+        for d_k in (1, 2, 4):
+            for d_sched in (0, 2):
+                cfg["p"] = wrs.TraceParams(0, 1e-5, 0.25, d_k, 128, d_sched, 4)
+                cfg["leaf"] = d_leaf
+                d_table.append((_time_ms(torch, fwd_bwd, 3), d_leaf, d_k, d_sched))
+    _, d_leaf, d_k, d_sched = min(d_table)
+    cfg["p"] = wrs.TraceParams(0, 1e-5, 0.25, d_k, 128, d_sched, 4)
+    cfg["leaf"] = d_leaf
+    for t in (col, opa, scl):
+        t.grad = None
     barrier()
     ms_f = max_over_ranks(_time_ms(torch, fwd, 5))
     ms_fb = max_over_ranks(_time_ms(torch, fwd_bwd, 5))
@@ -773,6 +786,9 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
     fit_s = time.perf_counter() - t_fit
     line["fwd_bwd"] = {"views": len(views), "splats": n, "client": [D.client_w, D.client_h],
                        "edge_softness": 0.25,
+                       "launch": {"leaf_size": d_leaf, "k_chunk": d_k,
+                                  "schedule": SCHEDULE_NAMES[d_sched], "bvh_width": 4,
+                                  "tuned_on": "forward + backward step"},
                        "forward_mrays_s": world * rays_d / (ms_f * 1e-3) / 1e6,
                        "forward_backward_mrays_s": world * rays_d / (ms_fb * 1e-3) / 1e6,
                        "forward_ms_per_view": ms_f / len(views),
@@ -780,10 +796,11 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
                        "fit": {"steps": 200, "optimizer": "Adam lr 1e-2 on per-splat radius scale",
                                "loss_curve": curve, "seconds": fit_s,
                                "scale_mean_after": float(scl.detach().mean())},
-                       "note": "forward = one LBVH rebuild with the current radius scales + a trace "
-                               "per view; backward = re-traversal adjoint per view, accumulated in "
-                               "place; L2 loss vs the GPU ray-cast novel views (which match the "
-                               "binary64 oracle ray caster to 1e-5)"}
+                       "note": "forward = one LBVH rebuild with the current radius scales + one "
+                               "launch tracing all views; backward = one launch of the "
+                               "re-traversal adjoint over all views, accumulated in place; L2 loss "
+                               "vs the GPU ray-cast novel views (which match the binary64 oracle "
+                               "ray caster to 1e-5)"}
 
     # ---------------- CPU oracle on the host cores (rank 0, N = 1) ------------------------------
     if rank == 0 and world == 1:

@@ -284,6 +284,17 @@ int wrs_trace(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* c
               const wrs_trace_params* params, float* rgba_out, int32_t* status,
               wrs_stream_t stream);
 
+/* Several client views of one scene in one launch: the novel views a client renders from one
+ * server frame (§4), traced together so that small views still fill the GPU.  cams: HOST array of
+ * n_views >= 1 cameras, all of the same width W and height H (WRS_ERR_ARG otherwise), read during
+ * the call.  rgba_out: device [n_views][H][W][4]; view v is bitwise the image wrs_trace writes for
+ * cams[v].  Schedules: PER_PIXEL and PACKET as in wrs_trace; PERSISTENT runs per pixel (the views
+ * together fill the GPU, which is what its lane refill is for).  Up to 32 views per launch
+ * (more are split into launches of 32). */
+int wrs_trace_views(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* cams,
+                    int32_t n_views, const wrs_trace_params* params, float* rgba_out,
+                    int32_t* status, wrs_stream_t stream);
+
 /* Same traversal, counting instead of writing an image: counters (device uint64[6]) receive the
  * totals over all rays of nodes visited, boxes tested, spheres tested, hits gathered, hits
  * composited and traversal passes.  Used for the roofline's algorithmic byte and flop counts. */
@@ -326,6 +337,19 @@ int wrs_trace_backward_accumulate(const wrs_lbvh* bvh, const wrs_splats* sorted,
                                   const float* radius_scale, float global_scale,
                                   const float* dL_drgba, float* g_rgba, float* g_opacity,
                                   float* g_scale, int32_t* status, wrs_stream_t stream);
+
+/* The adjoint of wrs_trace_views (spec S7): dL_drgba is device [n_views][H][W][4] (cams as for
+ * wrs_trace_views), and every view's gradients are added into the one set of per-splat outputs
+ * (float atomics; summation order not fixed), i.e. the sum of the views' wrs_trace_backward
+ * gradients.  accumulate = 0 zeroes the outputs first (as wrs_trace_backward), 1 adds to what
+ * they hold (as wrs_trace_backward_accumulate).  One thread per pixel, any schedule.  Not in the
+ * paper; used for multi-view fitting. */
+int wrs_trace_backward_views(const wrs_lbvh* bvh, const wrs_splats* sorted,
+                             const wrs_camera* cams, int32_t n_views,
+                             const wrs_trace_params* params, const float* radius_scale,
+                             float global_scale, const float* dL_drgba, float* g_rgba,
+                             float* g_opacity, float* g_scale, int32_t accumulate,
+                             int32_t* status, wrs_stream_t stream);
 
 /* The earlier 2.5D warping the paper compares against (§2, §5, Fig. 3): every splat of a set
  * (compacted or sorted; index = its position in that set) drawn as a point_size x point_size pixel

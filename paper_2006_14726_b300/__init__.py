@@ -149,6 +149,10 @@ _sig("wrs_trace", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats), ctypes.POI
      ctypes.POINTER(_Params), _P, _P, _P)
 _sig("wrs_trace_count", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats), ctypes.POINTER(Camera),
      ctypes.POINTER(_Params), _P, _P, _P)
+_sig("wrs_trace_views", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats), ctypes.POINTER(Camera),
+     _I, ctypes.POINTER(_Params), _P, _P, _P)
+_sig("wrs_trace_backward_views", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats),
+     ctypes.POINTER(Camera), _I, ctypes.POINTER(_Params), _P, _F, _P, _P, _P, _P, _I, _P, _P)
 _sig("wrs_session_tiles", _U, _I, _I)
 _sig("wrs_trace_batched", _I, _P, _I, _U, ctypes.POINTER(_Params), _P, _P, _P)
 _sig("wrs_trace_backward", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats), ctypes.POINTER(Camera),
@@ -519,6 +523,25 @@ def trace(bvh: LBVH, sorted: SplatBuffers, cam, params: TraceParams = TraceParam
     return out
 
 
+def _cams(cams) -> Tuple[ctypes.Array, int, int]:
+    arr = (Camera * len(cams))(*[_cam(c) for c in cams])
+    return arr, arr[0].width, arr[0].height
+
+
+def trace_views(bvh: LBVH, sorted: SplatBuffers, cams: Sequence, params: TraceParams = TraceParams(),
+                opacity: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None,
+                status: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Several same-size client views in one launch (wrs_trace_views); returns [V,H,W,4], view v
+    bitwise equal to ``trace(bvh, sorted, cams[v], ...)``."""
+    arr, w, h = _cams(cams)
+    if out is None:
+        out = torch.empty(len(cams), h, w, 4, dtype=torch.float32, device=sorted.pos_r.device)
+    b, s, p = bvh.c(), sorted.c(), params.c(opacity)
+    _check(_lib.wrs_trace_views(ctypes.byref(b), ctypes.byref(s), arr, len(cams), ctypes.byref(p),
+                                _ptr(out), _ptr(status), _stream(stream)), "wrs_trace_views")
+    return out
+
+
 COUNTER_NAMES = ("nodes", "boxes", "spheres", "gathered", "composited", "passes")
 
 
@@ -599,6 +622,31 @@ def trace_backward(bvh: LBVH, sorted: SplatBuffers, cam, dL_drgba: torch.Tensor,
     _check(fn(ctypes.byref(b), ctypes.byref(s), ctypes.byref(c), ctypes.byref(p),
               _ptr(radius_scale), float(global_scale), _ptr(dL_drgba.contiguous()), _ptr(g_rgba),
               _ptr(g_op), _ptr(g_sc), _ptr(status), _stream(stream)), name)
+    return g_rgba, g_op, g_sc
+
+
+def trace_backward_views(bvh: LBVH, sorted: SplatBuffers, cams: Sequence, dL_drgba: torch.Tensor,
+                         params: TraceParams = TraceParams(), opacity: Optional[torch.Tensor] = None,
+                         radius_scale: Optional[torch.Tensor] = None, global_scale: float = 1.0,
+                         want_opacity: bool = True, want_scale: bool = True,
+                         status: Optional[torch.Tensor] = None, stream=None, accumulate_into=None):
+    """Adjoint of :func:`trace_views` (dL_drgba [V,H,W,4]): the sum over the views of their
+    :func:`trace_backward` gradients, in one launch.  ``accumulate_into`` as for trace_backward."""
+    arr, _, _ = _cams(cams)
+    dev = sorted.pos_r.device
+    cap = max(sorted.capacity, 1)
+    if accumulate_into is not None:
+        g_rgba, g_op, g_sc = accumulate_into
+    else:
+        g_rgba = torch.empty(cap, 4, dtype=torch.float32, device=dev)
+        g_op = torch.empty(cap, dtype=torch.float32, device=dev) if want_opacity else None
+        g_sc = torch.empty(cap, dtype=torch.float32, device=dev) if want_scale else None
+    b, s, p = bvh.c(), sorted.c(), params.c(opacity)
+    _check(_lib.wrs_trace_backward_views(
+        ctypes.byref(b), ctypes.byref(s), arr, len(cams), ctypes.byref(p), _ptr(radius_scale),
+        float(global_scale), _ptr(dL_drgba.contiguous()), _ptr(g_rgba), _ptr(g_op), _ptr(g_sc),
+        1 if accumulate_into is not None else 0, _ptr(status), _stream(stream)),
+        "wrs_trace_backward_views")
     return g_rgba, g_op, g_sc
 
 

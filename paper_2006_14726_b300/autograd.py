@@ -5,7 +5,8 @@ The differentiable quantities are the per-splat colour (premultiplied RGBA), opa
 scale, all in compacted splat order.  The forward pass stores no hit lists: the backward kernel
 re-traverses every ray (spec S7).  The radius scale changes the spheres, so every forward call
 rebuilds the LBVH with the current scales; :func:`render_views` renders several views from one
-build and accumulates their gradients in place (wrs_trace_backward_accumulate).
+build, all views in one launch (wrs_trace_views), and their gradients in one launch into one
+set of buffers (wrs_trace_backward_views).
 """
 from __future__ import annotations
 
@@ -13,7 +14,8 @@ from typing import Optional, Sequence
 
 import torch
 
-from . import SplatBuffers, TraceParams, build_lbvh, trace, trace_backward
+from . import (SplatBuffers, TraceParams, build_lbvh, trace, trace_backward, trace_backward_views,
+               trace_views)
 
 
 class TraceFunction(torch.autograd.Function):
@@ -54,8 +56,9 @@ def render(splats: SplatBuffers, cam, rgba: torch.Tensor, opacity: Optional[torc
 
 
 class MultiViewTraceFunction(torch.autograd.Function):
-    """Several client views of one splat set: one LBVH build, one trace per view; the backward
-    pass accumulates every view's gradient into one buffer (no per-view buffers, no sums)."""
+    """Several client views of one splat set: one LBVH build and one launch for all views; the
+    backward pass, also one launch, accumulates every view's gradient into one buffer (no
+    per-view buffers, no sums)."""
 
     @staticmethod
     def forward(ctx, rgba: torch.Tensor, opacity: Optional[torch.Tensor],
@@ -69,12 +72,9 @@ class MultiViewTraceFunction(torch.autograd.Function):
         sc = None if radius_scale is None else radius_scale.detach().contiguous()
         bvh, sorted_ = build_lbvh(splats, leaf_size, radius_scale=sc)
         c0 = cams[0]
-        out = torch.empty(len(cams), c0.height, c0.width, 4, dtype=torch.float32,
-                          device=rgba.device)
-        for v, cam in enumerate(cams):
-            if (cam.width, cam.height) != (c0.width, c0.height):
-                raise ValueError("all views must have the same size")
-            trace(bvh, sorted_, cam, params, opacity=op, out=out[v])
+        if any((c.width, c.height) != (c0.width, c0.height) for c in cams):
+            raise ValueError("all views must have the same size")
+        out = trace_views(bvh, sorted_, cams, params, opacity=op)
         ctx.state = (bvh, sorted_, list(cams), params, op, sc, n)
         return out
 
@@ -82,16 +82,9 @@ class MultiViewTraceFunction(torch.autograd.Function):
     def backward(ctx, g_img: torch.Tensor):
         bvh, sorted_, cams, params, op, sc, n = ctx.state
         need_rgba, need_op, need_sc = ctx.needs_input_grad[:3]
-        cap = max(sorted_.capacity, 1)
-        dev = g_img.device
-        acc = (torch.zeros(cap, 4, dtype=torch.float32, device=dev),
-               torch.zeros(cap, dtype=torch.float32, device=dev) if need_op else None,
-               torch.zeros(cap, dtype=torch.float32, device=dev) if need_sc else None)
-        g_img = g_img.contiguous()
-        for v, cam in enumerate(cams):
-            trace_backward(bvh, sorted_, cam, g_img[v], params, opacity=op, radius_scale=sc,
-                           accumulate_into=acc)
-        g_rgba, g_op, g_sc = acc
+        g_rgba, g_op, g_sc = trace_backward_views(bvh, sorted_, cams, g_img.contiguous(), params,
+                                                  opacity=op, radius_scale=sc,
+                                                  want_opacity=need_op, want_scale=need_sc)
         return (g_rgba[:n] if need_rgba else None,
                 g_op[:n] if need_op else None,
                 g_sc[:n] if need_sc else None,

@@ -631,10 +631,10 @@ __device__ __forceinline__ void tile_pixel(int t, int& px, int& py) {
     py = (warp >> 1) * 4 + (lane >> 3);
 }
 
+// The pixel of this thread in the per-pixel grid (blockIdx.x, blockIdx.y) traced and written.
 template <int K, bool W4>
-__global__ void __launch_bounds__(PixelBounds<K, W4>::max_threads, PixelBounds<K, W4>::min_blocks)
-k_trace(Scene sc, Comp cp, wrs_camera cam,
-                                               float4* __restrict__ out, int32_t* status) {
+__device__ __forceinline__ void trace_pixel(const Scene& sc, const Comp& cp, const wrs_camera& cam,
+                                            float4* __restrict__ out, int32_t* status) {
     int px, py;
     tile_pixel(threadIdx.x, px, py);
     const int tile_h = (blockDim.x >> 6) * 4;
@@ -648,11 +648,32 @@ k_trace(Scene sc, Comp cp, wrs_camera cam,
     out[(size_t)y * cam.width + x] = o;
 }
 
+template <int K, bool W4>
+__global__ void __launch_bounds__(PixelBounds<K, W4>::max_threads, PixelBounds<K, W4>::min_blocks)
+k_trace(Scene sc, Comp cp, wrs_camera cam, float4* __restrict__ out, int32_t* status) {
+    trace_pixel<K, W4>(sc, cp, cam, out, status);
+}
+
+// Several views of one scene in one launch: blockIdx.z is the view; view v's camera is
+// vc.cam[v] (read in place from the kernel parameters) and its image starts at out + v * pixels.
+constexpr int kMaxViews = 32;
+struct ViewCams {
+    wrs_camera cam[kMaxViews];
+};
+
+template <int K, bool W4>
+__global__ void __launch_bounds__(PixelBounds<K, W4>::max_threads, PixelBounds<K, W4>::min_blocks)
+k_trace_views(Scene sc, Comp cp, const __grid_constant__ ViewCams vc, float4* __restrict__ out,
+              size_t pixels, int32_t* status) {
+    trace_pixel<K, W4>(sc, cp, vc.cam[blockIdx.z], out + blockIdx.z * pixels, status);
+}
+
 // Packet schedule (4-wide nodes only): every lane of the block stays to the end, lanes outside
 // the image take part in their warp's traversal without a ray.
 template <int K>
-__global__ void __launch_bounds__(256) k_trace_packet(Scene sc, Comp cp, wrs_camera cam,
-                                                      float4* __restrict__ out, int32_t* status) {
+__device__ __forceinline__ void trace_pixel_packet(const Scene& sc, const Comp& cp,
+                                                   const wrs_camera& cam, float4* __restrict__ out,
+                                                   int32_t* status) {
     int px, py;
     tile_pixel(threadIdx.x, px, py);
     const int tile_h = (blockDim.x >> 6) * 4;
@@ -663,6 +684,20 @@ __global__ void __launch_bounds__(256) k_trace_packet(Scene sc, Comp cp, wrs_cam
     const float4 o = trace_ray_packet<K>(sc, cp, rc, active, overflow);
     if (overflow) wrs::set_status(status, overflow);
     if (active) out[(size_t)y * cam.width + x] = o;
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) k_trace_packet(Scene sc, Comp cp, wrs_camera cam,
+                                                      float4* __restrict__ out, int32_t* status) {
+    trace_pixel_packet<K>(sc, cp, cam, out, status);
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) k_trace_packet_views(Scene sc, Comp cp,
+                                                            const __grid_constant__ ViewCams vc,
+                                                            float4* __restrict__ out,
+                                                            size_t pixels, int32_t* status) {
+    trace_pixel_packet<K>(sc, cp, vc.cam[blockIdx.z], out + blockIdx.z * pixels, status);
 }
 
 template <int K, bool W4>
@@ -923,9 +958,10 @@ __device__ __forceinline__ void chunk_adjoint(const Scene& sc, const Comp& cp, c
 }
 
 template <int K, bool W4>
-__global__ void __launch_bounds__(128) k_trace_bwd(Scene sc, Comp cp, wrs_camera cam,
-                                                   const float4* __restrict__ dimg, GradOut go,
-                                                   int32_t* status) {
+__device__ __forceinline__ void backward_pixel(const Scene& sc, const Comp& cp,
+                                               const wrs_camera& cam,
+                                               const float4* __restrict__ dimg, const GradOut& go,
+                                               int32_t* status) {
     int px, py;
     tile_pixel(threadIdx.x, px, py);
     const int tile_h = (blockDim.x >> 6) * 4;
@@ -976,6 +1012,24 @@ __global__ void __launch_bounds__(128) k_trace_bwd(Scene sc, Comp cp, wrs_camera
                          kid, cnt);
         chunk_adjoint<K>(sc, cp, rc.ray, ki, u, b_T[c], g, S, P, go);
     }
+}
+
+template <int K, bool W4>
+__global__ void __launch_bounds__(128) k_trace_bwd(Scene sc, Comp cp, wrs_camera cam,
+                                                   const float4* __restrict__ dimg, GradOut go,
+                                                   int32_t* status) {
+    backward_pixel<K, W4>(sc, cp, cam, dimg, go, status);
+}
+
+// Several views in one launch (blockIdx.z = view, as k_trace_views); every view's gradients
+// accumulate into the same per-splat buffers.
+template <int K, bool W4>
+__global__ void __launch_bounds__(128) k_trace_bwd_views(Scene sc, Comp cp,
+                                                         const __grid_constant__ ViewCams vc,
+                                                         const float4* __restrict__ dimg,
+                                                         size_t pixels, GradOut go,
+                                                         int32_t* status) {
+    backward_pixel<K, W4>(sc, cp, vc.cam[blockIdx.z], dimg + blockIdx.z * pixels, go, status);
 }
 
 // Persistent backward with lane refill: the per-pixel backward's two phases run as a per-lane
@@ -1186,6 +1240,24 @@ template <int K, bool W4> struct LaunchTrace {
         k_trace<K, W4><<<g, b, 0, s>>>(sc, cp, cam, o, st);
     }
 };
+template <int K, bool W4> struct LaunchTraceViews {
+    static void run(dim3 g, int b, cudaStream_t s, Scene sc, Comp cp, const ViewCams& vc,
+                    float4* o, size_t pixels, int32_t* st) {
+        k_trace_views<K, W4><<<g, b, 0, s>>>(sc, cp, vc, o, pixels, st);
+    }
+};
+template <int K, bool W4> struct LaunchPacketViews {  // 4-wide implied, as LaunchTracePacket
+    static void run(dim3 g, int b, cudaStream_t s, Scene sc, Comp cp, const ViewCams& vc,
+                    float4* o, size_t pixels, int32_t* st) {
+        k_trace_packet_views<K><<<g, b, 0, s>>>(sc, cp, vc, o, pixels, st);
+    }
+};
+template <int K, bool W4> struct LaunchBwdViews {
+    static void run(dim3 g, int b, cudaStream_t s, Scene sc, Comp cp, const ViewCams& vc,
+                    const float4* d, size_t pixels, GradOut go, int32_t* st) {
+        k_trace_bwd_views<K, W4><<<g, b, 0, s>>>(sc, cp, vc, d, pixels, go, st);
+    }
+};
 template <int K, bool W4> struct LaunchBatchedPP {
     static void run(uint32_t blocks, const wrs_session* ss, int ns, uint32_t tt, Comp cp,
                     int32_t* st, cudaStream_t s) {
@@ -1303,6 +1375,54 @@ int wrs_trace(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* c
     return WRS_OK;
 }
 
+// Views of one scene: every camera valid and of the first camera's size.
+static int check_views(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* cams,
+                       int n_views, const wrs_trace_params* params, const char* fn) {
+    if (!cams || n_views < 1) return wrs::fail(WRS_ERR_ARG, "%s: cams NULL or n_views < 1", fn);
+    if (int rc = check_trace_args(bvh, sorted, &cams[0], params, fn)) return rc;
+    for (int v = 1; v < n_views; v++) {
+        if (int rc = wrs::check_camera(&cams[v], fn)) return rc;
+        if (cams[v].width != cams[0].width || cams[v].height != cams[0].height)
+            return wrs::fail(WRS_ERR_ARG, "%s: view %d is %dx%d, view 0 is %dx%d", fn, v,
+                             cams[v].width, cams[v].height, cams[0].width, cams[0].height);
+    }
+    return WRS_OK;
+}
+
+int wrs_trace_views(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* cams,
+                    int32_t n_views, const wrs_trace_params* params, float* rgba_out,
+                    int32_t* status, wrs_stream_t stream) {
+    const char* fn = "wrs_trace_views";
+    if (int rc = check_views(bvh, sorted, cams, n_views, params, fn)) return rc;
+    if (!rgba_out || (reinterpret_cast<uintptr_t>(rgba_out) & 15))
+        return wrs::fail(WRS_ERR_ARG, "%s: rgba_out NULL or not 16-byte aligned", fn);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int K = effective_k(params), W = params->width;
+    const size_t pixels = (size_t)cams[0].width * cams[0].height;
+    const bool packet = params->schedule == WRS_SCHEDULE_PACKET;
+    // per-pixel blocks as wrs_trace; the persistent schedule runs per pixel here (the views
+    // together fill the GPU, which is what lane refill is for)
+    const int block = packet ? params->block
+                             : ((W == 4 && K <= 2 && params->block > 128) ? 128 : params->block);
+    const Scene sc = make_scene(bvh, sorted, params->opacity, packet ? 4 : W);
+    for (int v0 = 0; v0 < n_views; v0 += kMaxViews) {
+        const int nv = n_views - v0 < kMaxViews ? n_views - v0 : kMaxViews;
+        ViewCams vc;
+        for (int v = 0; v < nv; v++) vc.cam[v] = cams[v0 + v];
+        dim3 g = grid_for(&cams[0], block);
+        g.z = (unsigned)nv;
+        float4* out = reinterpret_cast<float4*>(rgba_out) + (size_t)v0 * pixels;
+        if (packet)
+            dispatch_k1<LaunchPacketViews, true>(K, g, block, s, sc, comp_of(params), vc, out,
+                                                 pixels, status);
+        else
+            dispatch_k<LaunchTraceViews>(K, W, g, block, s, sc, comp_of(params), vc, out, pixels,
+                                         status);
+        WRS_LAUNCH_CHECK(fn);
+    }
+    return WRS_OK;
+}
+
 int wrs_trace_count(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* cam,
                     const wrs_trace_params* params, unsigned long long* counters,
                     int32_t* status, wrs_stream_t stream) {
@@ -1404,6 +1524,43 @@ int wrs_trace_backward_accumulate(const wrs_lbvh* bvh, const wrs_splats* sorted,
     return trace_backward_impl(bvh, sorted, cam, params, radius_scale, global_scale, dL_drgba,
                                g_rgba, g_opacity, g_scale, status, stream, false,
                                "wrs_trace_backward_accumulate");
+}
+
+int wrs_trace_backward_views(const wrs_lbvh* bvh, const wrs_splats* sorted,
+                             const wrs_camera* cams, int32_t n_views,
+                             const wrs_trace_params* params, const float* radius_scale,
+                             float global_scale, const float* dL_drgba, float* g_rgba,
+                             float* g_opacity, float* g_scale, int32_t accumulate,
+                             int32_t* status, wrs_stream_t stream) {
+    const char* fn = "wrs_trace_backward_views";
+    if (int rc = check_views(bvh, sorted, cams, n_views, params, fn)) return rc;
+    if (!dL_drgba || !g_rgba || (reinterpret_cast<uintptr_t>(dL_drgba) & 15))
+        return wrs::fail(WRS_ERR_ARG, "%s: dL_drgba / g_rgba NULL or misaligned", fn);
+    const size_t cap = sorted->capacity;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!accumulate) {
+        cudaError_t e = cudaMemsetAsync(g_rgba, 0, 4 * sizeof(float) * cap, s);
+        if (e == cudaSuccess && g_opacity) e = cudaMemsetAsync(g_opacity, 0, sizeof(float) * cap, s);
+        if (e == cudaSuccess && g_scale) e = cudaMemsetAsync(g_scale, 0, sizeof(float) * cap, s);
+        if (e != cudaSuccess) return wrs::cuda_fail(e, fn);
+    }
+    const GradOut go = {radius_scale, global_scale, g_rgba, g_opacity, g_scale};
+    const int K = effective_k(params), W = params->width;
+    const Scene sc = make_scene(bvh, sorted, params->opacity, W);
+    const size_t pixels = (size_t)cams[0].width * cams[0].height;
+    const int block = params->block > 128 ? 128 : params->block;  // as wrs_trace_backward
+    for (int v0 = 0; v0 < n_views; v0 += kMaxViews) {
+        const int nv = n_views - v0 < kMaxViews ? n_views - v0 : kMaxViews;
+        ViewCams vc;
+        for (int v = 0; v < nv; v++) vc.cam[v] = cams[v0 + v];
+        dim3 g = grid_for(&cams[0], block);
+        g.z = (unsigned)nv;
+        dispatch_k<LaunchBwdViews>(K, W, g, block, s, sc, comp_of(params), vc,
+                                   reinterpret_cast<const float4*>(dL_drgba) + (size_t)v0 * pixels,
+                                   pixels, go, status);
+        WRS_LAUNCH_CHECK(fn);
+    }
+    return WRS_OK;
 }
 
 }  // extern "C"

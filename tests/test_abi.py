@@ -127,6 +127,17 @@ def test_host_validation_without_device(wrs):
     # misaligned output
     p = wrs._Params(0, 1e-5, 0.0, None, 8, 128)
     assert lib.wrs_trace(ctypes.byref(bv1), ctypes.byref(srt), ctypes.byref(_cam(wrs)), ctypes.byref(p), ctypes.c_void_p(0x1004), None, None) == wrs.WRS_ERR_ARG
+    # several views: none, a view of another size, a bad camera, a misaligned gradient image
+    cams = (wrs.Camera * 3)(_cam(wrs), _cam(wrs), _cam(wrs, w=9))
+    assert lib.wrs_trace_views(ctypes.byref(bv1), ctypes.byref(srt), cams, 0, ctypes.byref(p), fake, None, None) == wrs.WRS_ERR_ARG
+    assert lib.wrs_trace_views(ctypes.byref(bv1), ctypes.byref(srt), None, 2, ctypes.byref(p), fake, None, None) == wrs.WRS_ERR_ARG
+    assert lib.wrs_trace_views(ctypes.byref(bv1), ctypes.byref(srt), cams, 3, ctypes.byref(p), fake, None, None) == wrs.WRS_ERR_ARG
+    assert "view 2 is 9x8" in wrs.last_error()
+    cams[1].tan_half_fovy = 0.0
+    assert lib.wrs_trace_views(ctypes.byref(bv1), ctypes.byref(srt), cams, 2, ctypes.byref(p), fake, None, None) == wrs.WRS_ERR_ARG
+    cams[1].tan_half_fovy = 0.4
+    assert lib.wrs_trace_backward_views(ctypes.byref(bv1), ctypes.byref(srt), cams, 3, ctypes.byref(p), None, 1.0, fake, fake, None, None, 0, None, None) == wrs.WRS_ERR_ARG
+    assert lib.wrs_trace_backward_views(ctypes.byref(bv1), ctypes.byref(srt), cams, 2, ctypes.byref(p), None, 1.0, ctypes.c_void_p(0x1004), fake, None, None, 0, None, None) == wrs.WRS_ERR_ARG
     # batched: no sessions
     assert lib.wrs_trace_batched(fake, 0, 0, ctypes.byref(p), fake, None, None) == wrs.WRS_ERR_ARG
     # ray caster: bad dtype, bad size
