@@ -434,12 +434,19 @@ def main():
     # per cycle at the sampled SM clock
     winst = profiled("warp_instructions_per_launch")
     profiled_launch = sched == 0 and width == 4 and kc == 1 and leaf == 1  # the captured launch
+    fma = fma_rates(wrs, torch)
+    line["roofline"]["fp32_peak_tflops_measured"] = fma["tflops"]
     if winst is not None and profiled_launch and clk and clk.get("sm_mhz"):
         peak_gi = 148 * 4 * clk["sm_mhz"] * 1e6 / 1e9
         ach_gi = winst / (trace_ms * 1e-3) / 1e9
         line["roofline"]["issue"] = {"warp_instructions_per_launch": winst,
                                      "achieved_ginst_s": ach_gi, "peak_ginst_s": peak_gi,
                                      "frac": ach_gi / peak_gi,
+                                     "peak_ginst_s_measured": fma["ginst_s"],
+                                     "frac_of_measured": ach_gi / fma["ginst_s"],
+                                     "measured_by": "wrs_fma_peak: FFMA warp instructions per "
+                                                    "second of an FMA-only kernel, one wave of "
+                                                    "8 x 256 threads per SM",
                                      "note": "the kernel's binding limit (ALU pipe 66 %, issue "
                                              "70 % under ncu on one frame); warp instructions "
                                              "per launch counted by ncu over the 60 poses the "
@@ -452,6 +459,27 @@ def main():
     if rank == 0:
         print(json.dumps(line), flush=True)
     reps.close()
+
+
+def fma_rates(wrs, torch, iters=2000, reps=5):
+    """Measured binary32 FMA throughput (TFLOP/s) and FFMA warp-instruction rate (G/s) of this
+    GPU: wrs_fma_peak on 8 blocks of 256 threads per SM, median of reps (CUDA events)."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    blocks = sms * 8
+    out = torch.empty(blocks, dtype=torch.float32, device="cuda")
+    flops = 0.0
+    for _ in range(2):
+        flops = wrs.fma_peak(blocks, iters, out=out)
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        wrs.fma_peak(blocks, iters, out=out)
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b) * 1e-3)
+    t = statistics.median(ts)
+    return {"tflops": flops / t / 1e12, "ginst_s": flops / 2 / 32 / t / 1e9}
 
 
 def link_rates(torch, nbytes, reps=5):

@@ -364,6 +364,12 @@ int wrs_point_splat(const wrs_splats* splats, const wrs_camera* cam, int32_t poi
                     float* rgba_out, int32_t* index_out, void* scratch, size_t scratch_bytes,
                     wrs_stream_t stream);
 
+/* Measurement helper, not part of the method: blocks x 256 threads, each running iters x 128
+ * binary32 FMAs in 8 independent chains (2 flops each), so that a caller timing the launch gets
+ * the FP32 FMA throughput and the warp-instruction issue rate of ALU-bound code under the current
+ * clocks.  out: device float[blocks], never written in practice (it keeps the chains alive). */
+int wrs_fma_peak(float* out, int32_t blocks, int32_t iters, wrs_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -149,6 +149,7 @@ _sig("wrs_trace", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats), ctypes.POI
      ctypes.POINTER(_Params), _P, _P, _P)
 _sig("wrs_trace_count", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats), ctypes.POINTER(Camera),
      ctypes.POINTER(_Params), _P, _P, _P)
+_sig("wrs_fma_peak", _I, _P, _I, _I, _P)
 _sig("wrs_trace_views", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats), ctypes.POINTER(Camera),
      _I, ctypes.POINTER(_Params), _P, _P, _P)
 _sig("wrs_trace_backward_views", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats),
@@ -648,6 +649,15 @@ def trace_backward_views(bvh: LBVH, sorted: SplatBuffers, cams: Sequence, dL_drg
         1 if accumulate_into is not None else 0, _ptr(status), _stream(stream)),
         "wrs_trace_backward_views")
     return g_rgba, g_op, g_sc
+
+
+def fma_peak(blocks: int, iters: int, stream=None, out: Optional[torch.Tensor] = None):
+    """Launch the FP32 FMA throughput kernel (blocks x 256 threads x iters x 128 FMAs); the caller
+    times it.  Returns the flop count of the launch."""
+    if out is None or out.numel() < blocks:
+        out = torch.empty(blocks, dtype=torch.float32, device="cuda")
+    _check(_lib.wrs_fma_peak(_ptr(out), int(blocks), int(iters), _stream(stream)), "wrs_fma_peak")
+    return 2.0 * blocks * 256 * iters * 128
 
 
 def check_status(status: torch.Tensor, stream=None):

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libwrs.so")
-SOURCES = ["api.cu", "unproject.cu", "raycast.cu", "lbvh.cu", "trace.cu", "point_splat.cu", "codec.cu"]
+SOURCES = ["api.cu", "unproject.cu", "raycast.cu", "lbvh.cu", "trace.cu", "point_splat.cu", "codec.cu", "peak.cu"]
 HEADERS = [os.path.join(CSRC, "common.cuh"), os.path.join(CSRC, "codec.cuh"), os.path.join(INCLUDE, "wrs.h")]
 
 NVCC_FLAGS = [

@@ -1,10 +1,13 @@
 """Run one workload of the hot path once, with few launches, for profiling and inspection.
 
     python -m paper_2006_14726_b300.cases large --frames 3 [--leaf 1 --k 1 --block 128 --schedule 1]
+    python -m paper_2006_14726_b300.cases diff [--leaf 1 --k 4 --schedule 2]
 
 Sets up the server image with the GPU ray caster, frees the volume, then runs unproject, the
 LBVH build and ``frames`` client traces (each stage in its own NVTX range) and prints the CUDA
-event times.  Workloads: tiny, mid, large (see synth).
+event times.  Workloads: tiny, mid, large (see synth).  ``diff``: the differentiable workload
+(256^3 blobs, 512^2 server image, 8 views of 512^2, soft edges 0.25): two forward + backward
+steps of the 8 views (one launch each way per step) against the ray-cast views.
 """
 from __future__ import annotations
 
@@ -23,7 +26,7 @@ import synth  # noqa: E402
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("workload", choices=["tiny", "mid", "large"])
+    ap.add_argument("workload", choices=["tiny", "mid", "large", "diff"])
     ap.add_argument("--frames", type=int, default=3)
     ap.add_argument("--leaf", type=int, default=1)
     ap.add_argument("--k", type=int, default=1)
@@ -32,6 +35,9 @@ def main():
     ap.add_argument("--schedule", type=int, default=0, help="0 per pixel, 1 persistent")
     ap.add_argument("--width", type=int, default=4, help="2 binary nodes, 4 four-wide nodes")
     a = ap.parse_args()
+    if a.workload == "diff":
+        diff_case(a)
+        return
     W = {"tiny": synth.TINY, "mid": synth.MID, "large": synth.LARGE}[a.workload]
     dev = torch.device("cuda")
     srv = W.server_cam()
@@ -68,6 +74,35 @@ def main():
            "trace_ms": [ev[2 + f].elapsed_time(ev[3 + f]) for f in range(a.frames)],
            "device_bytes_allocated": torch.cuda.memory_allocated()}
     print(json.dumps(res))
+
+
+def diff_case(a):
+    D = synth.DIFF
+    dev = torch.device("cuda")
+    tf = torch.from_numpy(synth.tf_ramp()).to(dev)
+    vol = synth.gaussian_volume_device(D.vol_n, D.vol_param, D.seed)
+    srv = D.server_cam()
+    rgba, depth = wrs.raycast_volume(vol, tf, srv)
+    views = D.client_poses()
+    target = torch.stack([wrs.raycast_volume(vol, tf, v)[0] for v in views])
+    del vol
+    sp = wrs.unproject(rgba, depth, srv)
+    n = sp.count()
+    col = sp.rgba[:n].clone().requires_grad_(True)
+    opa = torch.ones(n, device=dev, requires_grad=True)
+    scl = torch.ones(n, device=dev, requires_grad=True)
+    params = wrs.TraceParams(0, 1e-5, 0.25, a.k, 128, a.schedule, 4)
+    ms = []
+    for _ in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        loss = ((wrs.render_views(sp, views, col, opa, scl, params, a.leaf) - target) ** 2).mean()
+        loss.backward()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    print(json.dumps({"workload": "diff", "splats": n, "views": len(views),
+                      "fwd_bwd_ms": ms, "loss": float(loss.detach())}))
 
 
 if __name__ == "__main__":
