@@ -878,9 +878,10 @@ __global__ void __launch_bounds__(128) k_trace_batched(const wrs_session* __rest
 // ---- adjoint (spec S7) ---------------------------------------------------------------------
 // Pass A replays the forward pass chunk by chunk and records, per chunk, its lower bound and the
 // transmittance at its start.  Pass B walks the chunks back to front; each chunk is gathered
-// again (same bound, same K hits), its transmittances recomputed forward from the recorded
-// start, and the hits are then visited back to front with the suffix composite S and the suffix
-// transmittance P, so no division by (1 - alpha) is needed.
+// again (same bound, same K hits; the last chunk's hits are still in the k-buffer, so it is not),
+// its transmittances recomputed forward from the recorded start, and the hits are then visited
+// back to front with the suffix composite S and the suffix transmittance P, so no division by
+// (1 - alpha) is needed.
 // Pass A for one gathered chunk: advance the transmittance over its used hits exactly as the
 // forward compositing does; *u = hits used in this chunk.  Returns true when the ray is finished.
 template <int K>
@@ -1007,9 +1008,11 @@ __device__ __forceinline__ void backward_pixel(const Scene& sc, const Comp& cp,
     for (int c = chunks - 1; c >= 0; c--) {
         const int u = b_used[c];
         if (u == 0) continue;
-        const bool hl = b_key[c] != -kInf;
-        gather<K, false, W4>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, hl, b_key[c], b_id[c], kk, ki,
-                         kid, cnt);
+        if (c != chunks - 1) {  // the last chunk's hits are still in the k-buffer from pass A
+            const bool hl = b_key[c] != -kInf;
+            gather<K, false, W4>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, hl, b_key[c], b_id[c],
+                                 kk, ki, kid, cnt);
+        }
         chunk_adjoint<K>(sc, cp, rc.ray, ki, u, b_T[c], g, S, P, go);
     }
 }
@@ -1134,7 +1137,9 @@ __global__ void __launch_bounds__(128) k_trace_bwd_pr(Scene sc, Comp cp, wrs_cam
             phase = 1;
             S = make_float3(0.f, 0.f, 0.f);
             P = 1.0f;
-            cur = chunks;
+            cur = chunks - 1;  // the last chunk's hits are still in the k-buffer: no re-gather
+            if (b_used[cur] != 0)
+                chunk_adjoint<K>(sc, cp, L.ray, L.ki, b_used[cur], b_T[cur], g, S, P, go);
         } else {  // chunk `cur` re-gathered: its adjoint
             chunk_adjoint<K>(sc, cp, L.ray, L.ki, b_used[cur], b_T[cur], g, S, P, go);
         }
