@@ -319,7 +319,8 @@ int wrs_trace_batched(const wrs_session* sessions, int32_t n_sessions, uint32_t 
 
 /* Adjoint of wrs_trace (spec S7): given dL/d(rgba_out) (device [H][W][4]), re-traverse every ray
  * to rebuild its hit list (nothing is stored by the forward pass) and accumulate, in COMPACTED
- * splat order, g_rgba[n][4] (dL/d rgba), g_opacity[n] (dL/d opacity, may be NULL) and
+ * splat order, g_rgba[n][4] (dL/d rgba; dL_drgba and g_rgba 16-byte aligned), g_opacity[n]
+ * (dL/d opacity, may be NULL) and
  * g_scale[n] (dL/d radius scale, may be NULL; zero when edge_softness = 0).  radius_scale /
  * global_scale must be the values the LBVH was built with.  The outputs are zeroed by this call
  * over the first in-capacity entries; accumulation uses float atomics (summation order is not

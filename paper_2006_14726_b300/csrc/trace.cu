@@ -937,10 +937,9 @@ __device__ __forceinline__ void chunk_adjoint(const Scene& sc, const Comp& cp, c
         const float pass = (h.x >= 0.0f && h.x <= 1.0f) ? 1.0f : 0.0f;
         const uint32_t src = __ldg(sc.src + k);
         const float tow = Ti * h.op * h.w;
-        atomicAdd(go.g_rgba + 4 * (size_t)src + 0, tow * g.x);
-        atomicAdd(go.g_rgba + 4 * (size_t)src + 1, tow * g.y);
-        atomicAdd(go.g_rgba + 4 * (size_t)src + 2, tow * g.z);
-        atomicAdd(go.g_rgba + 4 * (size_t)src + 3, dLda * pass * h.op * h.w);
+        // one 16-byte vector atomic for the four colour components (g_rgba is 16-byte aligned)
+        atomicAdd(reinterpret_cast<float4*>(go.g_rgba) + src,
+                  make_float4(tow * g.x, tow * g.y, tow * g.z, dLda * pass * h.op * h.w));
         if (go.g_op) atomicAdd(go.g_op + src, Ti * h.w * gC + dLda * pass * h.c.w * h.w);
         if (go.g_sc && cp.beta > 0.0f) {
             const float s_val = go.scale ? __ldg(go.scale + src) : go.gscale;
@@ -1486,8 +1485,9 @@ static int trace_backward_impl(const wrs_lbvh* bvh, const wrs_splats* sorted,
                                float* g_scale, int32_t* status, wrs_stream_t stream, bool zero,
                                const char* fn) {
     if (int rc = check_trace_args(bvh, sorted, cam, params, fn)) return rc;
-    if (!dL_drgba || !g_rgba || (reinterpret_cast<uintptr_t>(dL_drgba) & 15))
-        return wrs::fail(WRS_ERR_ARG, "%s: dL_drgba / g_rgba NULL or misaligned", fn);
+    if (!dL_drgba || !g_rgba ||
+        ((reinterpret_cast<uintptr_t>(dL_drgba) | reinterpret_cast<uintptr_t>(g_rgba)) & 15))
+        return wrs::fail(WRS_ERR_ARG, "%s: dL_drgba / g_rgba NULL or not 16-byte aligned", fn);
     const size_t cap = sorted->capacity;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (zero) {
@@ -1539,8 +1539,9 @@ int wrs_trace_backward_views(const wrs_lbvh* bvh, const wrs_splats* sorted,
                              int32_t* status, wrs_stream_t stream) {
     const char* fn = "wrs_trace_backward_views";
     if (int rc = check_views(bvh, sorted, cams, n_views, params, fn)) return rc;
-    if (!dL_drgba || !g_rgba || (reinterpret_cast<uintptr_t>(dL_drgba) & 15))
-        return wrs::fail(WRS_ERR_ARG, "%s: dL_drgba / g_rgba NULL or misaligned", fn);
+    if (!dL_drgba || !g_rgba ||
+        ((reinterpret_cast<uintptr_t>(dL_drgba) | reinterpret_cast<uintptr_t>(g_rgba)) & 15))
+        return wrs::fail(WRS_ERR_ARG, "%s: dL_drgba / g_rgba NULL or not 16-byte aligned", fn);
     const size_t cap = sorted->capacity;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (!accumulate) {
