@@ -436,6 +436,11 @@ def main():
     profiled_launch = sched == 0 and width == 4 and kc == 1 and leaf == 1  # the captured launch
     fma = fma_rates(wrs, torch)
     line["roofline"]["fp32_peak_tflops_measured"] = fma["tflops"]
+    # the same counted bytes against the L2 copy rate: rays re-read the upper tree levels and
+    # neighbouring splats from L2/L1, so this is the cache-side bound (own streaming copy)
+    cr = copy_rates(wrs, torch)
+    line["roofline"]["own_copy_gbs"] = cr
+    line["roofline"]["l2_frac"] = achieved / cr["l2_gbs"]
     if winst is not None and profiled_launch and clk and clk.get("sm_mhz"):
         peak_gi = 148 * 4 * clk["sm_mhz"] * 1e6 / 1e9
         ach_gi = winst / (trace_ms * 1e-3) / 1e9
@@ -480,6 +485,31 @@ def fma_rates(wrs, torch, iters=2000, reps=5):
         ts.append(a.elapsed_time(b) * 1e-3)
     t = statistics.median(ts)
     return {"tflops": flops / t / 1e12, "ginst_s": flops / 2 / 32 / t / 1e9}
+
+
+def copy_rates(wrs, torch, reps=5):
+    """Own copy-rate measurements (GB/s, bytes read + written): wrs_stream_copy over 1 GiB
+    buffers (HBM) and, 20 copies in a row, over 16 MiB buffers that stay in L2."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    out = {}
+    for name, nbytes, inner in (("hbm_gbs", 1 << 30, 1), ("l2_gbs", 16 << 20, 20)):
+        a = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        b = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        a.fill_(1)
+        for _ in range(3):
+            wrs.stream_copy(b, a, sms * 8)
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(inner):
+                wrs.stream_copy(b, a, sms * 8)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        out[name] = 2 * nbytes * inner / statistics.median(ts) / 1e9
+        del a, b
+    return out
 
 
 def link_rates(torch, nbytes, reps=5):

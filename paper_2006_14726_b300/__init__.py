@@ -150,6 +150,7 @@ _sig("wrs_trace", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats), ctypes.POI
 _sig("wrs_trace_count", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats), ctypes.POINTER(Camera),
      ctypes.POINTER(_Params), _P, _P, _P)
 _sig("wrs_fma_peak", _I, _P, _I, _I, _P)
+_sig("wrs_stream_copy", _I, _P, _P, _Z, _I, _P)
 _sig("wrs_trace_views", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats), ctypes.POINTER(Camera),
      _I, ctypes.POINTER(_Params), _P, _P, _P)
 _sig("wrs_trace_backward_views", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats),
@@ -658,6 +659,16 @@ def fma_peak(blocks: int, iters: int, stream=None, out: Optional[torch.Tensor] =
         out = torch.empty(blocks, dtype=torch.float32, device="cuda")
     _check(_lib.wrs_fma_peak(_ptr(out), int(blocks), int(iters), _stream(stream)), "wrs_fma_peak")
     return 2.0 * blocks * 256 * iters * 128
+
+
+def stream_copy(dst: torch.Tensor, src: torch.Tensor, blocks: int, stream=None):
+    """Copy src into dst (same byte size, device) with the streaming copy kernel; the caller
+    times it."""
+    nb = src.numel() * src.element_size()
+    if dst.numel() * dst.element_size() != nb:
+        raise ValueError("stream_copy: buffers of different sizes")
+    _check(_lib.wrs_stream_copy(_ptr(dst), _ptr(src), nb, int(blocks), _stream(stream)),
+           "wrs_stream_copy")
 
 
 def check_status(status: torch.Tensor, stream=None):

@@ -1,6 +1,7 @@
-// peak.cu -- measurement kernel for the compute side of the roofline: binary32 FMA throughput,
-// which on this GPU is also the warp-instruction issue rate of ALU-bound code (one FFMA per lane
-// per cycle on every scheduler).  Not part of the method; bench.py times it with CUDA events.
+// peak.cu -- measurement kernels for the roofline's denominators: binary32 FMA throughput, which
+// on this GPU is also the warp-instruction issue rate of ALU-bound code (one FFMA per lane per
+// cycle on every scheduler), and a streaming copy (HBM or L2 copy rate, by buffer size).  Not
+// part of the method; bench.py times them with CUDA events.
 #include "common.cuh"
 
 namespace {
@@ -28,9 +29,29 @@ __global__ void __launch_bounds__(256) k_fma_peak(float* __restrict__ out, int i
     if (s < 0.0f) out[blockIdx.x] = s;
 }
 
+// Streaming copy, 16 bytes per thread and grid-stride: dst[i] = src[i] for n float4.  Over a
+// buffer far larger than L2 it measures the HBM copy rate; over one that fits in L2, the L2 rate.
+__global__ void __launch_bounds__(256) k_stream_copy(float4* __restrict__ dst,
+                                                     const float4* __restrict__ src, size_t n) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        dst[i] = src[i];
+}
+
 }  // namespace
 
 extern "C" {
+
+int wrs_stream_copy(void* dst, const void* src, size_t bytes, int32_t blocks, wrs_stream_t stream) {
+    if (!dst || !src || blocks < 1 || (bytes & 15) ||
+        ((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15))
+        return wrs::fail(WRS_ERR_ARG, "wrs_stream_copy: NULL or misaligned buffer, bytes not a "
+                                      "multiple of 16, or blocks < 1");
+    k_stream_copy<<<blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        static_cast<float4*>(dst), static_cast<const float4*>(src), bytes / 16);
+    WRS_LAUNCH_CHECK("wrs_stream_copy");
+    return WRS_OK;
+}
 
 int wrs_fma_peak(float* out, int32_t blocks, int32_t iters, wrs_stream_t stream) {
     if (!out || blocks < 1 || iters < 1)
