@@ -489,21 +489,20 @@ def fma_rates(wrs, torch, iters=2000, reps=5):
 
 def copy_rates(wrs, torch, reps=5):
     """Own copy-rate measurements (GB/s, bytes read + written): wrs_stream_copy over 1 GiB
-    buffers (HBM) and, 20 copies in a row, over 16 MiB buffers that stay in L2."""
+    buffers (HBM) and, 100 times over in one launch, over 16 MiB buffers that stay in L2."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     out = {}
-    for name, nbytes, inner in (("hbm_gbs", 1 << 30, 1), ("l2_gbs", 16 << 20, 20)):
+    for name, nbytes, inner in (("hbm_gbs", 1 << 30, 1), ("l2_gbs", 16 << 20, 100)):
         a = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
         b = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
         a.fill_(1)
         for _ in range(3):
-            wrs.stream_copy(b, a, sms * 8)
+            wrs.stream_copy(b, a, sms * 8, inner)
         ts = []
         for _ in range(reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            for _ in range(inner):
-                wrs.stream_copy(b, a, sms * 8)
+            wrs.stream_copy(b, a, sms * 8, inner)
             e1.record()
             e1.synchronize()
             ts.append(e0.elapsed_time(e1) * 1e-3)

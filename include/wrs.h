@@ -372,10 +372,11 @@ int wrs_point_splat(const wrs_splats* splats, const wrs_camera* cam, int32_t poi
 int wrs_fma_peak(float* out, int32_t blocks, int32_t iters, wrs_stream_t stream);
 
 /* Measurement helper, not part of the method: copy `bytes` (a multiple of 16; both buffers
- * 16-byte aligned device memory) from src to dst with `blocks` x 256 threads, 16 bytes per thread
- * per step.  Timed by the caller: over buffers far larger than L2 the HBM copy rate (2 x bytes
- * moved), over buffers that fit in L2 the L2 rate. */
-int wrs_stream_copy(void* dst, const void* src, size_t bytes, int32_t blocks, wrs_stream_t stream);
+ * 16-byte aligned device memory) from src to dst, `reps` times over, with `blocks` x 256 threads
+ * (four 16-byte loads in flight per thread).  Timed by the caller: over buffers far larger than
+ * L2 the HBM copy rate (2 x bytes x reps moved), over buffers that fit in L2 the L2 rate. */
+int wrs_stream_copy(void* dst, const void* src, size_t bytes, int32_t blocks, int32_t reps,
+                    wrs_stream_t stream);
 
 #ifdef __cplusplus
 }

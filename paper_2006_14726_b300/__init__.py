@@ -150,7 +150,7 @@ _sig("wrs_trace", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats), ctypes.POI
 _sig("wrs_trace_count", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats), ctypes.POINTER(Camera),
      ctypes.POINTER(_Params), _P, _P, _P)
 _sig("wrs_fma_peak", _I, _P, _I, _I, _P)
-_sig("wrs_stream_copy", _I, _P, _P, _Z, _I, _P)
+_sig("wrs_stream_copy", _I, _P, _P, _Z, _I, _I, _P)
 _sig("wrs_trace_views", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats), ctypes.POINTER(Camera),
      _I, ctypes.POINTER(_Params), _P, _P, _P)
 _sig("wrs_trace_backward_views", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats),
@@ -661,13 +661,13 @@ def fma_peak(blocks: int, iters: int, stream=None, out: Optional[torch.Tensor] =
     return 2.0 * blocks * 256 * iters * 128
 
 
-def stream_copy(dst: torch.Tensor, src: torch.Tensor, blocks: int, stream=None):
-    """Copy src into dst (same byte size, device) with the streaming copy kernel; the caller
-    times it."""
+def stream_copy(dst: torch.Tensor, src: torch.Tensor, blocks: int, reps: int = 1, stream=None):
+    """Copy src into dst (same byte size, device) ``reps`` times with the streaming copy kernel;
+    the caller times it."""
     nb = src.numel() * src.element_size()
     if dst.numel() * dst.element_size() != nb:
         raise ValueError("stream_copy: buffers of different sizes")
-    _check(_lib.wrs_stream_copy(_ptr(dst), _ptr(src), nb, int(blocks), _stream(stream)),
+    _check(_lib.wrs_stream_copy(_ptr(dst), _ptr(src), nb, int(blocks), int(reps), _stream(stream)),
            "wrs_stream_copy")
 
 

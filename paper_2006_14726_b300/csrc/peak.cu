@@ -29,26 +29,40 @@ __global__ void __launch_bounds__(256) k_fma_peak(float* __restrict__ out, int i
     if (s < 0.0f) out[blockIdx.x] = s;
 }
 
-// Streaming copy, 16 bytes per thread and grid-stride: dst[i] = src[i] for n float4.  Over a
-// buffer far larger than L2 it measures the HBM copy rate; over one that fits in L2, the L2 rate.
+// Streaming copy, grid-stride, four 16-byte loads in flight per thread before their stores:
+// dst[i] = src[i] for n float4, `reps` times over the buffer.  Over a buffer far larger than L2 it
+// measures the HBM copy rate; over one that fits in L2 (with reps > 1), the L2 rate.
 __global__ void __launch_bounds__(256) k_stream_copy(float4* __restrict__ dst,
-                                                     const float4* __restrict__ src, size_t n) {
+                                                     const float4* __restrict__ src, size_t n,
+                                                     int reps) {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        dst[i] = src[i];
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int r = 0; r < reps; r++) {
+        size_t i = t;
+        for (; i + 3 * stride < n; i += 4 * stride) {
+            const float4 a = __ldcg(src + i), b = __ldcg(src + i + stride);
+            const float4 c = __ldcg(src + i + 2 * stride), d = __ldcg(src + i + 3 * stride);
+            __stcg(dst + i, a);
+            __stcg(dst + i + stride, b);
+            __stcg(dst + i + 2 * stride, c);
+            __stcg(dst + i + 3 * stride, d);
+        }
+        for (; i < n; i += stride) __stcg(dst + i, __ldcg(src + i));
+    }
 }
 
 }  // namespace
 
 extern "C" {
 
-int wrs_stream_copy(void* dst, const void* src, size_t bytes, int32_t blocks, wrs_stream_t stream) {
-    if (!dst || !src || blocks < 1 || (bytes & 15) ||
+int wrs_stream_copy(void* dst, const void* src, size_t bytes, int32_t blocks, int32_t reps,
+                    wrs_stream_t stream) {
+    if (!dst || !src || blocks < 1 || reps < 1 || (bytes & 15) ||
         ((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15))
         return wrs::fail(WRS_ERR_ARG, "wrs_stream_copy: NULL or misaligned buffer, bytes not a "
-                                      "multiple of 16, or blocks < 1");
+                                      "multiple of 16, blocks < 1 or reps < 1");
     k_stream_copy<<<blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-        static_cast<float4*>(dst), static_cast<const float4*>(src), bytes / 16);
+        static_cast<float4*>(dst), static_cast<const float4*>(src), bytes / 16, reps);
     WRS_LAUNCH_CHECK("wrs_stream_copy");
     return WRS_OK;
 }
