@@ -573,7 +573,7 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
             client.result(tk)
     e2e_run(5)
     torch.cuda.synchronize()
-    steps = 60
+    steps = 200
     barrier()
     t0 = time.perf_counter()
     e2e_run(steps)
