@@ -303,6 +303,22 @@ def test_trace_large_sampled(wrs):
         _assert_close(got, ref["rgba"], f"large H={H} k={k} schedule={sched} width={width}")
 
 
+def test_trace_large_full_image(wrs):
+    """Every pixel of a full-size frame in the launch the tuner picks on B300 (one thread per
+    pixel, 4-wide nodes, K 1, leaf 1): 1920x1080 server image (about 2 M splats) warped to a
+    1920x1080 client 10 degrees away, against the oracle's full image, with the composited-hit
+    count equal to the oracle's."""
+    rgba, depth = synth.synthetic_server_image(1920, 1080, 52)
+    srv = synth.LARGE.server_cam()
+    cli = synth.orbit(srv, (0.0, 1.0, 0.3), 10.0)
+    got, ref, (bvh, srt, params) = _trace_pair(wrs, rgba, depth, srv, cli, k=1, schedule=0,
+                                               width=4)
+    m = _assert_close(got, ref["rgba"], "large full image")
+    assert m < 1e-5  # hard edges: identical hit lists, only compositing rounding remains
+    cnt = wrs.trace_count(bvh, srt, cli, params)
+    assert cnt["composited"] == int(ref["nused"].sum())
+
+
 def test_trace_empty_and_single(wrs):
     cam = synth.server_camera(1.4, 30.0, 9, 9)
     sp = _gpu_splats(wrs, np.zeros((9, 9, 4), np.float32), np.full((9, 9), np.inf, np.float32), cam)
