@@ -51,6 +51,11 @@ def parse():
     ap.add_argument("--impl", default="wrs", choices=["wrs", "reference"])
     ap.add_argument("--no-extras", action="store_true",
                     help="skip batched / fwd+bwd / e2e / cpu baseline (main line only)")
+    ap.add_argument("--sizes", action="store_true",
+                    help="instead of the benchmark line, print one JSON line with the size "
+                         "scaling of unproject + LBVH (server 512^2 .. 4096^2) and of the trace "
+                         "(client 256^2 .. 4096^2 on the 1080p server frame), large workload "
+                         "volume, warm L2, 10 repetitions each")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the launch the tuner picks on B300 (leaf 1, K 1, 128 threads per "
                          "pixel, 4-wide nodes) instead of tuning; for profiler runs, where tuning "
@@ -287,6 +292,10 @@ def main():
         raise SystemExit("bench.py needs a CUDA device (there is no CPU path)")
     torch.cuda.set_device(local)
     import paper_2006_14726_b300 as wrs
+    if args.sizes:
+        if rank == 0:
+            print(json.dumps(size_scaling(wrs, torch)), flush=True)
+        return
     from paper_2006_14726_b300 import autotune
     from paper_2006_14726_b300.replicas import Replicas
     import synth
@@ -464,6 +473,63 @@ def main():
     if rank == 0:
         print(json.dumps(line), flush=True)
     reps.close()
+
+
+def size_scaling(wrs, torch):
+    """Unproject and LBVH (leaf 1) over server frames of 512^2 .. 4096^2 pixels of the large
+    workload's volume, and the trace (one thread per pixel and persistent, K 1 and 2, 4-wide
+    nodes) of the 1080p frame's splats into clients of 256^2 .. 4096^2 at one pose.  CUDA events,
+    warm L2, mean of 10 launches after 3."""
+    import synth
+
+    def tms(fn, reps=10, warm=3):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    dev = torch.device("cuda")
+    W = synth.LARGE
+    vol = torch.from_numpy(W.volume()).to(dev)
+    tf = torch.from_numpy(synth.tf_ramp()).to(dev)
+    base, pose = W.server_cam(), W.client_poses(2)[1]
+    builds, traces = [], []
+    for (w, h) in ((512, 512), (1024, 1024), (1920, 1080), (2048, 2048), (3840, 2160),
+                   (4096, 4096)):
+        srv = base.with_size(w, h)
+        r, d = wrs.raycast_volume(vol, tf, srv)
+        sp = wrs.unproject(r, d, srv)
+        scr = torch.empty(max(wrs.unproject_scratch_bytes(w, h), 256), dtype=torch.uint8,
+                          device=dev)
+        up = tms(lambda: wrs.unproject(r, d, srv, out=sp, scratch=scr))
+        bvh, srt = wrs.LBVH(w * h, 1), wrs.SplatBuffers(w * h, sorted=True)
+        bs = torch.empty(wrs.lbvh_scratch_bytes(w * h, 1), dtype=torch.uint8, device=dev)
+        lb = tms(lambda: wrs.build_lbvh(sp, 1, bvh=bvh, sorted=srt, scratch=bs))
+        n = sp.count()
+        builds.append({"server": [w, h], "splats": n, "unproject_ms": up, "lbvh_ms": lb,
+                       "lbvh_gsplat_s": n / lb / 1e6})
+        if (w, h) == (1920, 1080):
+            for (cw, ch) in ((256, 256), (512, 512), (1024, 1024), (1920, 1080), (2048, 2048),
+                             (3840, 2160), (4096, 4096)):
+                cli = wrs.make_camera(pose.with_size(cw, ch))
+                out = torch.empty(ch, cw, 4, device=dev)
+                row = {"client": [cw, ch]}
+                for sched in (0, 1):
+                    for k in (1, 2):
+                        p = wrs.TraceParams(0, 1e-5, 0.0, k, 128, sched, 4)
+                        t = tms(lambda: wrs.trace(bvh, srt, cli, p, out=out))
+                        row[f"{SCHEDULE_NAMES[sched]}, K {k}: Mrays/s"] = cw * ch / t / 1e3
+                traces.append(row)
+        del sp, bvh, srt, bs, scr, r, d
+        torch.cuda.empty_cache()
+    return {"size_scaling": {"build": builds, "trace_on_1080p_frame": traces,
+                             "workload": W.name, "leaf_size": 1, "l2": "warm"}}
 
 
 def fma_rates(wrs, torch, iters=2000, reps=5):
