@@ -140,6 +140,12 @@ def test_host_validation_without_device(wrs):
     assert lib.wrs_trace_backward_views(ctypes.byref(bv1), ctypes.byref(srt), cams, 2, ctypes.byref(p), None, 1.0, ctypes.c_void_p(0x1004), fake, None, None, 0, None, None) == wrs.WRS_ERR_ARG
     # batched: no sessions
     assert lib.wrs_trace_batched(fake, 0, 0, ctypes.byref(p), fake, None, None) == wrs.WRS_ERR_ARG
+    # measurement helpers: no output, no blocks or repetitions, misaligned or odd-sized copies
+    assert lib.wrs_fma_peak(None, 4, 10, None) == wrs.WRS_ERR_ARG
+    assert lib.wrs_fma_peak(fake, 0, 10, None) == wrs.WRS_ERR_ARG
+    assert lib.wrs_stream_copy(fake, fake, 24, 4, 1, None) == wrs.WRS_ERR_ARG
+    assert lib.wrs_stream_copy(fake, ctypes.c_void_p(0x1008), 32, 4, 1, None) == wrs.WRS_ERR_ARG
+    assert lib.wrs_stream_copy(fake, fake, 32, 4, 0, None) == wrs.WRS_ERR_ARG
     # ray caster: bad dtype, bad size
     assert lib.wrs_raycast_volume(fake, 5, 4, 4, 4, fake, ctypes.byref(_cam(wrs)), 0.5, 0.1, fake, fake, None) == wrs.WRS_ERR_ARG
     assert lib.wrs_raycast_volume(fake, 0, 0, 4, 4, fake, ctypes.byref(_cam(wrs)), 0.5, 0.1, fake, fake, None) == wrs.WRS_ERR_ARG
