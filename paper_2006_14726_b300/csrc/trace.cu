@@ -48,6 +48,45 @@ struct Counts {
 
 constexpr float kInf = __builtin_huge_valf();
 
+// A traversal stack entry: the node reference in the low word and the entry distance of its box
+// (>= 0, so its bits order like the value) in the high word.  A popped node whose box starts
+// beyond the current K-th nearest hit is dropped without a visit: its children would all fail
+// the same cut-off, so the result is unchanged.
+using StackEntry = unsigned long long;
+__device__ __forceinline__ StackEntry stack_entry(uint32_t ref, float tn) {
+    return ((StackEntry)__float_as_uint(tn) << 32) | ref;
+}
+__device__ __forceinline__ float entry_tn(StackEntry e) { return __uint_as_float((uint32_t)(e >> 32)); }
+
+// Pop the nearest pending node that still starts within the cut-off; false when none is left.
+__device__ __forceinline__ bool pop_within(const StackEntry* stack, int& sp, float cutoff,
+                                           uint32_t& ref) {
+    while (sp > 0) {
+        const StackEntry e = stack[--sp];
+        if (entry_tn(e) <= cutoff) {
+            ref = (uint32_t)e;
+            return true;
+        }
+    }
+    return false;
+}
+// Plain entries (the reference only; the lane-refill state machines keep these: they hold more
+// state, and the wider entries cost them registers).
+__device__ __forceinline__ int stack_entry_plain(uint32_t ref, float) { return (int)ref; }
+__device__ __forceinline__ bool pop_within(const int* stack, int& sp, float, uint32_t& ref) {
+    if (sp == 0) return false;
+    ref = (uint32_t)stack[--sp];
+    return true;
+}
+template <typename E>
+__device__ __forceinline__ E make_entry(uint32_t ref, float tn) {
+    return stack_entry(ref, tn);
+}
+template <>
+__device__ __forceinline__ int make_entry<int>(uint32_t ref, float tn) {
+    return stack_entry_plain(ref, tn);
+}
+
 // Test the splats of leaf `leafref` and insert qualifying hits into the sorted K-buffer: hits
 // strictly after (last_key, last_id) when has_last, keeping the K smallest (key, id).  The final
 // buffer does not depend on the order in which leaves are visited.
@@ -91,13 +130,13 @@ __device__ __forceinline__ void leaf_hits(const Scene& sc, const Ray& ray, uint3
 // node and leaf code); hit internal children are descended into, nearer first, the other pushed.
 // Returns the next internal node, or kLeafBit when the pass must pop; -1 stack overflow,
 // -2 malformed reference.
-template <int K, bool COUNT>
+template <int K, bool COUNT, typename E>
 __device__ __forceinline__ int64_t visit_node(const Scene& sc, const Ray& ray,
                                               const wrs::BoxRay& br, uint32_t ref, uint32_t n,
                                               uint32_t leaf, uint32_t m, bool has_last,
                                               float last_key, uint32_t last_id, float (&kk)[K],
                                               uint32_t (&ki)[K], uint32_t (&kid)[K], int& count,
-                                              int* stack, int& sp, Counts& cnt) {
+                                              E* stack, int& sp, Counts& cnt) {
     if (ref + 1 >= m) return -2;  // not an internal node of this tree
     const float lower = has_last ? last_key : -kInf;
     const float4* nd = sc.nodes + 4 * (size_t)ref;
@@ -120,7 +159,7 @@ __device__ __forceinline__ int64_t visit_node(const Scene& sc, const Ray& ray,
     if (h0 && h1) {
         const bool first0 = tn0 <= tn1;
         if (sp >= wrs::kStack) return -1;
-        stack[sp++] = (int)(first0 ? c1 : c0);
+        stack[sp++] = first0 ? make_entry<E>(c1, tn1) : make_entry<E>(c0, tn0);
         return first0 ? c0 : c1;
     }
     if (h0) return c0;
@@ -142,13 +181,13 @@ __device__ __forceinline__ void cswap(float& ka, uint32_t& ra, float& kb, uint32
 // structure-of-arrays loads; hit leaf entries are tested right away; hit internal entries are
 // sorted by entry distance (5-comparator network), the nearest is returned and the others pushed
 // far to near.  Same return convention as visit_node.
-template <int K, bool COUNT>
+template <int K, bool COUNT, typename E>
 __device__ __forceinline__ int64_t visit_node4(const Scene& sc, const Ray& ray,
                                                const wrs::BoxRay& br, uint32_t ref, uint32_t n,
                                                uint32_t leaf, uint32_t m, bool has_last,
                                                float last_key, uint32_t last_id, float (&kk)[K],
                                                uint32_t (&ki)[K], uint32_t (&kid)[K], int& count,
-                                               int* stack, int& sp, Counts& cnt) {
+                                               E* stack, int& sp, Counts& cnt) {
     if (ref + 1 >= m) return -2;  // not an internal node of this tree
     // hits of this pass lie at or beyond max(last key, 0): boxes ending before it are skipped
     const float low = has_last ? fmaxf(last_key, 0.0f) : 0.0f;
@@ -187,9 +226,9 @@ __device__ __forceinline__ int64_t visit_node4(const Scene& sc, const Ray& ray,
     if (!(key[0] < kInf)) return kLeafBit;
     const int extra = (key[1] < kInf) + (key[2] < kInf) + (key[3] < kInf);
     if (sp + extra > wrs::kStack) return -1;
-    if (key[3] < kInf) stack[sp++] = (int)r[3];
-    if (key[2] < kInf) stack[sp++] = (int)r[2];
-    if (key[1] < kInf) stack[sp++] = (int)r[1];
+    if (key[3] < kInf) stack[sp++] = make_entry<E>(r[3], key[3]);
+    if (key[2] < kInf) stack[sp++] = make_entry<E>(r[2], key[2]);
+    if (key[1] < kInf) stack[sp++] = make_entry<E>(r[1], key[1]);
     return r[0];
 }
 
@@ -211,21 +250,22 @@ __device__ __forceinline__ int gather(const Scene& sc, const Ray& ray, const wrs
                             kid, count, cnt);
         return count;
     }
-    int stack[wrs::kStack];
+    StackEntry stack[wrs::kStack];
     int sp = 0;
     uint32_t ref = (uint32_t)root;
     uint32_t budget = m + 1;  // internal node visits allowed in one pass
     while (true) {
         if (budget-- == 0) return -2;
         const int64_t next =
-            W4 ? visit_node4<K, COUNT>(sc, ray, br, ref, n, leaf, m, has_last, last_key, last_id,
-                                       kk, ki, kid, count, stack, sp, cnt)
-               : visit_node<K, COUNT>(sc, ray, br, ref, n, leaf, m, has_last, last_key, last_id,
-                                      kk, ki, kid, count, stack, sp, cnt);
+            W4 ? visit_node4<K, COUNT, StackEntry>(sc, ray, br, ref, n, leaf, m, has_last,
+                                                   last_key, last_id, kk, ki, kid, count, stack,
+                                                   sp, cnt)
+               : visit_node<K, COUNT, StackEntry>(sc, ray, br, ref, n, leaf, m, has_last,
+                                                  last_key, last_id, kk, ki, kid, count, stack, sp,
+                                                  cnt);
         if (next < 0) return (int)next;
         if (next != kLeafBit) { ref = (uint32_t)next; continue; }
-        if (sp == 0) break;
-        ref = (uint32_t)stack[--sp];
+        if (!pop_within(stack, sp, kk[K - 1], ref)) break;
     }
     return count;
 }
@@ -534,15 +574,14 @@ __device__ __forceinline__ int lane_step(const Scene& sc, Lane<K>& L, int* stack
     }
     if (L.budget-- == 0) return -2;
     const int64_t next =
-        W4 ? visit_node4<K, false>(sc, L.ray, L.br, L.ref, n, leaf, m, L.has_last, L.last_key,
-                                   L.last_id, L.kk, L.ki, L.kid, L.count, stack, L.sp, cnt)
-           : visit_node<K, false>(sc, L.ray, L.br, L.ref, n, leaf, m, L.has_last, L.last_key,
-                                  L.last_id, L.kk, L.ki, L.kid, L.count, stack, L.sp, cnt);
+        W4 ? visit_node4<K, false, int>(sc, L.ray, L.br, L.ref, n, leaf, m, L.has_last,
+                                        L.last_key, L.last_id, L.kk, L.ki, L.kid, L.count, stack,
+                                        L.sp, cnt)
+           : visit_node<K, false, int>(sc, L.ray, L.br, L.ref, n, leaf, m, L.has_last, L.last_key,
+                                       L.last_id, L.kk, L.ki, L.kid, L.count, stack, L.sp, cnt);
     if (next < 0) return (int)next;
     if (next != kLeafBit) { L.ref = (uint32_t)next; return 0; }
-    if (L.sp == 0) return 1;
-    L.ref = (uint32_t)stack[--L.sp];
-    return 0;
+    return pop_within(stack, L.sp, L.kk[K - 1], L.ref) ? 0 : 1;
 }
 
 template <int K, bool W4>
