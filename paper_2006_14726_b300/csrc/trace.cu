@@ -384,7 +384,7 @@ __device__ __forceinline__ int64_t visit_node4_packet(const Scene& sc, const Ray
                                                       bool part, bool has_last, float last_key,
                                                       uint32_t last_id, float (&kk)[K],
                                                       uint32_t (&ki)[K], uint32_t (&kid)[K],
-                                                      int& count, int* stack, int& sp) {
+                                                      int& count, StackEntry* stack, int& sp) {
     if (ref + 1 >= m) return -2;  // not an internal node of this tree (ref is warp-uniform)
     const float low = has_last ? fmaxf(last_key, 0.0f) : 0.0f;
     const float4* w = sc.wide + 8 * (size_t)ref;
@@ -420,9 +420,9 @@ __device__ __forceinline__ int64_t visit_node4_packet(const Scene& sc, const Ray
     if (!(key[0] < kInf)) return kLeafBit;
     const int extra = (key[1] < kInf) + (key[2] < kInf) + (key[3] < kInf);
     if (sp + extra > wrs::kStack) return -1;
-    if (key[3] < kInf) stack[sp++] = (int)r[3];
-    if (key[2] < kInf) stack[sp++] = (int)r[2];
-    if (key[1] < kInf) stack[sp++] = (int)r[1];
+    if (key[3] < kInf) stack[sp++] = stack_entry(r[3], key[3]);
+    if (key[2] < kInf) stack[sp++] = stack_entry(r[2], key[2]);
+    if (key[1] < kInf) stack[sp++] = stack_entry(r[1], key[1]);
     return r[0];
 }
 
@@ -443,7 +443,7 @@ __device__ __forceinline__ int gather_packet(const Scene& sc, const Ray& ray,
                                 ki, kid, count, none);
         return count;
     }
-    int stack[wrs::kStack];
+    StackEntry stack[wrs::kStack];
     int sp = 0;
     uint32_t ref = (uint32_t)root;
     uint32_t budget = m + 1;
@@ -453,8 +453,12 @@ __device__ __forceinline__ int gather_packet(const Scene& sc, const Ray& ray,
                                                    last_key, last_id, kk, ki, kid, count, stack, sp);
         if (next < 0) return (int)next;
         if (next != kLeafBit) { ref = (uint32_t)next; continue; }
-        if (sp == 0) break;
-        ref = (uint32_t)stack[--sp];
+        // the warp's cut-off: the largest K-th key over its rays (a stacked entry's key is the
+        // smallest entry distance over the lanes that enter it, so an entry beyond every lane's
+        // cut-off holds nothing any lane still needs); warp-uniform like the stack
+        const float cut = __uint_as_float(
+            __reduce_max_sync(0xffffffffu, __float_as_uint(part ? kk[K - 1] : 0.0f)));
+        if (!pop_within(stack, sp, cut, ref)) break;
     }
     return count;
 }
