@@ -522,12 +522,13 @@ struct PersistentMinBlocks {
 };
 
 // Launch bounds of the per-pixel kernel.  With the 4-wide traversal and K <= 2 it runs in blocks
-// of at most 128 threads with 9 resident blocks per SM (56 registers): measured 1 % faster than
-// no cap on the 1080p, 2 M splat workload, while caps of 40 and 48 registers spill and are 3-14 %
-// slower.  Other instances keep blocks of up to 256 threads and no register cap.  A build-time
-// knob: WRS_PIXEL_W4_MIN_BLOCKS (resident 128-thread blocks, 0 = no cap).
+// of at most 128 threads with 10 resident blocks per SM (48 registers, a few spilled): on the
+// 1080p, 2 M splat workload 2 % faster than 9 blocks (56 registers) and 4 % faster than 8 (64, no
+// spills), while 11 or 12 blocks (40 registers) are 7 % slower.  Other instances keep blocks of up
+// to 256 threads and no register cap.  A build-time knob: WRS_PIXEL_W4_MIN_BLOCKS (resident
+// 128-thread blocks, 0 = no cap).
 #ifndef WRS_PIXEL_W4_MIN_BLOCKS
-#define WRS_PIXEL_W4_MIN_BLOCKS 9
+#define WRS_PIXEL_W4_MIN_BLOCKS 10
 #endif
 template <int K, bool W4>
 struct PixelBounds {
