@@ -537,6 +537,26 @@ struct PixelBounds {
     static constexpr int min_blocks = capped ? WRS_PIXEL_W4_MIN_BLOCKS : 0;
 };
 
+// Resident 128-thread blocks per SM of the multi-session per-tile kernel and of the per-pixel
+// backward kernels.  The multi-session kernel with K <= 2 runs 8 (64 registers): on the 64
+// sessions 21 % faster than no cap (94 registers) and 10 % faster than 10 blocks.  The backward
+// with K = 4 runs 8 (64 registers, 7 % faster than 79); with K = 2 the same cap spills and is
+// slower, so the other instances keep no cap.  Build-time knobs (0 = no cap).
+#ifndef WRS_BATCHED_MIN_BLOCKS
+#define WRS_BATCHED_MIN_BLOCKS 8
+#endif
+#ifndef WRS_BWD_K4_MIN_BLOCKS
+#define WRS_BWD_K4_MIN_BLOCKS 8
+#endif
+template <int K, bool W4>
+struct BatchedBounds {
+    static constexpr int min_blocks = K <= 2 ? WRS_BATCHED_MIN_BLOCKS : 0;
+};
+template <int K, bool W4>
+struct BwdBounds {
+    static constexpr int min_blocks = K == 4 ? WRS_BWD_K4_MIN_BLOCKS : 0;
+};
+
 template <int K>
 struct Lane {
     Ray ray;
@@ -772,7 +792,7 @@ __global__ void __launch_bounds__(256) k_trace_count(Scene sc, Comp cp, wrs_came
 // concatenated tile space (session s owns tiles [tile_begin_s, tile_begin_s + tiles_s)); the
 // warp finds its session by binary search over the sessions' first tiles.
 template <int K, bool W4>
-__global__ void __launch_bounds__(128) k_trace_batched_pp(const wrs_session* __restrict__ sess,
+__global__ void __launch_bounds__(128, BatchedBounds<K, W4>::min_blocks) k_trace_batched_pp(const wrs_session* __restrict__ sess,
                                                           int n_sessions, uint32_t total_tiles,
                                                           Comp cp, int32_t* status) {
     const uint32_t tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -1061,7 +1081,7 @@ __device__ __forceinline__ void backward_pixel(const Scene& sc, const Comp& cp,
 }
 
 template <int K, bool W4>
-__global__ void __launch_bounds__(128) k_trace_bwd(Scene sc, Comp cp, wrs_camera cam,
+__global__ void __launch_bounds__(128, BwdBounds<K, W4>::min_blocks) k_trace_bwd(Scene sc, Comp cp, wrs_camera cam,
                                                    const float4* __restrict__ dimg, GradOut go,
                                                    int32_t* status) {
     backward_pixel<K, W4>(sc, cp, cam, dimg, go, status);
@@ -1070,7 +1090,7 @@ __global__ void __launch_bounds__(128) k_trace_bwd(Scene sc, Comp cp, wrs_camera
 // Several views in one launch (blockIdx.z = view, as k_trace_views); every view's gradients
 // accumulate into the same per-splat buffers.
 template <int K, bool W4>
-__global__ void __launch_bounds__(128) k_trace_bwd_views(Scene sc, Comp cp,
+__global__ void __launch_bounds__(128, BwdBounds<K, W4>::min_blocks) k_trace_bwd_views(Scene sc, Comp cp,
                                                          const __grid_constant__ ViewCams vc,
                                                          const float4* __restrict__ dimg,
                                                          size_t pixels, GradOut go,
