@@ -548,6 +548,11 @@ struct PixelBounds {
 #ifndef WRS_BWD_K4_MIN_BLOCKS
 #define WRS_BWD_K4_MIN_BLOCKS 8
 #endif
+// The packet kernels keep no cap: 5 or 6 resident 256-thread blocks (48 or 40 registers) spill
+// 180-230 bytes at K 4 and run 4-29 % slower.
+#ifndef WRS_PACKET_MIN_BLOCKS
+#define WRS_PACKET_MIN_BLOCKS 0
+#endif
 template <int K, bool W4>
 struct BatchedBounds {
     static constexpr int min_blocks = K <= 2 ? WRS_BATCHED_MIN_BLOCKS : 0;
@@ -751,13 +756,13 @@ __device__ __forceinline__ void trace_pixel_packet(const Scene& sc, const Comp& 
 }
 
 template <int K>
-__global__ void __launch_bounds__(256) k_trace_packet(Scene sc, Comp cp, wrs_camera cam,
+__global__ void __launch_bounds__(256, WRS_PACKET_MIN_BLOCKS) k_trace_packet(Scene sc, Comp cp, wrs_camera cam,
                                                       float4* __restrict__ out, int32_t* status) {
     trace_pixel_packet<K>(sc, cp, cam, out, status);
 }
 
 template <int K>
-__global__ void __launch_bounds__(256) k_trace_packet_views(Scene sc, Comp cp,
+__global__ void __launch_bounds__(256, WRS_PACKET_MIN_BLOCKS) k_trace_packet_views(Scene sc, Comp cp,
                                                             const __grid_constant__ ViewCams vc,
                                                             float4* __restrict__ out,
                                                             size_t pixels, int32_t* status) {
