@@ -522,19 +522,22 @@ struct PersistentMinBlocks {
 };
 
 // Launch bounds of the per-pixel kernel.  With the 4-wide traversal and K <= 2 it runs in blocks
-// of at most 128 threads with 10 resident blocks per SM (48 registers, a few spilled): on the
-// 1080p, 2 M splat workload 2 % faster than 9 blocks (56 registers) and 4 % faster than 8 (64, no
-// spills), while 11 or 12 blocks (40 registers) are 7 % slower.  Other instances keep blocks of up
+// of at most 128 threads; with K = 1, 10 resident blocks per SM (48 registers, a few spilled): on
+// the 1080p, 2 M splat workload 2 % faster than 9 blocks (56 registers) and 4 % faster than 8 (64,
+// no spills), while 11 or 12 blocks (40 registers) are 7 % slower.  Other instances keep blocks of up
 // to 256 threads and no register cap.  A build-time knob: WRS_PIXEL_W4_MIN_BLOCKS (resident
 // 128-thread blocks, 0 = no cap).
 #ifndef WRS_PIXEL_W4_MIN_BLOCKS
 #define WRS_PIXEL_W4_MIN_BLOCKS 10
 #endif
+#ifndef WRS_PIXEL_W4_K2_MIN_BLOCKS
+#define WRS_PIXEL_W4_K2_MIN_BLOCKS 9  // K = 2: 9 blocks (56 registers), 4 % faster than 10
+#endif
 template <int K, bool W4>
 struct PixelBounds {
     static constexpr bool capped = K <= 2 && W4;
     static constexpr int max_threads = capped ? 128 : 256;
-    static constexpr int min_blocks = capped ? WRS_PIXEL_W4_MIN_BLOCKS : 0;
+    static constexpr int min_blocks = !capped ? 0 : K == 1 ? WRS_PIXEL_W4_MIN_BLOCKS : WRS_PIXEL_W4_K2_MIN_BLOCKS;
 };
 
 // Resident 128-thread blocks per SM of the multi-session per-tile kernel and of the per-pixel
