@@ -508,13 +508,14 @@ constexpr int kRefill = 8;
 
 // Minimum resident 128-thread blocks per SM asked of the compiler for the single-view persistent
 // kernel with K <= 2 (it caps registers at 65536 / (128 * this)): 10 (48 registers) for the binary
-// traversal, 9 (56 registers) for the 4-wide one, both measured faster than no cap on the 1080p,
-// 2 M splat workload; larger K keep more state and get no cap.  Build-time tuning knobs (0 = no cap).
+// traversal, 8 (64 registers) for the 4-wide one (1 % faster than 9, 7 % faster than 10), both
+// measured on the 1080p, 2 M splat workload; larger K keep more state and get no cap.  Build-time
+// tuning knobs (0 = no cap).
 #ifndef WRS_PERSISTENT_MIN_BLOCKS
 #define WRS_PERSISTENT_MIN_BLOCKS 10
 #endif
 #ifndef WRS_PERSISTENT_W4_MIN_BLOCKS
-#define WRS_PERSISTENT_W4_MIN_BLOCKS 9
+#define WRS_PERSISTENT_W4_MIN_BLOCKS 8
 #endif
 template <int K, bool W4>
 struct PersistentMinBlocks {
