@@ -7,7 +7,8 @@ one arrives (§4, §4.2).  Here the network is replaced by pinned host buffers; 
 three CUDA streams:
 
 * ``h2d``: copies of incoming server frames into one of two device scene slots;
-* ``compute``: unprojection + LBVH build of a slot, then the traces of client views;
+* ``compute``: unprojection + LBVH build of a slot (the build replayed from a CUDA graph captured
+  per slot), then the traces of client views;
 * ``d2h``: copies of finished views into a ring of pinned host images.
 
 A scene slot is rebuilt only after the traces that read it have finished, and an image slot of the
@@ -40,6 +41,16 @@ class _Scene:
         self.copied = torch.cuda.Event()
         self.released = torch.cuda.Event()  # the last trace that read this slot has finished
         self.released.record()              # (nothing reads a fresh slot)
+        # the slot's LBVH build reads and writes only the slot's own buffers (the splat count
+        # stays on the device), so one CUDA graph of its launches serves every frame
+        self.build = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(device=device)
+        side.wait_stream(torch.cuda.current_stream(device))
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(self.build, stream=side):
+                build_lbvh(self.splats, leaf, bvh=self.bvh, sorted=self.sorted,
+                           scratch=self.bscratch, stream=side)
+        torch.cuda.current_stream(device).wait_stream(side)
 
 
 class WarpingClient:
@@ -88,8 +99,8 @@ class WarpingClient:
         self.compute.wait_event(sc.copied)
         unproject(sc.rgba, sc.depth, cam, self.radius_mode, self.voxel_diag, out=sc.splats,
                   scratch=sc.uscratch, stream=self.compute)
-        build_lbvh(sc.splats, self.leaf, bvh=sc.bvh, sorted=sc.sorted, scratch=sc.bscratch,
-                   stream=self.compute)
+        with torch.cuda.stream(self.compute):
+            sc.build.replay()
         self.current = slot
 
     # ---- client views -------------------------------------------------------------------------
