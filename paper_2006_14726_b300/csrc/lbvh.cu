@@ -342,10 +342,12 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(
 }
 
 // ---- Karras 2012 binary radix tree over the leaf keys --------------------------------------
+// Common prefix length of leaf keys i and j (a = key i, read once by the caller), index
+// tie-break for equal keys; -1 outside the leaves.
 __device__ __forceinline__ int delta(const uint32_t* __restrict__ codes, uint32_t leaf, int m,
-                                     int i, int j) {
+                                     int i, uint32_t a, int j) {
     if (j < 0 || j >= m) return -1;
-    const uint32_t a = __ldg(codes + (size_t)i * leaf), b = __ldg(codes + (size_t)j * leaf);
+    const uint32_t b = __ldg(codes + (size_t)j * leaf);
     if (a != b) return __clz(a ^ b);
     return 32 + __clz((uint32_t)i ^ (uint32_t)j);
 }
@@ -360,19 +362,20 @@ __global__ void __launch_bounds__(256) k_karras(const uint32_t* __restrict__ cod
     const uint32_t leaf = hdr->leaf;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m - 1) return;
-    const int d = (delta(codes, leaf, m, i, i + 1) - delta(codes, leaf, m, i, i - 1)) >= 0 ? 1 : -1;
-    const int dmin = delta(codes, leaf, m, i, i - d);
+    const uint32_t a = __ldg(codes + (size_t)i * leaf);
+    const int d = (delta(codes, leaf, m, i, a, i + 1) - delta(codes, leaf, m, i, a, i - 1)) >= 0 ? 1 : -1;
+    const int dmin = delta(codes, leaf, m, i, a, i - d);
     int lmax = 2;
-    while (delta(codes, leaf, m, i, i + lmax * d) > dmin) lmax <<= 1;
+    while (delta(codes, leaf, m, i, a, i + lmax * d) > dmin) lmax <<= 1;
     int l = 0;
     for (int t = lmax >> 1; t >= 1; t >>= 1)
-        if (delta(codes, leaf, m, i, i + (l + t) * d) > dmin) l += t;
+        if (delta(codes, leaf, m, i, a, i + (l + t) * d) > dmin) l += t;
     const int j = i + l * d;
-    const int dnode = delta(codes, leaf, m, i, j);
+    const int dnode = delta(codes, leaf, m, i, a, j);
     int s = 0, t = l;
     do {
         t = (t + 1) >> 1;
-        if (s + t < l && delta(codes, leaf, m, i, i + (s + t) * d) > dnode) s += t;
+        if (s + t < l && delta(codes, leaf, m, i, a, i + (s + t) * d) > dnode) s += t;
     } while (t > 1);
     const int g = i + s * d + min(d, 0);
     const int lo = min(i, j), hi = max(i, j);
