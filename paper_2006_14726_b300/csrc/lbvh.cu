@@ -189,21 +189,25 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t* __rest
                                                           const LbvhHeader* __restrict__ hdr,
                                                           int shift, uint32_t tiles,
                                                           uint32_t* __restrict__ hist) {
-    __shared__ uint32_t s_cnt[256];
-    s_cnt[threadIdx.x] = 0;
-    __syncthreads();
+    __shared__ uint32_t s_cnt[kSortWarps][256];  // one histogram per warp: fewer collisions
+    for (int w = 0; w < kSortWarps; w++) s_cnt[w][threadIdx.x] = 0;
     const uint32_t n = hdr->n;
     const uint32_t base = blockIdx.x * kSortTile;
-    const int lane = threadIdx.x & 31;
-    for (int k = 0; k < kSortItems; k++) {
+    const int warp = threadIdx.x >> 5;
+    uint32_t d[kSortItems];
+#pragma unroll
+    for (int k = 0; k < kSortItems; k++) {  // all loads in flight before the counting
         const uint32_t i = base + k * kSortThreads + threadIdx.x;
-        const bool valid = i < n;
-        const uint32_t d = valid ? (keys[i] >> shift) & 255u : 256u + lane;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);  // lanes with the same digit
-        if (valid && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&s_cnt[d], __popc(peers));
+        d[k] = i < n ? (keys[i] >> shift) & 255u : 256u;
     }
     __syncthreads();
-    hist[threadIdx.x * tiles + blockIdx.x] = s_cnt[threadIdx.x];
+#pragma unroll
+    for (int k = 0; k < kSortItems; k++)
+        if (d[k] < 256u) atomicAdd(&s_cnt[warp][d[k]], 1u);
+    __syncthreads();
+    uint32_t c = 0;
+    for (int w = 0; w < kSortWarps; w++) c += s_cnt[w][threadIdx.x];
+    hist[threadIdx.x * tiles + blockIdx.x] = c;
 }
 
 // One block per digit: exclusive scan of that digit's per-tile counts (contiguous in the
