@@ -345,7 +345,7 @@ def main():
     status = wrs.new_status()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-    launches_per_step = 3 + 17 + FRAMES_PER_IMAGE  # unproject 3, LBVH 17 kernels, traces
+    launches_per_step = 3 + 16 + FRAMES_PER_IMAGE  # unproject 3, LBVH 16 kernels, traces
 
     build_graph = []  # the LBVH build as a CUDA graph, once captured
 
@@ -382,7 +382,7 @@ def main():
     wrs.check_status(status)
 
     # The build reads and writes the same buffers every step (the splat count stays on the
-    # device), so one CUDA graph replays its 17 launches without launch gaps.
+    # device), so one CUDA graph replays its 16 launches without launch gaps.
     bg = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream()
     side.wait_stream(stream)
@@ -449,7 +449,7 @@ def main():
                 "schedule": SCHEDULE_NAMES[sched],
                 "bvh_width": width,
                 "l2": "flushed before every step (256 MiB write outside the timed events)",
-                "lbvh_launch": "one CUDA graph of its 17 kernels, replayed every step",
+                "lbvh_launch": "one CUDA graph of its 16 kernels, replayed every step",
                 "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
             "lbvh_ms": statistics.mean(bv_ms), "unproject_ms": statistics.mean(up_ms),
             "trace_ms": trace_ms, "trace_mrays_s": npix_c / (trace_ms * 1e-3) / 1e6,

@@ -3,6 +3,7 @@
 //
 //   k_bounds_partial / k_bounds_final : centre bounds and the largest radius (two-level reduction)
 //   k_morton                          : 30-bit Morton code of each centre (binary32 quantisation)
+//                                       and the per-tile counts of the first radix digit
 //   k_rs_hist / k_rs_scan / k_rs_scatter (x4) : stable LSD radix sort of (code, index), 8-bit digits
 //   k_karras                          : binary radix tree over leaf keys (Karras 2012)
 //   k_leaves_refit                    : gathers the splats into leaf order with their effective
@@ -161,14 +162,7 @@ __device__ __forceinline__ uint32_t spread10(uint32_t v) {
     return v;
 }
 
-__global__ void __launch_bounds__(256) k_morton(const float4* __restrict__ pos_r,
-                                                const LbvhHeader* __restrict__ hdr,
-                                                uint32_t* __restrict__ keys,
-                                                uint32_t* __restrict__ vals) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t n = hdr->n;
-    if (i >= n) return;
-    const float4 p = pos_r[i];
+__device__ __forceinline__ uint32_t morton_code(const float4 p, const LbvhHeader* __restrict__ hdr) {
     const float c[3] = {p.x, p.y, p.z};
     uint32_t q[3];
 #pragma unroll
@@ -178,8 +172,41 @@ __global__ void __launch_bounds__(256) k_morton(const float4* __restrict__ pos_r
         const float v = floorf(__fmul_rn(__fsub_rn(c[k], hdr->cmin[k]), sc));
         q[k] = v >= 1023.0f ? 1023u : (uint32_t)v;
     }
-    keys[i] = (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
-    vals[i] = i;
+    return (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+}
+
+// One sort tile per block (kSortTile splats, the sort's item layout): the codes and indices, and
+// the tile's counts of the first radix digit (bits 0..7), so the first sort pass needs no
+// histogram kernel.  hist is digit-major: hist[d * tiles + tile].
+__global__ void __launch_bounds__(kSortThreads) k_morton(const float4* __restrict__ pos_r,
+                                                         const LbvhHeader* __restrict__ hdr,
+                                                         uint32_t* __restrict__ keys,
+                                                         uint32_t* __restrict__ vals,
+                                                         uint32_t tiles, uint32_t* __restrict__ hist) {
+    __shared__ uint32_t s_cnt[kSortThreads / 32][256];  // one digit histogram per warp
+    for (int w = 0; w < kSortThreads / 32; w++) s_cnt[w][threadIdx.x] = 0;
+    const uint32_t n = hdr->n;
+    const uint32_t base = blockIdx.x * kSortTile;
+    const int warp = threadIdx.x >> 5;
+    uint32_t code[kSortItems];
+#pragma unroll
+    for (int k = 0; k < kSortItems; k++) {
+        const uint32_t i = base + k * kSortThreads + threadIdx.x;
+        code[k] = 0xFFFFFFFFu;
+        if (i < n) {
+            code[k] = morton_code(pos_r[i], hdr);
+            keys[i] = code[k];
+            vals[i] = i;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kSortItems; k++)
+        if (code[k] != 0xFFFFFFFFu) atomicAdd(&s_cnt[warp][code[k] & 255u], 1u);
+    __syncthreads();
+    uint32_t c = 0;
+    for (int w = 0; w < kSortThreads / 32; w++) c += s_cnt[w][threadIdx.x];
+    hist[threadIdx.x * tiles + blockIdx.x] = c;
 }
 
 // ---- stable LSD radix sort, 8-bit digits ---------------------------------------------------
@@ -620,7 +647,6 @@ int wrs_build_lbvh(const wrs_splats* in, const float* radius_scale, float global
     float4* nodes = wrs::lbvh_nodes(bvh->nodes);
     const float4* pos4 = reinterpret_cast<const float4*>(in->pos_r);
     const uint32_t m_cap = leaves_for(cap, leaf);
-    const uint32_t g256 = (cap + 255) / 256 ? (cap + 255) / 256 : 1;
     const uint32_t gm = (m_cap + 255) / 256;
 
     k_bounds_partial<<<kBoundsBlocks, 256, 0, s>>>(pos4, radius_scale, global_scale, in->n, cap,
@@ -629,11 +655,12 @@ int wrs_build_lbvh(const wrs_splats* in, const float* radius_scale, float global
     k_bounds_final<<<1, kBoundsBlocks, 0, s>>>(S.partials, in->n, cap, leaf, hdr, sorted->n);
     WRS_LAUNCH_CHECK("wrs_build_lbvh bounds final");
     if (cap == 0) return WRS_OK;
-    k_morton<<<g256, 256, 0, s>>>(pos4, hdr, S.keys0, S.vals0);
+    k_morton<<<S.tiles, kSortThreads, 0, s>>>(pos4, hdr, S.keys0, S.vals0, S.tiles, S.hist);
     WRS_LAUNCH_CHECK("wrs_build_lbvh morton");
     uint32_t *ki = S.keys0, *vi = S.vals0, *ko = S.keys1, *vo = S.vals1;
     for (int shift = 0; shift < 32; shift += 8) {
-        k_rs_hist<<<S.tiles, kSortThreads, 0, s>>>(ki, hdr, shift, S.tiles, S.hist);
+        if (shift > 0)  // the first digit was counted with the codes
+            k_rs_hist<<<S.tiles, kSortThreads, 0, s>>>(ki, hdr, shift, S.tiles, S.hist);
         k_rs_scan<<<256, 256, 0, s>>>(S.hist, S.tiles, S.totals);
         k_rs_scatter<<<S.tiles, kSortThreads, 0, s>>>(ki, vi, ko, vo, S.hist, S.totals, hdr, shift,
                                                       S.tiles);
