@@ -903,15 +903,17 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
             for d_sched in (0, 2):
                 cfg["p"] = wrs.TraceParams(0, 1e-5, 0.25, d_k, 128, d_sched, 4)
                 cfg["leaf"] = d_leaf
-                d_table.append((_time_ms(torch, fwd_bwd, 3), d_leaf, d_k, d_sched))
+                # the better of two 5-step timings: single timings of a few steps are noisy
+                d_table.append((min(_time_ms(torch, fwd_bwd, 5), _time_ms(torch, fwd_bwd, 5, 1)),
+                                d_leaf, d_k, d_sched))
     _, d_leaf, d_k, d_sched = min(d_table)
     cfg["p"] = wrs.TraceParams(0, 1e-5, 0.25, d_k, 128, d_sched, 4)
     cfg["leaf"] = d_leaf
     for t in (col, opa, scl):
         t.grad = None
     barrier()
-    ms_f = max_over_ranks(_time_ms(torch, fwd, 5))
-    ms_fb = max_over_ranks(_time_ms(torch, fwd_bwd, 5))
+    ms_f = max_over_ranks(_time_ms(torch, fwd, 20))
+    ms_fb = max_over_ranks(_time_ms(torch, fwd_bwd, 20))
     rays_d = sum(v.width * v.height for v in views)
     # fit the per-splat radius scales to the novel views: 200 Adam steps, lr 1e-2
     scl.data.fill_(1.0)
