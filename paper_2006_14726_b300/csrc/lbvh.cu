@@ -4,7 +4,8 @@
 //   k_bounds_partial / k_bounds_final : centre bounds and the largest radius (two-level reduction)
 //   k_morton                          : 30-bit Morton code of each centre (binary32 quantisation)
 //                                       and the per-tile counts of the first radix digit
-//   k_rs_hist / k_rs_scan / k_rs_scatter (x4) : stable LSD radix sort of (code, index), 8-bit digits
+//   k_rs_hist (x3) / k_rs_scan / k_rs_scatter (x4) : stable LSD radix sort of (code, index), 8-bit
+//                                       digits (the first digit's counts come from k_morton)
 //   k_karras                          : binary radix tree over leaf keys (Karras 2012)
 //   k_leaves_refit                    : gathers the splats into leaf order with their effective
 //                                       radius, computes leaf boxes and refits the internal nodes

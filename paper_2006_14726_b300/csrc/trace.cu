@@ -1,9 +1,11 @@
 // trace.cu -- ray tracing of the splat spheres (Fig. 2 caption, §4; spec S5, S6), its counting
-// variant, the persistent multi-session launch, and the adjoint (spec S7).
+// variant, several views of one scene in one launch, the multi-session launches, and the adjoint
+// (spec S7).
 //
-// Per ray: ordered BVH traversal with a short stack; the K nearest hits beyond the previous pass
-// are kept sorted by (key, id) in registers; nodes whose entry lies beyond the K-th key (or whose
-// exit lies before the previous pass's last key) are culled; after each pass the K hits are
+// Per ray: ordered BVH traversal with a short stack whose entries carry their boxes' entry
+// distances; the K nearest hits beyond the previous pass are kept sorted by (key, id) in
+// registers; nodes whose entry lies beyond the K-th key (or whose exit lies before the previous
+// pass's last key) are culled, when tested and again when popped; after each pass the K hits are
 // composited front to back.  A ray stops once its transmittance reaches t_stop, H hits are used,
 // or a pass finds fewer than K hits.  The 4-wide traversal (the default) reads seven float4 of a
 // 128-B node per visit (the near and far planes of the ray's direction, and the references); the
