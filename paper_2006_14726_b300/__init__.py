@@ -196,6 +196,20 @@ def _ptr(t: Optional[torch.Tensor]):
     return t.data_ptr()
 
 
+def _buf(t: Optional[torch.Tensor], numel: int, dtype, what: str) -> Optional[torch.Tensor]:
+    """A caller-provided output/input buffer the kernels index by the camera's size: it must be a
+    contiguous CUDA tensor of the given dtype with at least ``numel`` elements (the C ABI takes a
+    raw pointer and cannot check this)."""
+    if t is None:
+        return None
+    if t.dtype != dtype:
+        raise ValueError(f"{what}: dtype {t.dtype}, expected {dtype}")
+    if t.numel() < numel:
+        raise ValueError(f"{what}: {t.numel()} elements, at least {numel} needed")
+    _ptr(t)
+    return t
+
+
 def make_camera(cam) -> Camera:
     """Any object with eye/right/up/fwd/tan_half_fovy/width/height -> the C struct."""
     c = Camera()
@@ -316,6 +330,8 @@ def raycast_volume(vol: torch.Tensor, tf: torch.Tensor, cam, step_vox: float = 0
         rgba_out = torch.empty(c.height, c.width, 4, dtype=torch.float32, device=vol.device)
     if depth_out is None:
         depth_out = torch.empty(c.height, c.width, dtype=torch.float32, device=vol.device)
+    _buf(rgba_out, c.height * c.width * 4, torch.float32, "rgba_out")
+    _buf(depth_out, c.height * c.width, torch.float32, "depth_out")
     if param is None:
         param = 0.5 if heuristic == DEPTH_ACCUMULATED else tau
     _check(_lib.wrs_raycast_volume_heuristic(_ptr(vol), dt, nx, ny, nz, _ptr(tf), ctypes.byref(c),
@@ -462,6 +478,8 @@ def point_splat(splats: SplatBuffers, cam, point_size: int = 1, out: Optional[to
     dev = splats.pos_r.device
     if out is None:
         out = torch.empty(c.height, c.width, 4, dtype=torch.float32, device=dev)
+    _buf(out, c.height * c.width * 4, torch.float32, "point_splat out")
+    _buf(index, c.height * c.width, torch.int32, "point_splat index")
     if scratch is None:
         scratch = _scratch(point_splat_scratch_bytes(c.width, c.height), dev)
     sp = splats.c()
@@ -519,6 +537,7 @@ def trace(bvh: LBVH, sorted: SplatBuffers, cam, params: TraceParams = TraceParam
     c = _cam(cam)
     if out is None:
         out = torch.empty(c.height, c.width, 4, dtype=torch.float32, device=sorted.pos_r.device)
+    _buf(out, c.height * c.width * 4, torch.float32, "trace out")
     b, s, p = bvh.c(), sorted.c(), params.c(opacity)
     _check(_lib.wrs_trace(ctypes.byref(b), ctypes.byref(s), ctypes.byref(c), ctypes.byref(p),
                           _ptr(out), _ptr(status), _stream(stream)), "wrs_trace")
@@ -538,6 +557,7 @@ def trace_views(bvh: LBVH, sorted: SplatBuffers, cams: Sequence, params: TracePa
     arr, w, h = _cams(cams)
     if out is None:
         out = torch.empty(len(cams), h, w, 4, dtype=torch.float32, device=sorted.pos_r.device)
+    _buf(out, len(cams) * h * w * 4, torch.float32, "trace_views out")
     b, s, p = bvh.c(), sorted.c(), params.c(opacity)
     _check(_lib.wrs_trace_views(ctypes.byref(b), ctypes.byref(s), arr, len(cams), ctypes.byref(p),
                                 _ptr(out), _ptr(status), _stream(stream)), "wrs_trace_views")
@@ -612,8 +632,12 @@ def trace_backward(bvh: LBVH, sorted: SplatBuffers, cam, dL_drgba: torch.Tensor,
     c = _cam(cam)
     dev = sorted.pos_r.device
     cap = max(sorted.capacity, 1)
+    _buf(dL_drgba.contiguous(), c.height * c.width * 4, torch.float32, "dL_drgba")
     if accumulate_into is not None:
         g_rgba, g_op, g_sc = accumulate_into
+        _buf(g_rgba, sorted.capacity * 4, torch.float32, "g_rgba")
+        _buf(g_op, sorted.capacity, torch.float32, "g_opacity")
+        _buf(g_sc, sorted.capacity, torch.float32, "g_scale")
         fn, name = _lib.wrs_trace_backward_accumulate, "wrs_trace_backward_accumulate"
     else:
         g_rgba = torch.empty(cap, 4, dtype=torch.float32, device=dev)
@@ -634,11 +658,15 @@ def trace_backward_views(bvh: LBVH, sorted: SplatBuffers, cams: Sequence, dL_drg
                          status: Optional[torch.Tensor] = None, stream=None, accumulate_into=None):
     """Adjoint of :func:`trace_views` (dL_drgba [V,H,W,4]): the sum over the views of their
     :func:`trace_backward` gradients, in one launch.  ``accumulate_into`` as for trace_backward."""
-    arr, _, _ = _cams(cams)
+    arr, w, h = _cams(cams)
     dev = sorted.pos_r.device
     cap = max(sorted.capacity, 1)
+    _buf(dL_drgba.contiguous(), len(cams) * h * w * 4, torch.float32, "dL_drgba")
     if accumulate_into is not None:
         g_rgba, g_op, g_sc = accumulate_into
+        _buf(g_rgba, sorted.capacity * 4, torch.float32, "g_rgba")
+        _buf(g_op, sorted.capacity, torch.float32, "g_opacity")
+        _buf(g_sc, sorted.capacity, torch.float32, "g_scale")
     else:
         g_rgba = torch.empty(cap, 4, dtype=torch.float32, device=dev)
         g_op = torch.empty(cap, dtype=torch.float32, device=dev) if want_opacity else None

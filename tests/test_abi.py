@@ -156,3 +156,16 @@ def test_cpu_tensors_are_rejected(wrs):
     import torch
     with pytest.raises(ValueError):
         wrs._ptr(torch.zeros(4))
+
+
+def test_buffer_checks(wrs):
+    """Caller buffers the kernels index by the camera's size are checked before any call (the C ABI
+    takes raw pointers): dtype and element count (CPU tensors are refused as before)."""
+    import torch
+    with pytest.raises(ValueError, match="dtype"):
+        wrs._buf(torch.zeros(8, dtype=torch.float64), 8, torch.float32, "x")
+    with pytest.raises(ValueError, match="at least"):
+        wrs._buf(torch.zeros(7), 8, torch.float32, "x")
+    with pytest.raises(ValueError, match="CUDA"):
+        wrs._buf(torch.zeros(8), 8, torch.float32, "x")
+    assert wrs._buf(None, 8, torch.float32, "x") is None
