@@ -324,7 +324,9 @@ int wrs_trace_batched(const wrs_session* sessions, int32_t n_sessions, uint32_t 
  * g_scale[n] (dL/d radius scale, may be NULL; zero when edge_softness = 0).  radius_scale /
  * global_scale must be the values the LBVH was built with.  The outputs are zeroed by this call
  * over the first in-capacity entries; accumulation uses float atomics (summation order is not
- * fixed).  status: device word (CHUNK_OVERFLOW if a ray has more than 64 * k_chunk hits). */
+ * fixed).  status: device word (CHUNK_OVERFLOW if a ray has more than 64 * k_chunk hits).
+ * Schedules: PER_PIXEL one thread per pixel; PERSISTENT lane refill; PACKET the same per-ray work
+ * with every traversal shared by the warp (4-wide nodes, as wrs_trace's packet schedule). */
 int wrs_trace_backward(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* cam,
                        const wrs_trace_params* params, const float* radius_scale,
                        float global_scale, const float* dL_drgba, float* g_rgba,
@@ -343,8 +345,8 @@ int wrs_trace_backward_accumulate(const wrs_lbvh* bvh, const wrs_splats* sorted,
  * wrs_trace_views), and every view's gradients are added into the one set of per-splat outputs
  * (float atomics; summation order not fixed), i.e. the sum of the views' wrs_trace_backward
  * gradients.  accumulate = 0 zeroes the outputs first (as wrs_trace_backward), 1 adds to what
- * they hold (as wrs_trace_backward_accumulate).  One thread per pixel, any schedule.  Not in the
- * paper; used for multi-view fitting. */
+ * they hold (as wrs_trace_backward_accumulate).  Schedule PACKET runs the packet backward, any
+ * other one thread per pixel.  Not in the paper; used for multi-view fitting. */
 int wrs_trace_backward_views(const wrs_lbvh* bvh, const wrs_splats* sorted,
                              const wrs_camera* cams, int32_t n_views,
                              const wrs_trace_params* params, const float* radius_scale,

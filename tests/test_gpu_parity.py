@@ -402,7 +402,8 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("beta,k,sched,width", [(0.25, 8, 0, 2), (0.25, 1, 0, 4), (0.0, 4, 0, 2),
-                                                (0.25, 1, 1, 2), (0.25, 4, 1, 4), (0.0, 2, 1, 4)])
+                                                (0.25, 1, 1, 2), (0.25, 4, 1, 4), (0.0, 2, 1, 4),
+                                                (0.25, 4, 2, 4), (0.0, 1, 2, 4), (0.25, 16, 2, 4)])
 def test_backward_matches_oracle_adjoint(wrs, beta, k, sched, width):
     rgba, depth, srv, cli, ref_sp, op, sc, g = _bwd_instance(wrs)
     n = ref_sp.n

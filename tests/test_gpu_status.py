@@ -92,7 +92,7 @@ def test_backward_chunk_table_overflow_is_reported(wrs):
     wrs.check_status(st)
     assert float(img[..., 3].max()) > 0.05  # many layers composited
     g = torch.ones(H, W, 4, device="cuda")
-    for sched in (0, 1):
+    for sched in (0, 1, 2):
         wrs.trace_backward(bvh, srt, srv, g, wrs.TraceParams(k_chunk=1, schedule=sched), status=st)
         with pytest.raises(wrs.WrsError) as e:
             wrs.check_status(st)

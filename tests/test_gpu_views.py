@@ -3,8 +3,9 @@ against the single-view calls, which the parity tests pin to the oracle, and dir
 oracle on a small case.
 
 Forward: each view is bitwise the image of its own wrs_trace call, for every schedule, width and
-K, also when the views are split over several launches (more than 32 views).  Backward: the sum of
-the single-view gradients, up to the summation order of float atomics.
+K, also when the views are split over several launches (more than 32 views).  Backward (one thread
+per pixel, and the packet backward with a warp-shared traversal): the sum of the single-view
+gradients, up to the summation order of float atomics.
 """
 import numpy as np
 import pytest
@@ -86,15 +87,15 @@ def test_views_against_the_oracle(wrs):
         assert err.max() <= MAX_ABS and err.mean() <= MEAN_ABS, (v, err.max())
 
 
-@pytest.mark.parametrize("k,width", [(1, 4), (4, 2), (2, 4)])
-def test_backward_views_sum_the_single_view_gradients(wrs, k, width):
+@pytest.mark.parametrize("k,width,sched", [(1, 4, 0), (4, 2, 0), (2, 4, 0), (4, 4, 2), (1, 4, 2)])
+def test_backward_views_sum_the_single_view_gradients(wrs, k, width, sched):
     _, _, srv, sp = _scene(wrs)
     n = sp.count()
     scale = torch.full((n,), 1.3, device="cuda")
     opac = torch.full((n,), 0.8, device="cuda")
     bvh, srt = wrs.build_lbvh(sp, 1, radius_scale=scale)
     cams = _views(srv, 4)
-    params = wrs.TraceParams(edge_softness=0.25, k_chunk=k, width=width)
+    params = wrs.TraceParams(edge_softness=0.25, k_chunk=k, width=width, schedule=sched)
     g = torch.randn(len(cams), 64, 80, 4, device="cuda")
     st = wrs.new_status()
     gr, go, gs = wrs.trace_backward_views(bvh, srt, cams, g, params, opacity=opac,
@@ -112,6 +113,28 @@ def test_backward_views_sum_the_single_view_gradients(wrs, k, width):
                              accumulate_into=(gr, go, gs))
     for a, b in zip((gr, go, gs), acc):
         assert torch.allclose(a[:n], 2 * b[:n], rtol=1e-4, atol=2e-6)
+
+
+@pytest.mark.parametrize("k", [1, 4, 16])
+def test_packet_backward_equals_per_pixel_backward(wrs, k):
+    """The warp-shared traversal of the packet backward rebuilds each ray's own hit lists: its
+    gradients equal the per-pixel backward's up to the order of the float atomics."""
+    _, _, srv, sp = _scene(wrs, 96, 72, 21)
+    n = sp.count()
+    scale = torch.full((n,), 1.4, device="cuda")
+    bvh, srt = wrs.build_lbvh(sp, 1, radius_scale=scale)
+    cam = _views(srv, 2)[1]
+    g = torch.randn(64, 80, 4, device="cuda")
+    res = []
+    for sched in (0, 2):
+        st = wrs.new_status()
+        res.append(wrs.trace_backward(bvh, srt, cam, g, wrs.TraceParams(edge_softness=0.25,
+                                      k_chunk=k, width=4, schedule=sched), radius_scale=scale,
+                                      status=st))
+        wrs.check_status(st)
+    for a, b in zip(*res):
+        assert float(b[:n].abs().sum()) > 0
+        assert torch.allclose(a[:n], b[:n], rtol=1e-4, atol=1e-6)
 
 
 def test_views_of_different_sizes_are_rejected(wrs):
