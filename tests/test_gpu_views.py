@@ -115,6 +115,23 @@ def test_backward_views_sum_the_single_view_gradients(wrs, k, width, sched):
         assert torch.allclose(a[:n], 2 * b[:n], rtol=1e-4, atol=2e-6)
 
 
+@pytest.mark.parametrize("sched", [0, 2])
+def test_backward_over_more_views_than_one_launch_holds(wrs, sched):
+    """35 ragged views (two launches of 32 + 3): the sum of the 35 single-view gradients."""
+    _, _, srv, sp = _scene(wrs, 64, 48, 9)
+    n = sp.count()
+    bvh, srt = wrs.build_lbvh(sp, 1)
+    cams = _views(srv, 35, 37, 29)
+    params = wrs.TraceParams(edge_softness=0.25, k_chunk=2, width=4, schedule=sched)
+    g = torch.randn(len(cams), 29, 37, 4, device="cuda")
+    gr, go, _ = wrs.trace_backward_views(bvh, srt, cams, g, params, want_scale=False)
+    acc = (torch.zeros_like(gr), torch.zeros_like(go), None)
+    for v, c in enumerate(cams):
+        wrs.trace_backward(bvh, srt, c, g[v], params, accumulate_into=acc)
+    assert torch.allclose(gr[:n], acc[0][:n], rtol=1e-4, atol=1e-6)
+    assert torch.allclose(go[:n], acc[1][:n], rtol=1e-4, atol=1e-6)
+
+
 @pytest.mark.parametrize("k", [1, 4, 16])
 def test_packet_backward_equals_per_pixel_backward(wrs, k):
     """The warp-shared traversal of the packet backward rebuilds each ray's own hit lists: its
