@@ -780,18 +780,26 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
     rgba_m, depth_m = wrs.raycast_volume(vol_m, torch.from_numpy(synth.tf_ramp()).to(dev), srv_m)
     del vol_m
     sp_m = wrs.unproject(rgba_m, depth_m, srv_m)
-    bvh_m, srt_m = wrs.build_lbvh(sp_m, leaf)
     cams_m = [wrs.make_camera(c) for c in M.client_poses(seed_offset=rank)]
+    # the launch tuned on this workload (a trace-only number: no build share in the score)
+    tm = autotune.tune_trace(sp_m, cams_m[:4], use_cache=False) if not args.no_autotune else \
+        {"leaf": leaf, "k_chunk": params.k_chunk, "block": params.block,
+         "schedule": params.schedule, "width": params.width}
+    mparams = wrs.TraceParams(max_hits=0, t_stop=1e-5, k_chunk=tm["k_chunk"], block=tm["block"],
+                              schedule=tm["schedule"], width=tm["width"])
+    bvh_m, srt_m = wrs.build_lbvh(sp_m, tm["leaf"])
     out_m = torch.empty(M.client_h, M.client_w, 4, device=dev)
     per_pose = []
     for c in cams_m:
-        per_pose.append(_time_ms(torch, lambda: wrs.trace(bvh_m, srt_m, c, params, out=out_m), 10))
+        per_pose.append(_time_ms(torch, lambda: wrs.trace(bvh_m, srt_m, c, mparams, out=out_m), 10))
     ms_m = max_over_ranks(statistics.median(per_pose))
     line["mid"] = {"splats": sp_m.count(), "client": [M.client_w, M.client_h], "poses": len(cams_m),
                    "trace_ms_median": ms_m,
                    "trace_mrays_s": world * M.client_w * M.client_h / (ms_m * 1e-3) / 1e6,
+                   "launch": {"leaf_size": tm["leaf"], "k_chunk": tm["k_chunk"],
+                              "schedule": SCHEDULE_NAMES[tm["schedule"]], "bvh_width": tm["width"]},
                    "lbvh_ms": max_over_ranks(_time_ms(torch, lambda: wrs.build_lbvh(
-                       sp_m, leaf, bvh=bvh_m, sorted=srt_m), 10))}
+                       sp_m, tm["leaf"], bvh=bvh_m, sorted=srt_m), 10))}
     if rank == 0 and world == 1:
         import oracle
         oracle.build()
