@@ -112,8 +112,8 @@ typedef struct {
 #define WRS_SCHEDULE_PER_PIXEL 0   /* one thread per pixel, grid over the image */
 #define WRS_SCHEDULE_PERSISTENT 1  /* one resident wave of 128-thread blocks; warps refill idle
                                       lanes with new rays (block size fixed at 128) */
-#define WRS_SCHEDULE_PACKET 2      /* wrs_trace only: the 32 rays of an 8x4 tile share one
-                                      traversal of the 4-wide nodes (width is ignored) */
+#define WRS_SCHEDULE_PACKET 2      /* the 32 rays of an 8x4 tile share one traversal of the
+                                      4-wide nodes (width is ignored) */
 
 /* Compositing (spec S6) and performance parameters of a trace.  Results do not depend on
  * k_chunk, block or schedule (bitwise). */
@@ -125,9 +125,9 @@ typedef struct {
     int32_t k_chunk;      /* hits gathered per traversal pass: 1, 2, 4, 8 or 16 */
     int32_t block;        /* threads per block: 64, 128 or 256 (per-pixel schedule; the 4-wide
                              traversal with k_chunk <= 2 uses at most 128) */
-    int32_t schedule;     /* WRS_SCHEDULE_PER_PIXEL, WRS_SCHEDULE_PERSISTENT or (wrs_trace only)
-                             WRS_SCHEDULE_PACKET; wrs_trace_batched: PER_PIXEL = one warp per
-                             8x4 tile of all sessions, otherwise persistent with lane refill */
+    int32_t schedule;     /* WRS_SCHEDULE_PER_PIXEL, WRS_SCHEDULE_PERSISTENT or
+                             WRS_SCHEDULE_PACKET; wrs_trace_batched: PER_PIXEL and PACKET = one
+                             warp per 8x4 tile of all sessions, PERSISTENT = lane refill */
     int32_t width;        /* traversal: 2 (or 0) = binary nodes, 4 = the LBVH's 4-wide nodes */
 } wrs_trace_params;
 
@@ -308,9 +308,10 @@ uint32_t wrs_session_tiles(int32_t width, int32_t height);
 /* Many client sessions, each with its own LBVH, splats, camera and output, traced in ONE launch
  * of 128-thread blocks (params->block is ignored).  params->schedule WRS_SCHEDULE_PER_PIXEL: one
  * warp per 8x4 ray tile of the concatenated tile space (the warp finds its session by binary
- * search).  Otherwise persistent: one resident wave whose warps take chunks of four ray tiles of
- * any session from *work_counter (device uint32, reset by this call) and refill their idle lanes
- * from them.  sessions: device array of n_sessions descriptors whose tile_begin are the prefix
+ * search); WRS_SCHEDULE_PACKET: the same tiles, each traced by one warp-shared traversal of the
+ * session's 4-wide nodes.  WRS_SCHEDULE_PERSISTENT: one resident wave whose warps take chunks of
+ * four ray tiles of any session from *work_counter (device uint32, reset by this call) and refill
+ * their idle lanes from them.  sessions: device array of n_sessions descriptors whose tile_begin are the prefix
  * sums of wrs_session_tiles; total_tiles = their sum.  Each session's image equals wrs_trace's
  * bitwise. */
 int wrs_trace_batched(const wrs_session* sessions, int32_t n_sessions, uint32_t total_tiles,

@@ -612,8 +612,8 @@ class Batch:
 
 def trace_batched(batch: Batch, params: TraceParams = TraceParams(),
                   status: Optional[torch.Tensor] = None, stream=None) -> List[torch.Tensor]:
-    """All sessions of ``batch`` in one launch (params.schedule: per-pixel warps or persistent);
-    returns the per-session images."""
+    """All sessions of ``batch`` in one launch (params.schedule: per-pixel warps, persistent, or
+    one warp-shared traversal per tile); returns the per-session images."""
     p = params.c(None)
     _check(_lib.wrs_trace_batched(_ptr(batch.desc), batch.n_sessions, batch.total_tiles,
                                   ctypes.byref(p), _ptr(batch.work), _ptr(status), _stream(stream)),

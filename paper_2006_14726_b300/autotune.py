@@ -114,12 +114,13 @@ def tune_trace(splats: SplatBuffers, cams: Sequence, base: TraceParams = TracePa
 def tune_batched(batch: Batch, base: TraceParams = TraceParams(), ks: Iterable[int] = KS,
                  widths: Iterable[int] = WIDTHS, reps: int = 3) -> Dict:
     """Pick (k_chunk, width, schedule) for one multi-session launch (leaf sizes are fixed by the
-    sessions' LBVHs; blocks of 128 threads: one warp per tile, or one resident wave with lane
-    refill)."""
+    sessions' LBVHs; blocks of 128 threads: one warp per tile, one warp-shared traversal per
+    tile, or one resident wave with lane refill)."""
     best = None
-    for sched in (SCHEDULE_PER_PIXEL, SCHEDULE_PERSISTENT):
+    for sched in (SCHEDULE_PER_PIXEL, SCHEDULE_PERSISTENT, SCHEDULE_PACKET):
         for k in ks:
-            for width in widths:
+            # the packet schedule always walks the 4-wide nodes
+            for width in (widths if sched != SCHEDULE_PACKET else (4,)):
                 p = TraceParams(base.max_hits, base.t_stop, base.edge_softness, k, 128, sched, width)
                 ms = _time_ms(lambda: trace_batched(batch, p), reps)
                 if best is None or ms < best["ms"]:

@@ -799,26 +799,20 @@ __global__ void __launch_bounds__(256) k_trace_count(Scene sc, Comp cp, wrs_came
     }
 }
 
-// Multi-session trace, one thread per pixel: warp w of the grid traces 8x4 tile w of the
-// concatenated tile space (session s owns tiles [tile_begin_s, tile_begin_s + tiles_s)); the
-// warp finds its session by binary search over the sessions' first tiles.
-template <int K, bool W4>
-__global__ void __launch_bounds__(128, BatchedBounds<K, W4>::min_blocks) k_trace_batched_pp(const wrs_session* __restrict__ sess,
-                                                          int n_sessions, uint32_t total_tiles,
-                                                          Comp cp, int32_t* status) {
-    const uint32_t tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (tile >= total_tiles) return;
-    const uint32_t pos = threadIdx.x & 31u;
+// The session owning 8x4 tile `tile` of the concatenated tile space (session s owns tiles
+// [tile_begin_s, tile_begin_s + tiles_s)): binary search over the sessions' first tiles.
+__device__ __forceinline__ const wrs_session& session_of(const wrs_session* __restrict__ sess,
+                                                         int n_sessions, uint32_t tile) {
     int lo = 0, hi = n_sessions - 1;  // last session with tile_begin <= tile
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (sess[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
     }
-    const wrs_session& S = sess[lo];
-    const uint32_t W = (uint32_t)S.cam.width, H = (uint32_t)S.cam.height;
-    const uint32_t local = tile - S.tile_begin, tiles_x = (W + 7) / 8;
-    const uint32_t x = (local % tiles_x) * 8 + (pos & 7), y = (local / tiles_x) * 4 + (pos >> 3);
-    if (x >= W || y >= H) return;
+    return sess[lo];
+}
+
+template <bool W4>
+__device__ __forceinline__ Scene session_scene(const wrs_session& S) {
     Scene sc;
     sc.hdr = static_cast<const LbvhHeader*>(S.nodes);
     sc.nodes = wrs::lbvh_nodes(S.nodes);
@@ -828,12 +822,84 @@ __global__ void __launch_bounds__(128, BatchedBounds<K, W4>::min_blocks) k_trace
     sc.id = S.id;
     sc.src = S.src;
     sc.opacity = S.opacity;
+    return sc;
+}
+
+// Pixel (x, y) of lane `pos` in 8x4 tile `tile`, and the session it belongs to.
+__device__ __forceinline__ const wrs_session& tile_pixel_of(const wrs_session* __restrict__ sess,
+                                                            int n_sessions, uint32_t tile,
+                                                            uint32_t pos, uint32_t& x, uint32_t& y) {
+    const wrs_session& S = session_of(sess, n_sessions, tile);
+    const uint32_t local = tile - S.tile_begin, tiles_x = ((uint32_t)S.cam.width + 7) / 8;
+    x = (local % tiles_x) * 8 + (pos & 7);
+    y = (local / tiles_x) * 4 + (pos >> 3);
+    return S;
+}
+
+// Store the result of lane `pos` of tile `tile`, its output pixel found again: an opaque copy of
+// the tile index keeps the compiler from holding the session's output address and the pixel in
+// registers through the traversal (in the packet kernel 1 % faster than holding them).
+__device__ __forceinline__ void store_tile_pixel(const wrs_session* __restrict__ sess,
+                                                 int n_sessions, uint32_t tile, uint32_t pos,
+                                                 float4 o) {
+    asm volatile("" : "+r"(tile));
+    uint32_t x, y;
+    const wrs_session& S = tile_pixel_of(sess, n_sessions, tile, pos, x, y);
+    const uint32_t W = (uint32_t)S.cam.width;
+    if (x < W && y < (uint32_t)S.cam.height)
+        reinterpret_cast<float4*>(S.rgba_out)[(size_t)y * W + x] = o;
+}
+
+// Multi-session trace, one thread per pixel: warp w of the grid traces 8x4 tile w of the
+// concatenated tile space.
+template <int K, bool W4>
+__global__ void __launch_bounds__(128, BatchedBounds<K, W4>::min_blocks) k_trace_batched_pp(const wrs_session* __restrict__ sess,
+                                                          int n_sessions, uint32_t total_tiles,
+                                                          Comp cp, int32_t* status) {
+    const uint32_t tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (tile >= total_tiles) return;
+    const uint32_t pos = threadIdx.x & 31u;
+    uint32_t x, y;
+    const wrs_session& S = tile_pixel_of(sess, n_sessions, tile, pos, x, y);
+    const uint32_t W = (uint32_t)S.cam.width;
+    if (x >= W || y >= (uint32_t)S.cam.height) return;
+    const Scene sc = session_scene<W4>(S);
     const RayCtx rc = make_ray_ctx(sc, S.cam, (int)x, (int)y);
     uint32_t overflow;
     Counts cnt;
     const float4 o = trace_ray<K, false, W4>(sc, cp, rc, overflow, cnt);
     if (overflow) wrs::set_status(status, overflow);
+    // (finding the output pixel again after the traversal, as the packet kernel does, spills
+    // less but measured 1 % slower here)
     reinterpret_cast<float4*>(S.rgba_out)[(size_t)y * W + x] = o;
+}
+
+// Multi-session trace, packet schedule (4-wide nodes): warp w traces 8x4 tile w of the
+// concatenated tile space with one warp-shared traversal; lanes outside their session's image
+// take part without a ray (the tile, and so the session, is warp-uniform).
+// Resident 128-thread blocks per SM of the multi-session packet kernel: 8 (64 registers, some
+// spilled) takes 15.7 ms on the 64 sessions against 18.1 with 7 and 20.5 with no cap (94
+// registers); reading the session's scene pointers from shared memory at each use instead (no
+// spills) took 17.1 ms.
+#ifndef WRS_BATCHED_PACKET_MIN_BLOCKS
+#define WRS_BATCHED_PACKET_MIN_BLOCKS 8
+#endif
+template <int K>
+__global__ void __launch_bounds__(128, WRS_BATCHED_PACKET_MIN_BLOCKS) k_trace_batched_packet(const wrs_session* __restrict__ sess,
+                                                              int n_sessions, uint32_t total_tiles,
+                                                              Comp cp, int32_t* status) {
+    const uint32_t tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (tile >= total_tiles) return;
+    const uint32_t pos = threadIdx.x & 31u;
+    uint32_t x, y;
+    const wrs_session& S = tile_pixel_of(sess, n_sessions, tile, pos, x, y);
+    const bool active = x < (uint32_t)S.cam.width && y < (uint32_t)S.cam.height;
+    const Scene sc = session_scene<true>(S);
+    const RayCtx rc = make_ray_ctx(sc, S.cam, active ? (int)x : 0, active ? (int)y : 0);
+    uint32_t overflow;
+    const float4 o = trace_ray_packet<K>(sc, cp, rc, active, overflow);
+    if (overflow) wrs::set_status(status, overflow);
+    store_tile_pixel(sess, n_sessions, tile, pos, o);
 }
 
 // Persistent multi-session trace with lane refill.  Work is numbered in 8x4 ray tiles over all
@@ -1466,6 +1532,12 @@ template <int K, bool W4> struct LaunchBatchedPP {
         k_trace_batched_pp<K, W4><<<blocks, 128, 0, s>>>(ss, ns, tt, cp, st);
     }
 };
+template <int K, bool W4> struct LaunchBatchedPacket {  // 4-wide implied, as LaunchTracePacket
+    static void run(uint32_t blocks, const wrs_session* ss, int ns, uint32_t tt, Comp cp,
+                    int32_t* st, cudaStream_t s) {
+        k_trace_batched_packet<K><<<blocks, 128, 0, s>>>(ss, ns, tt, cp, st);
+    }
+};
 template <int K, bool W4> struct LaunchTracePacket {  // W4 is implied: the packet traversal is 4-wide
     static void run(dim3 g, int b, cudaStream_t s, Scene sc, Comp cp, wrs_camera cam, float4* o,
                     int32_t* st) {
@@ -1669,6 +1741,9 @@ int wrs_trace_batched(const wrs_session* sessions, int32_t n_sessions, uint32_t 
     if (params->schedule == WRS_SCHEDULE_PER_PIXEL)
         dispatch_k<LaunchBatchedPP>(K, W, (total_tiles + 3) / 4, sessions, n_sessions, total_tiles,
                                     comp_of(params), status, s);
+    else if (params->schedule == WRS_SCHEDULE_PACKET)
+        dispatch_k<LaunchBatchedPacket>(K, W, (total_tiles + 3) / 4, sessions, n_sessions,
+                                        total_tiles, comp_of(params), status, s);
     else
         dispatch_k<LaunchBatched>(K, W, resident_grid<LaunchBatched>(K, W), 128, s, sessions,
                                   n_sessions, total_tiles, comp_of(params), work_counter, status);

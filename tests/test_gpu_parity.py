@@ -370,7 +370,7 @@ def test_batched_equals_sequential_bitwise(wrs):
         refs.append(wrs.trace(bvh, srt, cli).cpu().numpy())
     batch = wrs.Batch(sessions)
     st = wrs.new_status()
-    for sched in (wrs.SCHEDULE_PER_PIXEL, wrs.SCHEDULE_PERSISTENT):
+    for sched in (wrs.SCHEDULE_PER_PIXEL, wrs.SCHEDULE_PERSISTENT, wrs.SCHEDULE_PACKET):
         for k, width in ((8, 2), (1, 4), (4, 2), (16, 4)):
             for o in batch.outputs:
                 o.fill_(-1.0)
