@@ -2,12 +2,15 @@
 
     python -m paper_2006_14726_b300.cases large --frames 3 [--leaf 1 --k 1 --block 128 --schedule 1]
     python -m paper_2006_14726_b300.cases diff [--leaf 1 --k 4 --schedule 2]
+    python -m paper_2006_14726_b300.cases batched --sessions 16 [--k 1 --schedule 0]
 
 Sets up the server image with the GPU ray caster, frees the volume, then runs unproject, the
 LBVH build and ``frames`` client traces (each stage in its own NVTX range) and prints the CUDA
 event times.  Workloads: tiny, mid, large (see synth).  ``diff``: the differentiable workload
 (256^3 blobs, 512^2 server image, 8 views of 512^2, soft edges 0.25): two forward + backward
-steps of the 8 views (one launch each way per step) against the ray-cast views.
+steps of the 8 views (one launch each way per step) against the ray-cast views.  ``batched``:
+the first ``sessions`` of the multi-session workload (server images of 256^2 to 1024^2, 1024^2
+clients), two launches of wrs_trace_batched (the second one is the one to profile).
 """
 from __future__ import annotations
 
@@ -26,17 +29,21 @@ import synth  # noqa: E402
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("workload", choices=["tiny", "mid", "large", "diff"])
+    ap.add_argument("workload", choices=["tiny", "mid", "large", "diff", "batched"])
+    ap.add_argument("--sessions", type=int, default=16)
     ap.add_argument("--frames", type=int, default=3)
     ap.add_argument("--leaf", type=int, default=1)
     ap.add_argument("--k", type=int, default=1)
     ap.add_argument("--block", type=int, default=128)
     ap.add_argument("--max-hits", type=int, default=0)
-    ap.add_argument("--schedule", type=int, default=0, help="0 per pixel, 1 persistent")
+    ap.add_argument("--schedule", type=int, default=0, help="0 per pixel, 1 persistent, 2 packet")
     ap.add_argument("--width", type=int, default=4, help="2 binary nodes, 4 four-wide nodes")
     a = ap.parse_args()
     if a.workload == "diff":
         diff_case(a)
+        return
+    if a.workload == "batched":
+        batched_case(a)
         return
     W = {"tiny": synth.TINY, "mid": synth.MID, "large": synth.LARGE}[a.workload]
     dev = torch.device("cuda")
@@ -103,6 +110,40 @@ def diff_case(a):
         ms.append(e0.elapsed_time(e1))
     print(json.dumps({"workload": "diff", "splats": n, "views": len(views),
                       "fwd_bwd_ms": ms, "loss": float(loss.detach())}))
+
+
+def batched_case(a):
+    dev = torch.device("cuda")
+    tf = torch.from_numpy(synth.tf_ramp()).to(dev)
+    sess = []
+    n_splats = 0
+    for s, (size, srv, cli) in enumerate(synth.batched_sessions(64, seed=4000)[: a.sessions]):
+        vol = synth.gaussian_volume_device(256, 64, 4000 + s)
+        rgba, depth = wrs.raycast_volume(vol, tf, srv)
+        del vol
+        sp = wrs.unproject(rgba, depth, srv)
+        bvh, srt = wrs.build_lbvh(sp, a.leaf)
+        n_splats += sp.count()
+        sess.append((bvh, srt, cli))
+        del sp
+    batch = wrs.Batch(sess)
+    params = wrs.TraceParams(max_hits=a.max_hits, k_chunk=a.k, schedule=a.schedule, width=a.width)
+    st = wrs.new_status()
+    ms = []
+    for _ in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.cuda.nvtx.range_push("batched")
+        wrs.trace_batched(batch, params, status=st)
+        torch.cuda.nvtx.range_pop()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    wrs.check_status(st)
+    rays = sum(c.width * c.height for _, _, c in sess)
+    print(json.dumps({"workload": "batched", "sessions": len(sess), "splats": n_splats,
+                      "rays": rays, "trace_batched_ms": ms,
+                      "device_bytes_allocated": torch.cuda.memory_allocated()}))
 
 
 if __name__ == "__main__":
