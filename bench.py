@@ -729,7 +729,11 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
                        "sequential_mrays_s": world * rays / (ms_seq * 1e-3) / 1e6,
                        "one_launch_ms": ms_graph, "sequential_ms": ms_seq,
                        "k_chunk": bt["k_chunk"], "block": bt["block"], "bvh_width": bt["width"],
-                       "schedule": SCHEDULE_NAMES[bt["schedule"]],
+                       "schedule": (SCHEDULE_NAMES[bt["schedule"]] if bt["schedule"] < 3 else
+                                    "per session: packet for the {} sessions with >= 2 client "
+                                    "pixels per splat slot, one thread per pixel for the other "
+                                    "{}".format(sum(v == wrs.SCHEDULE_PACKET for v in batch.schedules),
+                                                sum(v != wrs.SCHEDULE_PACKET for v in batch.schedules))),
                        "leaf_size": leaf}
     del sess, batch, outs, g
 

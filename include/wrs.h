@@ -114,6 +114,8 @@ typedef struct {
                                       lanes with new rays (block size fixed at 128) */
 #define WRS_SCHEDULE_PACKET 2      /* the 32 rays of an 8x4 tile share one traversal of the
                                       4-wide nodes (width is ignored) */
+#define WRS_SCHEDULE_PER_SESSION 3 /* wrs_trace_batched only: each session's own schedule field
+                                      (PER_PIXEL or PACKET) picks how its tiles are traced */
 
 /* Compositing (spec S6) and performance parameters of a trace.  Results do not depend on
  * k_chunk, block or schedule (bitwise). */
@@ -142,7 +144,9 @@ typedef struct {
     float* rgba_out;       /* [height][width][4] */
     wrs_camera cam;
     uint32_t tile_begin;   /* first work item of this session (prefix sum of wrs_session_tiles) */
-    uint32_t pad;
+    uint32_t schedule;     /* under WRS_SCHEDULE_PER_SESSION: WRS_SCHEDULE_PACKET traces this
+                              session's tiles with warp-shared traversals, any other value one
+                              thread per pixel; ignored by the other schedules */
 } wrs_session;
 
 const char* wrs_version(void);
@@ -309,7 +313,9 @@ uint32_t wrs_session_tiles(int32_t width, int32_t height);
  * of 128-thread blocks (params->block is ignored).  params->schedule WRS_SCHEDULE_PER_PIXEL: one
  * warp per 8x4 ray tile of the concatenated tile space (the warp finds its session by binary
  * search); WRS_SCHEDULE_PACKET: the same tiles, each traced by one warp-shared traversal of the
- * session's 4-wide nodes.  WRS_SCHEDULE_PERSISTENT: one resident wave whose warps take chunks of
+ * session's 4-wide nodes; WRS_SCHEDULE_PER_SESSION: the same tiles, each session traced as its
+ * own schedule field says (a sparse session, with several client pixels per splat, gains from
+ * the shared traversal; a dense one does not).  WRS_SCHEDULE_PERSISTENT: one resident wave whose warps take chunks of
  * four ray tiles of any session from *work_counter (device uint32, reset by this call) and refill
  * their idle lanes from them.  sessions: device array of n_sessions descriptors whose tile_begin are the prefix
  * sums of wrs_session_tiles; total_tiles = their sum.  Each session's image equals wrs_trace's

@@ -49,6 +49,7 @@ RADIUS_VOXEL = 1
 SCHEDULE_PER_PIXEL = 0
 SCHEDULE_PERSISTENT = 1
 SCHEDULE_PACKET = 2
+SCHEDULE_PER_SESSION = 3  # trace_batched only: each session's own schedule (Batch(schedules=...))
 DEPTH_FIRST_HIT = 0
 DEPTH_MAX_CONTRIBUTION = 1
 DEPTH_ACCUMULATED = 2
@@ -102,7 +103,7 @@ class Session(ctypes.Structure):
     _fields_ = [("nodes", ctypes.c_void_p), ("pos_r", ctypes.c_void_p), ("rgba", ctypes.c_void_p),
                 ("id", ctypes.c_void_p), ("src", ctypes.c_void_p), ("opacity", ctypes.c_void_p),
                 ("rgba_out", ctypes.c_void_p), ("cam", Camera), ("tile_begin", ctypes.c_uint32),
-                ("pad", ctypes.c_uint32)]
+                ("schedule", ctypes.c_uint32)]
 
 
 def _sig(name, res, *args):
@@ -583,13 +584,34 @@ def session_tiles(width: int, height: int) -> int:
     return int(_lib.wrs_session_tiles(int(width), int(height)))
 
 
+def sparse_schedules(sessions: Sequence[Tuple[LBVH, SplatBuffers, object]],
+                     ratio: float = 2.0) -> List[int]:
+    """Per-session schedules for SCHEDULE_PER_SESSION: the warp-shared traversal where the client
+    image has at least ``ratio`` pixels per splat slot (neighbouring rays then hit the same
+    splats), one thread per pixel elsewhere."""
+    out = []
+    for _, sp, cam in sessions:
+        c = _cam(cam)
+        out.append(SCHEDULE_PACKET if c.width * c.height >= ratio * sp.capacity
+                   else SCHEDULE_PER_PIXEL)
+    return out
+
+
 class Batch:
     """Descriptors of many client sessions for :func:`trace_batched` (device array + outputs)."""
 
     def __init__(self, sessions: Sequence[Tuple[LBVH, SplatBuffers, object]],
-                 opacity: Optional[Sequence[Optional[torch.Tensor]]] = None, device=None):
+                 opacity: Optional[Sequence[Optional[torch.Tensor]]] = None, device=None,
+                 schedules: Optional[Sequence[int]] = None):
+        """``schedules``: per session SCHEDULE_PER_PIXEL or SCHEDULE_PACKET, used by launches with
+        ``schedule=SCHEDULE_PER_SESSION`` (default: the packet traversal for sessions with at
+        least 2 client pixels per splat slot, see :func:`sparse_schedules`)."""
         device = device or torch.device("cuda")
         n = len(sessions)
+        if schedules is None:
+            schedules = sparse_schedules(sessions)
+        if len(schedules) != n:
+            raise ValueError("one schedule per session")
         arr = (Session * n)()
         self.outputs: List[torch.Tensor] = []
         self._keep = []
@@ -599,12 +621,13 @@ class Batch:
             out = torch.empty(c.height, c.width, 4, dtype=torch.float32, device=device)
             op = opacity[i] if opacity is not None else None
             arr[i] = Session(_ptr(bvh.nodes), _ptr(sp.pos_r), _ptr(sp.rgba), _ptr(sp.id),
-                             _ptr(sp.src), _ptr(op), _ptr(out), c, tile, 0)
+                             _ptr(sp.src), _ptr(op), _ptr(out), c, tile, int(schedules[i]))
             self.outputs.append(out)
             self._keep.append((bvh, sp, op))
             tile += session_tiles(c.width, c.height)
         self.total_tiles = tile
         self.n_sessions = n
+        self.schedules = [int(v) for v in schedules]
         raw = bytes(memoryview(arr).cast("B"))
         self.desc = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device)
         self.work = torch.zeros(1, dtype=torch.int32, device=device)

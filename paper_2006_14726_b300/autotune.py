@@ -16,7 +16,7 @@ from typing import Callable, Dict, Iterable, Optional, Sequence
 
 import torch
 
-from . import (SCHEDULE_PACKET, SCHEDULE_PER_PIXEL, SCHEDULE_PERSISTENT, Batch, SplatBuffers,
+from . import (SCHEDULE_PACKET, SCHEDULE_PER_PIXEL, SCHEDULE_PER_SESSION, SCHEDULE_PERSISTENT, Batch, SplatBuffers,
                TraceParams,
                build_lbvh, trace, trace_batched)
 
@@ -115,9 +115,10 @@ def tune_batched(batch: Batch, base: TraceParams = TraceParams(), ks: Iterable[i
                  widths: Iterable[int] = WIDTHS, reps: int = 3) -> Dict:
     """Pick (k_chunk, width, schedule) for one multi-session launch (leaf sizes are fixed by the
     sessions' LBVHs; blocks of 128 threads: one warp per tile, one warp-shared traversal per
-    tile, or one resident wave with lane refill)."""
+    tile, each session's own schedule of the two (``batch.schedules``), or one resident wave
+    with lane refill)."""
     best = None
-    for sched in (SCHEDULE_PER_PIXEL, SCHEDULE_PERSISTENT, SCHEDULE_PACKET):
+    for sched in (SCHEDULE_PER_PIXEL, SCHEDULE_PERSISTENT, SCHEDULE_PACKET, SCHEDULE_PER_SESSION):
         for k in ks:
             # the packet schedule always walks the 4-wide nodes
             for width in (widths if sched != SCHEDULE_PACKET else (4,)):

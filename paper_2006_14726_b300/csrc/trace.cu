@@ -902,6 +902,35 @@ __global__ void __launch_bounds__(128, WRS_BATCHED_PACKET_MIN_BLOCKS) k_trace_ba
     store_tile_pixel(sess, n_sessions, tile, pos, o);
 }
 
+// Multi-session trace with a schedule per session: the warp's tile belongs to one session, whose
+// schedule field picks one thread per pixel or one warp-shared traversal (a warp-uniform branch).
+template <int K, bool W4>
+__global__ void __launch_bounds__(128, WRS_BATCHED_PACKET_MIN_BLOCKS) k_trace_batched_mixed(
+        const wrs_session* __restrict__ sess, int n_sessions, uint32_t total_tiles, Comp cp,
+        int32_t* status) {
+    const uint32_t tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (tile >= total_tiles) return;
+    const uint32_t pos = threadIdx.x & 31u;
+    uint32_t x, y;
+    const wrs_session& S = tile_pixel_of(sess, n_sessions, tile, pos, x, y);
+    const uint32_t W = (uint32_t)S.cam.width;
+    const bool active = x < W && y < (uint32_t)S.cam.height;
+    const Scene sc = session_scene<true>(S);  // the per-pixel traversal reads wide only if W4
+    uint32_t overflow;
+    float4 o;
+    if (S.schedule == WRS_SCHEDULE_PACKET) {
+        const RayCtx rc = make_ray_ctx(sc, S.cam, active ? (int)x : 0, active ? (int)y : 0);
+        o = trace_ray_packet<K>(sc, cp, rc, active, overflow);
+    } else {
+        if (!active) return;
+        const RayCtx rc = make_ray_ctx(sc, S.cam, (int)x, (int)y);
+        Counts cnt;
+        o = trace_ray<K, false, W4>(sc, cp, rc, overflow, cnt);
+    }
+    if (overflow) wrs::set_status(status, overflow);
+    if (active) reinterpret_cast<float4*>(S.rgba_out)[(size_t)y * W + x] = o;
+}
+
 // Persistent multi-session trace with lane refill.  Work is numbered in 8x4 ray tiles over all
 // sessions (session s owns tiles [tile_begin_s, tile_begin_s + tiles_s)); a warp grabs chunks of
 // kChunkTiles tiles from the global counter and refills its idle lanes from its chunk.  Each lane
@@ -1538,6 +1567,12 @@ template <int K, bool W4> struct LaunchBatchedPacket {  // 4-wide implied, as La
         k_trace_batched_packet<K><<<blocks, 128, 0, s>>>(ss, ns, tt, cp, st);
     }
 };
+template <int K, bool W4> struct LaunchBatchedMixed {
+    static void run(uint32_t blocks, const wrs_session* ss, int ns, uint32_t tt, Comp cp,
+                    int32_t* st, cudaStream_t s) {
+        k_trace_batched_mixed<K, W4><<<blocks, 128, 0, s>>>(ss, ns, tt, cp, st);
+    }
+};
 template <int K, bool W4> struct LaunchTracePacket {  // W4 is implied: the packet traversal is 4-wide
     static void run(dim3 g, int b, cudaStream_t s, Scene sc, Comp cp, wrs_camera cam, float4* o,
                     int32_t* st) {
@@ -1733,6 +1768,8 @@ int wrs_trace_batched(const wrs_session* sessions, int32_t n_sessions, uint32_t 
         return wrs::fail(WRS_ERR_ARG, "%s: bad compositing parameters", fn);
     if (params->width != 0 && params->width != 2 && params->width != 4)
         return wrs::fail(WRS_ERR_ARG, "%s: width %d not 2 or 4 (0 = 2)", fn, params->width);
+    if (params->schedule < WRS_SCHEDULE_PER_PIXEL || params->schedule > WRS_SCHEDULE_PER_SESSION)
+        return wrs::fail(WRS_ERR_ARG, "%s: unknown schedule %d", fn, params->schedule);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(work_counter, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return wrs::cuda_fail(e, fn);
@@ -1744,6 +1781,9 @@ int wrs_trace_batched(const wrs_session* sessions, int32_t n_sessions, uint32_t 
     else if (params->schedule == WRS_SCHEDULE_PACKET)
         dispatch_k<LaunchBatchedPacket>(K, W, (total_tiles + 3) / 4, sessions, n_sessions,
                                         total_tiles, comp_of(params), status, s);
+    else if (params->schedule == WRS_SCHEDULE_PER_SESSION)
+        dispatch_k<LaunchBatchedMixed>(K, W, (total_tiles + 3) / 4, sessions, n_sessions,
+                                       total_tiles, comp_of(params), status, s);
     else
         dispatch_k<LaunchBatched>(K, W, resident_grid<LaunchBatched>(K, W), 128, s, sessions,
                                   n_sessions, total_tiles, comp_of(params), work_counter, status);

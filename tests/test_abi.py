@@ -138,8 +138,13 @@ def test_host_validation_without_device(wrs):
     cams[1].tan_half_fovy = 0.4
     assert lib.wrs_trace_backward_views(ctypes.byref(bv1), ctypes.byref(srt), cams, 3, ctypes.byref(p), None, 1.0, fake, fake, None, None, 0, None, None) == wrs.WRS_ERR_ARG
     assert lib.wrs_trace_backward_views(ctypes.byref(bv1), ctypes.byref(srt), cams, 2, ctypes.byref(p), None, 1.0, ctypes.c_void_p(0x1004), fake, None, None, 0, None, None) == wrs.WRS_ERR_ARG
-    # batched: no sessions
+    # batched: no sessions; an unknown schedule.  The per-session schedule is batched-only.
     assert lib.wrs_trace_batched(fake, 0, 0, ctypes.byref(p), fake, None, None) == wrs.WRS_ERR_ARG
+    ps = wrs._Params(0, 1e-5, 0.0, None, 1, 128, 4, 4)
+    assert lib.wrs_trace_batched(fake, 1, 1, ctypes.byref(ps), fake, None, None) == wrs.WRS_ERR_ARG
+    assert "unknown schedule 4" in wrs.last_error()
+    ps.schedule = wrs.SCHEDULE_PER_SESSION
+    assert lib.wrs_trace(ctypes.byref(bv1), ctypes.byref(srt), ctypes.byref(_cam(wrs)), ctypes.byref(ps), fake, None, None) == wrs.WRS_ERR_ARG
     # measurement helpers: no output, no blocks or repetitions, misaligned or odd-sized copies
     assert lib.wrs_fma_peak(None, 4, 10, None) == wrs.WRS_ERR_ARG
     assert lib.wrs_fma_peak(fake, 0, 10, None) == wrs.WRS_ERR_ARG

@@ -369,12 +369,17 @@ def test_batched_equals_sequential_bitwise(wrs):
         sessions.append((bvh, srt, cli))
         refs.append(wrs.trace(bvh, srt, cli).cpu().numpy())
     batch = wrs.Batch(sessions)
+    # per-session schedules: alternate, so that neighbouring sessions take both branches
+    mixed = wrs.Batch(sessions, schedules=[wrs.SCHEDULE_PACKET if s % 2 else wrs.SCHEDULE_PER_PIXEL
+                                           for s in range(len(sessions))])
     st = wrs.new_status()
-    for sched in (wrs.SCHEDULE_PER_PIXEL, wrs.SCHEDULE_PERSISTENT, wrs.SCHEDULE_PACKET):
+    for b, sched in ((batch, wrs.SCHEDULE_PER_PIXEL), (batch, wrs.SCHEDULE_PERSISTENT),
+                     (batch, wrs.SCHEDULE_PACKET), (batch, wrs.SCHEDULE_PER_SESSION),
+                     (mixed, wrs.SCHEDULE_PER_SESSION)):
         for k, width in ((8, 2), (1, 4), (4, 2), (16, 4)):
-            for o in batch.outputs:
+            for o in b.outputs:
                 o.fill_(-1.0)
-            outs = wrs.trace_batched(batch, wrs.TraceParams(k_chunk=k, width=width, schedule=sched),
+            outs = wrs.trace_batched(b, wrs.TraceParams(k_chunk=k, width=width, schedule=sched),
                                      status=st)
             wrs.check_status(st)
             for o, r in zip(outs, refs):
