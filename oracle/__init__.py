@@ -24,6 +24,8 @@ marshals numpy arrays through ctypes.  Functions and the paper passage each one 
   colour the server sends (§4.1, §6; bit layout: reading of spec S11).
 * :func:`trace` -- first-hit / multi-hit ray tracing of the samples as semi-transparent spheres
   with constant colour (Fig. 2 caption, §4), front-to-back compositing (spec S6).
+* :func:`trace64` -- the same trace with every decision in binary64, and which pixels are ties
+  (a move of at most 1e-6 can change their hit list): the exclusion list of the parity budget.
 * :func:`trace_backward` -- the adjoint of that compositing (spec S7; not in the paper).
 * :func:`lbvh` -- Morton codes, sorted order and the binary radix tree of the LBVH (§4.1, §4.2).
 
@@ -95,6 +97,9 @@ def _load():
         lib.orc_bvh_free.argtypes = [P]
         lib.orc_trace.argtypes = [ctypes.POINTER(_Scene), P, ctypes.POINTER(_Cam), P,
                                   ctypes.c_int64, P, P, P, P, P, P, ctypes.c_int]
+        lib.orc_primary_ray64.argtypes = [ctypes.POINTER(_Cam), ctypes.c_int, ctypes.c_int, P, P]
+        lib.orc_trace64.argtypes = [ctypes.POINTER(_Scene), P, ctypes.POINTER(_Cam), P,
+                                    ctypes.c_int64, ctypes.c_double, P, P, P, P, P, ctypes.c_int]
         lib.orc_trace_backward.argtypes = [ctypes.POINTER(_Scene), P, ctypes.POINTER(_Cam), P, P,
                                            P, P, ctypes.c_int]
         lib.orc_lbvh.argtypes = [P, P, ctypes.c_float, ctypes.c_int64, ctypes.c_int32, P, P, P, P,
@@ -405,6 +410,54 @@ def trace(scene: Scene, cam, pixels: Optional[np.ndarray] = None, bvh="auto", th
     if rc != 0:
         raise ValueError("orc_trace failed")
     return {"rgba": rgba, "T": T, "nused": nused, "nhits": nhits, "amb": amb, "hash": hsh}
+
+
+TIE = 1e-6  # decision margin (scene units: the volume is the unit cube) below which a pixel is a tie
+
+
+def primary_ray64(cam, x: int, y: int):
+    """The ray of pixel (x, y) evaluated in binary64 from the camera's fields (spec S1):
+    returns (o, d) as float64[3] arrays."""
+    o = np.zeros(3, np.float64)
+    d = np.zeros(3, np.float64)
+    _load().orc_primary_ray64(ctypes.byref(_cam(cam)), int(x), int(y), o.ctypes.data, d.ctypes.data)
+    return o, d
+
+
+def trace64(scene: Scene, cam, pixels: Optional[np.ndarray] = None, bvh="auto", tie: float = TIE,
+            threads: int = 0):
+    """:func:`trace` with every decision in binary64: the primary ray, hit or miss, entry
+    distance and hit order (Fig. 2 caption, §4; spec S5, S6 evaluated in double).
+
+    Returns dict: rgba float64 [npix,4], T, nused, nhits as :func:`trace`, ``tie_kind`` [npix]
+    uint8 and ``tie`` [npix] bool (= tie_kind != 0).  A pixel is a tie when moving the ray or a
+    sphere by at most ``tie`` (scene units; the volume is the unit cube) can change which
+    spheres it composites or their order: bit 1 a composited sphere can be missed, bit 2 two
+    entry distances can swap (one of them among the composited hits), bit 4 a missed sphere can
+    be hit in front of the point where compositing stopped.  Only tie pixels can differ between
+    this image and one whose decisions are taken in another precision.
+    """
+    lib = _load()
+    if isinstance(bvh, str):
+        bvh = BVH(scene) if scene.splats.n > 0 else None
+    if pixels is None:
+        npix = cam.width * cam.height
+        pix = None
+    else:
+        pix = _c(pixels, np.int32)
+        npix = pix.size
+    rgba = np.zeros((npix, 4), np.float64)
+    T = np.zeros(npix, np.float64)
+    nused = np.zeros(npix, np.int32)
+    nhits = np.zeros(npix, np.int32)
+    kind = np.zeros(npix, np.uint8)
+    sc = scene._c()
+    rc = lib.orc_trace64(ctypes.byref(sc), None if bvh is None else bvh.h, ctypes.byref(_cam(cam)),
+                         _ptr(pix), int(npix), float(tie), rgba.ctypes.data, T.ctypes.data,
+                         nused.ctypes.data, nhits.ctypes.data, kind.ctypes.data, int(threads))
+    if rc != 0:
+        raise ValueError("orc_trace64 failed")
+    return {"rgba": rgba, "T": T, "nused": nused, "nhits": nhits, "tie_kind": kind, "tie": kind != 0}
 
 
 def trace_backward(scene: Scene, cam, dL_dimg: np.ndarray, bvh="auto", threads: int = 0):

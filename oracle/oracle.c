@@ -797,6 +797,202 @@ int orc_trace(const orc_scene* s, const void* bvh, const orc_camera* cam, const 
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* The same trace with every decision in binary64 (the plain reading of Fig. 2's transparent   */
+/* spheres hit by the client's rays, §4): primary ray, hit or miss, entry distance and hit     */
+/* order all in double.  Kept apart from the binary32 path above; nothing is shared but the    */
+/* soft-edge weight, the BVH (an accelerator only) and the thread pool.                         */
+/*                                                                                              */
+/* Ties.  A pixel is a tie at distance t when moving the ray or a sphere by at most t (scene   */
+/* units) can change which spheres the pixel composites or their order: a composited sphere    */
+/* that the ray grazes within t, a near miss within t that could enter in front of the point   */
+/* where compositing stopped, two hits whose entry distances can swap (their ranges under such */
+/* a move overlap; a grazing hit's entry distance is ill-conditioned and its range is wide),   */
+/* or a sphere whose exit is within reach of the eye.  Arithmetic of another precision decides */
+/* such pixels either way; nothing else can differ.                                            */
+/* ------------------------------------------------------------------------------------------ */
+void orc_primary_ray64(const orc_camera* c, int x, int y, double o[3], double d[3]) {
+    double W = c->width, H = c->height, th = c->tan_half_fovy;
+    double u = ((2.0 * x + 1.0) / W - 1.0) * th * (W / H);
+    double v = (1.0 - (2.0 * y + 1.0) / H) * th;
+    double e[3], len = 0;
+    for (int k = 0; k < 3; k++) {
+        e[k] = (double)c->fwd[k] + u * (double)c->right[k] + v * (double)c->up[k];
+        len += e[k] * e[k];
+    }
+    len = sqrt(len);
+    for (int k = 0; k < 3; k++) {
+        d[k] = e[k] / len;
+        o[k] = c->eye[k];
+    }
+}
+
+typedef struct {
+    double key, rho;
+    double key_lo, key_hi;      /* range of the entry distance under a move of at most t */
+    int could_miss, could_hit;  /* the hit decision can flip under such a move */
+    uint32_t id; int32_t idx; int hit;
+} hit64_t;
+
+typedef struct { hit64_t* h; int64_t n, cap; } hitlist64;
+
+static void hl64_push(hitlist64* L, hit64_t h) {
+    if (L->n == L->cap) {
+        L->cap = L->cap ? 2 * L->cap : 64;
+        L->h = (hit64_t*)realloc(L->h, sizeof(hit64_t) * (size_t)L->cap);
+    }
+    L->h[L->n++] = h;
+}
+
+static int cmp_hit64(const void* a, const void* b) {
+    const hit64_t* x = (const hit64_t*)a;
+    const hit64_t* y = (const hit64_t*)b;
+    if (x->key < y->key) return -1;
+    if (x->key > y->key) return 1;
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+static double pos0(double x) { return x > 0 ? x : 0.0; }
+
+/* The ray-sphere test of S5 in binary64 on a binary64 ray: with oc = c - o, b = oc.d,
+ * f = oc - b d and q = r^2 - |f|^2, a hit iff q > 0 and the exit distance b + sqrt(q) > 0;
+ * key = max(b - sqrt(q), 0).  A move of at most t shifts b by up to t and the ray's distance
+ * from the centre |f| by up to t, which bounds the entry and exit distances. */
+static void sphere_f64(const double o[3], const double d[3], const float* c, double r, double t,
+                       hit64_t* h) {
+    double oc[3], f[3], b = 0, ff = 0;
+    for (int k = 0; k < 3; k++) oc[k] = (double)c[k] - o[k];
+    for (int k = 0; k < 3; k++) b += oc[k] * d[k];
+    for (int k = 0; k < 3; k++) { f[k] = oc[k] - b * d[k]; ff += f[k] * f[k]; }
+    double dist = sqrt(ff);
+    double q = r * r - ff;
+    double sq = q > 0 ? sqrt(q) : 0.0;
+    h->rho = r > 0 ? dist / r : 1.0;
+    h->hit = q > 0 && b + sq > 0;
+    h->key = pos0(b - sq);
+    double dn = pos0(dist - t), df = dist + t;
+    double sq_max = dn < r ? sqrt(r * r - dn * dn) : -1.0; /* -1: no hit under any move */
+    double sq_min = df < r ? sqrt(r * r - df * df) : 0.0;
+    h->key_lo = sq_max >= 0 ? pos0(b - t - sq_max) : INFINITY;
+    h->key_hi = pos0(b + t - sq_min);
+    int far_pos = sq_max >= 0 && b + t + sq_max > 0;   /* some move gives an exit beyond the eye */
+    int far_neg = !(df < r) || b - t + sq_min <= 0;    /* some move gives a miss */
+    h->could_hit = !h->hit && far_pos;
+    h->could_miss = h->hit && far_neg;
+}
+
+typedef struct {
+    const orc_scene* s; const orc_camera* cam; const orc_bvh* B; const int32_t* pix;
+    double tie;
+    double* rgba_out; double* T_out; int32_t* nused; int32_t* nhits; uint8_t* tie_out;
+    hitlist64* hits; hitlist64* near; /* per thread: hits, and misses a move of t can turn into hits */
+} tr64_ctx;
+
+static void test_prim64(const tr64_ctx* c, int32_t i, const double o[3], const double d[3],
+                        hitlist64* hits, hitlist64* near) {
+    const orc_scene* s = c->s;
+    double sc = s->scale ? (double)s->scale[i] : (double)s->global_scale;
+    if (!(sc > 0)) sc = 0;
+    double r = sc * (double)s->pos_r[4 * (int64_t)i + 3];
+    hit64_t h;
+    sphere_f64(o, d, s->pos_r + 4 * (int64_t)i, r, c->tie, &h);
+    h.id = s->id[i];
+    h.idx = i;
+    if (h.hit) hl64_push(hits, h);
+    else if (h.could_hit) hl64_push(near, h);
+}
+
+static void tr64_pixel(void* vctx, int64_t i, int tid) {
+    tr64_ctx* c = (tr64_ctx*)vctx;
+    const orc_scene* s = c->s;
+    int64_t p = c->pix ? c->pix[i] : i;
+    int W = c->cam->width;
+    double o[3], d[3];
+    orc_primary_ray64(c->cam, (int)(p % W), (int)(p / W), o, d);
+    hitlist64* L = &c->hits[tid];
+    hitlist64* N = &c->near[tid];
+    L->n = 0;
+    N->n = 0;
+    if (s->n > 0 && !c->B) {
+        for (int64_t k = 0; k < s->n; k++) test_prim64(c, (int32_t)k, o, d, L, N);
+    } else if (s->n > 0) {
+        double eps = 1e-6 * (1.0 + fabs(o[0]) + fabs(o[1]) + fabs(o[2])) + 2.0 * c->tie;
+        int32_t stack[256];
+        int sp = 0;
+        stack[sp++] = 0;
+        while (sp) {
+            const obvh_node* nd = &c->B->nodes[stack[--sp]];
+            if (!box_hit(nd->lo, nd->hi, o, d, eps)) continue;
+            if (nd->left < 0) {
+                for (int32_t a = nd->first; a < nd->first + nd->count; a++)
+                    test_prim64(c, c->B->prim[a], o, d, L, N);
+            } else {
+                stack[sp++] = nd->left;
+                stack[sp++] = nd->right;
+            }
+        }
+    }
+    qsort(L->h, (size_t)L->n, sizeof(hit64_t), cmp_hit64);
+    /* front-to-back compositing (S6), as in the binary32 path */
+    double T = 1.0, C[3] = {0, 0, 0};
+    int64_t used = 0;
+    for (; used < L->n; used++) {
+        if (s->max_hits > 0 && used == s->max_hits) break;
+        if (T <= s->t_stop) break;
+        const hit64_t* h = &L->h[used];
+        double w = soft_w(h->rho, s->beta);
+        double op = s->opacity ? (double)s->opacity[h->idx] : 1.0;
+        const float* col = s->rgba + 4 * (int64_t)h->idx;
+        double x = op * (double)col[3] * w;
+        double a = x < 0 ? 0 : (x > 1 ? 1 : x);
+        for (int ch = 0; ch < 3; ch++) C[ch] += T * (op * w) * (double)col[ch];
+        T *= 1.0 - a;
+    }
+    double* out = c->rgba_out + 4 * i;
+    out[0] = C[0]; out[1] = C[1]; out[2] = C[2]; out[3] = 1.0 - T;
+    if (c->T_out) c->T_out[i] = T;
+    if (c->nused) c->nused[i] = (int32_t)used;
+    if (c->nhits) c->nhits[i] = (int32_t)L->n;
+    if (!c->tie_out) return;
+    /* Which decisions can change the pixel.  When compositing stopped early (hit limit or
+     * T_stop), a sphere that cannot enter in front of the last composited hit changes nothing. */
+    uint8_t flag = 0;
+    /* compositing takes no further hit: hits left over, T at or below T_stop, or the limit */
+    int stopped = used < L->n || T <= s->t_stop || (s->max_hits > 0 && used >= s->max_hits);
+    double reach = INFINITY; /* largest entry distance at which a sphere still changes the pixel */
+    if (stopped) reach = used > 0 ? L->h[used - 1].key_hi : -INFINITY;
+    for (int64_t k = 0; k < used; k++) {
+        const hit64_t* a = &L->h[k];
+        if (a->could_miss) flag |= 1;
+        for (int64_t j = k + 1; j < L->n; j++) {
+            const hit64_t* b = &L->h[j];
+            if (a->key_hi == 0 && b->key_hi == 0) continue; /* both around the eye: id order */
+            if (b->key_lo <= a->key_hi) flag |= 2;
+        }
+    }
+    for (int64_t k = 0; k < N->n; k++)
+        if (N->h[k].key_lo <= reach) flag |= 4;
+    c->tie_out[i] = flag;
+}
+
+int orc_trace64(const orc_scene* s, const void* bvh, const orc_camera* cam, const int32_t* pix,
+                int64_t npix, double tie, double* rgba_out, double* T_out, int32_t* nused,
+                int32_t* nhits, uint8_t* tie_out, int nthreads) {
+    if (!s || !cam || !rgba_out || !(tie >= 0)) return -1;
+    if (!pix) npix = (int64_t)cam->width * cam->height;
+    int nt = nthreads > 0 ? nthreads : orc_default_threads();
+    if (nt > 256) nt = 256;
+    hitlist64* hits = (hitlist64*)calloc((size_t)nt, sizeof(hitlist64));
+    hitlist64* near = (hitlist64*)calloc((size_t)nt, sizeof(hitlist64));
+    tr64_ctx c = {s, cam, (const orc_bvh*)bvh, pix, tie, rgba_out, T_out, nused, nhits, tie_out,
+                  hits, near};
+    orc_parallel(tr64_pixel, &c, npix, nt);
+    for (int t = 0; t < nt; t++) { free(hits[t].h); free(near[t].h); }
+    free(hits);
+    free(near);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* S7: adjoint of the ordered compositing, binary64.  Gradients in compacted splat order.       */
 /* ------------------------------------------------------------------------------------------ */
 typedef struct {
