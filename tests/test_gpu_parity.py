@@ -387,70 +387,8 @@ def test_batched_equals_sequential_bitwise(wrs):
 
 
 # ---------------------------------------------------------------------------------------------
-# backward
+# multi-view backward (the adjoint against the oracle: tests/test_gpu_backward.py)
 # ---------------------------------------------------------------------------------------------
-def _bwd_instance(wrs, W=64, H=64, seed=0):
-    rgba, depth = synth.synthetic_server_image(W, H, seed, hole_frac=0.1)
-    srv = synth.server_camera(1.4, 30.0, W, H)
-    ref_sp = oracle.unproject(rgba, depth, srv)
-    n = ref_sp.n
-    rng = np.random.default_rng(seed)
-    op = rng.uniform(0.3, 1.0, n).astype(np.float32)
-    sc = rng.uniform(1.0, 2.5, n).astype(np.float32)
-    cli = synth.orbit(srv, (0.3, 1.0, 0.0), 10.0)
-    g = rng.normal(size=(cli.width * cli.height, 4))
-    return rgba, depth, srv, cli, ref_sp, op, sc, g
-
-
-def _rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
-
-
-@pytest.mark.parametrize("beta,k,sched,width", [(0.25, 8, 0, 2), (0.25, 1, 0, 4), (0.0, 4, 0, 2),
-                                                (0.25, 1, 1, 2), (0.25, 4, 1, 4), (0.0, 2, 1, 4),
-                                                (0.25, 4, 2, 4), (0.0, 1, 2, 4), (0.25, 16, 2, 4)])
-def test_backward_matches_oracle_adjoint(wrs, beta, k, sched, width):
-    rgba, depth, srv, cli, ref_sp, op, sc, g = _bwd_instance(wrs)
-    n = ref_sp.n
-    sp = _gpu_splats(wrs, rgba, depth, srv)
-    bvh, srt = wrs.build_lbvh(sp, 1, radius_scale=_cuda(sc))
-    params = wrs.TraceParams(edge_softness=beta, k_chunk=k, schedule=sched, width=width)
-    st = wrs.new_status()
-    gr, go, gs = wrs.trace_backward(bvh, srt, cli, _cuda(g.astype(np.float32).reshape(cli.height, cli.width, 4)),
-                                    params, opacity=_cuda(op), radius_scale=_cuda(sc), status=st)
-    wrs.check_status(st)
-    scene = oracle.Scene(ref_sp, scale=sc, opacity=op, beta=beta)
-    # the oracle adjoint takes the upstream gradient the GPU saw (rounded to binary32)
-    rr, ro, rs = oracle.trace_backward(scene, cli, g.astype(np.float32).astype(np.float64))
-    assert _rel(gr.cpu().numpy()[:n], rr) < 1e-3
-    assert _rel(go.cpu().numpy()[:n], ro) < 1e-3
-    if beta > 0:
-        assert np.abs(rs).max() > 0
-        assert _rel(gs.cpu().numpy()[:n], rs) < 1e-3
-    else:
-        assert np.all(gs.cpu().numpy()[:n] == 0)
-
-
-def test_autograd_function_matches_backward(wrs):
-    rgba, depth, srv, cli, ref_sp, op, sc, g = _bwd_instance(wrs, 48, 40, 3)
-    n = ref_sp.n
-    sp = _gpu_splats(wrs, rgba, depth, srv)
-    col = torch.tensor(ref_sp.rgba, device="cuda", requires_grad=True)
-    opt = torch.tensor(op, device="cuda", requires_grad=True)
-    sct = torch.tensor(sc, device="cuda", requires_grad=True)
-    params = wrs.TraceParams(edge_softness=0.25)
-    img = wrs.render(sp, cli, col, opt, sct, params)
-    gt = _cuda(g.astype(np.float32).reshape(cli.height, cli.width, 4))
-    (img * gt).sum().backward()
-    scene = oracle.Scene(ref_sp, scale=sc, opacity=op, beta=0.25)
-    ref_img = oracle.trace(scene, cli)["rgba"]
-    _assert_close(img.detach().cpu().numpy(), ref_img, "autograd forward")
-    rr, ro, rs = oracle.trace_backward(scene, cli, g.astype(np.float32).astype(np.float64))
-    assert _rel(col.grad.cpu().numpy(), rr) < 1e-3
-    assert _rel(opt.grad.cpu().numpy(), ro) < 1e-3
-    assert _rel(sct.grad.cpu().numpy(), rs) < 1e-3
-
-
 def test_render_views_accumulates_the_per_view_gradients(wrs):
     """Several views from one LBVH build: images equal the single-view renders bitwise, and the
     accumulated gradients equal the sum of the per-view gradients (float atomics: up to rounding)."""
