@@ -156,6 +156,12 @@ const char* wrs_last_error(void);
 size_t wrs_session_size(void);
 size_t wrs_camera_size(void);
 
+/* Colour weight of the server frame of age `age` (0 = newest) in a window accumulated with
+ * wrs_unproject_append: decay^age by repeated binary32 multiplication (spec S3a; the paper names
+ * accumulation over frames as future work, §6, without a rule).  Host function, no GPU work;
+ * decay outside (0, 1] returns NaN. */
+float wrs_window_weight(float decay, uint32_t age);
+
 /* Read the device status word (synchronises the stream), clear it, and return WRS_OK or
  * WRS_ERR_DEVICE (with the set bits described by wrs_last_error). */
 int wrs_check_status(int32_t* status, wrs_stream_t stream);
@@ -256,9 +262,13 @@ int wrs_unproject_append(const float* rgba, const float* depth, const wrs_camera
  * call.  This entry point allocates nothing: its work buffer is a fixed 512 KiB array inside the
  * library's device image, which every GPU that loads the library keeps until the process exits.
  * Inputs and outputs are the caller's, exactly as for wrs_unproject, with the same results.
- *  - Limit: width * height <= 67,108,864 (8192 x 8192); larger images return WRS_ERR_CAPACITY.
+ *  - Limit: width * height <= 67,108,864 pixels (for example 8192 x 8192 or 16384 x 4096);
+ *    larger images return WRS_ERR_CAPACITY.
  *  - The first call on a device looks up that device's address of the array (with the device
- *    current) and caches it; make that first call before any stream capture.
+ *    current) and caches it for the rest of the process; make that first call before any stream
+ *    capture.  The cached address dies with the device's primary context: after cudaDeviceReset
+ *    (or anything else that destroys that context) do not call this entry point again in the
+ *    same process.
  *  - All calls share the one array per device, which keeps the last call's contents.  Each call
  *    writes every entry it reads before reading it, so nothing needs clearing, but calls that
  *    overlap on the GPU (other streams, other host threads) race on it: serialise them. */

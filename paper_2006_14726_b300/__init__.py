@@ -126,6 +126,7 @@ _sig("wrs_last_error", ctypes.c_char_p)
 _sig("wrs_session_size", _Z)
 _sig("wrs_camera_size", _Z)
 _sig("wrs_check_status", _I, _P, _P)
+_sig("wrs_window_weight", _F, _F, _U)
 _sig("wrs_raycast_volume", _I, _P, _I, _I, _I, _I, _P, ctypes.POINTER(Camera), _F, _F, _P, _P, _P)
 _sig("wrs_raycast_volume_heuristic", _I, _P, _I, _I, _I, _I, _P, ctypes.POINTER(Camera), _F, _I, _F,
      _P, _P, _P)
@@ -363,6 +364,15 @@ def unproject(rgba: torch.Tensor, depth: torch.Tensor, cam, radius_mode: int = R
     return out
 
 
+def window_weight(decay: float, age: int) -> float:
+    """Colour weight of the server frame of age ``age`` in an accumulated window
+    (wrs_window_weight: decay^age in binary32)."""
+    w = float(_lib.wrs_window_weight(float(decay), int(age)))
+    if w != w:
+        raise ValueError("decay must lie in (0, 1]")
+    return w
+
+
 def unproject_append(rgba: torch.Tensor, depth: torch.Tensor, cam, out: SplatBuffers,
                      weight: float = 1.0, id_base: int = 0, radius_mode: int = RADIUS_FOOTPRINT,
                      voxel_diag: float = 0.0, status: Optional[torch.Tensor] = None,
@@ -587,12 +597,14 @@ def session_tiles(width: int, height: int) -> int:
 def sparse_schedules(sessions: Sequence[Tuple[LBVH, SplatBuffers, object]],
                      ratio: float = 2.0) -> List[int]:
     """Per-session schedules for SCHEDULE_PER_SESSION: the warp-shared traversal where the client
-    image has at least ``ratio`` pixels per splat slot (neighbouring rays then hit the same
-    splats), one thread per pixel elsewhere."""
+    image has at least ``ratio`` pixels per splat (neighbouring rays then hit the same splats),
+    one thread per pixel elsewhere.  The splat counts are read back from the device once (one
+    synchronisation), so a server image with a large empty background counts as sparse."""
+    counts = [sp.count() for _, sp, _ in sessions]
     out = []
-    for _, sp, cam in sessions:
+    for (_, _, cam), n in zip(sessions, counts):
         c = _cam(cam)
-        out.append(SCHEDULE_PACKET if c.width * c.height >= ratio * sp.capacity
+        out.append(SCHEDULE_PACKET if c.width * c.height >= ratio * max(n, 1)
                    else SCHEDULE_PER_PIXEL)
     return out
 
@@ -605,7 +617,7 @@ class Batch:
                  schedules: Optional[Sequence[int]] = None):
         """``schedules``: per session SCHEDULE_PER_PIXEL or SCHEDULE_PACKET, used by launches with
         ``schedule=SCHEDULE_PER_SESSION`` (default: the packet traversal for sessions with at
-        least 2 client pixels per splat slot, see :func:`sparse_schedules`)."""
+        least 2 client pixels per splat, see :func:`sparse_schedules`)."""
         device = device or torch.device("cuda")
         n = len(sessions)
         if schedules is None:

@@ -16,16 +16,13 @@ import torch
 
 from . import (LBVH, RADIUS_FOOTPRINT, SplatBuffers, TraceParams, _cam, _scratch, build_lbvh,
                lbvh_scratch_bytes, new_status, trace, unproject, unproject_append,
-               unproject_scratch_bytes)
+               unproject_scratch_bytes, window_weight)
 
 
 def window_weights(frames: int, decay: float = 1.0):
-    """decay^g for g = 0..frames-1, by repeated binary32 multiplication (spec S3a)."""
-    w = torch.ones(frames, dtype=torch.float32)
-    d = torch.tensor(decay, dtype=torch.float32)
-    for g in range(1, frames):
-        w[g] = w[g - 1] * d
-    return [float(x) for x in w]
+    """Colour weight of each frame of the window, newest first (wrs_window_weight: decay^g by
+    repeated binary32 multiplication, spec S3a)."""
+    return [window_weight(decay, g) for g in range(frames)]
 
 
 class FrameWindow:

@@ -33,6 +33,13 @@ size_t wrs_session_size(void) { return sizeof(wrs_session); }
 
 size_t wrs_camera_size(void) { return sizeof(wrs_camera); }
 
+float wrs_window_weight(float decay, uint32_t age) {
+    if (!(decay > 0.0f && decay <= 1.0f)) return __builtin_nanf("");
+    float w = 1.0f;
+    for (uint32_t g = 0; g < age; g++) w = w * decay;  // one binary32 rounding per frame of age
+    return w;
+}
+
 int wrs_check_status(int32_t* status, wrs_stream_t stream) {
     if (!status) return wrs::fail(WRS_ERR_ARG, "wrs_check_status: status is NULL");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

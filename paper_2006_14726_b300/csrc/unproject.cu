@@ -553,7 +553,8 @@ extern "C" int wrs_unproject_static(const float* rgba, const float* depth, const
     if (npix > kStaticMaxPixels)
         return wrs::fail(WRS_ERR_CAPACITY,
                          "%s: image of %zu pixels exceeds the fixed work buffer's limit of %u "
-                         "pixels (8192 x 8192); use wrs_unproject with caller scratch",
+                         "pixels (width x height, e.g. 8192 x 8192 or 16384 x 4096); use "
+                         "wrs_unproject with caller scratch",
                          fn, npix, kStaticMaxPixels);
     if (out->capacity < npix)
         return wrs::fail(WRS_ERR_CAPACITY, "%s: splat capacity %u < %zu pixels", fn, out->capacity,

@@ -174,3 +174,17 @@ def test_buffer_checks(wrs):
     with pytest.raises(ValueError, match="CUDA"):
         wrs._buf(torch.zeros(8), 8, torch.float32, "x")
     assert wrs._buf(None, 8, torch.float32, "x") is None
+
+
+def test_window_weight_is_the_oracle_power(wrs):
+    """wrs_window_weight (host function) against the oracle's binary32 powers of the decay."""
+    import numpy as np
+
+    import oracle
+    for decay in (1.0, 0.9, 0.75, 0.5, 0.3333):
+        ref = oracle.window_weights(9, decay)
+        got = np.array([wrs.window_weight(decay, g) for g in range(9)], np.float32)
+        assert np.array_equal(got.view(np.uint32), ref.view(np.uint32)), decay
+    for bad in (0.0, -0.5, 1.5, float("nan")):
+        with pytest.raises(ValueError):
+            wrs.window_weight(bad, 2)

@@ -201,7 +201,6 @@ def test_radix_tree_properties(orc, n, leaf, dup):
     lkey = [(int(codes[j * leaf]) << 32) | j for j in range(M)]  # index-augmented leaf keys
     for i, (a, b) in rng.items():
         assert i == a or i == b  # the node index is one end of its range (Karras numbering)
-        left = child[0] if False else None
         l_ref = int(ref["child"][i, 0])
         la, lb = (l_ref & 0x7FFFFFFF, l_ref & 0x7FFFFFFF) if l_ref < 0 else rng[l_ref]
         g = lb

