@@ -244,6 +244,7 @@ def unproject_interval(rgba: np.ndarray, depth_lo: np.ndarray, depth_hi: np.ndar
 
 
 STATUS_SPLAT_OVERFLOW = 8
+AMB_STOP64 = 4  # trace()["amb"] bit: a binary64 transmittance would stop at another hit
 
 
 def append_frame(acc: Optional[Splats], rgba: np.ndarray, depth: np.ndarray, cam, weight: float = 1.0,
@@ -384,8 +385,10 @@ def trace(scene: Scene, cam, pixels: Optional[np.ndarray] = None, bvh="auto", th
 
     Returns dict: rgba float64 [npix,4] (premultiplied), T [npix], nused [npix] (hits composited),
     nhits [npix] (all hits), amb [npix] (bit 1: a binary64 hit test would disagree, bit 2: a binary64
-    key would reorder the hits -- a diagnostic of the binary32 reading, not an exclusion), hash [npix]
-    (FNV-1a of the ids of the composited hits, in order).
+    key would reorder the hits, bit 4: the binary64 transmittance would stop at another hit than
+    the binary32 one the decision uses -- diagnostics of the binary32 reading, not exclusions;
+    a bit-4 pixel's image moves by about T_stop at most, the adjoint of its alpha by the later
+    hit's full weight), hash [npix] (FNV-1a of the ids of the composited hits, in order).
     ``bvh``: "auto" builds the oracle BVH, None = brute force, or a :class:`BVH`.
     """
     lib = _load()

@@ -7,9 +7,10 @@
  * library; the two share no source.
  *
  * Precision (the written spec, S0): every discrete decision -- volume sample above the depth
- * threshold, ray-sphere hit or miss, hit key, Morton code -- is taken in binary32 with the exact
- * operation sequence of the spec; every continuous quantity (colour, opacity, transmittance,
- * soft-edge weight, gradient) is computed in binary64.  Compile with -ffp-contract=off so that
+ * threshold, ray-sphere hit or miss, hit key, Morton code, the stop at T_stop -- is taken in
+ * binary32 with the exact operation sequence of the spec; every continuous quantity (colour,
+ * opacity, transmittance, soft-edge weight, gradient) is computed in binary64.  A second trace
+ * path (orc_trace64) takes every decision in binary64 instead.  Compile with -ffp-contract=off so that
  * the compiler never fuses a multiply and an add on its own.
  *
  * Pinning (tests/test_oracle_*.py): camera orientation against an independent projection; single
@@ -479,14 +480,17 @@ static inline float eff_radius(const float* pos_r, const float* scale, float gsc
     return s * pos_r[4 * i + 3];
 }
 
-/* returns 1 on a hit; *key = entry distance (binary32) */
-static int sphere32(const float o[3], const float d[3], const float c[3], float r, float* key) {
+/* returns 1 on a hit; *key = entry distance (binary32); *ff_out = squared distance of the ray
+ * from the centre (binary32, the same value the hit decision used) */
+static int sphere32(const float o[3], const float d[3], const float c[3], float r, float* key,
+                    float* ff_out) {
     float oc[3];
     for (int k = 0; k < 3; k++) oc[k] = c[k] - o[k];
     float b = fmaf(oc[2], d[2], fmaf(oc[1], d[1], oc[0] * d[0]));
     float f[3];
     for (int k = 0; k < 3; k++) f[k] = fmaf(-b, d[k], oc[k]);
     float ff = fmaf(f[2], f[2], fmaf(f[1], f[1], f[0] * f[0]));
+    *ff_out = ff;
     float q = fmaf(r, r, -ff);
     if (!(q > 0.0f)) return 0;
     float sq = sqrtf(q);
@@ -652,7 +656,10 @@ typedef struct {
     int32_t max_hits; double t_stop; double beta;
 } orc_scene;
 
-typedef struct { float key; uint32_t id; int32_t idx; double key64; int hit64; double rho; } hit_t;
+typedef struct {
+    float key; uint32_t id; int32_t idx; double key64; int hit64; double rho;
+    float rho32; /* |f| / r in binary32 from the decision's own |f|^2 (S0: feeds the stop decision) */
+} hit_t;
 
 static int cmp_hit(const void* a, const void* b) {
     const hit_t* x = (const hit_t*)a;
@@ -676,13 +683,14 @@ static void test_prim(const orc_scene* s, int32_t i, const float o[3], const flo
                       hitlist* L) {
     float r = eff_radius(s->pos_r, s->scale, s->global_scale, i);
     const float* c = s->pos_r + 4 * (int64_t)i;
-    float key;
-    double key64, rho;
-    int h32 = sphere32(o, d, c, r, &key);
+    float key = 0.0f, ff = 0.0f;
+    double key64 = 0.0, rho;
+    int h32 = sphere32(o, d, c, r, &key, &ff);
     int h64 = sphere64(o, d, c, r, &key64, &rho);
     if (h32 != h64) L->amb |= 1;
     if (!h32) return;
-    hit_t h = {key, s->id[i], i, key64, h64, rho};
+    float rho32 = r > 0.0f ? sqrtf(ff) / r : 1.0f;
+    hit_t h = {key, s->id[i], i, key64, h64, rho, rho32};
     hl_push(L, h);
 }
 
@@ -720,14 +728,31 @@ static void collect_hits(const orc_scene* s, const orc_bvh* B, const float o[3],
     }
 }
 
-/* Front-to-back compositing of the sorted hits (S6); returns the number of hits used. */
+/* S6 soft edge in binary32 (feeds only the stop decision) */
+static float soft_w32(float rho, float beta) {
+    if (beta <= 0.0f || rho <= 1.0f - beta) return 1.0f;
+    float u = fmaxf((1.0f - rho) / beta, 0.0f);
+    return u * u * (3.0f - 2.0f * u);
+}
+
+/* Front-to-back compositing of the sorted hits (S6); returns the number of hits used.
+ * Colours, alphas and the transmittance are binary64.  The decision to stop at T <= T_stop is
+ * a discrete decision, taken (S0) on the binary32 transmittance: alpha = clamp((o a) w) with w
+ * from the binary32 distance ratio, T <- T (1 - alpha), compared with T_stop in binary32.
+ * *stop64 (optional) is set when the binary64 transmittance would have stopped at another hit
+ * (a diagnostic: such a pixel's image moves by about T_stop at most, but the derivatives of its
+ * alpha with respect to the earlier hits depend on the later hit). */
 static int64_t composite(const orc_scene* s, const hitlist* L, double out[4], double* T_out,
-                         double* T_before /* optional, per used hit */) {
+                         double* T_before /* optional, per used hit */, int* stop64) {
+    const float t_stop32 = (float)s->t_stop, beta32 = (float)s->beta;
     double T = 1.0, C[3] = {0, 0, 0};
+    float T32 = 1.0f;
+    int differ = 0;
     int64_t k = 0;
     for (; k < L->n; k++) {
         if (s->max_hits > 0 && k == s->max_hits) break;
-        if (T <= s->t_stop) break;
+        if ((T <= s->t_stop) != (T32 <= t_stop32)) differ = 1;
+        if (T32 <= t_stop32) break;
         const hit_t* h = &L->h[k];
         double w = soft_w(h->rho, s->beta);
         double op = s->opacity ? (double)s->opacity[h->idx] : 1.0;
@@ -737,9 +762,15 @@ static int64_t composite(const orc_scene* s, const hitlist* L, double out[4], do
         if (T_before) T_before[k] = T;
         for (int ch = 0; ch < 3; ch++) C[ch] += T * (op * w) * (double)c[ch];
         T *= 1.0 - a;
+        float op32 = s->opacity ? s->opacity[h->idx] : 1.0f;
+        float w32 = beta32 > 0.0f ? soft_w32(h->rho32, beta32) : 1.0f;
+        float x32 = op32 * c[3] * w32;
+        float a32 = fminf(fmaxf(x32, 0.0f), 1.0f);
+        T32 = T32 * (1.0f - a32);
     }
     out[0] = C[0]; out[1] = C[1]; out[2] = C[2]; out[3] = 1.0 - T;
     if (T_out) *T_out = T;
+    if (stop64) *stop64 = differ;
     return k;
 }
 
@@ -758,11 +789,12 @@ static void tr_pixel(void* vctx, int64_t i, int tid) {
     hitlist* L = &c->lists[tid];
     collect_hits(c->s, c->B, o, d, L);
     double T;
-    int64_t used = composite(c->s, L, c->rgba_out + 4 * i, &T, NULL);
+    int stop64 = 0;
+    int64_t used = composite(c->s, L, c->rgba_out + 4 * i, &T, NULL, &stop64);
     if (c->T_out) c->T_out[i] = T;
     if (c->nused) c->nused[i] = (int32_t)used;
     if (c->nhits) c->nhits[i] = (int32_t)L->n;
-    if (c->amb) c->amb[i] = (uint8_t)L->amb;
+    if (c->amb) c->amb[i] = (uint8_t)(L->amb | (stop64 ? 4 : 0));
     if (c->hash) { /* FNV-1a over the ids of the used hits, in order */
         uint64_t h = 1469598103934665603ull;
         for (int64_t k = 0; k < used; k++) { h ^= L->h[k].id; h *= 1099511628211ull; }
@@ -1013,7 +1045,7 @@ static void bw_pixel(void* vctx, int64_t p, int tid) {
     if (L->n == 0) return;
     double* Tb = (double*)malloc(sizeof(double) * (size_t)L->n);
     double out[4], Tend;
-    int64_t used = composite(s, L, out, &Tend, Tb);
+    int64_t used = composite(s, L, out, &Tend, Tb, NULL);
     double S[3] = {0, 0, 0}, P = 1.0; /* suffix composite and suffix transmittance */
     double* gr = c->g_rgba[tid];
     double* go = c->g_op[tid];

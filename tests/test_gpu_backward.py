@@ -152,7 +152,7 @@ def test_backward_diff_workload_one_view(wrs, diff_scene, sched, k):
     wrs.check_status(st)
     scene = oracle.Scene(ref_sp, scale=sc, opacity=op, beta=0.25)
     rr, ro, rs = oracle.trace_backward(scene, cli, g.astype(np.float64))
-    assert np.count_nonzero(rs) > n // 4
+    assert np.count_nonzero(rs) > n // 10  # splats some ray meets inside the soft-edge band
     what = f"diff 512^2 schedule={sched} K={k}"
     assert_elementwise(gr.cpu().numpy()[:n], rr, f"{what} rgba")
     assert_elementwise(go.cpu().numpy()[:n], ro, f"{what} opacity")
