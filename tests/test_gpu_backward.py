@@ -14,7 +14,12 @@ sign make that sum larger than |g| itself, which the ATOL part covers up to a su
 the largest gradient.  With a soft edge the distance of the ray from a centre is binary32
 (relative error near 1e-5 at the rim) and enters the weight's derivative, whose slope is at
 most 6 / beta^2 = 96 at beta = 0.25: about 1e-3 relative on rim terms of the scale gradient,
-hence RTOL.
+hence RTOL.  The radius-scale group has a larger absolute part, ATOL_SCALE = 2e-3: the binary32
+ratio rho = |f| / r is off by up to about 5 ulp of the eye-to-centre distance over r (|f| is
+the small residual of two binary32 vectors of length |oc|), 4e-4 at the differentiation
+workload (eye 1.4 away, r near 1e-3), so the weight's derivative (slope at most 96) is off by up
+to 0.04 against its largest value 1.5 / beta = 6: 0.6 % of the largest scale term in the worst
+case, a few tenths of that typically (as in the images).
 
 Cases: the 64x64 instance (every schedule, K and node width), the autograd Function, the
 differentiation workload's size (512^2 server image of the 256^3 volume, 262,144 splats, one
@@ -32,6 +37,7 @@ pytestmark = pytest.mark.gpu
 
 RTOL = 1e-3
 ATOL = 1e-4
+ATOL_SCALE = 2e-3
 
 
 @pytest.fixture(scope="module")
@@ -94,7 +100,7 @@ def test_backward_matches_oracle_adjoint(wrs, beta, k, sched, width):
     assert_elementwise(go.cpu().numpy()[:n], ro, f"{what} opacity")
     if beta > 0:
         assert np.abs(rs).max() > 0
-        assert_elementwise(gs.cpu().numpy()[:n], rs, f"{what} scale")
+        assert_elementwise(gs.cpu().numpy()[:n], rs, f"{what} scale", atol=ATOL_SCALE)
     else:
         assert np.all(gs.cpu().numpy()[:n] == 0)
 
@@ -116,7 +122,7 @@ def test_autograd_function_matches_oracle(wrs):
     rr, ro, rs = oracle.trace_backward(scene, cli, g.astype(np.float64))
     assert_elementwise(col.grad.cpu().numpy(), rr, "autograd rgba")
     assert_elementwise(opt.grad.cpu().numpy(), ro, "autograd opacity")
-    assert_elementwise(sct.grad.cpu().numpy(), rs, "autograd scale")
+    assert_elementwise(sct.grad.cpu().numpy(), rs, "autograd scale", atol=ATOL_SCALE)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -156,7 +162,7 @@ def test_backward_diff_workload_one_view(wrs, diff_scene, sched, k):
     what = f"diff 512^2 schedule={sched} K={k}"
     assert_elementwise(gr.cpu().numpy()[:n], rr, f"{what} rgba")
     assert_elementwise(go.cpu().numpy()[:n], ro, f"{what} opacity")
-    assert_elementwise(gs.cpu().numpy()[:n], rs, f"{what} scale")
+    assert_elementwise(gs.cpu().numpy()[:n], rs, f"{what} scale", atol=ATOL_SCALE)
 
 
 def test_backward_diff_workload_eight_views_one_launch(wrs, diff_scene):
@@ -184,7 +190,7 @@ def test_backward_diff_workload_eight_views_one_launch(wrs, diff_scene):
         rs += c
     assert_elementwise(gr.cpu().numpy()[:n], rr, "diff 8 views rgba")
     assert_elementwise(go.cpu().numpy()[:n], ro, "diff 8 views opacity")
-    assert_elementwise(gs.cpu().numpy()[:n], rs, "diff 8 views scale")
+    assert_elementwise(gs.cpu().numpy()[:n], rs, "diff 8 views scale", atol=ATOL_SCALE)
 
 
 # ---------------------------------------------------------------------------------------------
