@@ -131,9 +131,10 @@ struct BoxRay {
 __device__ __forceinline__ BoxRay make_box_ray(const Ray& r, float eps) {
     auto guard = [](float v) { return fabsf(v) < 1e-12f ? copysignf(1e-12f, v) : v; };
     BoxRay b;
-    b.ix = 1.0f / guard(r.d.x);
-    b.iy = 1.0f / guard(r.d.y);
-    b.iz = 1.0f / guard(r.d.z);
+    // correctly rounded reciprocals (the value of 1.0f / x, without the division's slow path)
+    b.ix = __frcp_rn(guard(r.d.x));
+    b.iy = __frcp_rn(guard(r.d.y));
+    b.iz = __frcp_rn(guard(r.d.z));
     b.lx = -(r.o.x + eps) * b.ix;
     b.ly = -(r.o.y + eps) * b.iy;
     b.lz = -(r.o.z + eps) * b.iz;

@@ -226,8 +226,7 @@ __device__ __forceinline__ int64_t visit_node4(const Scene& sc, const Ray& ray,
     cswap(key[1], r[1], key[3], r[3]);
     cswap(key[1], r[1], key[2], r[2]);
     if (!(key[0] < kInf)) return kLeafBit;
-    const int extra = (key[1] < kInf) + (key[2] < kInf) + (key[3] < kInf);
-    if (sp + extra > wrs::kStack) return -1;
+    if (sp > wrs::kStack - 3) return -1;  // room for the (at most three) pushes: one compare
     if (key[3] < kInf) stack[sp++] = make_entry<E>(r[3], key[3]);
     if (key[2] < kInf) stack[sp++] = make_entry<E>(r[2], key[2]);
     if (key[1] < kInf) stack[sp++] = make_entry<E>(r[1], key[1]);
@@ -420,8 +419,7 @@ __device__ __forceinline__ int64_t visit_node4_packet(const Scene& sc, const Ray
     cswap(key[1], r[1], key[3], r[3]);
     cswap(key[1], r[1], key[2], r[2]);
     if (!(key[0] < kInf)) return kLeafBit;
-    const int extra = (key[1] < kInf) + (key[2] < kInf) + (key[3] < kInf);
-    if (sp + extra > wrs::kStack) return -1;
+    if (sp > wrs::kStack - 3) return -1;  // room for the (at most three) pushes: one compare
     if (key[3] < kInf) stack[sp++] = stack_entry(r[3], key[3]);
     if (key[2] < kInf) stack[sp++] = stack_entry(r[2], key[2]);
     if (key[1] < kInf) stack[sp++] = stack_entry(r[1], key[1]);
