@@ -902,8 +902,11 @@ __global__ void __launch_bounds__(128, WRS_BATCHED_PACKET_MIN_BLOCKS) k_trace_ba
 
 // Multi-session trace with a schedule per session: the warp's tile belongs to one session, whose
 // schedule field picks one thread per pixel or one warp-shared traversal (a warp-uniform branch).
+#ifndef WRS_BATCHED_MIXED_MIN_BLOCKS
+#define WRS_BATCHED_MIXED_MIN_BLOCKS WRS_BATCHED_PACKET_MIN_BLOCKS
+#endif
 template <int K, bool W4>
-__global__ void __launch_bounds__(128, WRS_BATCHED_PACKET_MIN_BLOCKS) k_trace_batched_mixed(
+__global__ void __launch_bounds__(128, WRS_BATCHED_MIXED_MIN_BLOCKS) k_trace_batched_mixed(
         const wrs_session* __restrict__ sess, int n_sessions, uint32_t total_tiles, Comp cp,
         int32_t* status) {
     const uint32_t tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
