@@ -193,9 +193,9 @@ def kernel_digest():
 
 
 def profiled(key):
-    """A figure of the committed ncu summary of the trace kernel over the timed loop's 60 client
-    poses (``- key: value`` lines, means per launch), if the summary was taken on the current
-    kernel source (it records the source digest); else None."""
+    """A figure of the committed ncu summary of the trace kernel (``- key: value`` lines, means
+    per captured launch), if the summary was taken on the current kernel source (it records the
+    source digest); else None."""
     path = os.path.join(ROOT, "profiles", "trace_large_1080p_bench_poses.md")
     try:
         txt = open(path).read()
@@ -506,7 +506,13 @@ def main():
     fpr = trace_flops_per_ray(cnt_tot, rays_counted)
     bytes_launch = bpr * npix_c
     achieved = bytes_launch / (trace_ms * 1e-3) / 1e9
+    # profiled per-launch figures (a few launches over poses spread across the set) scaled to the
+    # timed poses by node visits per launch (the traversal's unit of work)
+    nodes_profiled = profiled("node_visits_per_launch")
+    pscale = (cnt_tot["nodes"] / (rays_counted / npix_c)) / nodes_profiled if nodes_profiled else None
     traffic = profiled_traffic()
+    if traffic is not None and pscale is not None:
+        traffic *= pscale
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                 "kernel": ["k_trace", "k_trace_pr", "k_trace_packet"][sched],
@@ -516,9 +522,12 @@ def main():
                 "counts_per_ray": {k: v / rays_counted for k, v in cnt_tot.items()},
                 "traffic_source": "not measured in this run: dram__bytes_read.sum + "
                                   "dram__bytes_write.sum per launch from the committed ncu summary "
-                                  "profiles/trace_large_1080p_bench_poses.md, reported only while "
-                                  "its recorded kernel digest matches the current trace source "
-                                  "(else null)"}
+                                  "profiles/trace_large_1080p_bench_poses.md (4 launches over "
+                                  "depth-image groups spread across the pose set), scaled by "
+                                  "this run's counted node visits per launch over the profiled "
+                                  "launches' (profile_scale); reported only while its recorded "
+                                  "kernel digest matches the current trace source (else null)",
+                "profile_scale": pscale}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -545,6 +554,8 @@ def main():
     # kernel source) over the live launch time, against 148 SMs x 4 schedulers x 1 instruction
     # per cycle at the sampled SM clock
     winst = profiled("warp_instructions_per_launch")
+    if winst is not None and pscale is not None:
+        winst *= pscale
     profiled_launch = sched == 0 and width == 4 and kc == 1 and leaf == 1  # the captured launch
     fma = fma_rates(wrs, torch)
     line["roofline"]["fp32_peak_tflops_measured"] = fma["tflops"]
@@ -558,8 +569,9 @@ def main():
         ach_gi = winst / (trace_ms * 1e-3) / 1e9
         line["roofline"]["issue"] = {"source": "warp instructions per launch from the committed "
                                                "ncu summary profiles/trace_large_1080p_bench_poses.md "
-                                               "(digest-matched); launch time and SM clock live "
-                                               "from this run",
+                                               "(digest-matched), scaled by node visits to the "
+                                               "timed poses (profile_scale); launch time and SM "
+                                               "clock live from this run",
                                      "warp_instructions_per_launch": winst,
                                      "achieved_ginst_s": ach_gi, "peak_ginst_s": peak_gi,
                                      "frac": ach_gi / peak_gi,
@@ -568,10 +580,8 @@ def main():
                                      "measured_by": "wrs_fma_peak: FFMA warp instructions per "
                                                     "second of an FMA-only kernel, one wave of "
                                                     "8 x 256 threads per SM",
-                                     "note": "the kernel's binding limit (ALU pipe 66 %, issue "
-                                             "70 % under ncu on one frame); warp instructions "
-                                             "per launch counted by ncu over the 60 poses the "
-                                             "timed loop visits; the hbm entry is the "
+                                     "note": "the kernel's binding limit (ALU pipe 65 %, issue "
+                                             "70-72 % under ncu); the hbm entry is the "
                                              "counted-bytes roofline"}
 
     if not args.no_extras:
@@ -641,6 +651,10 @@ def run_case(a, wrs, torch):
         res["unproject_ms"].append(ev[0].elapsed_time(ev[1]))
         res["lbvh_ms"].append(ev[1].elapsed_time(ev[2]))
         res["trace_ms"] += [ev[2 + f].elapsed_time(ev[3 + f]) for f in range(len(clis))]
+        # counted work of each traced launch (k_trace_count, after the timed launches), so that
+        # profiled figures of these launches can be scaled to other poses by node visits
+        res.setdefault("node_visits", []).extend(
+            wrs.trace_count(bvh, srt, wrs.make_camera(c), params)["nodes"] for c in clis)
         del sp, bvh, srt
     wrs.check_status(st)
     res["device_bytes_allocated"] = torch.cuda.memory_allocated()
