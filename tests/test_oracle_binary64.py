@@ -268,8 +268,13 @@ def _budget(orc, scene, cam, bvh, what):
     differ = err.max(1) > 0
     excluded = err.max(1) > MAX_ABS
     npix = err.shape[0]
-    # only ties can differ, and few of them differ by more than the tolerance
-    assert not np.any(differ & ~b["tie"]), f"{what}: {np.count_nonzero(differ & ~b['tie'])} non-tie pixels differ"
+    # only ties can differ, and few of them differ by more than the tolerance; a pixel whose
+    # binary32 and binary64 transmittances stop at different hits (bit 4) may differ by the
+    # contribution of one hit behind T_stop, at most T_stop
+    stop = (a["amb"] & 4) != 0
+    assert np.all(err.max(1)[stop & ~b["tie"]] <= 1.01e-5), what
+    odd = differ & ~b["tie"] & ~stop
+    assert not np.any(odd), f"{what}: {np.count_nonzero(odd)} non-tie pixels differ"
     assert np.count_nonzero(excluded) <= BUDGET * npix, f"{what}: {np.count_nonzero(excluded)} excluded"
     rest = err[~excluded]
     assert rest.max() <= MAX_ABS and rest.mean() <= MEAN_ABS, what
