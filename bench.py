@@ -564,6 +564,16 @@ def main():
     cr = copy_rates(wrs, torch)
     line["roofline"]["own_copy_gbs"] = cr
     line["roofline"]["l2_frac"] = achieved / cr["l2_gbs"]
+    alu = profiled("alu_pipe_warp_instructions_per_launch")
+    alu_view = None
+    if alu is not None and pscale is not None and clk and clk.get("sm_mhz"):
+        # the ALU pipe (integer, compare, select, min/max) takes a warp instruction every second
+        # cycle per scheduler: its share of the launch's cycles
+        alu *= pscale
+        alu_view = {"warp_instructions_per_launch": alu,
+                    "frac": alu * 2 / (148 * 4 * clk["sm_mhz"] * 1e6 * trace_ms * 1e-3),
+                    "note": "ALU-pipe warp instructions (profiled, scaled) x 2 cycles over the "
+                            "launch's scheduler cycles at the sampled SM clock"}
     if winst is not None and profiled_launch and clk and clk.get("sm_mhz"):
         peak_gi = 148 * 4 * clk["sm_mhz"] * 1e6 / 1e9
         ach_gi = winst / (trace_ms * 1e-3) / 1e9
@@ -577,6 +587,7 @@ def main():
                                      "frac": ach_gi / peak_gi,
                                      "peak_ginst_s_measured": fma["ginst_s"],
                                      "frac_of_measured": ach_gi / fma["ginst_s"],
+                                     "alu_pipe": alu_view,
                                      "measured_by": "wrs_fma_peak: FFMA warp instructions per "
                                                     "second of an FMA-only kernel, one wave of "
                                                     "8 x 256 threads per SM",
