@@ -1165,13 +1165,17 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
 
     def fwd():
         with torch.no_grad():
-            wrs.render_views(sp, views, col, opa, scl, cfg["p"], cfg["leaf"])
+            wrs.render_views(sp, views, col, opa, scl, cfg["p"], cfg["leaf"], record_hits=0)
 
-    def loss_fn():
-        return ((wrs.render_views(sp, views, col, opa, scl, cfg["p"], cfg["leaf"]) - target) ** 2).mean()
+    def loss_fn(record=None):
+        return ((wrs.render_views(sp, views, col, opa, scl, cfg["p"], cfg["leaf"],
+                                  record_hits=record) - target) ** 2).mean()
 
-    def fwd_bwd():
+    def fwd_bwd():  # the forward pass records the hit lists, the adjoint runs from them
         loss_fn().backward()
+
+    def fwd_bwd_retraverse():  # the adjoint re-traverses every ray
+        loss_fn(0).backward()
 
     # the launch of this workload (soft edges, several hits per ray, 512^2 views) is tuned on the
     # forward + backward step itself: leaf size, K, and the per-pixel or packet schedule
@@ -1192,6 +1196,7 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
     barrier()
     ms_f = max_over_ranks(_time_ms(torch, fwd, 20))
     ms_fb = max_over_ranks(_time_ms(torch, fwd_bwd, 20))
+    ms_fbr = max_over_ranks(_time_ms(torch, fwd_bwd_retraverse, 20))
     rays_d = sum(v.width * v.height for v in views)
     # fit the per-splat radius scales to the novel views: 200 Adam steps, lr 1e-2, checkpointed
     # after step 100 and resumed from the checkpoint in a new fit object
@@ -1216,8 +1221,14 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
                                   "tuned_on": "forward + backward step"},
                        "forward_mrays_s": world * rays_d / (ms_f * 1e-3) / 1e6,
                        "forward_backward_mrays_s": world * rays_d / (ms_fb * 1e-3) / 1e6,
+                       "forward_backward_retraverse_mrays_s": world * rays_d / (ms_fbr * 1e-3) / 1e6,
                        "forward_ms_per_view": ms_f / len(views),
                        "forward_backward_ms_per_view": ms_fb / len(views),
+                       "adjoint": "forward_backward: the forward launch records each ray's "
+                                  "composited hits (16 per ray, the rest traced again) and the "
+                                  "adjoint runs from them without traversal; "
+                                  "forward_backward_retraverse: the adjoint traces every ray "
+                                  "again (replay and re-gather)",
                        "fit": {"steps": 200, "optimizer": "Adam lr 1e-2 on per-splat radius scale",
                                "loss_curve": curve, "seconds": fit_s,
                                "checkpoint": "saved after step 100, resumed in a new RadiusFit",

@@ -371,6 +371,36 @@ int wrs_trace_backward_views(const wrs_lbvh* bvh, const wrs_splats* sorted,
                              float* g_opacity, float* g_scale, int32_t accumulate,
                              int32_t* status, wrs_stream_t stream);
 
+/* wrs_trace_views that also records, for the adjoint, the hits each ray composited (spec S6, in
+ * compositing order), so that wrs_trace_backward_views_recorded needs no traversal (spec S7: the
+ * adjoint holds the hit set and order of the forward pass fixed; recording it is the choice when
+ * memory allows, re-traversing it the choice when it does not).  Ray r = v * H * W + y * W + x:
+ *  - hits: device [n_views * H * W][hit_capacity] uint32, the sorted-splat indices (positions in
+ *    `sorted`) of the composited hits of ray r in hits[r * hit_capacity + i], i < count;
+ *  - hit_count: device [n_views * H * W] uint32, the number of composited hits of ray r, or
+ *    hit_capacity + 1 when the ray composited more (then its list is incomplete and the adjoint
+ *    traces that ray again);
+ *  - hit_capacity in 1..32.  Images are bitwise those of wrs_trace_views.  Caller-owned buffers;
+ *    entries past a ray's count are left unwritten. */
+int wrs_trace_views_record(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* cams,
+                           int32_t n_views, const wrs_trace_params* params, float* rgba_out,
+                           uint32_t* hits, uint32_t* hit_count, uint32_t hit_capacity,
+                           int32_t* status, wrs_stream_t stream);
+
+/* wrs_trace_backward_views from the lists of wrs_trace_views_record (same bvh, sorted splats,
+ * cameras, parameters, opacity and radius scales as that call; lists unchanged since): the rays
+ * whose list is complete are differentiated from it without traversal, the others are traced
+ * again as wrs_trace_backward_views does.  The gradients equal wrs_trace_backward_views' up to the
+ * order of the float atomics.  accumulate as for wrs_trace_backward_views. */
+int wrs_trace_backward_views_recorded(const wrs_lbvh* bvh, const wrs_splats* sorted,
+                                      const wrs_camera* cams, int32_t n_views,
+                                      const wrs_trace_params* params, const float* radius_scale,
+                                      float global_scale, const uint32_t* hits,
+                                      const uint32_t* hit_count, uint32_t hit_capacity,
+                                      const float* dL_drgba, float* g_rgba, float* g_opacity,
+                                      float* g_scale, int32_t accumulate, int32_t* status,
+                                      wrs_stream_t stream);
+
 /* The earlier 2.5D warping the paper compares against (§2, §5, Fig. 3): every splat of a set
  * (compacted or sorted; index = its position in that set) drawn as a point_size x point_size pixel
  * square around its projection into cam, one depth per point (the view-axis distance z, points

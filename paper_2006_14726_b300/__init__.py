@@ -157,6 +157,11 @@ _sig("wrs_trace_views", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats), ctyp
      _I, ctypes.POINTER(_Params), _P, _P, _P)
 _sig("wrs_trace_backward_views", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats),
      ctypes.POINTER(Camera), _I, ctypes.POINTER(_Params), _P, _F, _P, _P, _P, _P, _I, _P, _P)
+_sig("wrs_trace_views_record", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats),
+     ctypes.POINTER(Camera), _I, ctypes.POINTER(_Params), _P, _P, _P, _U, _P, _P)
+_sig("wrs_trace_backward_views_recorded", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats),
+     ctypes.POINTER(Camera), _I, ctypes.POINTER(_Params), _P, _F, _P, _P, _U, _P, _P, _P, _P, _I,
+     _P, _P)
 _sig("wrs_session_tiles", _U, _I, _I)
 _sig("wrs_trace_batched", _I, _P, _I, _U, ctypes.POINTER(_Params), _P, _P, _P)
 _sig("wrs_trace_backward", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats), ctypes.POINTER(Camera),
@@ -575,6 +580,51 @@ def trace_views(bvh: LBVH, sorted: SplatBuffers, cams: Sequence, params: TracePa
     return out
 
 
+class HitLists:
+    """The composited hits of every ray of a multi-view trace (wrs_trace_views_record): ``hits``
+    [rays, capacity] sorted-splat indices in compositing order, ``count`` [rays] their number
+    (capacity + 1: more than fit, the adjoint traces that ray again); ray = view * H * W + pixel."""
+
+    MAX_CAPACITY = 32
+
+    def __init__(self, rays: int, capacity: int = 16, device=None):
+        if not 1 <= capacity <= self.MAX_CAPACITY:
+            raise ValueError(f"hit capacity {capacity} not in 1..{self.MAX_CAPACITY}")
+        device = device or torch.device("cuda")
+        self.rays, self.capacity = int(rays), int(capacity)
+        self.hits = torch.empty(self.rays, self.capacity, dtype=torch.int32, device=device)
+        self.count = torch.empty(self.rays, dtype=torch.int32, device=device)
+
+    @staticmethod
+    def nbytes(rays: int, capacity: int) -> int:
+        return 4 * int(rays) * (int(capacity) + 1)
+
+
+def trace_views_record(bvh: LBVH, sorted: SplatBuffers, cams: Sequence,
+                       params: TraceParams = TraceParams(), hit_capacity: int = 16,
+                       opacity: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None,
+                       lists: Optional[HitLists] = None, status: Optional[torch.Tensor] = None,
+                       stream=None) -> Tuple[torch.Tensor, HitLists]:
+    """trace_views that also records every ray's composited hits (wrs_trace_views_record) for
+    :func:`trace_backward_views_recorded`; returns (images [V,H,W,4], HitLists)."""
+    arr, w, h = _cams(cams)
+    dev = sorted.pos_r.device
+    if out is None:
+        out = torch.empty(len(cams), h, w, 4, dtype=torch.float32, device=dev)
+    _buf(out, len(cams) * h * w * 4, torch.float32, "trace_views_record out")
+    rays = len(cams) * h * w
+    if lists is None:
+        lists = HitLists(rays, hit_capacity, dev)
+    if lists.rays != rays:
+        raise ValueError(f"hit lists for {lists.rays} rays, the views have {rays}")
+    b, s, p = bvh.c(), sorted.c(), params.c(opacity)
+    _check(_lib.wrs_trace_views_record(ctypes.byref(b), ctypes.byref(s), arr, len(cams),
+                                       ctypes.byref(p), _ptr(out), _ptr(lists.hits),
+                                       _ptr(lists.count), lists.capacity, _ptr(status),
+                                       _stream(stream)), "wrs_trace_views_record")
+    return out, lists
+
+
 COUNTER_NAMES = ("nodes", "boxes", "spheres", "gathered", "composited", "passes")
 
 
@@ -712,6 +762,40 @@ def trace_backward_views(bvh: LBVH, sorted: SplatBuffers, cams: Sequence, dL_drg
         float(global_scale), _ptr(dL_drgba.contiguous()), _ptr(g_rgba), _ptr(g_op), _ptr(g_sc),
         1 if accumulate_into is not None else 0, _ptr(status), _stream(stream)),
         "wrs_trace_backward_views")
+    return g_rgba, g_op, g_sc
+
+
+def trace_backward_views_recorded(bvh: LBVH, sorted: SplatBuffers, cams: Sequence, lists: HitLists,
+                                  dL_drgba: torch.Tensor, params: TraceParams = TraceParams(),
+                                  opacity: Optional[torch.Tensor] = None,
+                                  radius_scale: Optional[torch.Tensor] = None,
+                                  global_scale: float = 1.0, want_opacity: bool = True,
+                                  want_scale: bool = True, status: Optional[torch.Tensor] = None,
+                                  stream=None, accumulate_into=None):
+    """:func:`trace_backward_views` from the hit lists of :func:`trace_views_record` (same scene,
+    cameras and parameters): no traversal for the rays whose list is complete."""
+    arr, w, h = _cams(cams)
+    dev = sorted.pos_r.device
+    cap = max(sorted.capacity, 1)
+    if lists.rays != len(cams) * h * w:
+        raise ValueError("hit lists do not belong to these views")
+    _buf(dL_drgba.contiguous(), len(cams) * h * w * 4, torch.float32, "dL_drgba")
+    if accumulate_into is not None:
+        g_rgba, g_op, g_sc = accumulate_into
+        _buf(g_rgba, sorted.capacity * 4, torch.float32, "g_rgba")
+        _buf(g_op, sorted.capacity, torch.float32, "g_opacity")
+        _buf(g_sc, sorted.capacity, torch.float32, "g_scale")
+    else:
+        g_rgba = torch.empty(cap, 4, dtype=torch.float32, device=dev)
+        g_op = torch.empty(cap, dtype=torch.float32, device=dev) if want_opacity else None
+        g_sc = torch.empty(cap, dtype=torch.float32, device=dev) if want_scale else None
+    b, s, p = bvh.c(), sorted.c(), params.c(opacity)
+    _check(_lib.wrs_trace_backward_views_recorded(
+        ctypes.byref(b), ctypes.byref(s), arr, len(cams), ctypes.byref(p), _ptr(radius_scale),
+        float(global_scale), _ptr(lists.hits), _ptr(lists.count), lists.capacity,
+        _ptr(dL_drgba.contiguous()), _ptr(g_rgba), _ptr(g_op), _ptr(g_sc),
+        1 if accumulate_into is not None else 0, _ptr(status), _stream(stream)),
+        "wrs_trace_backward_views_recorded")
     return g_rgba, g_op, g_sc
 
 

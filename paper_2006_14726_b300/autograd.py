@@ -2,11 +2,13 @@
 backward: wrs_trace_backward).
 
 The differentiable quantities are the per-splat colour (premultiplied RGBA), opacity and radius
-scale, all in compacted splat order.  The forward pass stores no hit lists: the backward kernel
-re-traverses every ray (spec S7).  The radius scale changes the spheres, so every forward call
+scale, all in compacted splat order.  The single-view Function stores no hit lists: its backward
+kernel re-traverses every ray (spec S7).  The radius scale changes the spheres, so every forward call
 rebuilds the LBVH with the current scales; :func:`render_views` renders several views from one
 build, all views in one launch (wrs_trace_views), and their gradients in one launch into one
-set of buffers (wrs_trace_backward_views).
+set of buffers (wrs_trace_backward_views).  When the per-ray hit lists fit in memory the forward
+pass records them (wrs_trace_views_record) and the adjoint runs from them without traversal
+(wrs_trace_backward_views_recorded); otherwise the adjoint re-traverses.
 """
 from __future__ import annotations
 
@@ -14,8 +16,14 @@ from typing import Optional, Sequence
 
 import torch
 
-from . import (SplatBuffers, TraceParams, build_lbvh, trace, trace_backward, trace_backward_views,
-               trace_views)
+from . import (HitLists, SplatBuffers, TraceParams, build_lbvh, trace, trace_backward,
+               trace_backward_views, trace_backward_views_recorded, trace_views,
+               trace_views_record)
+
+# Hit lists are recorded by the multi-view forward pass (and the adjoint then needs no traversal)
+# when they fit in this many bytes; beyond it the adjoint re-traverses every ray.
+RECORD_BUDGET_BYTES = 1 << 30
+RECORD_CAPACITY = 16
 
 
 class TraceFunction(torch.autograd.Function):
@@ -63,7 +71,7 @@ class MultiViewTraceFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, rgba: torch.Tensor, opacity: Optional[torch.Tensor],
                 radius_scale: Optional[torch.Tensor], splats: SplatBuffers, cams,
-                params: TraceParams, leaf_size: int):
+                params: TraceParams, leaf_size: int, record_hits: int):
         n = rgba.shape[0]
         if n > splats.capacity:
             raise ValueError("more colours than splats")
@@ -74,27 +82,45 @@ class MultiViewTraceFunction(torch.autograd.Function):
         c0 = cams[0]
         if any((c.width, c.height) != (c0.width, c0.height) for c in cams):
             raise ValueError("all views must have the same size")
-        out = trace_views(bvh, sorted_, cams, params, opacity=op)
-        ctx.state = (bvh, sorted_, list(cams), params, op, sc, n)
+        lists = None
+        if record_hits:
+            out, lists = trace_views_record(bvh, sorted_, cams, params, record_hits, opacity=op)
+        else:
+            out = trace_views(bvh, sorted_, cams, params, opacity=op)
+        ctx.state = (bvh, sorted_, list(cams), params, op, sc, n, lists)
         return out
 
     @staticmethod
     def backward(ctx, g_img: torch.Tensor):
-        bvh, sorted_, cams, params, op, sc, n = ctx.state
+        bvh, sorted_, cams, params, op, sc, n, lists = ctx.state
         need_rgba, need_op, need_sc = ctx.needs_input_grad[:3]
-        g_rgba, g_op, g_sc = trace_backward_views(bvh, sorted_, cams, g_img.contiguous(), params,
-                                                  opacity=op, radius_scale=sc,
-                                                  want_opacity=need_op, want_scale=need_sc)
+        if lists is not None:
+            g_rgba, g_op, g_sc = trace_backward_views_recorded(
+                bvh, sorted_, cams, lists, g_img.contiguous(), params, opacity=op,
+                radius_scale=sc, want_opacity=need_op, want_scale=need_sc)
+        else:
+            g_rgba, g_op, g_sc = trace_backward_views(bvh, sorted_, cams, g_img.contiguous(),
+                                                      params, opacity=op, radius_scale=sc,
+                                                      want_opacity=need_op, want_scale=need_sc)
         return (g_rgba[:n] if need_rgba else None,
                 g_op[:n] if need_op else None,
                 g_sc[:n] if need_sc else None,
-                None, None, None, None)
+                None, None, None, None, None)
 
 
 def render_views(splats: SplatBuffers, cams: Sequence, rgba: torch.Tensor,
                  opacity: Optional[torch.Tensor] = None,
                  radius_scale: Optional[torch.Tensor] = None, params: TraceParams = TraceParams(),
-                 leaf_size: int = 1) -> torch.Tensor:
-    """Differentiable images [V,H,W,4] of several same-size client views of the splats."""
-    return MultiViewTraceFunction.apply(rgba, opacity, radius_scale, splats, list(cams), params,
-                                        leaf_size)
+                 leaf_size: int = 1, record_hits: Optional[int] = None) -> torch.Tensor:
+    """Differentiable images [V,H,W,4] of several same-size client views of the splats.
+
+    ``record_hits``: capacity of the per-ray hit lists the forward pass records so that the
+    adjoint needs no traversal (rays with more hits are traced again); 0 = always re-traverse;
+    None = RECORD_CAPACITY when the lists fit in RECORD_BUDGET_BYTES, else 0."""
+    cams = list(cams)
+    if record_hits is None:
+        rays = len(cams) * cams[0].width * cams[0].height
+        record_hits = (RECORD_CAPACITY if HitLists.nbytes(rays, RECORD_CAPACITY)
+                       <= RECORD_BUDGET_BYTES else 0)
+    return MultiViewTraceFunction.apply(rgba, opacity, radius_scale, splats, cams, params,
+                                        leaf_size, int(record_hits))

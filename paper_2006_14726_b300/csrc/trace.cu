@@ -48,6 +48,22 @@ struct Counts {
     uint32_t nodes, boxes, spheres, gathered, composited, passes;
 };
 
+// The composited hits of the rays of a multi-view launch, recorded by the forward pass for a
+// traversal-free adjoint: the sorted-splat indices in compositing order, hits[ray * cap + i], and
+// their number count[ray] (cap + 1: the ray composited more than cap hits; none are kept and the
+// adjoint re-traverses it).  ray = view * pixels + pixel.
+struct HitRecord {
+    uint32_t* hits;
+    uint32_t* count;
+    uint32_t cap;
+};
+// The rays a re-traversing adjoint launch handles: all (count == nullptr), or only those whose
+// recorded list went over capacity.
+struct HitFilter {
+    const uint32_t* count;
+    uint32_t cap;
+};
+
 constexpr float kInf = __builtin_huge_valf();
 
 // A traversal stack entry: the node reference in the low word and the entry distance of its box
@@ -341,14 +357,33 @@ __device__ __forceinline__ bool composite_chunk(const Scene& sc, const Comp& cp,
     return (cp.max_hits > 0 && used == cp.max_hits) || T <= cp.t_stop;
 }
 
+// Record the hits composited from one gathered chunk (used0 .. used) at their places in the ray's
+// list; the ones beyond the list's capacity are dropped (the count marks the list as over).
+template <int K>
+__device__ __forceinline__ void record_chunk(const uint32_t (&ki)[K], int used0, int used,
+                                             uint32_t* rec_hits, uint32_t cap) {
+#pragma unroll
+    for (int s = 0; s < K; s++) {
+        const int i = used0 + s;
+        if (i < used && (uint32_t)i < cap) rec_hits[i] = ki[s];
+    }
+}
+
 // Forward trace of one ray (spec S6).  overflow_bits: status bits of a traversal failure.
-template <int K, bool COUNT, bool W4>
+// With REC, the composited hits go to rec_hits[0 .. cap) and their number (cap + 1 beyond cap)
+// to *rec_count.
+template <int K, bool COUNT, bool W4, bool REC = false>
 __device__ __forceinline__ float4 trace_ray(const Scene& sc, const Comp& cp, const RayCtx& rc,
-                                            uint32_t& overflow_bits, Counts& cnt) {
+                                            uint32_t& overflow_bits, Counts& cnt,
+                                            uint32_t* rec_hits = nullptr,
+                                            uint32_t* rec_count = nullptr, uint32_t cap = 0) {
     float T = 1.0f;
     float3 C = make_float3(0.f, 0.f, 0.f);
     overflow_bits = 0;
-    if (rc.n == 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+    if (rc.n == 0) {
+        if constexpr (REC) *rec_count = 0;
+        return make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     int used = 0;
     bool has_last = false;
     float last_key = 0.0f;
@@ -360,11 +395,19 @@ __device__ __forceinline__ float4 trace_ray(const Scene& sc, const Comp& cp, con
                                                last_key, last_id, kk, ki, kid, cnt);
         if (COUNT) cnt.passes++;
         if (count < 0) { overflow_bits = count == -1 ? WRS_STATUS_STACK_OVERFLOW : WRS_STATUS_MALFORMED_TREE; break; }
-        if (composite_chunk<K, COUNT>(sc, cp, rc.ray, ki, count, T, C, used, cnt)) break;
+        if constexpr (REC) {
+            const int u0 = used;
+            const bool fin = composite_chunk<K, COUNT>(sc, cp, rc.ray, ki, count, T, C, used, cnt);
+            record_chunk<K>(ki, u0, used, rec_hits, cap);
+            if (fin) break;
+        } else {
+            if (composite_chunk<K, COUNT>(sc, cp, rc.ray, ki, count, T, C, used, cnt)) break;
+        }
         has_last = true;
         last_key = kk[K - 1];
         last_id = kid[K - 1];
     }
+    if constexpr (REC) *rec_count = (uint32_t)used > cap ? cap + 1 : (uint32_t)used;
     return make_float4(C.x, C.y, C.z, 1.0f - T);
 }
 
@@ -464,10 +507,13 @@ __device__ __forceinline__ int gather_packet(const Scene& sc, const Ray& ray,
 }
 
 // Forward trace of the warp's rays; lanes with active = false take part without a ray.
-template <int K>
+template <int K, bool REC = false>
 __device__ __forceinline__ float4 trace_ray_packet(const Scene& sc, const Comp& cp,
                                                    const RayCtx& rc, bool active,
-                                                   uint32_t& overflow_bits) {
+                                                   uint32_t& overflow_bits,
+                                                   uint32_t* rec_hits = nullptr,
+                                                   uint32_t* rec_count = nullptr,
+                                                   uint32_t cap = 0) {
     float T = 1.0f;
     float3 C = make_float3(0.f, 0.f, 0.f);
     overflow_bits = 0;
@@ -489,11 +535,20 @@ __device__ __forceinline__ float4 trace_ray_packet(const Scene& sc, const Comp& 
             break;
         }
         if (!done) {
-            done = composite_chunk<K, false>(sc, cp, rc.ray, ki, count, T, C, used, none);
+            if constexpr (REC) {
+                const int u0 = used;
+                done = composite_chunk<K, false>(sc, cp, rc.ray, ki, count, T, C, used, none);
+                record_chunk<K>(ki, u0, used, rec_hits, cap);
+            } else {
+                done = composite_chunk<K, false>(sc, cp, rc.ray, ki, count, T, C, used, none);
+            }
             has_last = true;
             last_key = kk[K - 1];
             last_id = kid[K - 1];
         }
+    }
+    if constexpr (REC) {
+        if (active) *rec_count = (uint32_t)used > cap ? cap + 1 : (uint32_t)used;
     }
     return make_float4(C.x, C.y, C.z, 1.0f - T);
 }
@@ -704,10 +759,12 @@ __device__ __forceinline__ void tile_pixel(int t, int& px, int& py) {
     py = (warp >> 1) * 4 + (lane >> 3);
 }
 
-// The pixel of this thread in the per-pixel grid (blockIdx.x, blockIdx.y) traced and written.
-template <int K, bool W4>
+// The pixel of this thread in the per-pixel grid (blockIdx.x, blockIdx.y) traced and written;
+// with REC its composited hits are recorded at ray index ray_base + pixel.
+template <int K, bool W4, bool REC = false>
 __device__ __forceinline__ void trace_pixel(const Scene& sc, const Comp& cp, const wrs_camera& cam,
-                                            float4* __restrict__ out, int32_t* status) {
+                                            float4* __restrict__ out, int32_t* status,
+                                            const HitRecord* hr = nullptr, size_t ray_base = 0) {
     int px, py;
     tile_pixel(threadIdx.x, px, py);
     const int tile_h = (blockDim.x >> 6) * 4;
@@ -716,9 +773,18 @@ __device__ __forceinline__ void trace_pixel(const Scene& sc, const Comp& cp, con
     const RayCtx rc = make_ray_ctx(sc, cam, x, y);
     uint32_t overflow;
     Counts cnt;
-    const float4 o = trace_ray<K, false, W4>(sc, cp, rc, overflow, cnt);
-    if (overflow) wrs::set_status(status, overflow);
-    out[(size_t)y * cam.width + x] = o;
+    if constexpr (REC) {
+        const size_t pix = (size_t)y * cam.width + x, ray = ray_base + pix;
+        const float4 o = trace_ray<K, false, W4, true>(sc, cp, rc, overflow, cnt,
+                                                       hr->hits + ray * hr->cap, hr->count + ray,
+                                                       hr->cap);
+        if (overflow) wrs::set_status(status, overflow);
+        out[pix] = o;
+    } else {
+        const float4 o = trace_ray<K, false, W4>(sc, cp, rc, overflow, cnt);
+        if (overflow) wrs::set_status(status, overflow);
+        out[(size_t)y * cam.width + x] = o;
+    }
 }
 
 template <int K, bool W4>
@@ -741,12 +807,22 @@ k_trace_views(Scene sc, Comp cp, const __grid_constant__ ViewCams vc, float4* __
     trace_pixel<K, W4>(sc, cp, vc.cam[blockIdx.z], out + blockIdx.z * pixels, status);
 }
 
+// k_trace_views that records every ray's composited hits (ray = (view0 + view) * pixels + pixel).
+template <int K, bool W4>
+__global__ void __launch_bounds__(PixelBounds<K, W4>::max_threads, PixelBounds<K, W4>::min_blocks)
+k_trace_views_rec(Scene sc, Comp cp, const __grid_constant__ ViewCams vc, float4* __restrict__ out,
+                  size_t pixels, HitRecord hr, size_t ray0, int32_t* status) {
+    trace_pixel<K, W4, true>(sc, cp, vc.cam[blockIdx.z], out + blockIdx.z * pixels, status, &hr,
+                             ray0 + blockIdx.z * pixels);
+}
+
 // Packet schedule (4-wide nodes only): every lane of the block stays to the end, lanes outside
 // the image take part in their warp's traversal without a ray.
-template <int K>
+template <int K, bool REC = false>
 __device__ __forceinline__ void trace_pixel_packet(const Scene& sc, const Comp& cp,
                                                    const wrs_camera& cam, float4* __restrict__ out,
-                                                   int32_t* status) {
+                                                   int32_t* status, const HitRecord* hr = nullptr,
+                                                   size_t ray_base = 0) {
     int px, py;
     tile_pixel(threadIdx.x, px, py);
     const int tile_h = (blockDim.x >> 6) * 4;
@@ -754,9 +830,18 @@ __device__ __forceinline__ void trace_pixel_packet(const Scene& sc, const Comp& 
     const bool active = x < cam.width && y < cam.height;
     const RayCtx rc = make_ray_ctx(sc, cam, active ? x : 0, active ? y : 0);
     uint32_t overflow;
-    const float4 o = trace_ray_packet<K>(sc, cp, rc, active, overflow);
-    if (overflow) wrs::set_status(status, overflow);
-    if (active) out[(size_t)y * cam.width + x] = o;
+    if constexpr (REC) {
+        const size_t pix = active ? (size_t)y * cam.width + x : 0, ray = ray_base + pix;
+        const float4 o = trace_ray_packet<K, true>(sc, cp, rc, active, overflow,
+                                                   hr->hits + ray * hr->cap, hr->count + ray,
+                                                   hr->cap);
+        if (overflow) wrs::set_status(status, overflow);
+        if (active) out[pix] = o;
+    } else {
+        const float4 o = trace_ray_packet<K>(sc, cp, rc, active, overflow);
+        if (overflow) wrs::set_status(status, overflow);
+        if (active) out[(size_t)y * cam.width + x] = o;
+    }
 }
 
 template <int K>
@@ -771,6 +856,14 @@ __global__ void __launch_bounds__(256, WRS_PACKET_MIN_BLOCKS) k_trace_packet_vie
                                                             float4* __restrict__ out,
                                                             size_t pixels, int32_t* status) {
     trace_pixel_packet<K>(sc, cp, vc.cam[blockIdx.z], out + blockIdx.z * pixels, status);
+}
+
+template <int K>
+__global__ void __launch_bounds__(256, WRS_PACKET_MIN_BLOCKS) k_trace_packet_views_rec(
+        Scene sc, Comp cp, const __grid_constant__ ViewCams vc, float4* __restrict__ out,
+        size_t pixels, HitRecord hr, size_t ray0, int32_t* status) {
+    trace_pixel_packet<K, true>(sc, cp, vc.cam[blockIdx.z], out + blockIdx.z * pixels, status, &hr,
+                                ray0 + blockIdx.z * pixels);
 }
 
 template <int K, bool W4>
@@ -1081,9 +1174,41 @@ struct GradOut {
     float* g_sc;
 };
 
+// The adjoint of one composited hit k (sorted-splat index) with transmittance Ti in front of it,
+// given the suffix composite S and suffix transmittance P of the hits behind it (spec S7); S and
+// P are then extended over this hit.  Gradients go to the compacted splat order.
+__device__ __forceinline__ void hit_adjoint(const Scene& sc, const Comp& cp, const Ray& ray,
+                                            uint32_t k, float Ti, const float4 g, float3& S,
+                                            float& P, const GradOut& go) {
+    const HitTerms h = hit_terms(sc, cp, ray, k);
+    const float gC = g.x * h.c.x + g.y * h.c.y + g.z * h.c.z;
+    const float gS = g.x * S.x + g.y * S.y + g.z * S.z;
+    const float dLda = Ti * (g.w * P - gS);
+    const float pass = (h.x >= 0.0f && h.x <= 1.0f) ? 1.0f : 0.0f;
+    const uint32_t src = __ldg(sc.src + k);
+    const float tow = Ti * h.op * h.w;
+    // one 16-byte vector atomic for the four colour components (g_rgba is 16-byte aligned)
+    atomicAdd(reinterpret_cast<float4*>(go.g_rgba) + src,
+              make_float4(tow * g.x, tow * g.y, tow * g.z, dLda * pass * h.op * h.w));
+    if (go.g_op) atomicAdd(go.g_op + src, Ti * h.w * gC + dLda * pass * h.c.w * h.w);
+    if (go.g_sc && cp.beta > 0.0f) {
+        const float s_val = go.scale ? __ldg(go.scale + src) : go.gscale;
+        const float dw = wrs::soft_dw(h.rho, cp.beta);
+        if (s_val > 0.0f && dw != 0.0f) {
+            const float dLdw = Ti * h.op * gC + dLda * pass * h.op * h.c.w;
+            atomicAdd(go.g_sc + src, dLdw * dw * (-h.rho / s_val));
+        }
+    }
+    const float ow = h.op * h.w;
+    S.x = fmaf(1.0f - h.a, S.x, ow * h.c.x);
+    S.y = fmaf(1.0f - h.a, S.y, ow * h.c.y);
+    S.z = fmaf(1.0f - h.a, S.z, ow * h.c.z);
+    P = P * (1.0f - h.a);
+}
+
 // Pass B for one re-gathered chunk: transmittances forward from the chunk's recorded start T0,
 // then the adjoint of its u used hits back to front with the suffix composite S and suffix
-// transmittance P of the later chunks (spec S7); gradients go to the compacted splat order.
+// transmittance P of the later chunks.
 template <int K>
 __device__ __forceinline__ void chunk_adjoint(const Scene& sc, const Comp& cp, const Ray& ray,
                                               const uint32_t (&ki)[K], int u, float T0,
@@ -1099,32 +1224,7 @@ __device__ __forceinline__ void chunk_adjoint(const Scene& sc, const Comp& cp, c
 #pragma unroll
     for (int s = K - 1; s >= 0; s--) {
         if (s >= u) continue;
-        const uint32_t k = ki[s];
-        const HitTerms h = hit_terms(sc, cp, ray, k);
-        const float Ti = Tk[s];
-        const float gC = g.x * h.c.x + g.y * h.c.y + g.z * h.c.z;
-        const float gS = g.x * S.x + g.y * S.y + g.z * S.z;
-        const float dLda = Ti * (g.w * P - gS);
-        const float pass = (h.x >= 0.0f && h.x <= 1.0f) ? 1.0f : 0.0f;
-        const uint32_t src = __ldg(sc.src + k);
-        const float tow = Ti * h.op * h.w;
-        // one 16-byte vector atomic for the four colour components (g_rgba is 16-byte aligned)
-        atomicAdd(reinterpret_cast<float4*>(go.g_rgba) + src,
-                  make_float4(tow * g.x, tow * g.y, tow * g.z, dLda * pass * h.op * h.w));
-        if (go.g_op) atomicAdd(go.g_op + src, Ti * h.w * gC + dLda * pass * h.c.w * h.w);
-        if (go.g_sc && cp.beta > 0.0f) {
-            const float s_val = go.scale ? __ldg(go.scale + src) : go.gscale;
-            const float dw = wrs::soft_dw(h.rho, cp.beta);
-            if (s_val > 0.0f && dw != 0.0f) {
-                const float dLdw = Ti * h.op * gC + dLda * pass * h.op * h.c.w;
-                atomicAdd(go.g_sc + src, dLdw * dw * (-h.rho / s_val));
-            }
-        }
-        const float ow = h.op * h.w;
-        S.x = fmaf(1.0f - h.a, S.x, ow * h.c.x);
-        S.y = fmaf(1.0f - h.a, S.y, ow * h.c.y);
-        S.z = fmaf(1.0f - h.a, S.z, ow * h.c.z);
-        P = P * (1.0f - h.a);
+        hit_adjoint(sc, cp, ray, ki[s], Tk[s], g, S, P, go);
     }
 }
 
@@ -1132,13 +1232,16 @@ template <int K, bool W4>
 __device__ __forceinline__ void backward_pixel(const Scene& sc, const Comp& cp,
                                                const wrs_camera& cam,
                                                const float4* __restrict__ dimg, const GradOut& go,
-                                               int32_t* status) {
+                                               int32_t* status, HitFilter flt = HitFilter{nullptr, 0},
+                                               size_t ray_base = 0) {
     int px, py;
     tile_pixel(threadIdx.x, px, py);
     const int tile_h = (blockDim.x >> 6) * 4;
     const int x = blockIdx.x * 16 + px, y = blockIdx.y * tile_h + py;
     if (x >= cam.width || y >= cam.height) return;
-    const float4 g = dimg[(size_t)y * cam.width + x];
+    const size_t pix = (size_t)y * cam.width + x;
+    if (flt.count && flt.count[ray_base + pix] <= flt.cap) return;  // its recorded list serves
+    const float4 g = dimg[pix];
     if (g.x == 0.f && g.y == 0.f && g.z == 0.f && g.w == 0.f) return;
     const RayCtx rc = make_ray_ctx(sc, cam, x, y);
     if (rc.n == 0) return;
@@ -1201,8 +1304,10 @@ __global__ void __launch_bounds__(128, BwdBounds<K, W4>::min_blocks) k_trace_bwd
                                                          const __grid_constant__ ViewCams vc,
                                                          const float4* __restrict__ dimg,
                                                          size_t pixels, GradOut go,
+                                                         HitFilter flt, size_t ray0,
                                                          int32_t* status) {
-    backward_pixel<K, W4>(sc, cp, vc.cam[blockIdx.z], dimg + blockIdx.z * pixels, go, status);
+    backward_pixel<K, W4>(sc, cp, vc.cam[blockIdx.z], dimg + blockIdx.z * pixels, go, status, flt,
+                          ray0 + blockIdx.z * pixels);
 }
 
 // Packet backward (4-wide nodes): backward_pixel's two passes with every traversal shared by the
@@ -1214,7 +1319,9 @@ template <int K>
 __device__ __forceinline__ void backward_pixel_packet(const Scene& sc, const Comp& cp,
                                                       const wrs_camera& cam,
                                                       const float4* __restrict__ dimg,
-                                                      const GradOut& go, int32_t* status) {
+                                                      const GradOut& go, int32_t* status,
+                                                      HitFilter flt = HitFilter{nullptr, 0},
+                                                      size_t ray_base = 0) {
     int px, py;
     tile_pixel(threadIdx.x, px, py);
     const int tile_h = (blockDim.x >> 6) * 4;
@@ -1222,6 +1329,8 @@ __device__ __forceinline__ void backward_pixel_packet(const Scene& sc, const Com
     const bool inside = x < cam.width && y < cam.height;
     const float4 g = inside ? dimg[(size_t)y * cam.width + x] : make_float4(0.f, 0.f, 0.f, 0.f);
     bool run = inside && !(g.x == 0.f && g.y == 0.f && g.z == 0.f && g.w == 0.f);
+    if (run && flt.count && flt.count[ray_base + (size_t)y * cam.width + x] <= flt.cap)
+        run = false;  // its recorded list serves
     const RayCtx rc = make_ray_ctx(sc, cam, inside ? x : 0, inside ? y : 0);
     if (rc.n == 0) return;  // the same for every thread of the launch
     float b_key[wrs::kBwdChunks];
@@ -1312,8 +1421,47 @@ __global__ void __launch_bounds__(256, WRS_BWD_PACKET_MIN_BLOCKS) k_trace_bwd_pa
                                                                 const __grid_constant__ ViewCams vc,
                                                                 const float4* __restrict__ dimg,
                                                                 size_t pixels, GradOut go,
+                                                                HitFilter flt, size_t ray0,
                                                                 int32_t* status) {
-    backward_pixel_packet<K>(sc, cp, vc.cam[blockIdx.z], dimg + blockIdx.z * pixels, go, status);
+    backward_pixel_packet<K>(sc, cp, vc.cam[blockIdx.z], dimg + blockIdx.z * pixels, go, status,
+                             flt, ray0 + blockIdx.z * pixels);
+}
+
+// The adjoint from recorded hit lists (no traversal): for each ray of each view whose list was
+// kept, the transmittances in front of its hits are rebuilt forward from the list (the forward
+// pass's own sequence), then the hits are visited back to front with hit_adjoint.  Rays whose list
+// went over capacity are left to a re-traversing launch (HitFilter).
+constexpr uint32_t kMaxRecord = 32;  // largest hit-list capacity (transmittances kept per thread)
+__global__ void __launch_bounds__(128) k_trace_bwd_recorded(Scene sc, Comp cp,
+                                                            const __grid_constant__ ViewCams vc,
+                                                            const float4* __restrict__ dimg,
+                                                            size_t pixels, GradOut go,
+                                                            const uint32_t* __restrict__ hits,
+                                                            const uint32_t* __restrict__ count,
+                                                            uint32_t cap, size_t ray0) {
+    const wrs_camera& cam = vc.cam[blockIdx.z];
+    int px, py;
+    tile_pixel(threadIdx.x, px, py);
+    const int tile_h = (blockDim.x >> 6) * 4;
+    const int x = blockIdx.x * 16 + px, y = blockIdx.y * tile_h + py;
+    if (x >= cam.width || y >= cam.height) return;
+    const size_t pix = (size_t)y * cam.width + x;
+    const size_t ray = ray0 + blockIdx.z * pixels + pix;
+    const uint32_t n = count[ray];
+    if (n == 0 || n > cap) return;
+    const float4 g = dimg[blockIdx.z * pixels + pix];
+    if (g.x == 0.f && g.y == 0.f && g.z == 0.f && g.w == 0.f) return;
+    const Ray r = wrs::primary_ray(cam, x, y);
+    const uint32_t* h = hits + ray * cap;
+    float Tb[kMaxRecord];
+    float t = 1.0f;
+    for (uint32_t i = 0; i < n; i++) {
+        Tb[i] = t;
+        t = t * (1.0f - hit_terms(sc, cp, r, __ldg(h + i)).a);
+    }
+    float3 S = make_float3(0.f, 0.f, 0.f);
+    float P = 1.0f;
+    for (int i = (int)n - 1; i >= 0; i--) hit_adjoint(sc, cp, r, __ldg(h + i), Tb[i], g, S, P, go);
 }
 
 // Persistent backward with lane refill: the per-pixel backward's two phases run as a per-lane
@@ -1540,8 +1688,21 @@ template <int K, bool W4> struct LaunchPacketViews {  // 4-wide implied, as Laun
 };
 template <int K, bool W4> struct LaunchBwdViews {
     static void run(dim3 g, int b, cudaStream_t s, Scene sc, Comp cp, const ViewCams& vc,
-                    const float4* d, size_t pixels, GradOut go, int32_t* st) {
-        k_trace_bwd_views<K, W4><<<g, b, 0, s>>>(sc, cp, vc, d, pixels, go, st);
+                    const float4* d, size_t pixels, GradOut go, HitFilter flt, size_t ray0,
+                    int32_t* st) {
+        k_trace_bwd_views<K, W4><<<g, b, 0, s>>>(sc, cp, vc, d, pixels, go, flt, ray0, st);
+    }
+};
+template <int K, bool W4> struct LaunchTraceViewsRec {
+    static void run(dim3 g, int b, cudaStream_t s, Scene sc, Comp cp, const ViewCams& vc,
+                    float4* o, size_t pixels, HitRecord hr, size_t ray0, int32_t* st) {
+        k_trace_views_rec<K, W4><<<g, b, 0, s>>>(sc, cp, vc, o, pixels, hr, ray0, st);
+    }
+};
+template <int K, bool W4> struct LaunchPacketViewsRec {  // 4-wide implied
+    static void run(dim3 g, int b, cudaStream_t s, Scene sc, Comp cp, const ViewCams& vc,
+                    float4* o, size_t pixels, HitRecord hr, size_t ray0, int32_t* st) {
+        k_trace_packet_views_rec<K><<<g, b, 0, s>>>(sc, cp, vc, o, pixels, hr, ray0, st);
     }
 };
 template <int K, bool W4> struct LaunchBwdPacket {  // 4-wide implied, as LaunchTracePacket
@@ -1552,8 +1713,9 @@ template <int K, bool W4> struct LaunchBwdPacket {  // 4-wide implied, as Launch
 };
 template <int K, bool W4> struct LaunchBwdPacketViews {
     static void run(dim3 g, int b, cudaStream_t s, Scene sc, Comp cp, const ViewCams& vc,
-                    const float4* d, size_t pixels, GradOut go, int32_t* st) {
-        k_trace_bwd_packet_views<K><<<g, b, 0, s>>>(sc, cp, vc, d, pixels, go, st);
+                    const float4* d, size_t pixels, GradOut go, HitFilter flt, size_t ray0,
+                    int32_t* st) {
+        k_trace_bwd_packet_views<K><<<g, b, 0, s>>>(sc, cp, vc, d, pixels, go, flt, ray0, st);
     }
 };
 template <int K, bool W4> struct LaunchBatchedPP {
@@ -1699,10 +1861,13 @@ static int check_views(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_
     return WRS_OK;
 }
 
-int wrs_trace_views(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* cams,
-                    int32_t n_views, const wrs_trace_params* params, float* rgba_out,
-                    int32_t* status, wrs_stream_t stream) {
-    const char* fn = "wrs_trace_views";
+}  // extern "C"
+
+namespace {
+// wrs_trace_views, recording the composited hits when rec is given.
+int trace_views_impl(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* cams,
+                     int32_t n_views, const wrs_trace_params* params, float* rgba_out,
+                     const HitRecord* rec, int32_t* status, wrs_stream_t stream, const char* fn) {
     if (int rc = check_views(bvh, sorted, cams, n_views, params, fn)) return rc;
     if (!rgba_out || (reinterpret_cast<uintptr_t>(rgba_out) & 15))
         return wrs::fail(WRS_ERR_ARG, "%s: rgba_out NULL or not 16-byte aligned", fn);
@@ -1722,7 +1887,14 @@ int wrs_trace_views(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_cam
         dim3 g = grid_for(&cams[0], block);
         g.z = (unsigned)nv;
         float4* out = reinterpret_cast<float4*>(rgba_out) + (size_t)v0 * pixels;
-        if (packet)
+        const size_t ray0 = (size_t)v0 * pixels;
+        if (rec && packet)
+            dispatch_k1<LaunchPacketViewsRec, true>(K, g, block, s, sc, comp_of(params), vc, out,
+                                                    pixels, *rec, ray0, status);
+        else if (rec)
+            dispatch_k<LaunchTraceViewsRec>(K, W, g, block, s, sc, comp_of(params), vc, out,
+                                            pixels, *rec, ray0, status);
+        else if (packet)
             dispatch_k1<LaunchPacketViews, true>(K, g, block, s, sc, comp_of(params), vc, out,
                                                  pixels, status);
         else
@@ -1731,6 +1903,35 @@ int wrs_trace_views(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_cam
         WRS_LAUNCH_CHECK(fn);
     }
     return WRS_OK;
+}
+
+int check_record(const uint32_t* hits, const uint32_t* hit_count, uint32_t hit_capacity,
+                 const char* fn) {
+    if (!hits || !hit_count) return wrs::fail(WRS_ERR_ARG, "%s: hits / hit_count NULL", fn);
+    if (hit_capacity < 1 || hit_capacity > kMaxRecord)
+        return wrs::fail(WRS_ERR_ARG, "%s: hit_capacity %u not in 1..%u", fn, hit_capacity,
+                         kMaxRecord);
+    return WRS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int wrs_trace_views(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* cams,
+                    int32_t n_views, const wrs_trace_params* params, float* rgba_out,
+                    int32_t* status, wrs_stream_t stream) {
+    return trace_views_impl(bvh, sorted, cams, n_views, params, rgba_out, nullptr, status, stream,
+                            "wrs_trace_views");
+}
+
+int wrs_trace_views_record(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* cams,
+                           int32_t n_views, const wrs_trace_params* params, float* rgba_out,
+                           uint32_t* hits, uint32_t* hit_count, uint32_t hit_capacity,
+                           int32_t* status, wrs_stream_t stream) {
+    const char* fn = "wrs_trace_views_record";
+    if (int rc = check_record(hits, hit_count, hit_capacity, fn)) return rc;
+    const HitRecord rec = {hits, hit_count, hit_capacity};
+    return trace_views_impl(bvh, sorted, cams, n_views, params, rgba_out, &rec, status, stream, fn);
 }
 
 int wrs_trace_count(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* cam,
@@ -1849,13 +2050,15 @@ int wrs_trace_backward_accumulate(const wrs_lbvh* bvh, const wrs_splats* sorted,
                                "wrs_trace_backward_accumulate");
 }
 
-int wrs_trace_backward_views(const wrs_lbvh* bvh, const wrs_splats* sorted,
-                             const wrs_camera* cams, int32_t n_views,
-                             const wrs_trace_params* params, const float* radius_scale,
-                             float global_scale, const float* dL_drgba, float* g_rgba,
-                             float* g_opacity, float* g_scale, int32_t accumulate,
-                             int32_t* status, wrs_stream_t stream) {
-    const char* fn = "wrs_trace_backward_views";
+}  // extern "C"
+
+namespace {
+// wrs_trace_backward_views; with filter.count, only the rays whose recorded list is over capacity.
+int backward_views_impl(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* cams,
+                        int32_t n_views, const wrs_trace_params* params, const float* radius_scale,
+                        float global_scale, const float* dL_drgba, float* g_rgba,
+                        float* g_opacity, float* g_scale, int32_t accumulate, HitFilter filter,
+                        int32_t* status, wrs_stream_t stream, const char* fn) {
     if (int rc = check_views(bvh, sorted, cams, n_views, params, fn)) return rc;
     if (!dL_drgba || !g_rgba ||
         ((reinterpret_cast<uintptr_t>(dL_drgba) | reinterpret_cast<uintptr_t>(g_rgba)) & 15))
@@ -1885,10 +2088,61 @@ int wrs_trace_backward_views(const wrs_lbvh* bvh, const wrs_splats* sorted,
         const float4* d = reinterpret_cast<const float4*>(dL_drgba) + (size_t)v0 * pixels;
         if (packet)
             dispatch_k1<LaunchBwdPacketViews, true>(K, g, block, s, scp, comp_of(params), vc, d,
-                                                    pixels, go, status);
+                                                    pixels, go, filter, (size_t)v0 * pixels,
+                                                    status);
         else
             dispatch_k<LaunchBwdViews>(K, W, g, block, s, sc, comp_of(params), vc, d, pixels, go,
-                                       status);
+                                       filter, (size_t)v0 * pixels, status);
+        WRS_LAUNCH_CHECK(fn);
+    }
+    return WRS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int wrs_trace_backward_views(const wrs_lbvh* bvh, const wrs_splats* sorted,
+                             const wrs_camera* cams, int32_t n_views,
+                             const wrs_trace_params* params, const float* radius_scale,
+                             float global_scale, const float* dL_drgba, float* g_rgba,
+                             float* g_opacity, float* g_scale, int32_t accumulate,
+                             int32_t* status, wrs_stream_t stream) {
+    return backward_views_impl(bvh, sorted, cams, n_views, params, radius_scale, global_scale,
+                               dL_drgba, g_rgba, g_opacity, g_scale, accumulate,
+                               HitFilter{nullptr, 0}, status, stream, "wrs_trace_backward_views");
+}
+
+int wrs_trace_backward_views_recorded(const wrs_lbvh* bvh, const wrs_splats* sorted,
+                                      const wrs_camera* cams, int32_t n_views,
+                                      const wrs_trace_params* params, const float* radius_scale,
+                                      float global_scale, const uint32_t* hits,
+                                      const uint32_t* hit_count, uint32_t hit_capacity,
+                                      const float* dL_drgba, float* g_rgba, float* g_opacity,
+                                      float* g_scale, int32_t accumulate, int32_t* status,
+                                      wrs_stream_t stream) {
+    const char* fn = "wrs_trace_backward_views_recorded";
+    if (int rc = check_record(hits, hit_count, hit_capacity, fn)) return rc;
+    // the rays whose list went over capacity: re-traversed (this also zeroes the gradients and
+    // checks every argument)
+    const HitFilter over = {hit_count, hit_capacity};
+    if (int rc = backward_views_impl(bvh, sorted, cams, n_views, params, radius_scale,
+                                     global_scale, dL_drgba, g_rgba, g_opacity, g_scale,
+                                     accumulate, over, status, stream, fn))
+        return rc;
+    // the others from their lists
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const GradOut go = {radius_scale, global_scale, g_rgba, g_opacity, g_scale};
+    const Scene sc = make_scene(bvh, sorted, params->opacity, 2);
+    const size_t pixels = (size_t)cams[0].width * cams[0].height;
+    for (int v0 = 0; v0 < n_views; v0 += kMaxViews) {
+        const int nv = n_views - v0 < kMaxViews ? n_views - v0 : kMaxViews;
+        ViewCams vc;
+        for (int v = 0; v < nv; v++) vc.cam[v] = cams[v0 + v];
+        dim3 g = grid_for(&cams[0], 128);
+        g.z = (unsigned)nv;
+        const float4* d = reinterpret_cast<const float4*>(dL_drgba) + (size_t)v0 * pixels;
+        k_trace_bwd_recorded<<<g, 128, 0, s>>>(sc, comp_of(params), vc, d, pixels, go, hits,
+                                               hit_count, hit_capacity, (size_t)v0 * pixels);
         WRS_LAUNCH_CHECK(fn);
     }
     return WRS_OK;

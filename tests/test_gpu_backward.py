@@ -261,3 +261,36 @@ def test_gpu_gradient_matches_central_differences(wrs):
             checked += 1
     print(f"finite differences: {checked} parameters checked, {skipped} skipped (hit list changes)")
     assert checked >= 4 * 48 - 24
+
+
+def test_recorded_adjoint_diff_workload_eight_views(wrs, diff_scene):
+    """The 8 views of the differentiation workload with recorded hit lists (the forward pass
+    records, the adjoint runs without traversal): the accumulated gradient against the sum of the
+    8 oracle adjoints, element by element."""
+    sp, ref_sp, sc, op, cams = diff_scene
+    n = ref_sp.n
+    bvh, srt = wrs.build_lbvh(sp, 1, radius_scale=_cuda(sc))
+    V = len(cams)
+    h, w = cams[0].height, cams[0].width
+    g = np.random.default_rng(8).normal(size=(V, h * w, 4)).astype(np.float32)
+    params = wrs.TraceParams(edge_softness=0.25, k_chunk=4, schedule=2, width=4)
+    st = wrs.new_status()
+    _, lists = wrs.trace_views_record(bvh, srt, cams, params, 16, opacity=_cuda(op), status=st)
+    over = int((lists.count > 16).sum())
+    gr, go, gs = wrs.trace_backward_views_recorded(bvh, srt, cams, lists, _cuda(g.reshape(V, h, w, 4)),
+                                                   params, opacity=_cuda(op), radius_scale=_cuda(sc),
+                                                   status=st)
+    wrs.check_status(st)
+    scene = oracle.Scene(ref_sp, scale=sc, opacity=op, beta=0.25)
+    rr = np.zeros((n, 4))
+    ro = np.zeros(n)
+    rs = np.zeros(n)
+    for v, cam in enumerate(cams):
+        a, b, c = oracle.trace_backward(scene, cam, g[v].astype(np.float64))
+        rr += a
+        ro += b
+        rs += c
+    print(f"rays over the list capacity (re-traversed): {over}")
+    assert_elementwise(gr.cpu().numpy()[:n], rr, "recorded 8 views rgba")
+    assert_elementwise(go.cpu().numpy()[:n], ro, "recorded 8 views opacity")
+    assert_elementwise(gs.cpu().numpy()[:n], rs, "recorded 8 views scale", atol=ATOL_SCALE)
