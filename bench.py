@@ -1168,8 +1168,9 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
             wrs.render_views(sp, views, col, opa, scl, cfg["p"], cfg["leaf"], record_hits=0)
 
     def loss_fn(record=None):
-        return ((wrs.render_views(sp, views, col, opa, scl, cfg["p"], cfg["leaf"],
-                                  record_hits=record) - target) ** 2).mean()
+        return torch.nn.functional.mse_loss(
+            wrs.render_views(sp, views, col, opa, scl, cfg["p"], cfg["leaf"], record_hits=record),
+            target)
 
     def fwd_bwd():  # the forward pass records the hit lists, the adjoint runs from them
         loss_fn().backward()
@@ -1198,16 +1199,25 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
     ms_fb = max_over_ranks(_time_ms(torch, fwd_bwd, 20))
     ms_fbr = max_over_ranks(_time_ms(torch, fwd_bwd_retraverse, 20))
     rays_d = sum(v.width * v.height for v in views)
-    # fit the per-splat radius scales to the novel views: 200 Adam steps, lr 1e-2, checkpointed
-    # after step 100 and resumed from the checkpoint in a new fit object
-    from paper_2006_14726_b300.fit import RadiusFit
+    # one step of the radius fit (rebuild, trace, loss, adjoint, Adam), eager and replayed from a
+    # CUDA graph; the timed steps are real steps of two throw-away fits
+    from paper_2006_14726_b300.fit import GRAPH_WARMUP, RadiusFit
+    fit_ms = {}
+    for graphed in (False, True):
+        fz = RadiusFit(sp, views, target, cfg["p"], cfg["leaf"], lr=1e-2, rgba=col.detach(),
+                       opacity=opa.detach(), graph=graphed)
+        fz.run(GRAPH_WARMUP + 2)
+        fit_ms[graphed] = max_over_ranks(_time_ms(torch, fz._step_async, 20))
+        del fz
+    # fit the per-splat radius scales to the novel views: 200 graphed Adam steps, lr 1e-2,
+    # checkpointed after step 100 and resumed from the checkpoint in a new fit object
     ck = os.path.join(tempfile.gettempdir(), f"wrs_radius_fit_rank{rank}.pt")
     t_fit = time.perf_counter()
     f1 = RadiusFit(sp, views, target, cfg["p"], cfg["leaf"], lr=1e-2, rgba=col.detach(),
-                   opacity=opa.detach())
+                   opacity=opa.detach(), graph=True)
     f1.run(100, checkpoint=ck, every=100)
     f2 = RadiusFit(sp, views, target, cfg["p"], cfg["leaf"], lr=1e-2, rgba=col.detach(),
-                   opacity=opa.detach())
+                   opacity=opa.detach(), graph=True)
     f2.load(ck)
     f2.run(100)
     fit_s = time.perf_counter() - t_fit
@@ -1229,15 +1239,23 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
                                   "adjoint runs from them without traversal; "
                                   "forward_backward_retraverse: the adjoint traces every ray "
                                   "again (replay and re-gather)",
-                       "fit": {"steps": 200, "optimizer": "Adam lr 1e-2 on per-splat radius scale",
+                       "fit_step_mrays_s": world * rays_d / (fit_ms[False] * 1e-3) / 1e6,
+                       "fit_step_graphed_mrays_s": world * rays_d / (fit_ms[True] * 1e-3) / 1e6,
+                       "fit_step_ms": fit_ms[False], "fit_step_graphed_ms": fit_ms[True],
+                       "fit": {"steps": 200, "optimizer": "Adam lr 1e-2 on per-splat radius scale "
+                                                        "(fused, capturable)",
                                "loss_curve": curve, "seconds": fit_s,
+                               "graph": "each fit object runs 3 eager steps, captures the step "
+                                        "in a CUDA graph and replays it",
                                "checkpoint": "saved after step 100, resumed in a new RadiusFit",
                                "reference_views": target_src,
                                "scale_mean_after": float(scl.detach().mean())},
                        "note": "forward = one LBVH rebuild with the current radius scales + one "
-                               "launch tracing all views; backward = one launch of the "
-                               "re-traversal adjoint over all views, accumulated in place; L2 loss "
-                               "vs the reference views"}
+                               "launch tracing all views; backward = one launch of the adjoint "
+                               "over all views, accumulated in place; L2 loss vs the reference "
+                               "views; forward_backward* are eager autograd steps (colour, "
+                               "opacity and scale gradients); fit_step* is the fit's step (scale "
+                               "gradient and the Adam update), eager and graph-replayed"}
 
     # ---------------- CPU oracle on the host cores (rank 0, N = 1) ------------------------------
     if rank == 0 and world == 1:

@@ -282,7 +282,8 @@ int wrs_unproject_static(const float* rgba, const float* depth, const wrs_camera
  * r = max(s, 0) * r0 (s = radius_scale[i] in compacted order, or global_scale if radius_scale is
  * NULL) is baked into sorted->pos_r[.].w; sorted also receives rgba, id, src (= compacted index)
  * and *sorted->n (*in->n is clamped to in->capacity).  bvh->capacity and sorted->capacity must be
- * >= in->capacity.
+ * >= in->capacity.  The build writes the tree header, every node a traversal can reach and
+ * rows [0, n) of sorted, so neither buffer needs clearing before the call.
  * Buffer sizes: wrs_lbvh_bytes() for bvh->nodes, wrs_lbvh_scratch_bytes() for scratch. */
 size_t wrs_lbvh_bytes(uint32_t capacity, uint32_t leaf_size);
 size_t wrs_lbvh_scratch_bytes(uint32_t capacity, uint32_t leaf_size);

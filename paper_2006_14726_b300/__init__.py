@@ -187,8 +187,17 @@ def _check(rc: int, fn: str):
         raise WrsError(rc, f"{fn}: {last_error()}")
 
 
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+_cur_device = getattr(torch._C, "_cuda_getDevice", None)
+
+
 def _stream(stream) -> Optional[int]:
+    """The cudaStream_t handle: ``stream`` (a torch.cuda.Stream or a raw handle), else torch's
+    current stream of the current device (read without building a Stream object: the lookup is
+    on every call of every entry point)."""
     if stream is None:
+        if _raw_stream is not None and _cur_device is not None:
+            return _raw_stream(_cur_device())
         stream = torch.cuda.current_stream()
     return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
 
@@ -240,15 +249,17 @@ class SplatBuffers:
 
     ``id`` and ``src`` are int32 tensors holding uint32 values (< 2^31)."""
 
-    def __init__(self, capacity: int, device=None, sorted: bool = False):
+    def __init__(self, capacity: int, device=None, sorted: bool = False, _fill: bool = True):
         device = device or torch.device("cuda")
         cap = max(int(capacity), 1)
         self.capacity = int(capacity)
-        self.pos_r = torch.zeros(cap, 4, dtype=torch.float32, device=device)
-        self.rgba = torch.zeros(cap, 4, dtype=torch.float32, device=device)
-        self.id = torch.zeros(cap, dtype=torch.int32, device=device)
-        self.src = torch.zeros(cap, dtype=torch.int32, device=device) if sorted else None
-        self.n = torch.zeros(1, dtype=torch.int32, device=device)
+        # zero-filled (count 0) unless a producer writes count and rows before any reader runs
+        new = torch.zeros if _fill else torch.empty
+        self.pos_r = new(cap, 4, dtype=torch.float32, device=device)
+        self.rgba = new(cap, 4, dtype=torch.float32, device=device)
+        self.id = new(cap, dtype=torch.int32, device=device)
+        self.src = new(cap, dtype=torch.int32, device=device) if sorted else None
+        self.n = new(1, dtype=torch.int32, device=device)
 
     def c(self) -> _Splats:
         return _Splats(_ptr(self.pos_r), _ptr(self.rgba), _ptr(self.id), _ptr(self.src),
@@ -269,14 +280,15 @@ class SplatBuffers:
 class LBVH:
     """Device LBVH buffer (see wrs_lbvh)."""
 
-    def __init__(self, capacity: int, leaf_size: int = 1, device=None):
+    def __init__(self, capacity: int, leaf_size: int = 1, device=None, _fill: bool = True):
         device = device or torch.device("cuda")
         nbytes = _lib.wrs_lbvh_bytes(int(capacity), int(leaf_size))
         if nbytes == 0:
             raise ValueError(f"leaf_size {leaf_size} not in 1..16")
         self.capacity = int(capacity)
         self.leaf_size = int(leaf_size)
-        self.nodes = torch.zeros(nbytes, dtype=torch.uint8, device=device)
+        # zero-filled (an empty tree) unless a build writes the header before any reader runs
+        self.nodes = (torch.zeros if _fill else torch.empty)(nbytes, dtype=torch.uint8, device=device)
 
     def c(self) -> _Lbvh:
         return _Lbvh(_ptr(self.nodes), self.capacity, self.leaf_size)
@@ -515,10 +527,12 @@ def build_lbvh(splats: SplatBuffers, leaf_size: int = 1, radius_scale: Optional[
                stream=None) -> Tuple[LBVH, SplatBuffers]:
     """LBVH over the splats; returns (bvh, sorted splats with baked effective radius)."""
     dev = splats.pos_r.device
+    # buffers made here are returned only after the build wrote the header, the count and every
+    # node and row that a traversal can reach, so they need no zero fill
     if bvh is None:
-        bvh = LBVH(splats.capacity, leaf_size, device=dev)
+        bvh = LBVH(splats.capacity, leaf_size, device=dev, _fill=False)
     if sorted is None:
-        sorted = SplatBuffers(splats.capacity, device=dev, sorted=True)
+        sorted = SplatBuffers(splats.capacity, device=dev, sorted=True, _fill=False)
     need = lbvh_scratch_bytes(splats.capacity, bvh.leaf_size)
     if scratch is None:
         scratch = _scratch(need, dev)
