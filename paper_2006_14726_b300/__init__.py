@@ -659,7 +659,7 @@ def session_tiles(width: int, height: int) -> int:
 
 
 def sparse_schedules(sessions: Sequence[Tuple[LBVH, SplatBuffers, object]],
-                     ratio: float = 2.0) -> List[int]:
+                     ratio: float = 8.0) -> List[int]:
     """Per-session schedules for SCHEDULE_PER_SESSION: the warp-shared traversal where the client
     image has at least ``ratio`` pixels per splat (neighbouring rays then hit the same splats),
     one thread per pixel elsewhere.  The splat counts are read back from the device once (one
@@ -681,7 +681,7 @@ class Batch:
                  schedules: Optional[Sequence[int]] = None):
         """``schedules``: per session SCHEDULE_PER_PIXEL or SCHEDULE_PACKET, used by launches with
         ``schedule=SCHEDULE_PER_SESSION`` (default: the packet traversal for sessions with at
-        least 2 client pixels per splat, see :func:`sparse_schedules`)."""
+        least 8 client pixels per splat, see :func:`sparse_schedules`)."""
         device = device or torch.device("cuda")
         n = len(sessions)
         if schedules is None:

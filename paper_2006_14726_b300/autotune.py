@@ -18,7 +18,7 @@ import torch
 
 from . import (SCHEDULE_PACKET, SCHEDULE_PER_PIXEL, SCHEDULE_PER_SESSION, SCHEDULE_PERSISTENT, Batch, SplatBuffers,
                TraceParams,
-               build_lbvh, trace, trace_batched)
+               build_lbvh, trace, trace_batched, version)
 
 LEAVES = (1, 2, 4)
 KS = (1, 2, 4, 8)
@@ -66,7 +66,9 @@ def _time_ms(fn: Callable[[], None], reps: int, warm: int = 2) -> float:
 def signature(kind: str, n_splats: int, width: int, height: int, base: TraceParams) -> str:
     gpu = torch.cuda.get_device_name()
     nb = 1 << max(0, int(n_splats).bit_length() - 1)  # power-of-two bucket of the splat count
-    return f"{gpu}|{kind}|n~{nb}|{width}x{height}|H{base.max_hits}|b{base.edge_softness:g}"
+    # the library version is part of the key: a choice measured on other kernels is not reused
+    return (f"{version()}|{gpu}|{kind}|n~{nb}|{width}x{height}|H{base.max_hits}"
+            f"|b{base.edge_softness:g}")
 
 
 def tune_trace(splats: SplatBuffers, cams: Sequence, base: TraceParams = TraceParams(),

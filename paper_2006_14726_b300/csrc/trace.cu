@@ -411,6 +411,169 @@ __device__ __forceinline__ float4 trace_ray(const Scene& sc, const Comp& cp, con
     return make_float4(C.x, C.y, C.z, 1.0f - T);
 }
 
+// ---- per-ray 4-wide traversal with warp-wide leaf steps -------------------------------------
+// The per-pixel kernels' 4-wide traversal.  Each lane traverses its own ray, but leaf entries are
+// not tested inside the node visit that finds them: they are sorted with the internal entries by
+// entry distance, the nearest is the lane's next step and the others are pushed (so a leaf that
+// starts beyond the current K-th key is dropped when popped, like a node).  Every iteration of
+// the warp runs either a node step, for the lanes whose next entry is an internal node, or a leaf
+// step, for the lanes whose next entry is a leaf: the leaf step when at least as many lanes want
+// one as want a node step (a ballot), or when no lane wants a node step.  Lanes meet their leaves
+// at different visits; tested in the visit that found them, a warp ran about 16 leaf tests of ~3
+// active lanes per 32 rays, a divergent block per node slot.  The hit set of each pass, and so
+// the image, is that of any other traversal order (the K-buffer keeps the K smallest (key, id)).
+// All 32 lanes of the warp call these functions together; a lane without a ray passes
+// active = false.
+constexpr int64_t kPopNext = (int64_t)1 << 32;  // visit result: no entry hit, pop the next one
+
+template <int K, bool COUNT>
+__device__ __forceinline__ int64_t visit_node4_sorted(const Scene& sc, const wrs::BoxRay& br,
+                                                      uint32_t ref, uint32_t m, bool has_last,
+                                                      float last_key, const float (&kk)[K],
+                                                      StackEntry* stack, int& sp, Counts& cnt) {
+    if (ref + 1 >= m) return -2;  // not an internal node of this tree
+    const float low = has_last ? fmaxf(last_key, 0.0f) : 0.0f;
+    const float4* w = sc.wide + 8 * (size_t)ref;
+    const float4 nx = __ldg(w + br.sx), ny = __ldg(w + 1 + br.sy), nz = __ldg(w + 2 + br.sz);
+    const float4 fx = __ldg(w + 3 - br.sx), fy = __ldg(w + 4 - br.sy), fz = __ldg(w + 5 - br.sz);
+    const float4 rf = __ldg(w + 6);
+    if (COUNT) { cnt.nodes++; cnt.boxes += 4; }
+    float tn[4], tf[4];
+    wrs::box_test_nf(br, nx.x, ny.x, nz.x, fx.x, fy.x, fz.x, low, tn[0], tf[0]);
+    wrs::box_test_nf(br, nx.y, ny.y, nz.y, fx.y, fy.y, fz.y, low, tn[1], tf[1]);
+    wrs::box_test_nf(br, nx.z, ny.z, nz.z, fx.z, fy.z, fz.z, low, tn[2], tf[2]);
+    wrs::box_test_nf(br, nx.w, ny.w, nz.w, fx.w, fy.w, fz.w, low, tn[3], tf[3]);
+    uint32_t r[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
+                     __float_as_uint(rf.w)};
+    float key[4];
+#pragma unroll
+    for (int e = 0; e < 4; e++) key[e] = tn[e] <= fminf(tf[e], kk[K - 1]) ? tn[e] : kInf;
+    cswap(key[0], r[0], key[1], r[1]);
+    cswap(key[2], r[2], key[3], r[3]);
+    cswap(key[0], r[0], key[2], r[2]);
+    cswap(key[1], r[1], key[3], r[3]);
+    cswap(key[1], r[1], key[2], r[2]);
+    if (!(key[0] < kInf)) return kPopNext;
+    if (sp > wrs::kStack - 3) return -1;  // room for the (at most three) pushes
+    if (key[3] < kInf) stack[sp++] = stack_entry(r[3], key[3]);
+    if (key[2] < kInf) stack[sp++] = stack_entry(r[2], key[2]);
+    if (key[1] < kInf) stack[sp++] = stack_entry(r[1], key[1]);
+    return r[0];
+}
+
+// One pass of every lane with part = true (gather's contract); the others take part in the
+// warp's steps without a ray.
+template <int K, bool COUNT>
+__device__ __forceinline__ int gather_warp(const Scene& sc, const Ray& ray, const wrs::BoxRay& br,
+                                           uint32_t n, uint32_t leaf, int32_t root, bool part,
+                                           bool has_last, float last_key, uint32_t last_id,
+                                           float (&kk)[K], uint32_t (&ki)[K], uint32_t (&kid)[K],
+                                           Counts& cnt) {
+#pragma unroll
+    for (int s = 0; s < K; s++) { kk[s] = kInf; ki[s] = 0xFFFFFFFFu; kid[s] = 0xFFFFFFFFu; }
+    int count = 0;
+    const uint32_t m = (n + leaf - 1) / leaf;
+    StackEntry stack[wrs::kStack];
+    int sp = 0;
+    uint32_t cur = (uint32_t)root;  // the lane's next entry (a single-leaf tree starts at a leaf)
+    bool live = part;
+    int err = 0;
+    uint32_t budget = m + 1;  // internal node visits allowed in one pass
+    // Every iteration advances at least one lane by a node visit (bounded by the budget) or a
+    // pop (bounded by the pushes), so the loop ends; its exit and branches are warp-uniform.
+    while (true) {
+        const bool at_leaf = live && (cur & kLeafBit);
+        const bool at_node = live && !(cur & kLeafBit);
+        const unsigned lm = __ballot_sync(0xffffffffu, at_leaf);
+        const unsigned nm = __ballot_sync(0xffffffffu, at_node);
+        if ((lm | nm) == 0) break;
+        if (lm != 0 && (nm == 0 || __popc(lm) >= __popc(nm))) {
+            if (at_leaf) {
+                leaf_hits<K, COUNT>(sc, ray, cur, n, leaf, has_last, last_key, last_id, kk, ki,
+                                    kid, count, cnt);
+                live = pop_within(stack, sp, kk[K - 1], cur);
+            }
+        } else if (at_node) {
+            if (budget-- == 0) {
+                err = -2;
+                live = false;
+            } else {
+                const int64_t next = visit_node4_sorted<K, COUNT>(sc, br, cur, m, has_last,
+                                                                  last_key, kk, stack, sp, cnt);
+                if (next < 0) {
+                    err = (int)next;
+                    live = false;
+                } else if (next == kPopNext) {
+                    live = pop_within(stack, sp, kk[K - 1], cur);
+                } else {
+                    cur = (uint32_t)next;
+                }
+            }
+        }
+    }
+    return err ? err : count;
+}
+
+// trace_ray for the whole warp with 4-wide nodes; lanes with active = false take part without a
+// ray (and return zero).  Passes continue while any lane of the warp still needs hits.
+template <int K, bool COUNT, bool REC = false>
+__device__ __forceinline__ float4 trace_ray_warp4(const Scene& sc, const Comp& cp,
+                                                  const RayCtx& rc, bool active,
+                                                  uint32_t& overflow_bits, Counts& cnt,
+                                                  uint32_t* rec_hits = nullptr,
+                                                  uint32_t* rec_count = nullptr,
+                                                  uint32_t cap = 0) {
+    float T = 1.0f;
+    float3 C = make_float3(0.f, 0.f, 0.f);
+    overflow_bits = 0;
+    bool done = !active || rc.n == 0;
+    int used = 0;
+    bool has_last = false;
+    float last_key = 0.0f;
+    uint32_t last_id = 0;
+    float kk[K];
+    uint32_t ki[K], kid[K];
+    while (__any_sync(0xffffffffu, !done)) {
+        const int count = gather_warp<K, COUNT>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, !done,
+                                                has_last, last_key, last_id, kk, ki, kid, cnt);
+        if (done) continue;
+        if (COUNT) cnt.passes++;
+        if (count < 0) {
+            overflow_bits = count == -1 ? WRS_STATUS_STACK_OVERFLOW : WRS_STATUS_MALFORMED_TREE;
+            done = true;
+            continue;
+        }
+        const int u0 = used;
+        done = composite_chunk<K, COUNT>(sc, cp, rc.ray, ki, count, T, C, used, cnt);
+        if constexpr (REC) record_chunk<K>(ki, u0, used, rec_hits, cap);
+        has_last = true;
+        last_key = kk[K - 1];
+        last_id = kid[K - 1];
+    }
+    if constexpr (REC) {
+        if (active) *rec_count = (uint32_t)used > cap ? cap + 1 : (uint32_t)used;
+    }
+    return make_float4(C.x, C.y, C.z, 1.0f - T);
+}
+
+// The per-pixel trace of a warp's rays: the warp-wide 4-wide traversal, or per lane with binary
+// nodes.  All 32 lanes call it.
+template <int K, bool COUNT, bool W4, bool REC = false>
+__device__ __forceinline__ float4 trace_ray_warp(const Scene& sc, const Comp& cp, const RayCtx& rc,
+                                                 bool active, uint32_t& overflow_bits, Counts& cnt,
+                                                 uint32_t* rec_hits = nullptr,
+                                                 uint32_t* rec_count = nullptr, uint32_t cap = 0) {
+    if constexpr (W4) {
+        return trace_ray_warp4<K, COUNT, REC>(sc, cp, rc, active, overflow_bits, cnt, rec_hits,
+                                              rec_count, cap);
+    } else {
+        overflow_bits = 0;
+        if (!active) return make_float4(0.f, 0.f, 0.f, 0.f);
+        return trace_ray<K, COUNT, false, REC>(sc, cp, rc, overflow_bits, cnt, rec_hits,
+                                               rec_count, cap);
+    }
+}
+
 // ---- packet schedule: one traversal per warp ------------------------------------------------
 // The 32 rays of an 8x4 pixel tile share one traversal of the 4-wide nodes: every lane tests the
 // node's four boxes against its own ray (its own pass bound and k-buffer cut-off), a child is
@@ -578,13 +741,13 @@ struct PersistentMinBlocks {
 };
 
 // Launch bounds of the per-pixel kernel.  With the 4-wide traversal and K <= 2 it runs in blocks
-// of at most 128 threads; with K = 1, 10 resident blocks per SM (48 registers, a few spilled): on
-// the 1080p, 2 M splat workload 2 % faster than 9 blocks (56 registers) and 4 % faster than 8 (64,
-// no spills), while 11 or 12 blocks (40 registers) are 7 % slower.  Other instances keep blocks of up
-// to 256 threads and no register cap.  A build-time knob: WRS_PIXEL_W4_MIN_BLOCKS (resident
-// 128-thread blocks, 0 = no cap).
+// of at most 128 threads; with K = 1, 9 resident blocks per SM (56 registers, no spills): on the
+// 1080p, 2 M splat workload 14 % faster than 10 blocks (48 registers, 112 B spilled), 2 % faster
+// than 8 (64 registers) and 8-16 % faster than 7, 6 or no cap (70 registers).  Other instances
+// keep blocks of up to 256 threads and no register cap.  A build-time knob:
+// WRS_PIXEL_W4_MIN_BLOCKS (resident 128-thread blocks, 0 = no cap).
 #ifndef WRS_PIXEL_W4_MIN_BLOCKS
-#define WRS_PIXEL_W4_MIN_BLOCKS 10
+#define WRS_PIXEL_W4_MIN_BLOCKS 9
 #endif
 #ifndef WRS_PIXEL_W4_K2_MIN_BLOCKS
 #define WRS_PIXEL_W4_K2_MIN_BLOCKS 9  // K = 2: 9 blocks (56 registers), 4 % faster than 10
@@ -760,7 +923,9 @@ __device__ __forceinline__ void tile_pixel(int t, int& px, int& py) {
 }
 
 // The pixel of this thread in the per-pixel grid (blockIdx.x, blockIdx.y) traced and written;
-// with REC its composited hits are recorded at ray index ray_base + pixel.
+// with REC its composited hits are recorded at ray index ray_base + pixel.  Every lane of the
+// block stays to the end (the 4-wide traversal takes warp-wide steps); lanes outside the image
+// take part without a ray.
 template <int K, bool W4, bool REC = false>
 __device__ __forceinline__ void trace_pixel(const Scene& sc, const Comp& cp, const wrs_camera& cam,
                                             float4* __restrict__ out, int32_t* status,
@@ -769,22 +934,21 @@ __device__ __forceinline__ void trace_pixel(const Scene& sc, const Comp& cp, con
     tile_pixel(threadIdx.x, px, py);
     const int tile_h = (blockDim.x >> 6) * 4;
     const int x = blockIdx.x * 16 + px, y = blockIdx.y * tile_h + py;
-    if (x >= cam.width || y >= cam.height) return;
-    const RayCtx rc = make_ray_ctx(sc, cam, x, y);
+    const bool active = x < cam.width && y < cam.height;
+    const RayCtx rc = make_ray_ctx(sc, cam, active ? x : 0, active ? y : 0);
     uint32_t overflow;
     Counts cnt;
+    float4 o;
     if constexpr (REC) {
-        const size_t pix = (size_t)y * cam.width + x, ray = ray_base + pix;
-        const float4 o = trace_ray<K, false, W4, true>(sc, cp, rc, overflow, cnt,
-                                                       hr->hits + ray * hr->cap, hr->count + ray,
-                                                       hr->cap);
-        if (overflow) wrs::set_status(status, overflow);
-        out[pix] = o;
+        const size_t ray = ray_base + (active ? (size_t)y * cam.width + x : 0);
+        o = trace_ray_warp<K, false, W4, true>(sc, cp, rc, active, overflow, cnt,
+                                               hr->hits + ray * hr->cap, hr->count + ray, hr->cap);
     } else {
-        const float4 o = trace_ray<K, false, W4>(sc, cp, rc, overflow, cnt);
-        if (overflow) wrs::set_status(status, overflow);
-        out[(size_t)y * cam.width + x] = o;
+        o = trace_ray_warp<K, false, W4>(sc, cp, rc, active, overflow, cnt);
     }
+    if (overflow) wrs::set_status(status, overflow);
+    // (the output index is formed after the traversal: kept live across it, it costs registers)
+    if (active) out[(size_t)y * cam.width + x] = o;
 }
 
 template <int K, bool W4>
@@ -874,12 +1038,11 @@ __global__ void __launch_bounds__(256) k_trace_count(Scene sc, Comp cp, wrs_came
     const int tile_h = (blockDim.x >> 6) * 4;
     const int x = blockIdx.x * 16 + px, y = blockIdx.y * tile_h + py;
     Counts cnt = {0, 0, 0, 0, 0, 0};
-    if (x < cam.width && y < cam.height) {
-        const RayCtx rc = make_ray_ctx(sc, cam, x, y);
-        uint32_t overflow;
-        trace_ray<K, true, W4>(sc, cp, rc, overflow, cnt);
-        if (overflow) wrs::set_status(status, overflow);
-    }
+    const bool active = x < cam.width && y < cam.height;
+    const RayCtx rc = make_ray_ctx(sc, cam, active ? x : 0, active ? y : 0);
+    uint32_t overflow;
+    trace_ray_warp<K, true, W4>(sc, cp, rc, active, overflow, cnt);
+    if (overflow) wrs::set_status(status, overflow);
     unsigned long long v[6] = {cnt.nodes, cnt.boxes, cnt.spheres, cnt.gathered, cnt.composited,
                                cnt.passes};
 #pragma unroll
@@ -953,16 +1116,16 @@ __global__ void __launch_bounds__(128, BatchedBounds<K, W4>::min_blocks) k_trace
     uint32_t x, y;
     const wrs_session& S = tile_pixel_of(sess, n_sessions, tile, pos, x, y);
     const uint32_t W = (uint32_t)S.cam.width;
-    if (x >= W || y >= (uint32_t)S.cam.height) return;
+    const bool active = x < W && y < (uint32_t)S.cam.height;  // the tile is warp-uniform
     const Scene sc = session_scene<W4>(S);
-    const RayCtx rc = make_ray_ctx(sc, S.cam, (int)x, (int)y);
+    const RayCtx rc = make_ray_ctx(sc, S.cam, active ? (int)x : 0, active ? (int)y : 0);
     uint32_t overflow;
     Counts cnt;
-    const float4 o = trace_ray<K, false, W4>(sc, cp, rc, overflow, cnt);
+    const float4 o = trace_ray_warp<K, false, W4>(sc, cp, rc, active, overflow, cnt);
     if (overflow) wrs::set_status(status, overflow);
     // (finding the output pixel again after the traversal, as the packet kernel does, spills
     // less but measured 1 % slower here)
-    reinterpret_cast<float4*>(S.rgba_out)[(size_t)y * W + x] = o;
+    if (active) reinterpret_cast<float4*>(S.rgba_out)[(size_t)y * W + x] = o;
 }
 
 // Multi-session trace, packet schedule (4-wide nodes): warp w traces 8x4 tile w of the
@@ -1016,10 +1179,9 @@ __global__ void __launch_bounds__(128, WRS_BATCHED_MIXED_MIN_BLOCKS) k_trace_bat
         const RayCtx rc = make_ray_ctx(sc, S.cam, active ? (int)x : 0, active ? (int)y : 0);
         o = trace_ray_packet<K>(sc, cp, rc, active, overflow);
     } else {
-        if (!active) return;
-        const RayCtx rc = make_ray_ctx(sc, S.cam, (int)x, (int)y);
+        const RayCtx rc = make_ray_ctx(sc, S.cam, active ? (int)x : 0, active ? (int)y : 0);
         Counts cnt;
-        o = trace_ray<K, false, W4>(sc, cp, rc, overflow, cnt);
+        o = trace_ray_warp<K, false, W4>(sc, cp, rc, active, overflow, cnt);
     }
     if (overflow) wrs::set_status(status, overflow);
     if (active) reinterpret_cast<float4*>(S.rgba_out)[(size_t)y * W + x] = o;

@@ -405,7 +405,9 @@ def test_render_views_accumulates_the_per_view_gradients(wrs):
         assert torch.equal(img, imgs[v].detach())
         (img * g[v]).sum().backward()
     for t, a in zip((col, opa, scl), acc):
-        assert torch.allclose(t.grad, a, rtol=1e-4, atol=1e-6)
+        # the same float32 sums in another atomic order: an element's rounding error is a few
+        # ulp of its largest contributions (of both signs), so atol scales with the buffer's max
+        assert torch.allclose(t.grad, a, rtol=1e-4, atol=max(1e-5 * float(a.abs().max()), 1e-7))
 
 
 def _multi_view_instance(wrs):

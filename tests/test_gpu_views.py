@@ -20,6 +20,15 @@ MAX_ABS = 2e-3
 MEAN_ABS = 1e-4
 
 
+def _same_sum(a, b):
+    """a and b hold the same float32 sums accumulated by atomics in different orders.  An element
+    sums the contributions of every hit of every view, of both signs (random upstream gradients),
+    so its rounding error is a few ulp of its largest contributions, not of the (often much
+    smaller) sum: the absolute tolerance is relative to the largest element of the buffer."""
+    scale = float(b.abs().max()) if b.numel() else 0.0
+    return torch.allclose(a, b, rtol=1e-4, atol=max(1e-5 * scale, 1e-7))
+
+
 @pytest.fixture(scope="module")
 def wrs():
     if not torch.cuda.is_available():
@@ -106,13 +115,13 @@ def test_backward_views_sum_the_single_view_gradients(wrs, k, width, sched):
         wrs.trace_backward(bvh, srt, c, g[v], params, opacity=opac, radius_scale=scale,
                            accumulate_into=acc)
     for a, b in zip((gr, go, gs), acc):
-        assert torch.allclose(a[:n], b[:n], rtol=1e-4, atol=1e-6)
+        assert _same_sum(a[:n], b[:n])
     assert float(gs[:n].abs().sum()) > 0  # the soft edges give the radius a gradient
     # accumulate = 1 adds to the buffers: twice the gradient
     wrs.trace_backward_views(bvh, srt, cams, g, params, opacity=opac, radius_scale=scale,
                              accumulate_into=(gr, go, gs))
     for a, b in zip((gr, go, gs), acc):
-        assert torch.allclose(a[:n], 2 * b[:n], rtol=1e-4, atol=2e-6)
+        assert _same_sum(a[:n], 2 * b[:n])
 
 
 @pytest.mark.parametrize("sched", [0, 2])
@@ -128,8 +137,8 @@ def test_backward_over_more_views_than_one_launch_holds(wrs, sched):
     acc = (torch.zeros_like(gr), torch.zeros_like(go), None)
     for v, c in enumerate(cams):
         wrs.trace_backward(bvh, srt, c, g[v], params, accumulate_into=acc)
-    assert torch.allclose(gr[:n], acc[0][:n], rtol=1e-4, atol=1e-6)
-    assert torch.allclose(go[:n], acc[1][:n], rtol=1e-4, atol=1e-6)
+    assert _same_sum(gr[:n], acc[0][:n])
+    assert _same_sum(go[:n], acc[1][:n])
 
 
 @pytest.mark.parametrize("k", [1, 4, 16])
@@ -151,7 +160,7 @@ def test_packet_backward_equals_per_pixel_backward(wrs, k):
         wrs.check_status(st)
     for a, b in zip(*res):
         assert float(b[:n].abs().sum()) > 0
-        assert torch.allclose(a[:n], b[:n], rtol=1e-4, atol=1e-6)
+        assert _same_sum(a[:n], b[:n])
 
 
 def test_views_of_different_sizes_are_rejected(wrs):
