@@ -528,6 +528,16 @@ def main():
                                   "launches' (profile_scale); reported only while its recorded "
                                   "kernel digest matches the current trace source (else null)",
                 "profile_scale": pscale}
+    if traffic is not None:
+        # what DRAM really moves per launch, as a rate against the same peak
+        roofline["dram_frac"] = traffic / (trace_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]
+    if roofline["frac"] > 1.0:
+        roofline["frac_note"] = (
+            "above 1: the counted bytes (the node and splat records each ray reads, counted by "
+            "wrs_trace_count) are mostly re-read from L1 (73 % hit under ncu) and L2, not from "
+            "DRAM; DRAM moves `traffic` bytes per launch (dram_frac of the HBM rate); against the "
+            "L2-resident copy rate the counted bytes reach l2_frac; the binding limit is "
+            "instruction issue on the ALU pipe (`issue`)")
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -591,8 +601,8 @@ def main():
                                      "measured_by": "wrs_fma_peak: FFMA warp instructions per "
                                                     "second of an FMA-only kernel, one wave of "
                                                     "8 x 256 threads per SM",
-                                     "note": "the kernel's binding limit (ALU pipe 65 %, issue "
-                                             "70-72 % under ncu); the hbm entry is the "
+                                     "note": "the kernel's binding limit (ALU pipe 69 %, issue "
+                                             "70-71 % under ncu); the hbm entry is the "
                                              "counted-bytes roofline"}
 
     if not args.no_extras:
@@ -1178,26 +1188,51 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
     def fwd_bwd_retraverse():  # the adjoint re-traverses every ray
         loss_fn(0).backward()
 
+    def graphed(step):
+        """``step`` captured in a CUDA graph after three eager runs on a side stream; the
+        gradients are cleared before the capture, so every replay writes them afresh."""
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                step()
+        torch.cuda.current_stream().wait_stream(side)
+        for t in (col, opa, scl):
+            t.grad = None
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr):
+            step()
+        return gr
+
     # the launch of this workload (soft edges, several hits per ray, 512^2 views) is tuned on the
-    # forward + backward step itself: leaf size, K, and the per-pixel or packet schedule
+    # forward + backward step itself, replayed from a CUDA graph (GPU time; the eager step's host
+    # issue time depends on the host): leaf size, K, and the per-pixel or packet schedule
     d_table = []
     for d_leaf in (1, 2):
         for d_k in (1, 2, 4):
             for d_sched in (0, 2):
                 cfg["p"] = wrs.TraceParams(0, 1e-5, 0.25, d_k, 128, d_sched, 4)
                 cfg["leaf"] = d_leaf
-                # the better of two 5-step timings: single timings of a few steps are noisy
-                d_table.append((min(_time_ms(torch, fwd_bwd, 5), _time_ms(torch, fwd_bwd, 5, 1)),
-                                d_leaf, d_k, d_sched))
+                gr = graphed(fwd_bwd)
+                d_table.append((_time_ms(torch, gr.replay, 10), d_leaf, d_k, d_sched))
+                del gr
+                for t in (col, opa, scl):
+                    t.grad = None
     _, d_leaf, d_k, d_sched = min(d_table)
     cfg["p"] = wrs.TraceParams(0, 1e-5, 0.25, d_k, 128, d_sched, 4)
     cfg["leaf"] = d_leaf
-    for t in (col, opa, scl):
-        t.grad = None
     barrier()
     ms_f = max_over_ranks(_time_ms(torch, fwd, 20))
     ms_fb = max_over_ranks(_time_ms(torch, fwd_bwd, 20))
     ms_fbr = max_over_ranks(_time_ms(torch, fwd_bwd_retraverse, 20))
+    gr = graphed(fwd_bwd)
+    ms_fb_g = max_over_ranks(_time_ms(torch, gr.replay, 20))
+    del gr
+    gr = graphed(fwd_bwd_retraverse)
+    ms_fbr_g = max_over_ranks(_time_ms(torch, gr.replay, 20))
+    del gr
+    for t in (col, opa, scl):
+        t.grad = None
     rays_d = sum(v.width * v.height for v in views)
     # one step of the radius fit (rebuild, trace, loss, adjoint, Adam), eager and replayed from a
     # CUDA graph; the timed steps are real steps of two throw-away fits
@@ -1228,10 +1263,14 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
                        "edge_softness": 0.25,
                        "launch": {"leaf_size": d_leaf, "k_chunk": d_k,
                                   "schedule": SCHEDULE_NAMES[d_sched], "bvh_width": 4,
-                                  "tuned_on": "forward + backward step"},
+                                  "tuned_on": "forward + backward step replayed from a CUDA "
+                                              "graph"},
                        "forward_mrays_s": world * rays_d / (ms_f * 1e-3) / 1e6,
                        "forward_backward_mrays_s": world * rays_d / (ms_fb * 1e-3) / 1e6,
                        "forward_backward_retraverse_mrays_s": world * rays_d / (ms_fbr * 1e-3) / 1e6,
+                       "forward_backward_graphed_mrays_s": world * rays_d / (ms_fb_g * 1e-3) / 1e6,
+                       "forward_backward_retraverse_graphed_mrays_s":
+                           world * rays_d / (ms_fbr_g * 1e-3) / 1e6,
                        "forward_ms_per_view": ms_f / len(views),
                        "forward_backward_ms_per_view": ms_fb / len(views),
                        "adjoint": "forward_backward: the forward launch records each ray's "
@@ -1253,9 +1292,11 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
                        "note": "forward = one LBVH rebuild with the current radius scales + one "
                                "launch tracing all views; backward = one launch of the adjoint "
                                "over all views, accumulated in place; L2 loss vs the reference "
-                               "views; forward_backward* are eager autograd steps (colour, "
-                               "opacity and scale gradients); fit_step* is the fit's step (scale "
-                               "gradient and the Adam update), eager and graph-replayed"}
+                               "views; forward_backward* are autograd steps (colour, opacity "
+                               "and scale gradients), eager and replayed from a CUDA graph "
+                               "(*_graphed: GPU time, the eager step's host issue time depends on "
+                               "the host); fit_step* is the fit's step (scale gradient and the "
+                               "Adam update), eager and graph-replayed"}
 
     # ---------------- CPU oracle on the host cores (rank 0, N = 1) ------------------------------
     if rank == 0 and world == 1:
