@@ -996,9 +996,10 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
                                           "launch alone is one_launch vs sequential_same_knobs",
                        "k_chunk": bt["k_chunk"], "block": bt["block"], "bvh_width": bt["width"],
                        "schedule": (SCHEDULE_NAMES[bt["schedule"]] if bt["schedule"] < 3 else
-                                    "per session: packet for the {} sessions with >= 2 client "
-                                    "pixels per splat, one thread per pixel for the other "
+                                    "per session: packet for the {} sessions with >= {:g} "
+                                    "client pixels per splat, one thread per pixel for the other "
                                     "{}".format(sum(v == wrs.SCHEDULE_PACKET for v in batch.schedules),
+                                                wrs.SPARSE_PIXELS_PER_SPLAT,
                                                 sum(v != wrs.SCHEDULE_PACKET for v in batch.schedules))),
                        "leaf_size": leaf}
     del sess, batch, outs, g

@@ -658,8 +658,14 @@ def session_tiles(width: int, height: int) -> int:
     return int(_lib.wrs_session_tiles(int(width), int(height)))
 
 
+# client pixels per splat from which a session of a multi-session launch takes the warp-shared
+# traversal by default (SCHEDULE_PER_SESSION): on the 64-session workload the per-pixel traversal
+# wins below it
+SPARSE_PIXELS_PER_SPLAT = 8.0
+
+
 def sparse_schedules(sessions: Sequence[Tuple[LBVH, SplatBuffers, object]],
-                     ratio: float = 8.0) -> List[int]:
+                     ratio: float = SPARSE_PIXELS_PER_SPLAT) -> List[int]:
     """Per-session schedules for SCHEDULE_PER_SESSION: the warp-shared traversal where the client
     image has at least ``ratio`` pixels per splat (neighbouring rays then hit the same splats),
     one thread per pixel elsewhere.  The splat counts are read back from the device once (one
@@ -681,7 +687,7 @@ class Batch:
                  schedules: Optional[Sequence[int]] = None):
         """``schedules``: per session SCHEDULE_PER_PIXEL or SCHEDULE_PACKET, used by launches with
         ``schedule=SCHEDULE_PER_SESSION`` (default: the packet traversal for sessions with at
-        least 8 client pixels per splat, see :func:`sparse_schedules`)."""
+        least SPARSE_PIXELS_PER_SPLAT client pixels per splat, see :func:`sparse_schedules`)."""
         device = device or torch.device("cuda")
         n = len(sessions)
         if schedules is None:
