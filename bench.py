@@ -544,8 +544,9 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(W, statistics.mean(n_splats), {
                 "leaf_size": leaf, "k_chunk": kc,
-                # the 4-wide per-pixel kernel with K <= 2 runs 128-thread blocks whatever is asked
-                "block": min(block, 128) if (width == 4 and kc <= 2 and sched == 0) else block,
+                # the 4-wide per-pixel kernel with K 1, 2, 4 runs 128-thread blocks whatever is
+                # asked
+                "block": min(block, 128) if (width == 4 and kc in (1, 2, 4) and sched == 0) else block,
                 "autotuned": not args.no_autotune,
                 "schedule": SCHEDULE_NAMES[sched],
                 "bvh_width": width,

@@ -7,7 +7,9 @@
 // registers; nodes whose entry lies beyond the K-th key (or whose exit lies before the previous
 // pass's last key) are culled, when tested and again when popped; after each pass the K hits are
 // composited front to back.  A ray stops once its transmittance reaches t_stop, H hits are used,
-// or a pass finds fewer than K hits.  The 4-wide traversal (the default) reads seven float4 of a
+// or a pass finds fewer than K hits.  With 4-wide nodes the per-pixel kernels run each lane's
+// traversal in warp-wide steps: leaf entries are sorted and stacked with the internal ones, and
+// each iteration of the warp takes either a node step or a leaf step for the lanes that want it.  The 4-wide traversal (the default) reads seven float4 of a
 // 128-B node per visit (the near and far planes of the ray's direction, and the references); the
 // binary traversal reads a 64-B node (four float4); both through the read-only path.  A splat is
 // one float4 for the test and one float4 for its colour.
@@ -752,18 +754,28 @@ struct PersistentMinBlocks {
 #ifndef WRS_PIXEL_W4_K2_MIN_BLOCKS
 #define WRS_PIXEL_W4_K2_MIN_BLOCKS 9  // K = 2: 9 blocks (56 registers), 4 % faster than 10
 #endif
+#ifndef WRS_PIXEL_W4_K4_MIN_BLOCKS
+#define WRS_PIXEL_W4_K4_MIN_BLOCKS 8  // K = 4: 8 blocks (64 registers), 5 % faster than no cap (75)
+#endif
+// Resident 128-thread blocks of the per-pixel kernel for (K, node width) (0 = no cap), and
+// whether it is built for blocks of at most 128 threads (the host clamps the block to it).
+constexpr int pixel_min_blocks(int K, bool w4) {
+    return !w4 ? 0 : K == 1 ? WRS_PIXEL_W4_MIN_BLOCKS : K == 2 ? WRS_PIXEL_W4_K2_MIN_BLOCKS
+                   : K == 4 ? WRS_PIXEL_W4_K4_MIN_BLOCKS : 0;
+}
+constexpr bool pixel_block_128(int K, bool w4) { return (w4 && K <= 2) || pixel_min_blocks(K, w4) > 0; }
 template <int K, bool W4>
 struct PixelBounds {
-    static constexpr bool capped = K <= 2 && W4;
-    static constexpr int max_threads = capped ? 128 : 256;
-    static constexpr int min_blocks = !capped ? 0 : K == 1 ? WRS_PIXEL_W4_MIN_BLOCKS : WRS_PIXEL_W4_K2_MIN_BLOCKS;
+    static constexpr int max_threads = pixel_block_128(K, W4) ? 128 : 256;
+    static constexpr int min_blocks = pixel_min_blocks(K, W4);
 };
 
 // Resident 128-thread blocks per SM of the multi-session per-tile kernel and of the per-pixel
 // backward kernels.  The multi-session kernel with K <= 2 runs 8 (64 registers): on the 64
 // sessions 21 % faster than no cap (94 registers) and 10 % faster than 10 blocks.  The backward
-// with K = 4 runs 8 (64 registers, 7 % faster than 79); with K = 2 the same cap spills and is
-// slower, so the other instances keep no cap.  Build-time knobs (0 = no cap).
+// with K = 4 runs 8 (64 registers; with warp-wide leaf steps 12 % faster than no cap at 84
+// registers and equal to 6 blocks); with K = 2 the same cap spills and is slower, so the other
+// instances keep no cap.  Build-time knobs (0 = no cap).
 #ifndef WRS_BATCHED_MIN_BLOCKS
 #define WRS_BATCHED_MIN_BLOCKS 8
 #endif
@@ -1452,32 +1464,31 @@ __device__ __forceinline__ void backward_pixel(const Scene& sc, const Comp& cp,
     }
 }
 
-template <int K, bool W4>
-__global__ void __launch_bounds__(128, BwdBounds<K, W4>::min_blocks) k_trace_bwd(Scene sc, Comp cp, wrs_camera cam,
-                                                   const float4* __restrict__ dimg, GradOut go,
-                                                   int32_t* status) {
-    backward_pixel<K, W4>(sc, cp, cam, dimg, go, status);
+
+// The warp's backward (4-wide nodes): backward_pixel's two passes with every traversal taken by
+// the whole warp, either one traversal shared by the warp (PACKET, gather_packet: the replay and
+// the re-gathers run with all lanes active) or each lane's own traversal in warp-wide node and
+// leaf steps (gather_warp).  Each lane keeps its own chunk table and k-buffer, so its hits are
+// those of backward_pixel and its gradients equal backward_pixel's up to the order of the float
+// atomics.  All 32 lanes of a warp take part in every gather (lanes without work pass
+// part = false); the loops are warp-uniform.  A shared traversal fails for the whole warp; a
+// lane's own traversal fails for that lane only (its status bit is set, it adds no more
+// gradients).
+template <int K, bool PACKET>
+__device__ __forceinline__ int gather_bwd(const Scene& sc, const RayCtx& rc, bool part,
+                                          bool has_last, float last_key, uint32_t last_id,
+                                          float (&kk)[K], uint32_t (&ki)[K], uint32_t (&kid)[K]) {
+    if constexpr (PACKET) {
+        return gather_packet<K>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, part, has_last,
+                                last_key, last_id, kk, ki, kid);
+    } else {
+        Counts none;
+        return gather_warp<K, false>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, part, has_last,
+                                     last_key, last_id, kk, ki, kid, none);
+    }
 }
 
-// Several views in one launch (blockIdx.z = view, as k_trace_views); every view's gradients
-// accumulate into the same per-splat buffers.
-template <int K, bool W4>
-__global__ void __launch_bounds__(128, BwdBounds<K, W4>::min_blocks) k_trace_bwd_views(Scene sc, Comp cp,
-                                                         const __grid_constant__ ViewCams vc,
-                                                         const float4* __restrict__ dimg,
-                                                         size_t pixels, GradOut go,
-                                                         HitFilter flt, size_t ray0,
-                                                         int32_t* status) {
-    backward_pixel<K, W4>(sc, cp, vc.cam[blockIdx.z], dimg + blockIdx.z * pixels, go, status, flt,
-                          ray0 + blockIdx.z * pixels);
-}
-
-// Packet backward (4-wide nodes): backward_pixel's two passes with every traversal shared by the
-// warp (gather_packet), so the replay and the re-gathers run with all lanes active.  Each lane
-// keeps its own chunk table and k-buffer, so its hits are those of backward_pixel and its
-// gradients equal backward_pixel's up to the order of the float atomics.  All 32 lanes of a warp
-// take part in every gather (lanes without work pass part = false); the loops are warp-uniform.
-template <int K>
+template <int K, bool PACKET = true>
 __device__ __forceinline__ void backward_pixel_packet(const Scene& sc, const Comp& cp,
                                                       const wrs_camera& cam,
                                                       const float4* __restrict__ dimg,
@@ -1515,14 +1526,20 @@ __device__ __forceinline__ void backward_pixel_packet(const Scene& sc, const Com
             run = false;
             ok = false;
         }
-        const int count = gather_packet<K>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, run,
-                                           has_last, last_key, last_id, kk, ki, kid);
-        if (count < 0) {  // warp-uniform: the shared traversal failed for every lane
+        const int count = gather_bwd<K, PACKET>(sc, rc, run, has_last, last_key, last_id, kk, ki,
+                                                kid);
+        if (PACKET && count < 0) {  // warp-uniform: the shared traversal failed for every lane
             if (inside)
                 wrs::set_status(status, count == -1 ? WRS_STATUS_STACK_OVERFLOW : WRS_STATUS_MALFORMED_TREE);
             return;
         }
         if (!run) continue;
+        if (count < 0) {  // this lane's own traversal failed
+            wrs::set_status(status, count == -1 ? WRS_STATUS_STACK_OVERFLOW : WRS_STATUS_MALFORMED_TREE);
+            run = false;
+            ok = false;
+            continue;
+        }
         b_key[chunks] = has_last ? last_key : -kInf;
         b_id[chunks] = last_id;
         b_T[chunks] = T;
@@ -1550,13 +1567,18 @@ __device__ __forceinline__ void backward_pixel_packet(const Scene& sc, const Com
         const bool regather = mine && c != chunks - 1;  // the last chunk's hits are in last_ki
         if (__any_sync(0xffffffffu, regather)) {
             const bool hl = regather && b_key[c] != -kInf;
-            const int count = gather_packet<K>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, regather,
-                                               hl, regather ? b_key[c] : 0.f,
-                                               regather ? b_id[c] : 0u, kk, ki, kid);
-            if (count < 0) {
+            const int count = gather_bwd<K, PACKET>(sc, rc, regather, hl,
+                                                    regather ? b_key[c] : 0.f,
+                                                    regather ? b_id[c] : 0u, kk, ki, kid);
+            if (PACKET && count < 0) {
                 if (inside)
                     wrs::set_status(status, count == -1 ? WRS_STATUS_STACK_OVERFLOW : WRS_STATUS_MALFORMED_TREE);
                 return;
+            }
+            if (!PACKET && regather && count < 0) {  // (pass A traversed the same passes)
+                wrs::set_status(status, count == -1 ? WRS_STATUS_STACK_OVERFLOW : WRS_STATUS_MALFORMED_TREE);
+                chunks = 0;
+                continue;
             }
         }
         if (mine) {
@@ -1564,6 +1586,39 @@ __device__ __forceinline__ void backward_pixel_packet(const Scene& sc, const Com
             chunk_adjoint<K>(sc, cp, rc.ray, hits, b_used[c], b_T[c], g, S, P, go);
         }
     }
+}
+
+// The per-pixel backward: each lane's own traversal, in warp-wide node and leaf steps with 4-wide
+// nodes, per lane with binary nodes.
+template <int K, bool W4>
+__device__ __forceinline__ void backward_pixel_any(const Scene& sc, const Comp& cp,
+                                                   const wrs_camera& cam,
+                                                   const float4* __restrict__ dimg,
+                                                   const GradOut& go, int32_t* status,
+                                                   HitFilter flt = HitFilter{nullptr, 0},
+                                                   size_t ray_base = 0) {
+    if constexpr (W4) backward_pixel_packet<K, false>(sc, cp, cam, dimg, go, status, flt, ray_base);
+    else backward_pixel<K, false>(sc, cp, cam, dimg, go, status, flt, ray_base);
+}
+
+template <int K, bool W4>
+__global__ void __launch_bounds__(128, BwdBounds<K, W4>::min_blocks) k_trace_bwd(Scene sc, Comp cp, wrs_camera cam,
+                                                   const float4* __restrict__ dimg, GradOut go,
+                                                   int32_t* status) {
+    backward_pixel_any<K, W4>(sc, cp, cam, dimg, go, status);
+}
+
+// Several views in one launch (blockIdx.z = view, as k_trace_views); every view's gradients
+// accumulate into the same per-splat buffers.
+template <int K, bool W4>
+__global__ void __launch_bounds__(128, BwdBounds<K, W4>::min_blocks) k_trace_bwd_views(Scene sc, Comp cp,
+                                                         const __grid_constant__ ViewCams vc,
+                                                         const float4* __restrict__ dimg,
+                                                         size_t pixels, GradOut go,
+                                                         HitFilter flt, size_t ray0,
+                                                         int32_t* status) {
+    backward_pixel_any<K, W4>(sc, cp, vc.cam[blockIdx.z], dimg + blockIdx.z * pixels, go, status,
+                              flt, ray0 + blockIdx.z * pixels);
 }
 
 // 4 resident 256-thread blocks (64 registers): 6 % faster at K 4 and 13 % at K 2 than no cap
@@ -2000,8 +2055,8 @@ int wrs_trace(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* c
                                              make_scene(bvh, sorted, params->opacity, 4),
                                              comp_of(params), *cam, out, status);
     else {
-        // the 4-wide kernel with K <= 2 is built for blocks of at most 128 threads
-        const int block = (W == 4 && K <= 2 && params->block > 128) ? 128 : params->block;
+        // a capped kernel is built for blocks of at most 128 threads
+        const int block = (pixel_block_128(K, W == 4) && params->block > 128) ? 128 : params->block;
         dispatch_k<LaunchTrace>(K, W, grid_for(cam, block), block, s, sc, comp_of(params), *cam,
                                 out, status);
     }
@@ -2040,7 +2095,7 @@ int trace_views_impl(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_ca
     // per-pixel blocks as wrs_trace; the persistent schedule runs per pixel here (the views
     // together fill the GPU, which is what lane refill is for)
     const int block = packet ? params->block
-                             : ((W == 4 && K <= 2 && params->block > 128) ? 128 : params->block);
+                             : ((pixel_block_128(K, W == 4) && params->block > 128) ? 128 : params->block);
     const Scene sc = make_scene(bvh, sorted, params->opacity, packet ? 4 : W);
     for (int v0 = 0; v0 < n_views; v0 += kMaxViews) {
         const int nv = n_views - v0 < kMaxViews ? n_views - v0 : kMaxViews;
