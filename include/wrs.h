@@ -126,7 +126,7 @@ typedef struct {
     const float* opacity; /* device [n] per-splat opacity in COMPACTED order, or NULL (= 1) */
     int32_t k_chunk;      /* hits gathered per traversal pass: 1, 2, 4, 8 or 16 */
     int32_t block;        /* threads per block: 64, 128 or 256 (per-pixel schedule; the 4-wide
-                             traversal with k_chunk <= 2 uses at most 128) */
+                             traversal with k_chunk 1, 2 or 4 uses at most 128) */
     int32_t schedule;     /* WRS_SCHEDULE_PER_PIXEL, WRS_SCHEDULE_PERSISTENT or
                              WRS_SCHEDULE_PACKET; wrs_trace_batched: PER_PIXEL and PACKET = one
                              warp per 8x4 tile of all sessions, PERSISTENT = lane refill */
@@ -343,7 +343,8 @@ int wrs_trace_batched(const wrs_session* sessions, int32_t n_sessions, uint32_t 
  * global_scale must be the values the LBVH was built with.  The outputs are zeroed by this call
  * over the first in-capacity entries; accumulation uses float atomics (summation order is not
  * fixed).  status: device word (CHUNK_OVERFLOW if a ray has more than 64 * k_chunk hits).
- * Schedules: PER_PIXEL one thread per pixel; PERSISTENT lane refill; PACKET the same per-ray work
+ * Schedules: PER_PIXEL one thread per pixel (with 4-wide nodes each warp's lanes take their node
+ * and leaf steps together, as in wrs_trace); PERSISTENT lane refill; PACKET the same per-ray work
  * with every traversal shared by the warp (4-wide nodes, as wrs_trace's packet schedule). */
 int wrs_trace_backward(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* cam,
                        const wrs_trace_params* params, const float* radius_scale,

@@ -200,7 +200,8 @@ __device__ __forceinline__ void cswap(float& ka, uint32_t& ra, float& kb, uint32
 // One visit of the 4-wide node of binary node `ref` (its grandchildren): four box tests from
 // structure-of-arrays loads; hit leaf entries are tested right away; hit internal entries are
 // sorted by entry distance (5-comparator network), the nearest is returned and the others pushed
-// far to near.  Same return convention as visit_node.
+// far to near.  Same return convention as visit_node.  (The lane-refill schedule's visit; the
+// per-pixel kernels use visit_node4_sorted, which stacks leaf entries too.)
 template <int K, bool COUNT, typename E>
 __device__ __forceinline__ int64_t visit_node4(const Scene& sc, const Ray& ray,
                                                const wrs::BoxRay& br, uint32_t ref, uint32_t n,
