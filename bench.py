@@ -76,6 +76,8 @@ def parse():
     cs.add_argument("--max-hits", type=int, default=0)
     cs.add_argument("--schedule", type=int, default=0, help="0 per pixel, 1 persistent, 2 packet")
     cs.add_argument("--width", type=int, default=4, help="2 binary nodes, 4 four-wide nodes")
+    cs.add_argument("--retraverse", action="store_true",
+                    help="diff: the adjoint traces every ray again (no recorded hit lists)")
     return ap.parse_args()
 
 
@@ -623,7 +625,8 @@ def run_case(a, wrs, torch):
     the benchmark (pose 4g) and traces ``--frames`` of its client poses, so that a few launches
     sample poses spread over the set; without it, the server camera and the first ``--frames``
     poses.  diff: two forward + backward steps of the 8 views of the differentiation workload
-    (one launch each way per step).  batched: the first ``--sessions`` of the multi-session
+    (one launch each way per step; the forward records the hit lists and the adjoint runs from
+    them, or with ``--retraverse`` the adjoint traces every ray again).  batched: the first ``--sessions`` of the multi-session
     workload, two launches of wrs_trace_batched (the second is the one to profile)."""
     import synth
     if a.case == "diff":
@@ -703,12 +706,15 @@ def _case_diff(a, wrs, torch, synth):
     for _ in range(2):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        loss = ((wrs.render_views(sp, views, col, opa, scl, params, a.leaf) - target) ** 2).mean()
+        loss = torch.nn.functional.mse_loss(
+            wrs.render_views(sp, views, col, opa, scl, params, a.leaf,
+                             record_hits=0 if a.retraverse else None), target)
         loss.backward()
         e1.record()
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
     print(json.dumps({"workload": "diff", "splats": n, "views": len(views),
+                      "adjoint": "re-traversal" if a.retraverse else "recorded hit lists",
                       "fwd_bwd_ms": ms, "loss": float(loss.detach())}))
 
 
