@@ -252,11 +252,12 @@ __device__ __forceinline__ int64_t visit_node4(const Scene& sc, const Ray& ray,
     return r[0];
 }
 
-// One traversal pass: the K smallest hits (key, id) strictly after (last_key, last_id).
-// Returns the number gathered (<= K); -1 if the stack overflowed; -2 if the pass met a reference
-// outside the tree or visited more nodes than the tree has (impossible for a well-formed tree; it
-// bounds the loop regardless).
-template <int K, bool COUNT, bool W4>
+// One traversal pass of one lane over the binary nodes: the K smallest hits (key, id) strictly
+// after (last_key, last_id).  Returns the number gathered (<= K); -1 if the stack overflowed; -2
+// if the pass met a reference outside the tree or visited more nodes than the tree has
+// (impossible for a well-formed tree; it bounds the loop regardless).  (The 4-wide nodes are
+// traversed by the whole warp: gather_warp, gather_packet.)
+template <int K, bool COUNT>
 __device__ __forceinline__ int gather(const Scene& sc, const Ray& ray, const wrs::BoxRay& br,
                                       uint32_t n, uint32_t leaf, int32_t root, bool has_last,
                                       float last_key, uint32_t last_id, float (&kk)[K],
@@ -276,13 +277,9 @@ __device__ __forceinline__ int gather(const Scene& sc, const Ray& ray, const wrs
     uint32_t budget = m + 1;  // internal node visits allowed in one pass
     while (true) {
         if (budget-- == 0) return -2;
-        const int64_t next =
-            W4 ? visit_node4<K, COUNT, StackEntry>(sc, ray, br, ref, n, leaf, m, has_last,
-                                                   last_key, last_id, kk, ki, kid, count, stack,
-                                                   sp, cnt)
-               : visit_node<K, COUNT, StackEntry>(sc, ray, br, ref, n, leaf, m, has_last,
-                                                  last_key, last_id, kk, ki, kid, count, stack, sp,
-                                                  cnt);
+        const int64_t next = visit_node<K, COUNT, StackEntry>(sc, ray, br, ref, n, leaf, m,
+                                                              has_last, last_key, last_id, kk, ki,
+                                                              kid, count, stack, sp, cnt);
         if (next < 0) return (int)next;
         if (next != kLeafBit) { ref = (uint32_t)next; continue; }
         if (!pop_within(stack, sp, kk[K - 1], ref)) break;
@@ -372,10 +369,10 @@ __device__ __forceinline__ void record_chunk(const uint32_t (&ki)[K], int used0,
     }
 }
 
-// Forward trace of one ray (spec S6).  overflow_bits: status bits of a traversal failure.
-// With REC, the composited hits go to rec_hits[0 .. cap) and their number (cap + 1 beyond cap)
-// to *rec_count.
-template <int K, bool COUNT, bool W4, bool REC = false>
+// Forward trace of one ray over the binary nodes (spec S6).  overflow_bits: status bits of a
+// traversal failure.  With REC, the composited hits go to rec_hits[0 .. cap) and their number
+// (cap + 1 beyond cap) to *rec_count.
+template <int K, bool COUNT, bool REC = false>
 __device__ __forceinline__ float4 trace_ray(const Scene& sc, const Comp& cp, const RayCtx& rc,
                                             uint32_t& overflow_bits, Counts& cnt,
                                             uint32_t* rec_hits = nullptr,
@@ -394,8 +391,8 @@ __device__ __forceinline__ float4 trace_ray(const Scene& sc, const Comp& cp, con
     float kk[K];
     uint32_t ki[K], kid[K];
     while (true) {
-        const int count = gather<K, COUNT, W4>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, has_last,
-                                               last_key, last_id, kk, ki, kid, cnt);
+        const int count = gather<K, COUNT>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, has_last,
+                                           last_key, last_id, kk, ki, kid, cnt);
         if (COUNT) cnt.passes++;
         if (count < 0) { overflow_bits = count == -1 ? WRS_STATUS_STACK_OVERFLOW : WRS_STATUS_MALFORMED_TREE; break; }
         if constexpr (REC) {
@@ -572,7 +569,7 @@ __device__ __forceinline__ float4 trace_ray_warp(const Scene& sc, const Comp& cp
     } else {
         overflow_bits = 0;
         if (!active) return make_float4(0.f, 0.f, 0.f, 0.f);
-        return trace_ray<K, COUNT, false, REC>(sc, cp, rc, overflow_bits, cnt, rec_hits,
+        return trace_ray<K, COUNT, REC>(sc, cp, rc, overflow_bits, cnt, rec_hits,
                                                rec_count, cap);
     }
 }
@@ -1403,7 +1400,9 @@ __device__ __forceinline__ void chunk_adjoint(const Scene& sc, const Comp& cp, c
     }
 }
 
-template <int K, bool W4>
+// The per-lane backward over the binary nodes (the 4-wide nodes take backward_pixel_packet's
+// warp-wide structure).
+template <int K>
 __device__ __forceinline__ void backward_pixel(const Scene& sc, const Comp& cp,
                                                const wrs_camera& cam,
                                                const float4* __restrict__ dimg, const GradOut& go,
@@ -1435,7 +1434,7 @@ __device__ __forceinline__ void backward_pixel(const Scene& sc, const Comp& cp,
     uint32_t last_id = 0;
     while (true) {
         if (chunks == wrs::kBwdChunks) { wrs::set_status(status, WRS_STATUS_CHUNK_OVERFLOW); return; }
-        const int count = gather<K, false, W4>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, has_last,
+        const int count = gather<K, false>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, has_last,
                                            last_key, last_id, kk, ki, kid, cnt);
         if (count < 0) { wrs::set_status(status, count == -1 ? WRS_STATUS_STACK_OVERFLOW : WRS_STATUS_MALFORMED_TREE); return; }
         b_key[chunks] = has_last ? last_key : -kInf;
@@ -1458,7 +1457,7 @@ __device__ __forceinline__ void backward_pixel(const Scene& sc, const Comp& cp,
         if (u == 0) continue;
         if (c != chunks - 1) {  // the last chunk's hits are still in the k-buffer from pass A
             const bool hl = b_key[c] != -kInf;
-            gather<K, false, W4>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, hl, b_key[c], b_id[c],
+            gather<K, false>(sc, rc.ray, rc.br, rc.n, rc.leaf, rc.root, hl, b_key[c], b_id[c],
                                  kk, ki, kid, cnt);
         }
         chunk_adjoint<K>(sc, cp, rc.ray, ki, u, b_T[c], g, S, P, go);
@@ -1599,7 +1598,7 @@ __device__ __forceinline__ void backward_pixel_any(const Scene& sc, const Comp& 
                                                    HitFilter flt = HitFilter{nullptr, 0},
                                                    size_t ray_base = 0) {
     if constexpr (W4) backward_pixel_packet<K, false>(sc, cp, cam, dimg, go, status, flt, ray_base);
-    else backward_pixel<K, false>(sc, cp, cam, dimg, go, status, flt, ray_base);
+    else backward_pixel<K>(sc, cp, cam, dimg, go, status, flt, ray_base);
 }
 
 template <int K, bool W4>
