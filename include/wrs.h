@@ -291,6 +291,20 @@ int wrs_build_lbvh(const wrs_splats* in, const float* radius_scale, float global
                    const wrs_lbvh* bvh, wrs_splats* sorted, void* scratch, size_t scratch_bytes,
                    wrs_stream_t stream);
 
+/* The same tree with new radii: a tree's leaf order and shape depend on the splat centres only
+ * (the Morton codes), so when only the radius scales change (the radius fit) the boxes can be
+ * refitted over the existing tree.  Recomputes the header, the effective radii of sorted (and its
+ * other arrays), every binary and 4-wide node box, bottom-up over the leaf order and parent links
+ * that the last wrs_build_lbvh call left in `scratch`: the result is bitwise the tree
+ * wrs_build_lbvh would build with these radius scales, at the cost of the bounds and the refit
+ * (no Morton codes, sort or radix tree).  Contract: the same in, bvh, sorted and scratch as that
+ * build, and since then no change to the splat centres or count and no other use of the scratch;
+ * otherwise the result is undefined (no access leaves the buffers and the kernels still end).
+ * Arguments and errors as wrs_build_lbvh. */
+int wrs_refit_lbvh(const wrs_splats* in, const float* radius_scale, float global_scale,
+                   const wrs_lbvh* bvh, wrs_splats* sorted, void* scratch, size_t scratch_bytes,
+                   wrs_stream_t stream);
+
 /* Trace the client camera's primary rays through the spheres and composite (spec S5, S6; the
  * paper's first-hit query is max_hits = 1).  Hits ordered by (entry distance, id); each
  * composited hit adds T (o w) rgb and multiplies T by 1 - clamp(o a w, 0, 1).  rgba_out:

@@ -147,6 +147,8 @@ _sig("wrs_lbvh_bytes", _Z, _U, _U)
 _sig("wrs_lbvh_scratch_bytes", _Z, _U, _U)
 _sig("wrs_build_lbvh", _I, ctypes.POINTER(_Splats), _P, _F, ctypes.POINTER(_Lbvh),
      ctypes.POINTER(_Splats), _P, _Z, _P)
+_sig("wrs_refit_lbvh", _I, ctypes.POINTER(_Splats), _P, _F, ctypes.POINTER(_Lbvh),
+     ctypes.POINTER(_Splats), _P, _Z, _P)
 _sig("wrs_trace", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats), ctypes.POINTER(Camera),
      ctypes.POINTER(_Params), _P, _P, _P)
 _sig("wrs_trace_count", _I, ctypes.POINTER(_Lbvh), ctypes.POINTER(_Splats), ctypes.POINTER(Camera),
@@ -541,6 +543,48 @@ def build_lbvh(splats: SplatBuffers, leaf_size: int = 1, radius_scale: Optional[
                                ctypes.byref(o), _ptr(scratch), scratch.numel(), _stream(stream)),
            "wrs_build_lbvh")
     return bvh, sorted
+
+
+def refit_lbvh(splats: SplatBuffers, bvh: LBVH, sorted: SplatBuffers, scratch: torch.Tensor,
+               radius_scale: Optional[torch.Tensor] = None, global_scale: float = 1.0,
+               stream=None) -> Tuple[LBVH, SplatBuffers]:
+    """wrs_refit_lbvh: the tree that :func:`build_lbvh` built into ``bvh``/``sorted`` with
+    ``scratch`` over the same splat centres, with new radius scales (bitwise the tree a new build
+    would give; no Morton codes, sort or radix tree).  The splat centres, their count and the
+    scratch must be unchanged since that build."""
+    _buf(scratch, lbvh_scratch_bytes(splats.capacity, bvh.leaf_size), torch.uint8, "scratch")
+    a, b, o = splats.c(), bvh.c(), sorted.c()
+    _check(_lib.wrs_refit_lbvh(ctypes.byref(a), _ptr(radius_scale), float(global_scale), ctypes.byref(b),
+                               ctypes.byref(o), _ptr(scratch), scratch.numel(), _stream(stream)),
+           "wrs_refit_lbvh")
+    return bvh, sorted
+
+
+class RefitTree:
+    """An LBVH over splats whose centres stay fixed while their radius scales change (a radius
+    fit): the first :meth:`update` builds it (wrs_build_lbvh), later ones refit it
+    (wrs_refit_lbvh) in the same buffers.  The buffers are reused: a tree handed to a traversal
+    must have been used before the next update (an autograd step's backward runs before the next
+    step's forward)."""
+
+    def __init__(self, splats: SplatBuffers, leaf_size: int = 1):
+        dev = splats.pos_r.device
+        self.splats = splats
+        self.leaf_size = int(leaf_size)
+        self.bvh = LBVH(splats.capacity, leaf_size, device=dev, _fill=False)
+        self.sorted = SplatBuffers(splats.capacity, device=dev, sorted=True, _fill=False)
+        self.scratch = _scratch(lbvh_scratch_bytes(splats.capacity, leaf_size), dev)
+        self.built = False
+
+    def update(self, radius_scale: Optional[torch.Tensor] = None, global_scale: float = 1.0,
+               stream=None) -> Tuple[LBVH, SplatBuffers]:
+        if self.built:
+            return refit_lbvh(self.splats, self.bvh, self.sorted, self.scratch, radius_scale,
+                              global_scale, stream)
+        build_lbvh(self.splats, self.leaf_size, radius_scale, global_scale, bvh=self.bvh,
+                   sorted=self.sorted, scratch=self.scratch, stream=stream)
+        self.built = True
+        return self.bvh, self.sorted
 
 
 @dataclass

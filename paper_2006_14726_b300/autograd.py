@@ -8,7 +8,9 @@ rebuilds the LBVH with the current scales; :func:`render_views` renders several 
 build, all views in one launch (wrs_trace_views), and their gradients in one launch into one
 set of buffers (wrs_trace_backward_views).  When the per-ray hit lists fit in memory the forward
 pass records them (wrs_trace_views_record) and the adjoint runs from them without traversal
-(wrs_trace_backward_views_recorded); otherwise the adjoint re-traverses.
+(wrs_trace_backward_views_recorded); otherwise the adjoint re-traverses.  Given a RefitTree (splat
+centres fixed, only the radius scales change, as in a radius fit) the forward refits that tree
+(wrs_refit_lbvh) instead of building a new one.
 """
 from __future__ import annotations
 
@@ -16,7 +18,7 @@ from typing import Optional, Sequence
 
 import torch
 
-from . import (HitLists, SplatBuffers, TraceParams, build_lbvh, trace, trace_backward,
+from . import (HitLists, RefitTree, SplatBuffers, TraceParams, build_lbvh, trace, trace_backward,
                trace_backward_views, trace_backward_views_recorded, trace_views,
                trace_views_record)
 
@@ -71,14 +73,20 @@ class MultiViewTraceFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, rgba: torch.Tensor, opacity: Optional[torch.Tensor],
                 radius_scale: Optional[torch.Tensor], splats: SplatBuffers, cams,
-                params: TraceParams, leaf_size: int, record_hits: int):
+                params: TraceParams, leaf_size: int, record_hits: int,
+                tree: Optional[RefitTree]):
         n = rgba.shape[0]
         if n > splats.capacity:
             raise ValueError("more colours than splats")
         splats.rgba[:n].copy_(rgba.detach())
         op = None if opacity is None else opacity.detach().contiguous()
         sc = None if radius_scale is None else radius_scale.detach().contiguous()
-        bvh, sorted_ = build_lbvh(splats, leaf_size, radius_scale=sc)
+        if tree is not None:
+            if tree.splats is not splats or tree.leaf_size != leaf_size:
+                raise ValueError("the tree belongs to other splats or another leaf size")
+            bvh, sorted_ = tree.update(sc)
+        else:
+            bvh, sorted_ = build_lbvh(splats, leaf_size, radius_scale=sc)
         c0 = cams[0]
         if any((c.width, c.height) != (c0.width, c0.height) for c in cams):
             raise ValueError("all views must have the same size")
@@ -105,22 +113,25 @@ class MultiViewTraceFunction(torch.autograd.Function):
         return (g_rgba[:n] if need_rgba else None,
                 g_op[:n] if need_op else None,
                 g_sc[:n] if need_sc else None,
-                None, None, None, None, None)
+                None, None, None, None, None, None)
 
 
 def render_views(splats: SplatBuffers, cams: Sequence, rgba: torch.Tensor,
                  opacity: Optional[torch.Tensor] = None,
                  radius_scale: Optional[torch.Tensor] = None, params: TraceParams = TraceParams(),
-                 leaf_size: int = 1, record_hits: Optional[int] = None) -> torch.Tensor:
+                 leaf_size: int = 1, record_hits: Optional[int] = None,
+                 tree: Optional[RefitTree] = None) -> torch.Tensor:
     """Differentiable images [V,H,W,4] of several same-size client views of the splats.
 
     ``record_hits``: capacity of the per-ray hit lists the forward pass records so that the
     adjoint needs no traversal (rays with more hits are traced again); 0 = always re-traverse;
-    None = RECORD_CAPACITY when the lists fit in RECORD_BUDGET_BYTES, else 0."""
+    None = RECORD_CAPACITY when the lists fit in RECORD_BUDGET_BYTES, else 0.
+    ``tree``: a RefitTree over ``splats`` (same leaf size) to refit with the radius scales instead
+    of building a new LBVH; the splat centres must not change while it is used."""
     cams = list(cams)
     if record_hits is None:
         rays = len(cams) * cams[0].width * cams[0].height
         record_hits = (RECORD_CAPACITY if HitLists.nbytes(rays, RECORD_CAPACITY)
                        <= RECORD_BUDGET_BYTES else 0)
     return MultiViewTraceFunction.apply(rgba, opacity, radius_scale, splats, cams, params,
-                                        leaf_size, int(record_hits))
+                                        leaf_size, int(record_hits), tree)

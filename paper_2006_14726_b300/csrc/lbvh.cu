@@ -548,7 +548,9 @@ __global__ void __launch_bounds__(kRefitBlock) k_leaves_refit(
     if (m < 2) return;
     uint32_t pp = leaf_parent[j];
     bool local = true;  // ancestors of a node that spans blocks span blocks too
-    while (true) {
+    // a climb has fewer levels than the tree has leaves; the bound only matters if the links are
+    // not those of this splat set (wrs_refit_lbvh with another build's scratch): it then ends
+    for (uint32_t level = 0; level < m; level++) {
         const uint32_t node = pp >> 1, slot = pp & 1u;
         if (node + 1 >= m) return;  // never taken for a well-formed tree
         const uint32_t gp = node != 0 ? node_parent[node] : 0u;  // node's own link to its parent
@@ -611,10 +613,10 @@ size_t wrs_lbvh_scratch_bytes(uint32_t capacity, uint32_t leaf_size) {
     return scratch_layout(capacity, leaf_size, nullptr, nullptr);
 }
 
-int wrs_build_lbvh(const wrs_splats* in, const float* radius_scale, float global_scale,
-                   const wrs_lbvh* bvh, wrs_splats* sorted, void* scratch, size_t scratch_bytes,
-                   wrs_stream_t stream) {
-    const char* fn = "wrs_build_lbvh";
+// Arguments of wrs_build_lbvh and wrs_refit_lbvh.
+static int check_lbvh_args(const wrs_splats* in, const float* radius_scale, float global_scale,
+                           const wrs_lbvh* bvh, const wrs_splats* sorted, const void* scratch,
+                           size_t scratch_bytes, const char* fn) {
     if (!in || !bvh || !sorted) return wrs::fail(WRS_ERR_ARG, "%s: NULL struct", fn);
     if (!in->pos_r || !in->rgba || !in->id || !in->n)
         return wrs::fail(WRS_ERR_ARG, "%s: NULL input splat array", fn);
@@ -634,13 +636,23 @@ int wrs_build_lbvh(const wrs_splats* in, const float* radius_scale, float global
         return wrs::fail(WRS_ERR_ARG, "%s: float4 arrays and nodes must be 16-byte aligned", fn);
     if (!radius_scale && !(global_scale == global_scale))
         return wrs::fail(WRS_ERR_ARG, "%s: global_scale is NaN", fn);
-    const uint32_t cap = in->capacity;
-    const size_t need = scratch_layout(cap, leaf, nullptr, nullptr);
+    const size_t need = scratch_layout(in->capacity, leaf, nullptr, nullptr);
     if (!scratch || scratch_bytes < need)
         return wrs::fail(WRS_ERR_SCRATCH, "%s: scratch needs %zu bytes, got %zu", fn, need,
                          scratch_bytes);
     if (reinterpret_cast<uintptr_t>(scratch) & 255)
         return wrs::fail(WRS_ERR_ARG, "%s: scratch must be 256-byte aligned", fn);
+    return WRS_OK;
+}
+
+int wrs_build_lbvh(const wrs_splats* in, const float* radius_scale, float global_scale,
+                   const wrs_lbvh* bvh, wrs_splats* sorted, void* scratch, size_t scratch_bytes,
+                   wrs_stream_t stream) {
+    if (int rc = check_lbvh_args(in, radius_scale, global_scale, bvh, sorted, scratch,
+                                 scratch_bytes, "wrs_build_lbvh"))
+        return rc;
+    const uint32_t leaf = bvh->leaf_size;
+    const uint32_t cap = in->capacity;
     Scratch S;
     scratch_layout(cap, leaf, static_cast<char*>(scratch), &S);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -683,6 +695,44 @@ int wrs_build_lbvh(const wrs_splats* in, const float* radius_scale, float global
                                       sorted->src,
                                       nodes + 4 * (size_t)wrs::lbvh_binary_slots(cap, leaf));
     WRS_LAUNCH_CHECK("wrs_build_lbvh refit");
+    return WRS_OK;
+}
+
+int wrs_refit_lbvh(const wrs_splats* in, const float* radius_scale, float global_scale,
+                   const wrs_lbvh* bvh, wrs_splats* sorted, void* scratch, size_t scratch_bytes,
+                   wrs_stream_t stream) {
+    if (int rc = check_lbvh_args(in, radius_scale, global_scale, bvh, sorted, scratch,
+                                 scratch_bytes, "wrs_refit_lbvh"))
+        return rc;
+    const uint32_t leaf = bvh->leaf_size;
+    const uint32_t cap = in->capacity;
+    Scratch S;
+    scratch_layout(cap, leaf, static_cast<char*>(scratch), &S);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    LbvhHeader* hdr = static_cast<LbvhHeader*>(bvh->nodes);
+    float4* nodes = wrs::lbvh_nodes(bvh->nodes);
+    const float4* pos4 = reinterpret_cast<const float4*>(in->pos_r);
+    const uint32_t m_cap = leaves_for(cap, leaf);
+    // the header again (the centre bounds come out as before; the largest radius and the
+    // traversal's coordinate bound follow the new radii), then the leaves and the climb over the
+    // order and the links the build left in scratch (vals0 and the parent links)
+    k_bounds_partial<<<kBoundsBlocks, 256, 0, s>>>(pos4, radius_scale, global_scale, in->n, cap,
+                                                   S.partials);
+    WRS_LAUNCH_CHECK("wrs_refit_lbvh bounds");
+    k_bounds_final<<<1, kBoundsBlocks, 0, s>>>(S.partials, in->n, cap, leaf, hdr, sorted->n);
+    WRS_LAUNCH_CHECK("wrs_refit_lbvh bounds final");
+    if (cap == 0) return WRS_OK;
+    cudaError_t e = cudaMemsetAsync(S.visit, 0, sizeof(uint32_t) * m_cap, s);
+    if (e != cudaSuccess) return wrs::cuda_fail(e, "wrs_refit_lbvh memset");
+    const uint32_t grefit = (m_cap + kRefitBlock - 1) / kRefitBlock;
+    k_leaves_refit<<<grefit, kRefitBlock, 0, s>>>(S.vals0, pos4, reinterpret_cast<const float4*>(in->rgba),
+                                      in->id, radius_scale, global_scale, hdr, nodes, S.leaf_parent,
+                                      S.node_parent, S.node_range, S.visit,
+                                      reinterpret_cast<float4*>(sorted->pos_r),
+                                      reinterpret_cast<float4*>(sorted->rgba), sorted->id,
+                                      sorted->src,
+                                      nodes + 4 * (size_t)wrs::lbvh_binary_slots(cap, leaf));
+    WRS_LAUNCH_CHECK("wrs_refit_lbvh refit");
     return WRS_OK;
 }
 

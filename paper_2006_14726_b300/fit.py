@@ -4,8 +4,9 @@ The paper suggests taking the splat radius from the data rather than from a fixe
 differentiable renderer (wrs_trace_backward behind :mod:`.autograd`) makes that a gradient
 descent: the radius scales s (r = max(s, 0) r0, compacted splat order) are moved by Adam to
 lower the mean squared error between the rendered client views and reference images of the same
-poses.  Every step is one LBVH rebuild with the current scales, one launch tracing all views and
-one launch of the adjoint over all views.
+poses.  Every step refits the LBVH to the current scales (the splat centres do not move, so the
+tree's order and shape stay; wrs_refit_lbvh), then one launch traces all views and one launch
+runs the adjoint over all views.
 
 With ``graph=True`` (CUDA only) the whole step — rebuild, trace, loss, adjoint and the Adam
 update — is captured once in a CUDA graph and replayed: a step then costs one graph launch of
@@ -25,6 +26,7 @@ from typing import Callable, List, Optional, Sequence
 import torch
 import torch.nn.functional as F
 
+from . import RefitTree
 from .autograd import render_views
 
 # eager steps before the capture of a graphed fit
@@ -54,9 +56,11 @@ class RadiusFit:
             self.opacity = (opacity if opacity is not None
                             else torch.ones(n, device=dev)).detach()
             cams = list(cams)
+            self.tree = RefitTree(splats, leaf_size)
 
             def render(s):
-                return render_views(splats, cams, self.rgba, self.opacity, s, params, leaf_size)
+                return render_views(splats, cams, self.rgba, self.opacity, s, params, leaf_size,
+                                    tree=self.tree)
         self.render = render
         if scale is None:
             n = splats.count() if splats is not None else targets.shape[0]

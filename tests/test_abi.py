@@ -119,6 +119,13 @@ def test_host_validation_without_device(wrs):
     small = wrs._Lbvh(fake.value, 8, 1)
     assert lib.wrs_build_lbvh(ctypes.byref(big), None, 1.0, ctypes.byref(small), ctypes.byref(srt), fake, 1 << 30, None) == wrs.WRS_ERR_CAPACITY
     assert lib.wrs_build_lbvh(ctypes.byref(big), None, 1.0, ctypes.byref(bv1), ctypes.byref(srt), fake, 16, None) == wrs.WRS_ERR_SCRATCH
+    # the refit takes the build's arguments and checks them the same way
+    assert lib.wrs_refit_lbvh(ctypes.byref(big), None, 1.0, ctypes.byref(bv), ctypes.byref(srt), fake, 1 << 30, None) == wrs.WRS_ERR_ARG
+    assert "wrs_refit_lbvh" in wrs.last_error()
+    assert lib.wrs_refit_lbvh(ctypes.byref(big), None, 1.0, ctypes.byref(bv1), ctypes.byref(nosrc), fake, 1 << 30, None) == wrs.WRS_ERR_ARG
+    assert lib.wrs_refit_lbvh(ctypes.byref(big), None, 1.0, ctypes.byref(small), ctypes.byref(srt), fake, 1 << 30, None) == wrs.WRS_ERR_CAPACITY
+    assert lib.wrs_refit_lbvh(ctypes.byref(big), None, 1.0, ctypes.byref(bv1), ctypes.byref(srt), fake, 16, None) == wrs.WRS_ERR_SCRATCH
+    assert lib.wrs_refit_lbvh(ctypes.byref(big), None, float("nan"), ctypes.byref(bv1), ctypes.byref(srt), fake, 1 << 30, None) == wrs.WRS_ERR_ARG
     # trace: bad k_chunk / block / t_stop / edge softness
     for p in (wrs._Params(0, 1e-5, 0.0, None, 3, 128), wrs._Params(0, 1e-5, 0.0, None, 8, 96),
               wrs._Params(0, 1.5, 0.0, None, 8, 128), wrs._Params(0, 1e-5, 1.0, None, 8, 128),
