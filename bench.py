@@ -1303,8 +1303,9 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
                                "views; forward_backward* are autograd steps (colour, opacity "
                                "and scale gradients), eager and replayed from a CUDA graph "
                                "(*_graphed: GPU time, the eager step's host issue time depends on "
-                               "the host); fit_step* is the fit's step (scale gradient and the "
-                               "Adam update), eager and graph-replayed"}
+                               "the host); fit_step* is the fit's step (the LBVH refitted to "
+                               "the new radius scales, the scale gradient and the Adam update), "
+                               "eager and graph-replayed"}
 
     # ---------------- CPU oracle on the host cores (rank 0, N = 1) ------------------------------
     if rank == 0 and world == 1:
