@@ -110,3 +110,20 @@ def test_render_views_tree_checks(wrs):
     with pytest.raises(ValueError):
         wrs.render_views(sp, cams, col, None, torch.ones(n, device="cuda"),
                          tree=wrs.RefitTree(sp, 2))
+
+
+def test_refit_equals_build_1080p(wrs):
+    """The full-size case: a 1080p server image (about 2 M splats), refitted to per-splat scales
+    after a build with scale 1, against a new build: every record, 4-wide node and sorted splat."""
+    rgba, depth = synth.synthetic_server_image(1920, 1080, 52)
+    srv = synth.LARGE.server_cam()
+    sp = wrs.unproject(torch.from_numpy(rgba).cuda(), torch.from_numpy(depth).cuda(), srv)
+    n = sp.count()
+    assert n > 1_500_000
+    tree = wrs.RefitTree(sp, 1)
+    tree.update(None, 1.0)
+    g = torch.Generator(device="cpu").manual_seed(9)
+    sc = (0.25 + 1.5 * torch.rand(n, generator=g)).cuda()
+    bvh, srt = tree.update(sc)
+    ref_bvh, ref_srt = wrs.build_lbvh(sp, 1, radius_scale=sc)
+    _same_tree(wrs, bvh, srt, ref_bvh, ref_srt)
