@@ -165,20 +165,15 @@ def test_backward_diff_workload_one_view(wrs, diff_scene, sched, k):
     assert_elementwise(gs.cpu().numpy()[:n], rs, f"{what} scale", atol=ATOL_SCALE)
 
 
-def test_backward_diff_workload_eight_views_one_launch(wrs, diff_scene):
-    """All 8 views of the differentiation workload in one backward launch: the accumulated
-    gradient against the sum of the 8 oracle adjoints."""
+@pytest.fixture(scope="module")
+def diff_eight_views(diff_scene):
+    """Random upstream gradients of the 8 views and the sum of the 8 oracle adjoints (computed once
+    for the tests below)."""
     sp, ref_sp, sc, op, cams = diff_scene
     n = ref_sp.n
-    bvh, srt = wrs.build_lbvh(sp, 1, radius_scale=_cuda(sc))
     V = len(cams)
     h, w = cams[0].height, cams[0].width
     g = np.random.default_rng(8).normal(size=(V, h * w, 4)).astype(np.float32)
-    params = wrs.TraceParams(edge_softness=0.25, k_chunk=4, schedule=2, width=4)
-    st = wrs.new_status()
-    gr, go, gs = wrs.trace_backward_views(bvh, srt, cams, _cuda(g.reshape(V, h, w, 4)), params,
-                                          opacity=_cuda(op), radius_scale=_cuda(sc), status=st)
-    wrs.check_status(st)
     scene = oracle.Scene(ref_sp, scale=sc, opacity=op, beta=0.25)
     rr = np.zeros((n, 4))
     ro = np.zeros(n)
@@ -188,9 +183,27 @@ def test_backward_diff_workload_eight_views_one_launch(wrs, diff_scene):
         rr += a
         ro += b
         rs += c
-    assert_elementwise(gr.cpu().numpy()[:n], rr, "diff 8 views rgba")
-    assert_elementwise(go.cpu().numpy()[:n], ro, "diff 8 views opacity")
-    assert_elementwise(gs.cpu().numpy()[:n], rs, "diff 8 views scale", atol=ATOL_SCALE)
+    return g.reshape(V, h, w, 4), rr, ro, rs
+
+
+# the packet launch and the per-pixel launch the bench's tuner picks (K 4, 8 resident blocks)
+@pytest.mark.parametrize("sched", [2, 0])
+def test_backward_diff_workload_eight_views_one_launch(wrs, diff_scene, diff_eight_views, sched):
+    """All 8 views of the differentiation workload in one backward launch: the accumulated
+    gradient against the sum of the 8 oracle adjoints."""
+    sp, ref_sp, sc, op, cams = diff_scene
+    g, rr, ro, rs = diff_eight_views
+    n = ref_sp.n
+    bvh, srt = wrs.build_lbvh(sp, 1, radius_scale=_cuda(sc))
+    params = wrs.TraceParams(edge_softness=0.25, k_chunk=4, schedule=sched, width=4)
+    st = wrs.new_status()
+    gr, go, gs = wrs.trace_backward_views(bvh, srt, cams, _cuda(g), params,
+                                          opacity=_cuda(op), radius_scale=_cuda(sc), status=st)
+    wrs.check_status(st)
+    what = f"diff 8 views schedule={sched}"
+    assert_elementwise(gr.cpu().numpy()[:n], rr, f"{what} rgba")
+    assert_elementwise(go.cpu().numpy()[:n], ro, f"{what} opacity")
+    assert_elementwise(gs.cpu().numpy()[:n], rs, f"{what} scale", atol=ATOL_SCALE)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -263,34 +276,25 @@ def test_gpu_gradient_matches_central_differences(wrs):
     assert checked >= 4 * 48 - 24
 
 
-def test_recorded_adjoint_diff_workload_eight_views(wrs, diff_scene):
+@pytest.mark.parametrize("sched", [2, 0])
+def test_recorded_adjoint_diff_workload_eight_views(wrs, diff_scene, diff_eight_views, sched):
     """The 8 views of the differentiation workload with recorded hit lists (the forward pass
     records, the adjoint runs without traversal): the accumulated gradient against the sum of the
     8 oracle adjoints, element by element."""
     sp, ref_sp, sc, op, cams = diff_scene
+    g, rr, ro, rs = diff_eight_views
     n = ref_sp.n
     bvh, srt = wrs.build_lbvh(sp, 1, radius_scale=_cuda(sc))
-    V = len(cams)
-    h, w = cams[0].height, cams[0].width
-    g = np.random.default_rng(8).normal(size=(V, h * w, 4)).astype(np.float32)
-    params = wrs.TraceParams(edge_softness=0.25, k_chunk=4, schedule=2, width=4)
+    params = wrs.TraceParams(edge_softness=0.25, k_chunk=4, schedule=sched, width=4)
     st = wrs.new_status()
     _, lists = wrs.trace_views_record(bvh, srt, cams, params, 16, opacity=_cuda(op), status=st)
     over = int((lists.count > 16).sum())
-    gr, go, gs = wrs.trace_backward_views_recorded(bvh, srt, cams, lists, _cuda(g.reshape(V, h, w, 4)),
-                                                   params, opacity=_cuda(op), radius_scale=_cuda(sc),
+    gr, go, gs = wrs.trace_backward_views_recorded(bvh, srt, cams, lists, _cuda(g), params,
+                                                   opacity=_cuda(op), radius_scale=_cuda(sc),
                                                    status=st)
     wrs.check_status(st)
-    scene = oracle.Scene(ref_sp, scale=sc, opacity=op, beta=0.25)
-    rr = np.zeros((n, 4))
-    ro = np.zeros(n)
-    rs = np.zeros(n)
-    for v, cam in enumerate(cams):
-        a, b, c = oracle.trace_backward(scene, cam, g[v].astype(np.float64))
-        rr += a
-        ro += b
-        rs += c
     print(f"rays over the list capacity (re-traversed): {over}")
-    assert_elementwise(gr.cpu().numpy()[:n], rr, "recorded 8 views rgba")
-    assert_elementwise(go.cpu().numpy()[:n], ro, "recorded 8 views opacity")
-    assert_elementwise(gs.cpu().numpy()[:n], rs, "recorded 8 views scale", atol=ATOL_SCALE)
+    what = f"recorded 8 views schedule={sched}"
+    assert_elementwise(gr.cpu().numpy()[:n], rr, f"{what} rgba")
+    assert_elementwise(go.cpu().numpy()[:n], ro, f"{what} opacity")
+    assert_elementwise(gs.cpu().numpy()[:n], rs, f"{what} scale", atol=ATOL_SCALE)

@@ -51,7 +51,7 @@ def _fnv(ids):
     return h
 
 
-@pytest.mark.parametrize("sched,k,cap", [(0, 2, 16), (2, 4, 16), (0, 1, 3), (2, 4, 2)])
+@pytest.mark.parametrize("sched,k,cap", [(0, 2, 16), (2, 4, 16), (0, 4, 16), (0, 1, 3), (2, 4, 2)])
 def test_record_images_and_lists(wrs, sched, k, cap):
     sp, ref_sp, cams, sc, op = _instance(wrs)
     bvh, srt = wrs.build_lbvh(sp, 1, radius_scale=_cuda(sc))
@@ -83,7 +83,7 @@ def test_record_images_and_lists(wrs, sched, k, cap):
         assert over < 0.01 * len(cams) * npix  # a few deep pixels only
 
 
-@pytest.mark.parametrize("sched,k,cap", [(0, 2, 16), (2, 4, 16), (2, 4, 2), (0, 1, 1)])
+@pytest.mark.parametrize("sched,k,cap", [(0, 2, 16), (2, 4, 16), (0, 4, 16), (2, 4, 2), (0, 1, 1)])
 def test_recorded_adjoint_equals_retraversal(wrs, sched, k, cap):
     sp, ref_sp, cams, sc, op = _instance(wrs, 45)
     n = ref_sp.n
