@@ -179,6 +179,12 @@ def measured_peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
 
 
+def launched_block(block, k_chunk, width, schedule):
+    """The block size a trace launch runs: the 4-wide per-pixel kernel with K 1, 2, 4 or 8 is
+    built for blocks of at most 128 threads, and the library clamps the asked size to it."""
+    return min(block, 128) if (width == 4 and k_chunk in (1, 2, 4, 8) and schedule == 0) else block
+
+
 def kernel_digest():
     """Digest of the trace kernel's code (trace.cu and common.cuh with comments, blank lines and
     trailing spaces removed), so that a profile stays attached to the code it measured."""
@@ -546,9 +552,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(W, statistics.mean(n_splats), {
                 "leaf_size": leaf, "k_chunk": kc,
-                # the 4-wide per-pixel kernel with K 1, 2, 4 runs 128-thread blocks whatever is
-                # asked
-                "block": min(block, 128) if (width == 4 and kc in (1, 2, 4) and sched == 0) else block,
+                "block": launched_block(block, kc, width, sched),
                 "autotuned": not args.no_autotune,
                 "schedule": SCHEDULE_NAMES[sched],
                 "bvh_width": width,
@@ -1044,7 +1048,9 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
                           "mrays_s": world * FRAMES_PER_IMAGE * npix_c / (ms_acc * 1e-3) / 1e6,
                           "ms_per_step": ms_acc, "rebuild_ms": ms_rebuild,
                           "trace_ms": (ms_acc - ms_rebuild) / FRAMES_PER_IMAGE,
-                          "leaf_size": at["leaf"], "k_chunk": at["k_chunk"], "block": at["block"],
+                          "leaf_size": at["leaf"], "k_chunk": at["k_chunk"],
+                          "block": launched_block(at["block"], at["k_chunk"], at["width"],
+                                                  at["schedule"]),
                           "schedule": SCHEDULE_NAMES[at["schedule"]], "bvh_width": at["width"],
                           "note": "step = push one 1080p server frame into the window of the 4 "
                                   "newest (4 unprojections into one set + LBVH over about 8 M "

@@ -126,7 +126,7 @@ typedef struct {
     const float* opacity; /* device [n] per-splat opacity in COMPACTED order, or NULL (= 1) */
     int32_t k_chunk;      /* hits gathered per traversal pass: 1, 2, 4, 8 or 16 */
     int32_t block;        /* threads per block: 64, 128 or 256 (per-pixel schedule; the 4-wide
-                             traversal with k_chunk 1, 2 or 4 uses at most 128) */
+                             traversal with k_chunk 1, 2, 4 or 8 uses at most 128) */
     int32_t schedule;     /* WRS_SCHEDULE_PER_PIXEL, WRS_SCHEDULE_PERSISTENT or
                              WRS_SCHEDULE_PACKET; wrs_trace_batched: PER_PIXEL and PACKET = one
                              warp per 8x4 tile of all sessions, PERSISTENT = lane refill */

@@ -755,11 +755,14 @@ struct PersistentMinBlocks {
 #ifndef WRS_PIXEL_W4_K4_MIN_BLOCKS
 #define WRS_PIXEL_W4_K4_MIN_BLOCKS 8  // K = 4: 8 blocks (64 registers), 5 % faster than no cap (75)
 #endif
+#ifndef WRS_PIXEL_W4_K8_MIN_BLOCKS
+#define WRS_PIXEL_W4_K8_MIN_BLOCKS 7  // K = 8: 7 blocks (72 registers), 9 % faster than no cap (80)
+#endif
 // Resident 128-thread blocks of the per-pixel kernel for (K, node width) (0 = no cap), and
 // whether it is built for blocks of at most 128 threads (the host clamps the block to it).
 constexpr int pixel_min_blocks(int K, bool w4) {
     return !w4 ? 0 : K == 1 ? WRS_PIXEL_W4_MIN_BLOCKS : K == 2 ? WRS_PIXEL_W4_K2_MIN_BLOCKS
-                   : K == 4 ? WRS_PIXEL_W4_K4_MIN_BLOCKS : 0;
+                   : K == 4 ? WRS_PIXEL_W4_K4_MIN_BLOCKS : K == 8 ? WRS_PIXEL_W4_K8_MIN_BLOCKS : 0;
 }
 constexpr bool pixel_block_128(int K, bool w4) { return (w4 && K <= 2) || pixel_min_blocks(K, w4) > 0; }
 template <int K, bool W4>
