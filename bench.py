@@ -76,6 +76,9 @@ def parse():
     cs.add_argument("--max-hits", type=int, default=0)
     cs.add_argument("--schedule", type=int, default=0, help="0 per pixel, 1 persistent, 2 packet")
     cs.add_argument("--width", type=int, default=4, help="2 binary nodes, 4 four-wide nodes")
+    cs.add_argument("--layout", choices=["auto", "full", "wide"], default="auto",
+                    help="large/mid/tiny: LBVH layout (auto: the 4-wide-only layout when the "
+                         "traces walk the 4-wide nodes, as in the benchmark)")
     cs.add_argument("--retraverse", action="store_true",
                     help="diff: the adjoint traces every ray again (no recorded hit lists)")
     return ap.parse_args()
@@ -183,6 +186,11 @@ def launched_block(block, k_chunk, width, schedule):
     """The block size a trace launch runs: the 4-wide per-pixel kernel with K 1, 2, 4 or 8 is
     built for blocks of at most 128 threads, and the library clamps the asked size to it."""
     return min(block, 128) if (width == 4 and k_chunk in (1, 2, 4, 8) and schedule == 0) else block
+
+
+def tree_layout(wrs, width, schedule):
+    """The LBVH layout a launch needs: the 4-wide nodes only, unless it walks the binary nodes."""
+    return wrs.tree_layout(wrs.TraceParams(schedule=schedule, width=width))
 
 
 def kernel_digest():
@@ -422,7 +430,8 @@ def main():
 
     # ---------------- buffers, allocated once -------------------------------------------------
     splats = wrs.SplatBuffers(npix_s)
-    bvh = wrs.LBVH(npix_s, leaf)
+    layout = tree_layout(wrs, width, sched)
+    bvh = wrs.LBVH(npix_s, leaf, layout=layout)
     srt = wrs.SplatBuffers(npix_s, sorted=True)
     up_scratch = torch.empty(wrs.unproject_scratch_bytes(W.server_w, W.server_h), dtype=torch.uint8, device=dev)
     bv_scratch = torch.empty(wrs.lbvh_scratch_bytes(npix_s, leaf), dtype=torch.uint8, device=dev)
@@ -558,6 +567,8 @@ def main():
                 "bvh_width": width,
                 "l2": "flushed before every step (256 MiB write outside the timed events)",
                 "lbvh_launch": "one CUDA graph of its 16 kernels, replayed every step",
+                "lbvh_layout": ("4-wide nodes only (no binary records inside a refit block)"
+                                if layout == wrs.LBVH_WIDE else "binary records and 4-wide nodes"),
                 "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
             "lbvh_ms": statistics.mean(bv_ms), "unproject_ms": statistics.mean(up_ms),
             "trace_ms": trace_ms, "trace_mrays_s": npix_c / (trace_ms * 1e-3) / 1e6,
@@ -655,10 +666,12 @@ def run_case(a, wrs, torch):
     torch.cuda.empty_cache()
     params = wrs.TraceParams(max_hits=a.max_hits, k_chunk=a.k, block=a.block, schedule=a.schedule,
                              width=a.width)
+    layout = {"auto": wrs.tree_layout(params), "full": wrs.LBVH_FULL,
+              "wide": wrs.LBVH_WIDE}[a.layout]
     st = wrs.new_status()
     out = torch.empty(W.client_h, W.client_w, 4, device=dev)
-    res = {"workload": a.case, "groups": a.groups or None, "splats": [], "unproject_ms": [],
-           "lbvh_ms": [], "trace_ms": []}
+    res = {"workload": a.case, "groups": a.groups or None, "layout": layout, "splats": [],
+           "unproject_ms": [], "lbvh_ms": [], "trace_ms": []}
     for (srv, clis), (rgba, depth) in zip(plan, images):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 + len(clis))]
         ev[0].record()
@@ -667,7 +680,7 @@ def run_case(a, wrs, torch):
         torch.cuda.nvtx.range_pop()
         ev[1].record()
         torch.cuda.nvtx.range_push("lbvh")
-        bvh, srt = wrs.build_lbvh(sp, a.leaf)
+        bvh, srt = wrs.build_lbvh(sp, a.leaf, layout=layout)
         torch.cuda.nvtx.range_pop()
         ev[2].record()
         for f, c in enumerate(clis):
@@ -1027,7 +1040,8 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
     del probe
     aparams = wrs.TraceParams(max_hits=0, t_stop=1e-5, k_chunk=at["k_chunk"], block=at["block"],
                               schedule=at["schedule"], width=at["width"])
-    win = wrs.FrameWindow(F_WIN, W.server_w, W.server_h, decay=0.9, leaf_size=at["leaf"])
+    win = wrs.FrameWindow(F_WIN, W.server_w, W.server_h, decay=0.9, leaf_size=at["leaf"],
+                          layout=tree_layout(wrs, at["width"], at["schedule"]))
     for g_i in range(F_WIN):
         win.push(*groups[g_i][:3])
     outs = [torch.empty(W.client_h, W.client_w, 4, device=dev) for _ in range(FRAMES_PER_IMAGE)]
@@ -1071,7 +1085,8 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
          "schedule": params.schedule, "width": params.width}
     mparams = wrs.TraceParams(max_hits=0, t_stop=1e-5, k_chunk=tm["k_chunk"], block=tm["block"],
                               schedule=tm["schedule"], width=tm["width"])
-    bvh_m, srt_m = wrs.build_lbvh(sp_m, tm["leaf"])
+    bvh_m, srt_m = wrs.build_lbvh(sp_m, tm["leaf"],
+                                  layout=tree_layout(wrs, tm["width"], tm["schedule"]))
     out_m = torch.empty(M.client_h, M.client_w, 4, device=dev)
     per_pose = []
     for c in cams_m:

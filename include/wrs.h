@@ -99,6 +99,14 @@ typedef struct {
     uint32_t capacity;
 } wrs_splats;
 
+/* Tree layouts (wrs_lbvh.layout).  Both hold the same 4-wide nodes, bitwise.  FULL also holds
+ * every binary record, which the binary traversal (width 2) reads.  WIDE is for the 4-wide
+ * traversal only: the build writes the binary records of the nodes whose leaves span several
+ * of its refit blocks (it passes boxes between blocks through them) and leaves the others as
+ * they were, which saves about a tenth of the build. */
+#define WRS_LBVH_FULL 0
+#define WRS_LBVH_WIDE 1
+
 /* An LBVH: one device buffer of wrs_lbvh_bytes(capacity, leaf_size) bytes holding a 64-byte
  * header, the binary internal nodes (64 B each: both children's boxes and references) and, for
  * every binary internal node, a 4-wide node over its grandchildren (128 B). */
@@ -106,6 +114,8 @@ typedef struct {
     void* nodes;
     uint32_t capacity;  /* maximum splats */
     uint32_t leaf_size; /* splats per leaf, 1..16 */
+    uint32_t layout;    /* WRS_LBVH_FULL (0) or WRS_LBVH_WIDE: what the build writes; a trace
+                           passes the layout the tree was built with, and width 2 needs FULL */
 } wrs_lbvh;
 
 /* Trace schedules (performance only; results are bitwise identical). */
@@ -130,7 +140,9 @@ typedef struct {
     int32_t schedule;     /* WRS_SCHEDULE_PER_PIXEL, WRS_SCHEDULE_PERSISTENT or
                              WRS_SCHEDULE_PACKET; wrs_trace_batched: PER_PIXEL and PACKET = one
                              warp per 8x4 tile of all sessions, PERSISTENT = lane refill */
-    int32_t width;        /* traversal: 2 (or 0) = binary nodes, 4 = the LBVH's 4-wide nodes */
+    int32_t width;        /* traversal: 2 (or 0) = binary nodes, 4 = the LBVH's 4-wide nodes;
+                             the binary traversal (width 2 under any schedule but PACKET) of a
+                             tree built with layout WRS_LBVH_WIDE is refused: WRS_ERR_ARG */
 } wrs_trace_params;
 
 /* One client session of wrs_trace_batched (device array of these). */
@@ -282,8 +294,9 @@ int wrs_unproject_static(const float* rgba, const float* depth, const wrs_camera
  * r = max(s, 0) * r0 (s = radius_scale[i] in compacted order, or global_scale if radius_scale is
  * NULL) is baked into sorted->pos_r[.].w; sorted also receives rgba, id, src (= compacted index)
  * and *sorted->n (*in->n is clamped to in->capacity).  bvh->capacity and sorted->capacity must be
- * >= in->capacity.  The build writes the tree header, every node a traversal can reach and
- * rows [0, n) of sorted, so neither buffer needs clearing before the call.
+ * >= in->capacity.  The build writes the tree header (with bvh->layout), every node a traversal
+ * of that layout can reach and rows [0, n) of sorted, so neither buffer needs clearing before
+ * the call.  bvh->layout not WRS_LBVH_FULL or WRS_LBVH_WIDE: WRS_ERR_ARG.
  * Buffer sizes: wrs_lbvh_bytes() for bvh->nodes, wrs_lbvh_scratch_bytes() for scratch. */
 size_t wrs_lbvh_bytes(uint32_t capacity, uint32_t leaf_size);
 size_t wrs_lbvh_scratch_bytes(uint32_t capacity, uint32_t leaf_size);
@@ -297,8 +310,8 @@ int wrs_build_lbvh(const wrs_splats* in, const float* radius_scale, float global
  * other arrays), every binary and 4-wide node box, bottom-up over the leaf order and parent links
  * that the last wrs_build_lbvh call left in `scratch`: the result is bitwise the tree
  * wrs_build_lbvh would build with these radius scales, at the cost of the bounds and the refit
- * (no Morton codes, sort or radix tree).  Contract: the same in, bvh, sorted and scratch as that
- * build, and since then no change to the splat centres or count and no other use of the scratch;
+ * (no Morton codes, sort or radix tree).  Contract: the same in, bvh (layout included), sorted
+ * and scratch as that build, and since then no change to the splat centres or count and no other use of the scratch;
  * otherwise the result is undefined (no access leaves the buffers and the kernels still end).
  * Arguments and errors as wrs_build_lbvh. */
 int wrs_refit_lbvh(const wrs_splats* in, const float* radius_scale, float global_scale,
@@ -344,7 +357,9 @@ uint32_t wrs_session_tiles(int32_t width, int32_t height);
  * four ray tiles of any session from *work_counter (device uint32, reset by this call) and refill
  * their idle lanes from them.  sessions: device array of n_sessions descriptors whose tile_begin are the prefix
  * sums of wrs_session_tiles; total_tiles = their sum.  Each session's image equals wrs_trace's
- * bitwise. */
+ * bitwise.  A session whose tree was built with layout WRS_LBVH_WIDE and that would be traced
+ * over binary nodes (width 2, schedule not PACKET) sets WRS_STATUS_MALFORMED_TREE in *status
+ * (checked on the device from the trees' headers; its image is then undefined). */
 int wrs_trace_batched(const wrs_session* sessions, int32_t n_sessions, uint32_t total_tiles,
                       const wrs_trace_params* params, uint32_t* work_counter, int32_t* status,
                       wrs_stream_t stream);

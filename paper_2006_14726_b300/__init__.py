@@ -50,6 +50,8 @@ SCHEDULE_PER_PIXEL = 0
 SCHEDULE_PERSISTENT = 1
 SCHEDULE_PACKET = 2
 SCHEDULE_PER_SESSION = 3  # trace_batched only: each session's own schedule (Batch(schedules=...))
+LBVH_FULL = 0  # tree layouts: binary records and 4-wide nodes (any traversal)
+LBVH_WIDE = 1  # the 4-wide nodes only (width 4 or the packet schedule); a faster build
 DEPTH_FIRST_HIT = 0
 DEPTH_MAX_CONTRIBUTION = 1
 DEPTH_ACCUMULATED = 2
@@ -76,7 +78,7 @@ class _Splats(ctypes.Structure):
 
 class _Lbvh(ctypes.Structure):
     _fields_ = [("nodes", ctypes.c_void_p), ("capacity", ctypes.c_uint32),
-                ("leaf_size", ctypes.c_uint32)]
+                ("leaf_size", ctypes.c_uint32), ("layout", ctypes.c_uint32)]
 
 
 class _Params(ctypes.Structure):
@@ -280,20 +282,24 @@ class SplatBuffers:
 
 
 class LBVH:
-    """Device LBVH buffer (see wrs_lbvh)."""
+    """Device LBVH buffer (see wrs_lbvh).  ``layout``: :data:`LBVH_FULL` (binary records and
+    4-wide nodes) or :data:`LBVH_WIDE` (4-wide nodes only: traced with width 4 or the packet
+    schedule; the build skips most binary records)."""
 
-    def __init__(self, capacity: int, leaf_size: int = 1, device=None, _fill: bool = True):
+    def __init__(self, capacity: int, leaf_size: int = 1, device=None, _fill: bool = True,
+                 layout: int = LBVH_FULL):
         device = device or torch.device("cuda")
         nbytes = _lib.wrs_lbvh_bytes(int(capacity), int(leaf_size))
         if nbytes == 0:
             raise ValueError(f"leaf_size {leaf_size} not in 1..16")
         self.capacity = int(capacity)
         self.leaf_size = int(leaf_size)
+        self.layout = int(layout)
         # zero-filled (an empty tree) unless a build writes the header before any reader runs
         self.nodes = (torch.zeros if _fill else torch.empty)(nbytes, dtype=torch.uint8, device=device)
 
     def c(self) -> _Lbvh:
-        return _Lbvh(_ptr(self.nodes), self.capacity, self.leaf_size)
+        return _Lbvh(_ptr(self.nodes), self.capacity, self.leaf_size, self.layout)
 
     def header(self) -> dict:
         h = self.nodes[:64].cpu()
@@ -301,7 +307,7 @@ class LBVH:
         f = h.view(torch.float32)
         return {"n": int(u[0]), "m": int(u[1]), "leaf": int(u[2]), "root": int(u[3]),
                 "cmin": f[4:7].tolist(), "cmax": f[7:10].tolist(), "maxabs": float(f[10]),
-                "rmax": float(f[11])}
+                "rmax": float(f[11]), "layout": int(u[13])}
 
     def node_table(self) -> Tuple[torch.Tensor, torch.Tensor]:
         """(boxes [M-1, 2, 6] float32, child refs [M-1, 2] int32) of the internal nodes."""
@@ -526,13 +532,14 @@ def lbvh_scratch_bytes(capacity: int, leaf_size: int) -> int:
 def build_lbvh(splats: SplatBuffers, leaf_size: int = 1, radius_scale: Optional[torch.Tensor] = None,
                global_scale: float = 1.0, bvh: Optional[LBVH] = None,
                sorted: Optional[SplatBuffers] = None, scratch: Optional[torch.Tensor] = None,
-               stream=None) -> Tuple[LBVH, SplatBuffers]:
-    """LBVH over the splats; returns (bvh, sorted splats with baked effective radius)."""
+               stream=None, layout: int = LBVH_FULL) -> Tuple[LBVH, SplatBuffers]:
+    """LBVH over the splats; returns (bvh, sorted splats with baked effective radius).  A new
+    ``bvh`` gets ``layout``; a given one keeps its own."""
     dev = splats.pos_r.device
     # buffers made here are returned only after the build wrote the header, the count and every
     # node and row that a traversal can reach, so they need no zero fill
     if bvh is None:
-        bvh = LBVH(splats.capacity, leaf_size, device=dev, _fill=False)
+        bvh = LBVH(splats.capacity, leaf_size, device=dev, _fill=False, layout=layout)
     if sorted is None:
         sorted = SplatBuffers(splats.capacity, device=dev, sorted=True, _fill=False)
     need = lbvh_scratch_bytes(splats.capacity, bvh.leaf_size)
@@ -567,11 +574,11 @@ class RefitTree:
     must have been used before the next update (an autograd step's backward runs before the next
     step's forward)."""
 
-    def __init__(self, splats: SplatBuffers, leaf_size: int = 1):
+    def __init__(self, splats: SplatBuffers, leaf_size: int = 1, layout: int = LBVH_FULL):
         dev = splats.pos_r.device
         self.splats = splats
         self.leaf_size = int(leaf_size)
-        self.bvh = LBVH(splats.capacity, leaf_size, device=dev, _fill=False)
+        self.bvh = LBVH(splats.capacity, leaf_size, device=dev, _fill=False, layout=layout)
         self.sorted = SplatBuffers(splats.capacity, device=dev, sorted=True, _fill=False)
         self.scratch = _scratch(lbvh_scratch_bytes(splats.capacity, leaf_size), dev)
         self.built = False
@@ -602,6 +609,13 @@ class TraceParams:
         return _Params(int(self.max_hits), float(self.t_stop), float(self.edge_softness),
                        _ptr(opacity), int(self.k_chunk), int(self.block), int(self.schedule),
                        int(self.width))
+
+
+def tree_layout(params: TraceParams) -> int:
+    """The LBVH layout that traces with ``params`` need: LBVH_WIDE (the 4-wide nodes only, a
+    faster build) unless they walk the binary nodes (width 2 under a schedule other than the
+    packet one)."""
+    return LBVH_WIDE if (params.width == 4 or params.schedule == SCHEDULE_PACKET) else LBVH_FULL
 
 
 def trace(bvh: LBVH, sorted: SplatBuffers, cam, params: TraceParams = TraceParams(),

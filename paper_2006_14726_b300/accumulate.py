@@ -14,7 +14,7 @@ from typing import Optional
 
 import torch
 
-from . import (LBVH, RADIUS_FOOTPRINT, SplatBuffers, TraceParams, _cam, _scratch, build_lbvh,
+from . import (LBVH, LBVH_FULL, RADIUS_FOOTPRINT, SplatBuffers, TraceParams, _cam, _scratch, build_lbvh,
                lbvh_scratch_bytes, new_status, trace, unproject, unproject_append,
                unproject_scratch_bytes, window_weight)
 
@@ -29,11 +29,12 @@ class FrameWindow:
     """The splats of the ``frames`` newest server frames (all of one size) in one LBVH.
 
     ``push`` keeps references to the given device tensors (the caller does not overwrite them
-    while they are in the window) and rebuilds the set; ``trace`` renders a client view of it."""
+    while they are in the window) and rebuilds the set; ``trace`` renders a client view of it.
+    ``layout``: the LBVH's (LBVH_WIDE when every trace walks the 4-wide nodes)."""
 
     def __init__(self, frames: int, width: int, height: int, decay: float = 1.0,
                  leaf_size: int = 1, radius_mode: int = RADIUS_FOOTPRINT, voxel_diag: float = 0.0,
-                 device=None):
+                 device=None, layout: int = LBVH_FULL):
         if frames < 1:
             raise ValueError("a window holds at least one frame")
         if not (0.0 < decay <= 1.0):
@@ -47,7 +48,7 @@ class FrameWindow:
         self.radius_mode, self.voxel_diag = int(radius_mode), float(voxel_diag)
         self.capacity = self.frames * self.npix
         self.splats = SplatBuffers(self.capacity, device=device)
-        self.bvh = LBVH(self.capacity, leaf_size, device=device)
+        self.bvh = LBVH(self.capacity, leaf_size, device=device, layout=layout)
         self.sorted = SplatBuffers(self.capacity, device=device, sorted=True)
         self._uscratch = _scratch(unproject_scratch_bytes(self.width, self.height), device)
         self._bscratch = _scratch(lbvh_scratch_bytes(self.capacity, leaf_size), device)

@@ -20,7 +20,7 @@ import torch
 
 from . import (HitLists, RefitTree, SplatBuffers, TraceParams, build_lbvh, trace, trace_backward,
                trace_backward_views, trace_backward_views_recorded, trace_views,
-               trace_views_record)
+               trace_views_record, tree_layout)
 
 # Hit lists are recorded by the multi-view forward pass (and the adjoint then needs no traversal)
 # when they fit in this many bytes; beyond it the adjoint re-traverses every ray.
@@ -39,7 +39,7 @@ class TraceFunction(torch.autograd.Function):
         splats.rgba[:n].copy_(rgba.detach())
         op = None if opacity is None else opacity.detach().contiguous()
         sc = None if radius_scale is None else radius_scale.detach().contiguous()
-        bvh, sorted_ = build_lbvh(splats, leaf_size, radius_scale=sc)
+        bvh, sorted_ = build_lbvh(splats, leaf_size, radius_scale=sc, layout=tree_layout(params))
         img = trace(bvh, sorted_, cam, params, opacity=op)
         ctx.state = (bvh, sorted_, cam, params, op, sc, n)
         return img
@@ -86,7 +86,8 @@ class MultiViewTraceFunction(torch.autograd.Function):
                 raise ValueError("the tree belongs to other splats or another leaf size")
             bvh, sorted_ = tree.update(sc)
         else:
-            bvh, sorted_ = build_lbvh(splats, leaf_size, radius_scale=sc)
+            bvh, sorted_ = build_lbvh(splats, leaf_size, radius_scale=sc,
+                                      layout=tree_layout(params))
         c0 = cams[0]
         if any((c.width, c.height) != (c0.width, c0.height) for c in cams):
             raise ValueError("all views must have the same size")

@@ -16,9 +16,9 @@ from typing import Callable, Dict, Iterable, Optional, Sequence
 
 import torch
 
-from . import (SCHEDULE_PACKET, SCHEDULE_PER_PIXEL, SCHEDULE_PER_SESSION, SCHEDULE_PERSISTENT, Batch, SplatBuffers,
-               TraceParams,
-               build_lbvh, trace, trace_batched, version)
+from . import (LBVH_WIDE, SCHEDULE_PACKET, SCHEDULE_PER_PIXEL, SCHEDULE_PER_SESSION,
+               SCHEDULE_PERSISTENT, Batch, SplatBuffers, TraceParams, build_lbvh, trace,
+               trace_batched, version)
 
 LEAVES = (1, 2, 4)
 KS = (1, 2, 4, 8)
@@ -77,7 +77,9 @@ def tune_trace(splats: SplatBuffers, cams: Sequence, base: TraceParams = TracePa
                use_cache: bool = True, build_weight: float = 0.0) -> Dict:
     """Pick (leaf_size, k_chunk, block, schedule, width) minimising the mean wrs_trace time over
     ``cams`` plus ``build_weight`` times the LBVH build time of the leaf size (the share of a
-    build per traced view, e.g. 1/4 when a server frame serves four client views)."""
+    build per traced view, e.g. 1/4 when a server frame serves four client views).  A launch
+    that walks the 4-wide nodes is charged the build of the 4-wide-only layout (LBVH_WIDE), the
+    binary traversal the full one."""
     c0 = cams[0]
     key = signature("trace", splats.count(), c0.width, c0.height, base) + f"|w{build_weight:g}"
     if use_cache:
@@ -89,6 +91,9 @@ def tune_trace(splats: SplatBuffers, cams: Sequence, base: TraceParams = TracePa
     for leaf in leaves:
         bvh, srt = build_lbvh(splats, leaf)
         build_ms = _time_ms(lambda: build_lbvh(splats, leaf, bvh=bvh, sorted=srt), reps)
+        wb, ws = build_lbvh(splats, leaf, layout=LBVH_WIDE)
+        build_wide_ms = _time_ms(lambda: build_lbvh(splats, leaf, bvh=wb, sorted=ws), reps)
+        del wb, ws
         outs = [torch.empty(c.height, c.width, 4, device=splats.pos_r.device) for c in cams]
         shapes = [(b, SCHEDULE_PER_PIXEL) for b in blocks] + [(128, SCHEDULE_PERSISTENT),
                                                               (128, SCHEDULE_PACKET)]
@@ -103,11 +108,12 @@ def tune_trace(splats: SplatBuffers, cams: Sequence, base: TraceParams = TracePa
                         for c, o in zip(cams, outs):
                             trace(bvh, srt, c, p, out=o)
                     ms = _time_ms(run, reps) / len(cams)
-                    score = ms + build_weight * build_ms
-                    table.append((leaf, k, block, sched, width, ms, build_ms))
+                    bms = build_wide_ms if (width == 4 or sched == SCHEDULE_PACKET) else build_ms
+                    score = ms + build_weight * bms
+                    table.append((leaf, k, block, sched, width, ms, bms))
                     if best is None or score < best["score"]:
                         best = {"leaf": leaf, "k_chunk": k, "block": block, "schedule": sched,
-                                "width": width, "ms": ms, "build_ms": build_ms, "score": score}
+                                "width": width, "ms": ms, "build_ms": bms, "score": score}
     best["table"] = table
     _store(key, best)
     return best

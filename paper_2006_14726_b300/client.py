@@ -23,16 +23,16 @@ from typing import List, Optional
 import torch
 
 from . import (LBVH, RADIUS_FOOTPRINT, SplatBuffers, TraceParams, build_lbvh, lbvh_scratch_bytes,
-               make_camera, new_status, trace, unproject, unproject_scratch_bytes)
+               make_camera, new_status, trace, tree_layout, unproject, unproject_scratch_bytes)
 
 
 class _Scene:
-    def __init__(self, sw: int, sh: int, leaf: int, device):
+    def __init__(self, sw: int, sh: int, leaf: int, device, layout: int):
         npix = sw * sh
         self.rgba = torch.empty(sh, sw, 4, dtype=torch.float32, device=device)
         self.depth = torch.empty(sh, sw, dtype=torch.float32, device=device)
         self.splats = SplatBuffers(npix, device=device)
-        self.bvh = LBVH(npix, leaf, device=device)
+        self.bvh = LBVH(npix, leaf, device=device, layout=layout)
         self.sorted = SplatBuffers(npix, device=device, sorted=True)
         self.uscratch = torch.empty(max(unproject_scratch_bytes(sw, sh), 256), dtype=torch.uint8,
                                     device=device)
@@ -74,7 +74,9 @@ class WarpingClient:
         self.compute = torch.cuda.Stream(device=device)
         self.h2d = torch.cuda.Stream(device=device)
         self.d2h = torch.cuda.Stream(device=device)
-        self.scenes = [_Scene(self.sw, self.sh, self.leaf, device) for _ in range(2)]
+        # a client that walks the 4-wide nodes builds trees without the binary records
+        self.scenes = [_Scene(self.sw, self.sh, self.leaf, device, tree_layout(params))
+                       for _ in range(2)]
         self.current: Optional[int] = None
         self.status = new_status(device)
         self.dev_out = [torch.empty(self.ch, self.cw, 4, dtype=torch.float32, device=device)

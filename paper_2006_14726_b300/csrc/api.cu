@@ -25,7 +25,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 extern "C" {
 
-const char* wrs_version(void) { return "wrs 0.2 (sm_103a)"; }
+const char* wrs_version(void) { return "wrs 0.3 (sm_103a)"; }
 
 const char* wrs_last_error(void) { return wrs::g_err; }
 

@@ -31,7 +31,8 @@ struct LbvhHeader {
     float maxabs;      // largest |coordinate| of any sphere bound (traversal epsilon scale)
     float rmax;        // largest effective radius
     uint32_t wide_start;  // 64-byte slots of binary nodes before the 4-wide nodes
-    uint32_t pad[3];
+    uint32_t layout;      // WRS_LBVH_FULL or WRS_LBVH_WIDE (the binary records are not all written)
+    uint32_t pad[2];
 };
 static_assert(sizeof(LbvhHeader) == 64, "header must be 64 bytes");
 
@@ -43,7 +44,8 @@ static_assert(sizeof(LbvhHeader) == 64, "header must be 64 bytes");
 // 4-wide node i (one per binary internal node i) = 8 x float4 = 128 B, structure of arrays over
 // the grandchildren of binary node i (a leaf child counts as its own grandchild):
 //   float4 0..2: lo.x, lo.y, lo.z of the 4 entries; 3..5: hi.x, hi.y, hi.z; 6: references
-//   (int bits; internal references name binary nodes, whose 4-wide node is visited next); 7: unused.
+//   (int bits; internal references name binary nodes, whose 4-wide node is visited next); 7: zero
+//   (written all the same: a 32-byte sector written in part costs DRAM a read-modify-write).
 //   Unused entries carry the reference kNoChild, low x = +inf and high x = -inf (their other
 //   planes are not written): the direction-ordered slab test (box_test_nf) gets tn = +inf from
 //   the x slab and tf = -inf (three-input min/max ignore a NaN in the other planes), so no ray

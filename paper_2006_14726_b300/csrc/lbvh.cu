@@ -12,6 +12,11 @@
 //                                       bottom-up (second thread to reach a node continues); the
 //                                       same climb fills the 4-wide nodes
 //
+// Layout WRS_LBVH_WIDE (a tree for the 4-wide traversal only): k_karras writes no child
+// references and the refit no binary record of a node inside one refit block; the records of
+// the nodes that span blocks still carry the boxes between blocks.  The 4-wide nodes are the
+// same, bitwise.
+//
 // The splat count is read on the device from the header, so the whole build runs without a host
 // synchronisation and can be captured into a CUDA graph.  No kernel waits on another block.
 #include "common.cuh"
@@ -114,7 +119,7 @@ __global__ void __launch_bounds__(256) k_bounds_partial(const float4* __restrict
 
 __global__ void __launch_bounds__(kBoundsBlocks) k_bounds_final(
     const float* __restrict__ partials, const uint32_t* __restrict__ n_in, uint32_t cap,
-    uint32_t leaf, LbvhHeader* __restrict__ hdr, uint32_t* __restrict__ n_sorted) {
+    uint32_t leaf, uint32_t layout, LbvhHeader* __restrict__ hdr, uint32_t* __restrict__ n_sorted) {
     __shared__ float s[7][kBoundsBlocks / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int b = threadIdx.x;  // one partial per thread
@@ -139,6 +144,7 @@ __global__ void __launch_bounds__(kBoundsBlocks) k_bounds_final(
     LbvhHeader h = {};
     h.n = n;
     h.leaf = leaf;
+    h.layout = layout;
     h.wide_start = wrs::lbvh_binary_slots(cap, leaf);
     h.m = n == 0 ? 0 : (n + leaf - 1) / leaf;
     h.root = h.m <= 1 ? (int32_t)kLeafBit : 0;
@@ -386,7 +392,7 @@ __device__ __forceinline__ int delta(const uint32_t* __restrict__ codes, uint32_
 
 __global__ void __launch_bounds__(256) k_karras(const uint32_t* __restrict__ codes,
                                                 const LbvhHeader* __restrict__ hdr,
-                                                float4* __restrict__ nodes,
+                                                float4* __restrict__ nodes, bool binary,
                                                 uint32_t* __restrict__ leaf_parent,
                                                 uint32_t* __restrict__ node_parent,
                                                 uint4* __restrict__ node_range) {
@@ -411,9 +417,11 @@ __global__ void __launch_bounds__(256) k_karras(const uint32_t* __restrict__ cod
     } while (t > 1);
     const int g = i + s * d + min(d, 0);
     const int lo = min(i, j), hi = max(i, j);
-    const uint32_t left = (lo == g) ? (kLeafBit | (uint32_t)g) : (uint32_t)g;
-    const uint32_t right = (hi == g + 1) ? (kLeafBit | (uint32_t)(g + 1)) : (uint32_t)(g + 1);
-    nodes[4 * i + 3] = make_float4(__uint_as_float(left), __uint_as_float(right), 0.0f, 0.0f);
+    if (binary) {  // the record's child references (its boxes come from the refit)
+        const uint32_t left = (lo == g) ? (kLeafBit | (uint32_t)g) : (uint32_t)g;
+        const uint32_t right = (hi == g + 1) ? (kLeafBit | (uint32_t)(g + 1)) : (uint32_t)(g + 1);
+        nodes[4 * i + 3] = make_float4(__uint_as_float(left), __uint_as_float(right), 0.0f, 0.0f);
+    }
     node_range[i] = make_uint4((uint32_t)lo, (uint32_t)hi, (uint32_t)g, 0u);
     if (lo == g) leaf_parent[g] = (uint32_t)i << 1;
     else node_parent[g] = (uint32_t)i << 1;
@@ -484,6 +492,7 @@ __device__ __forceinline__ void write_pair(float4* __restrict__ wide, uint32_t i
 #pragma unroll
     for (int q = 0; q < 6; q++) *reinterpret_cast<float2*>(w + 4 * q) = make_float2(b[q], b[6 + q]);
     *reinterpret_cast<float2*>(w + 24) = make_float2(__uint_as_float(r0), __uint_as_float(r1));
+    *reinterpret_cast<float2*>(w + 28) = make_float2(0.0f, 0.0f);
 }
 
 // Slots 2c and 2c + 1 of 4-wide node i for a leaf child c: the leaf (box b[0..5], reference r)
@@ -496,6 +505,7 @@ __device__ __forceinline__ void write_leaf_pair(float4* __restrict__ wide, uint3
         *reinterpret_cast<float2*>(w + 4 * q) =
             make_float2(b[q], q == 0 ? INFINITY : (q == 3 ? -INFINITY : 0.0f));
     *reinterpret_cast<float2*>(w + 24) = make_float2(__uint_as_float(r), __uint_as_float(wrs::kNoChild));
+    *reinterpret_cast<float2*>(w + 28) = make_float2(0.0f, 0.0f);
 }
 
 // The whole 4-wide node of a binary node whose two children are the leaves l0 (slot 0) and l1
@@ -512,13 +522,14 @@ __device__ __forceinline__ void write_cherry(float4* __restrict__ wide, uint32_t
     w[5] = make_float4(a[5], 0.0f, a[11], 0.0f);
     w[6] = make_float4(__uint_as_float(kLeafBit | l0), __uint_as_float(wrs::kNoChild),
                        __uint_as_float(kLeafBit | l1), __uint_as_float(wrs::kNoChild));
+    w[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
 
 __global__ void __launch_bounds__(kRefitBlock) k_leaves_refit(
     const uint32_t* __restrict__ order, const float4* __restrict__ pos_r,
     const float4* __restrict__ rgba, const uint32_t* __restrict__ id,
     const float* __restrict__ scale, float gscale, const LbvhHeader* __restrict__ hdr,
-    float4* __restrict__ nodes, const uint32_t* __restrict__ leaf_parent,
+    float4* __restrict__ nodes, bool binary, const uint32_t* __restrict__ leaf_parent,
     const uint32_t* __restrict__ node_parent, const uint4* __restrict__ node_range,
     uint32_t* __restrict__ visit, float4* __restrict__ s_pos, float4* __restrict__ s_rgba,
     uint32_t* __restrict__ s_id, uint32_t* __restrict__ s_src, float4* __restrict__ wide) {
@@ -562,12 +573,14 @@ __global__ void __launch_bounds__(kRefitBlock) k_leaves_refit(
             if (add_acq_rel_cta_shared(&sh_cnt[node - j0]) == 0u) return;  // first child: done
 #pragma unroll
             for (int k = 0; k < 12; k++) a[k] = sh_box[node - j0][k];
-            // the node's binary record (both child boxes) in three 16-byte stores; the traversal
-            // reads it after the kernel
-            float4* rec = nodes + 4 * (size_t)node;
-            __stcg(rec + 0, make_float4(a[0], a[1], a[2], a[3]));
-            __stcg(rec + 1, make_float4(a[4], a[5], a[6], a[7]));
-            __stcg(rec + 2, make_float4(a[8], a[9], a[10], a[11]));
+            // the node's binary record (both child boxes) in three 16-byte stores; the binary
+            // traversal reads it after the kernel (not written for the 4-wide-only layout)
+            if (binary) {
+                float4* rec = nodes + 4 * (size_t)node;
+                __stcg(rec + 0, make_float4(a[0], a[1], a[2], a[3]));
+                __stcg(rec + 1, make_float4(a[4], a[5], a[6], a[7]));
+                __stcg(rec + 2, make_float4(a[8], a[9], a[10], a[11]));
+            }
         } else {
             // a node spanning blocks: each child's box goes to the record before the release, the
             // second child reads the other one from there
@@ -623,6 +636,8 @@ static int check_lbvh_args(const wrs_splats* in, const float* radius_scale, floa
     if (!sorted->pos_r || !sorted->rgba || !sorted->id || !sorted->src || !sorted->n)
         return wrs::fail(WRS_ERR_ARG, "%s: NULL sorted splat array (src is required)", fn);
     if (!bvh->nodes) return wrs::fail(WRS_ERR_ARG, "%s: bvh->nodes is NULL", fn);
+    if (bvh->layout != WRS_LBVH_FULL && bvh->layout != WRS_LBVH_WIDE)
+        return wrs::fail(WRS_ERR_ARG, "%s: unknown tree layout %u", fn, bvh->layout);
     const uint32_t leaf = bvh->leaf_size;
     if (leaf < 1 || leaf > (uint32_t)wrs::kMaxLeaf)
         return wrs::fail(WRS_ERR_ARG, "%s: leaf_size %u not in 1..16", fn, leaf);
@@ -665,7 +680,8 @@ int wrs_build_lbvh(const wrs_splats* in, const float* radius_scale, float global
     k_bounds_partial<<<kBoundsBlocks, 256, 0, s>>>(pos4, radius_scale, global_scale, in->n, cap,
                                                    S.partials);
     WRS_LAUNCH_CHECK("wrs_build_lbvh bounds");
-    k_bounds_final<<<1, kBoundsBlocks, 0, s>>>(S.partials, in->n, cap, leaf, hdr, sorted->n);
+    k_bounds_final<<<1, kBoundsBlocks, 0, s>>>(S.partials, in->n, cap, leaf, bvh->layout, hdr,
+                                              sorted->n);
     WRS_LAUNCH_CHECK("wrs_build_lbvh bounds final");
     if (cap == 0) return WRS_OK;
     k_morton<<<S.tiles, kSortThreads, 0, s>>>(pos4, hdr, S.keys0, S.vals0, S.tiles, S.hist);
@@ -682,13 +698,15 @@ int wrs_build_lbvh(const wrs_splats* in, const float* radius_scale, float global
         t = vi; vi = vo; vo = t;
     }
     // four passes: the sorted keys / values are back in keys0 / vals0
-    k_karras<<<gm, 256, 0, s>>>(ki, hdr, nodes, S.leaf_parent, S.node_parent, S.node_range);
+    k_karras<<<gm, 256, 0, s>>>(ki, hdr, nodes, bvh->layout == WRS_LBVH_FULL, S.leaf_parent,
+                                S.node_parent, S.node_range);
     WRS_LAUNCH_CHECK("wrs_build_lbvh karras");
     cudaError_t e = cudaMemsetAsync(S.visit, 0, sizeof(uint32_t) * m_cap, s);
     if (e != cudaSuccess) return wrs::cuda_fail(e, "wrs_build_lbvh memset");
     const uint32_t grefit = (m_cap + kRefitBlock - 1) / kRefitBlock;
     k_leaves_refit<<<grefit, kRefitBlock, 0, s>>>(vi, pos4, reinterpret_cast<const float4*>(in->rgba),
-                                      in->id, radius_scale, global_scale, hdr, nodes, S.leaf_parent,
+                                      in->id, radius_scale, global_scale, hdr, nodes,
+                                      bvh->layout == WRS_LBVH_FULL, S.leaf_parent,
                                       S.node_parent, S.node_range, S.visit,
                                       reinterpret_cast<float4*>(sorted->pos_r),
                                       reinterpret_cast<float4*>(sorted->rgba), sorted->id,
@@ -719,14 +737,16 @@ int wrs_refit_lbvh(const wrs_splats* in, const float* radius_scale, float global
     k_bounds_partial<<<kBoundsBlocks, 256, 0, s>>>(pos4, radius_scale, global_scale, in->n, cap,
                                                    S.partials);
     WRS_LAUNCH_CHECK("wrs_refit_lbvh bounds");
-    k_bounds_final<<<1, kBoundsBlocks, 0, s>>>(S.partials, in->n, cap, leaf, hdr, sorted->n);
+    k_bounds_final<<<1, kBoundsBlocks, 0, s>>>(S.partials, in->n, cap, leaf, bvh->layout, hdr,
+                                              sorted->n);
     WRS_LAUNCH_CHECK("wrs_refit_lbvh bounds final");
     if (cap == 0) return WRS_OK;
     cudaError_t e = cudaMemsetAsync(S.visit, 0, sizeof(uint32_t) * m_cap, s);
     if (e != cudaSuccess) return wrs::cuda_fail(e, "wrs_refit_lbvh memset");
     const uint32_t grefit = (m_cap + kRefitBlock - 1) / kRefitBlock;
     k_leaves_refit<<<grefit, kRefitBlock, 0, s>>>(S.vals0, pos4, reinterpret_cast<const float4*>(in->rgba),
-                                      in->id, radius_scale, global_scale, hdr, nodes, S.leaf_parent,
+                                      in->id, radius_scale, global_scale, hdr, nodes,
+                                      bvh->layout == WRS_LBVH_FULL, S.leaf_parent,
                                       S.node_parent, S.node_range, S.visit,
                                       reinterpret_cast<float4*>(sorted->pos_r),
                                       reinterpret_cast<float4*>(sorted->rgba), sorted->id,

@@ -1804,6 +1804,18 @@ __global__ void __launch_bounds__(128) k_trace_bwd_pr(Scene sc, Comp cp, wrs_cam
     }
 }
 
+// Batched trace over binary nodes: flags every session whose tree was built without all its
+// binary records (layout WRS_LBVH_WIDE), unless the session's own schedule walks the 4-wide
+// nodes (per_session and a packet session).
+__global__ void k_check_binary_layout(const wrs_session* __restrict__ sess, int n_sessions,
+                                      bool per_session, int32_t* status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_sessions) return;
+    if (per_session && sess[i].schedule == WRS_SCHEDULE_PACKET) return;
+    const LbvhHeader* h = static_cast<const LbvhHeader*>(sess[i].nodes);
+    if (h->layout != WRS_LBVH_FULL) wrs::set_status(status, WRS_STATUS_MALFORMED_TREE);
+}
+
 // ---- host dispatch -------------------------------------------------------------------------
 int check_trace_args(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_camera* cam,
                      const wrs_trace_params* p, const char* fn) {
@@ -1825,6 +1837,12 @@ int check_trace_args(const wrs_lbvh* bvh, const wrs_splats* sorted, const wrs_ca
         return wrs::fail(WRS_ERR_ARG, "%s: unknown schedule %d", fn, p->schedule);
     if (p->width != 0 && p->width != 2 && p->width != 4)
         return wrs::fail(WRS_ERR_ARG, "%s: width %d not 2 or 4 (0 = 2)", fn, p->width);
+    if (bvh->layout != WRS_LBVH_FULL && bvh->layout != WRS_LBVH_WIDE)
+        return wrs::fail(WRS_ERR_ARG, "%s: unknown tree layout %u", fn, bvh->layout);
+    if (bvh->layout == WRS_LBVH_WIDE && p->width != 4 && p->schedule != WRS_SCHEDULE_PACKET)
+        return wrs::fail(WRS_ERR_ARG,
+                         "%s: the binary traversal (width %d) needs a tree built with layout "
+                         "WRS_LBVH_FULL; this one has only its 4-wide nodes", fn, p->width);
     if (!(p->t_stop >= 0.0f && p->t_stop < 1.0f))
         return wrs::fail(WRS_ERR_ARG, "%s: t_stop must be in [0, 1)", fn);
     if (!(p->edge_softness >= 0.0f && p->edge_softness < 1.0f))
@@ -2197,6 +2215,11 @@ int wrs_trace_batched(const wrs_session* sessions, int32_t n_sessions, uint32_t 
     if (e != cudaSuccess) return wrs::cuda_fail(e, fn);
     if (total_tiles == 0) return WRS_OK;
     const int K = effective_k(params), W = params->width;
+    if (W != 4 && params->schedule != WRS_SCHEDULE_PACKET && status) {
+        k_check_binary_layout<<<(n_sessions + 127) / 128, 128, 0, s>>>(
+            sessions, n_sessions, params->schedule == WRS_SCHEDULE_PER_SESSION, status);
+        WRS_LAUNCH_CHECK(fn);
+    }
     if (params->schedule == WRS_SCHEDULE_PER_PIXEL)
         dispatch_k<LaunchBatchedPP>(K, W, (total_tiles + 3) / 4, sessions, n_sessions, total_tiles,
                                     comp_of(params), status, s);

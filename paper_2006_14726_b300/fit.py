@@ -26,7 +26,7 @@ from typing import Callable, List, Optional, Sequence
 import torch
 import torch.nn.functional as F
 
-from . import RefitTree
+from . import RefitTree, tree_layout
 from .autograd import render_views
 
 # eager steps before the capture of a graphed fit
@@ -56,7 +56,7 @@ class RadiusFit:
             self.opacity = (opacity if opacity is not None
                             else torch.ones(n, device=dev)).detach()
             cams = list(cams)
-            self.tree = RefitTree(splats, leaf_size)
+            self.tree = RefitTree(splats, leaf_size, layout=tree_layout(params))
 
             def render(s):
                 return render_views(splats, cams, self.rgba, self.opacity, s, params, leaf_size,

@@ -164,6 +164,38 @@ def test_host_validation_without_device(wrs):
     assert lib.wrs_check_status(None, None) == wrs.WRS_ERR_ARG
 
 
+def test_tree_layout_checks_without_device(wrs):
+    """The 4-wide-only layout (WRS_LBVH_WIDE): the binding's constants are the header's; an
+    unknown layout is refused by the build, the refit and the traces; the binary traversal (width
+    2 or 0 under any schedule but the packet one) of such a tree is refused before any CUDA call."""
+    import re
+    hdr = open(os.path.join(ROOT, "include", "wrs.h")).read()
+    consts = dict(re.findall(r"#define (WRS_LBVH_\w+) (\d+)", hdr))
+    assert int(consts["WRS_LBVH_FULL"]) == wrs.LBVH_FULL == 0
+    assert int(consts["WRS_LBVH_WIDE"]) == wrs.LBVH_WIDE
+    lib = wrs.lib
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: validation fails first
+    big = wrs._Splats(fake.value, fake.value, fake.value, None, fake.value, 64)
+    srt = wrs._Splats(fake.value, fake.value, fake.value, fake.value, fake.value, 64)
+    odd = wrs._Lbvh(fake.value, 64, 1, 2)
+    for fn in (lib.wrs_build_lbvh, lib.wrs_refit_lbvh):
+        assert fn(ctypes.byref(big), None, 1.0, ctypes.byref(odd), ctypes.byref(srt), fake, 1 << 30, None) == wrs.WRS_ERR_ARG
+        assert "layout 2" in wrs.last_error()
+    p4 = wrs._Params(0, 1e-5, 0.0, None, 8, 128, 0, 4)
+    assert lib.wrs_trace(ctypes.byref(odd), ctypes.byref(srt), ctypes.byref(_cam(wrs)), ctypes.byref(p4), fake, None, None) == wrs.WRS_ERR_ARG
+    wide = wrs._Lbvh(fake.value, 64, 1, wrs.LBVH_WIDE)
+    cams = (wrs.Camera * 2)(_cam(wrs), _cam(wrs))
+    for width in (2, 0):
+        for sched in (wrs.SCHEDULE_PER_PIXEL, wrs.SCHEDULE_PERSISTENT):
+            p2 = wrs._Params(0, 1e-5, 0.0, None, 8, 128, sched, width)
+            assert lib.wrs_trace(ctypes.byref(wide), ctypes.byref(srt), ctypes.byref(_cam(wrs)), ctypes.byref(p2), fake, None, None) == wrs.WRS_ERR_ARG
+            assert "WRS_LBVH_FULL" in wrs.last_error()
+        assert lib.wrs_trace_views(ctypes.byref(wide), ctypes.byref(srt), cams, 2, ctypes.byref(p2), fake, None, None) == wrs.WRS_ERR_ARG
+        assert lib.wrs_trace_count(ctypes.byref(wide), ctypes.byref(srt), ctypes.byref(_cam(wrs)), ctypes.byref(p2), fake, None, None) == wrs.WRS_ERR_ARG
+        assert lib.wrs_trace_backward_views(ctypes.byref(wide), ctypes.byref(srt), cams, 2, ctypes.byref(p2), None, 1.0, fake, fake, None, None, 0, None, None) == wrs.WRS_ERR_ARG
+        assert "WRS_LBVH_FULL" in wrs.last_error()
+
+
 def test_cpu_tensors_are_rejected(wrs):
     import torch
     with pytest.raises(ValueError):
