@@ -39,6 +39,7 @@ class _Scene:
         self.bscratch = torch.empty(max(lbvh_scratch_bytes(npix, leaf), 256), dtype=torch.uint8,
                                     device=device)
         self.copied = torch.cuda.Event()
+        self.built = torch.cuda.Event()     # the slot's splats and LBVH are complete
         self.released = torch.cuda.Event()  # the last trace that read this slot has finished
         self.released.record()              # (nothing reads a fresh slot)
         # the slot's LBVH build reads and writes only the slot's own buffers (the splat count
@@ -60,7 +61,9 @@ class WarpingClient:
     [Hs, Ws, 4] float32, depth [Hs, Ws] float32, the server camera) and queues its copy, splats and
     LBVH; ``render(cam)`` queues a client view of the newest submitted frame and its copy back,
     returning a ticket; ``result(ticket)`` waits for that copy and returns the pinned host image
-    (valid until the ring of ``ring`` images wraps onto it)."""
+    (valid until the ring of ``ring`` images wraps onto it).  Four streams: host → device copies,
+    the splats and LBVH of a new frame (a stream of higher priority, so that they overlap the
+    views still being traced from the previous frame), the traces, and device → host copies."""
 
     def __init__(self, server_w: int, server_h: int, client_w: int, client_h: int,
                  params: TraceParams = TraceParams(width=4, k_chunk=1), leaf_size: int = 1,
@@ -72,6 +75,7 @@ class WarpingClient:
         self.radius_mode, self.voxel_diag = int(radius_mode), float(voxel_diag)
         self.sw, self.sh, self.cw, self.ch = int(server_w), int(server_h), int(client_w), int(client_h)
         self.compute = torch.cuda.Stream(device=device)
+        self.build = torch.cuda.Stream(device=device, priority=-1)  # the higher priority
         self.h2d = torch.cuda.Stream(device=device)
         self.d2h = torch.cuda.Stream(device=device)
         # a client that walks the 4-wide nodes builds trees without the binary records
@@ -98,11 +102,12 @@ class WarpingClient:
             sc.rgba.copy_(h_rgba, non_blocking=True)
             sc.depth.copy_(h_depth, non_blocking=True)
         sc.copied.record(self.h2d)
-        self.compute.wait_event(sc.copied)
+        self.build.wait_event(sc.copied)
         unproject(sc.rgba, sc.depth, cam, self.radius_mode, self.voxel_diag, out=sc.splats,
-                  scratch=sc.uscratch, stream=self.compute)
-        with torch.cuda.stream(self.compute):
+                  scratch=sc.uscratch, stream=self.build)
+        with torch.cuda.stream(self.build):
             sc.build.replay()
+        sc.built.record(self.build)
         self.current = slot
 
     # ---- client views -------------------------------------------------------------------------
@@ -116,6 +121,7 @@ class WarpingClient:
             self.copied[k].synchronize()
         self.compute.wait_event(self.copied[k])  # its previous copy out has finished
         sc = self.scenes[self.current]
+        self.compute.wait_event(sc.built)
         trace(sc.bvh, sc.sorted, make_camera(cam), self.params, out=self.dev_out[k],
               status=self.status, stream=self.compute)
         self.traced[k].record(self.compute)
@@ -140,6 +146,6 @@ class WarpingClient:
 
     def synchronize(self):
         """Wait for all queued work of the three streams."""
-        for s in (self.h2d, self.compute, self.d2h):
+        for s in (self.h2d, self.build, self.compute, self.d2h):
             s.synchronize()
         self.pending = [False] * len(self.pending)
