@@ -188,6 +188,19 @@ def launched_block(block, k_chunk, width, schedule):
     return min(block, 128) if (width == 4 and k_chunk in (1, 2, 4, 8) and schedule == 0) else block
 
 
+def lbvh_bytes_per_splat(leaf, full_layout, per_splat_scale=False):
+    """Algorithmic DRAM bytes of one LBVH build per splat, kernel by kernel: bounds (read pos_r
+    16, + 4 per-splat scale), Morton codes (read 16, write key and index 8), three digit
+    histograms (read keys 3 x 4), four scatter passes (read and write key and index, 4 x 16),
+    Karras (read keys 4; write node range 16 and parent links 8, + child references 16 in the
+    full layout), the visit counters (4), the refit (read order 4, pos_r 16, rgba 16, id 4,
+    parent links 8 and node range 16 (+ scale 4); write the sorted splats 40, the 4-wide node
+    128, + the binary record's boxes 48 in the full layout).  Per-leaf items scale by 1/leaf."""
+    per_splat = 16 + 24 + 12 + 64 + 4 + 16 + 4 + 16 + 4 + 40 + (8 if per_splat_scale else 0)
+    per_leaf = 16 + 8 + 4 + 8 + 16 + 128 + (16 + 48 if full_layout else 0)
+    return per_splat + per_leaf / leaf
+
+
 def tree_layout(wrs, width, schedule):
     """The LBVH layout a launch needs: the 4-wide nodes only, unless it walks the binary nodes."""
     return wrs.tree_layout(wrs.TraceParams(schedule=schedule, width=width))
@@ -626,6 +639,15 @@ def main():
             "L2-resident copy rate the counted bytes reach l2_frac; the binding limit is "
             "instruction issue on the ALU pipe (`issue`)")
 
+    lbvh_bps = lbvh_bytes_per_splat(leaf, layout == wrs.LBVH_FULL)
+    lbvh_gbs = lbvh_bps * statistics.mean(n_splats) / (statistics.mean(bv_ms) * 1e-3) / 1e9
+    lbvh_roof = {"bound": "hbm", "bytes_per_splat": lbvh_bps, "achieved": lbvh_gbs,
+                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": lbvh_gbs / peaks["hbm_gbs"],
+                 "gsplat_s": statistics.mean(n_splats) / (statistics.mean(bv_ms) * 1e-3) / 1e9,
+                 "note": "algorithmic bytes of the build's 16 kernels (lbvh_bytes_per_splat) over "
+                         "the sequential loop's LBVH time; the build is latency-bound (the "
+                         "refit's climb, Karras' divergent searches, the sort's scatter), not "
+                         "bandwidth-bound"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -652,7 +674,8 @@ def main():
                            "note": "the same steps one after another on one stream, each "
                                    "bracketed by its own events after an L2 flush; the stage "
                                    "split below is from this loop"},
-            "lbvh_ms": statistics.mean(bv_ms), "unproject_ms": statistics.mean(up_ms),
+            "lbvh_ms": statistics.mean(bv_ms), "lbvh_roofline": lbvh_roof,
+            "unproject_ms": statistics.mean(up_ms),
             "trace_ms": trace_ms, "trace_mrays_s": npix_c / (trace_ms * 1e-3) / 1e6,
             "wall_s_timed_region": wall_p,
             "paper_context": {"hardware": "RTX 2080", "lbvh_ms_623k": 11, "compact_ms": 23,
