@@ -6,7 +6,8 @@
 //                                       and the per-tile counts of the first radix digit
 //   k_rs_hist (x3) / k_rs_scan / k_rs_scatter (x4) : stable LSD radix sort of (code, index), 8-bit
 //                                       digits (the first digit's counts come from k_morton)
-//   k_karras                          : binary radix tree over leaf keys (Karras 2012)
+//   k_karras                          : binary radix tree over leaf keys (Karras 2012); also
+//                                       zeroes the refit's arrival counters
 //   k_leaves_refit                    : gathers the splats into leaf order with their effective
 //                                       radius, computes leaf boxes and refits the internal nodes
 //                                       bottom-up (second thread to reach a node continues); the
@@ -395,11 +396,13 @@ __global__ void __launch_bounds__(256) k_karras(const uint32_t* __restrict__ cod
                                                 float4* __restrict__ nodes, bool binary,
                                                 uint32_t* __restrict__ leaf_parent,
                                                 uint32_t* __restrict__ node_parent,
-                                                uint4* __restrict__ node_range) {
+                                                uint4* __restrict__ node_range,
+                                                uint32_t* __restrict__ visit) {
     const int m = (int)hdr->m;
     const uint32_t leaf = hdr->leaf;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m - 1) return;
+    visit[i] = 0u;  // the refit's arrival counter of internal node i
     const uint32_t a = __ldg(codes + (size_t)i * leaf);
     const int d = (delta(codes, leaf, m, i, a, i + 1) - delta(codes, leaf, m, i, a, i - 1)) >= 0 ? 1 : -1;
     const int dmin = delta(codes, leaf, m, i, a, i - d);
@@ -699,10 +702,8 @@ int wrs_build_lbvh(const wrs_splats* in, const float* radius_scale, float global
     }
     // four passes: the sorted keys / values are back in keys0 / vals0
     k_karras<<<gm, 256, 0, s>>>(ki, hdr, nodes, bvh->layout == WRS_LBVH_FULL, S.leaf_parent,
-                                S.node_parent, S.node_range);
+                                S.node_parent, S.node_range, S.visit);
     WRS_LAUNCH_CHECK("wrs_build_lbvh karras");
-    cudaError_t e = cudaMemsetAsync(S.visit, 0, sizeof(uint32_t) * m_cap, s);
-    if (e != cudaSuccess) return wrs::cuda_fail(e, "wrs_build_lbvh memset");
     const uint32_t grefit = (m_cap + kRefitBlock - 1) / kRefitBlock;
     k_leaves_refit<<<grefit, kRefitBlock, 0, s>>>(vi, pos4, reinterpret_cast<const float4*>(in->rgba),
                                       in->id, radius_scale, global_scale, hdr, nodes,
