@@ -186,6 +186,34 @@ __device__ __forceinline__ void box_test_nf(const BoxRay& r, float nx, float ny,
     tf = min3f(bx, by, bz);
 }
 
+// Two single-precision FMAs in one packed instruction (each lane rounds to nearest, as fmaf).
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    unsigned long long ra, rb, rc, rd;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rc) : "f"(c.x), "f"(c.y));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
+    float2 d;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+    return d;
+}
+
+// box_test_nf for two boxes at once (two slots of a 4-wide node, whose planes sit side by side
+// in the node's float4s): the six slab products as packed pairs, bitwise the scalar results.
+__device__ __forceinline__ void box_test_nf2(const BoxRay& r, float2 nx, float2 ny, float2 nz,
+                                             float2 fx, float2 fy, float2 fz, float low,
+                                             float& tn0, float& tf0, float& tn1, float& tf1) {
+    const float2 ix = make_float2(r.ix, r.ix), iy = make_float2(r.iy, r.iy);
+    const float2 iz = make_float2(r.iz, r.iz);
+    const float2 ax = fma2(nx, ix, make_float2(r.nx, r.nx)), bx = fma2(fx, ix, make_float2(r.fx, r.fx));
+    const float2 ay = fma2(ny, iy, make_float2(r.ny, r.ny)), by = fma2(fy, iy, make_float2(r.fy, r.fy));
+    const float2 az = fma2(nz, iz, make_float2(r.nz, r.nz)), bz = fma2(fz, iz, make_float2(r.fz, r.fz));
+    tn0 = max3f(ax.x, ay.x, fmaxf(az.x, low));
+    tf0 = min3f(bx.x, by.x, bz.x);
+    tn1 = max3f(ax.y, ay.y, fmaxf(az.y, low));
+    tf1 = min3f(bx.y, by.y, bz.y);
+}
+
 // Traversal epsilon: far above the binary32 error of the sphere test (a few units in the last
 // place of |o| + |c|), far below a sphere radius.
 __device__ __forceinline__ float traversal_eps(const Ray& r, float scene_maxabs) {

@@ -202,6 +202,33 @@ __device__ __forceinline__ void cswap(float& ka, uint32_t& ra, float& kb, uint32
 // sorted by entry distance (5-comparator network), the nearest is returned and the others pushed
 // far to near.  Same return convention as visit_node.  (The lane-refill schedule's visit; the
 // per-pixel kernels use visit_node4_sorted, which stacks leaf entries too.)
+#ifndef WRS_PACKED_MAX_K
+#define WRS_PACKED_MAX_K 4  // K 8 and 16 measured faster with one box at a time (register pressure)
+#endif
+// The four box tests of a 4-wide node visit: slot pairs with packed FMAs (K <= WRS_PACKED_MAX_K)
+// or one box at a time; bitwise the same distances.
+template <int K>
+__device__ __forceinline__ void box_tests4(const wrs::BoxRay& br, const float4& nx,
+                                           const float4& ny, const float4& nz, const float4& fx,
+                                           const float4& fy, const float4& fz, float low,
+                                           float (&tn)[4], float (&tf)[4]) {
+    if constexpr (K <= WRS_PACKED_MAX_K) {
+        wrs::box_test_nf2(br, make_float2(nx.x, nx.y), make_float2(ny.x, ny.y),
+                          make_float2(nz.x, nz.y), make_float2(fx.x, fx.y),
+                          make_float2(fy.x, fy.y), make_float2(fz.x, fz.y), low, tn[0], tf[0],
+                          tn[1], tf[1]);
+        wrs::box_test_nf2(br, make_float2(nx.z, nx.w), make_float2(ny.z, ny.w),
+                          make_float2(nz.z, nz.w), make_float2(fx.z, fx.w),
+                          make_float2(fy.z, fy.w), make_float2(fz.z, fz.w), low, tn[2], tf[2],
+                          tn[3], tf[3]);
+    } else {
+        wrs::box_test_nf(br, nx.x, ny.x, nz.x, fx.x, fy.x, fz.x, low, tn[0], tf[0]);
+        wrs::box_test_nf(br, nx.y, ny.y, nz.y, fx.y, fy.y, fz.y, low, tn[1], tf[1]);
+        wrs::box_test_nf(br, nx.z, ny.z, nz.z, fx.z, fy.z, fz.z, low, tn[2], tf[2]);
+        wrs::box_test_nf(br, nx.w, ny.w, nz.w, fx.w, fy.w, fz.w, low, tn[3], tf[3]);
+    }
+}
+
 template <int K, bool COUNT, typename E>
 __device__ __forceinline__ int64_t visit_node4(const Scene& sc, const Ray& ray,
                                                const wrs::BoxRay& br, uint32_t ref, uint32_t n,
@@ -220,10 +247,7 @@ __device__ __forceinline__ int64_t visit_node4(const Scene& sc, const Ray& ray,
     const float4 rf = __ldg(w + 6);
     if (COUNT) { cnt.nodes++; cnt.boxes += 4; }
     float tn[4], tf[4];
-    wrs::box_test_nf(br, nx.x, ny.x, nz.x, fx.x, fy.x, fz.x, low, tn[0], tf[0]);
-    wrs::box_test_nf(br, nx.y, ny.y, nz.y, fx.y, fy.y, fz.y, low, tn[1], tf[1]);
-    wrs::box_test_nf(br, nx.z, ny.z, nz.z, fx.z, fy.z, fz.z, low, tn[2], tf[2]);
-    wrs::box_test_nf(br, nx.w, ny.w, nz.w, fx.w, fy.w, fz.w, low, tn[3], tf[3]);
+    box_tests4<K>(br, nx, ny, nz, fx, fy, fz, low, tn, tf);
     uint32_t r[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
                      __float_as_uint(rf.w)};
     float key[4];
@@ -439,10 +463,7 @@ __device__ __forceinline__ int64_t visit_node4_sorted(const Scene& sc, const wrs
     const float4 rf = __ldg(w + 6);
     if (COUNT) { cnt.nodes++; cnt.boxes += 4; }
     float tn[4], tf[4];
-    wrs::box_test_nf(br, nx.x, ny.x, nz.x, fx.x, fy.x, fz.x, low, tn[0], tf[0]);
-    wrs::box_test_nf(br, nx.y, ny.y, nz.y, fx.y, fy.y, fz.y, low, tn[1], tf[1]);
-    wrs::box_test_nf(br, nx.z, ny.z, nz.z, fx.z, fy.z, fz.z, low, tn[2], tf[2]);
-    wrs::box_test_nf(br, nx.w, ny.w, nz.w, fx.w, fy.w, fz.w, low, tn[3], tf[3]);
+    box_tests4<K>(br, nx, ny, nz, fx, fy, fz, low, tn, tf);
     uint32_t r[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
                      __float_as_uint(rf.w)};
     float key[4];
@@ -599,10 +620,7 @@ __device__ __forceinline__ int64_t visit_node4_packet(const Scene& sc, const Ray
     const float4 fx = __ldg(w + 3 - br.sx), fy = __ldg(w + 4 - br.sy), fz = __ldg(w + 5 - br.sz);
     const float4 rf = __ldg(w + 6);
     float tn[4], tf[4];
-    wrs::box_test_nf(br, nx.x, ny.x, nz.x, fx.x, fy.x, fz.x, low, tn[0], tf[0]);
-    wrs::box_test_nf(br, nx.y, ny.y, nz.y, fx.y, fy.y, fz.y, low, tn[1], tf[1]);
-    wrs::box_test_nf(br, nx.z, ny.z, nz.z, fx.z, fy.z, fz.z, low, tn[2], tf[2]);
-    wrs::box_test_nf(br, nx.w, ny.w, nz.w, fx.w, fy.w, fz.w, low, tn[3], tf[3]);
+    box_tests4<K>(br, nx, ny, nz, fx, fy, fz, low, tn, tf);
     uint32_t r[4] = {__float_as_uint(rf.x), __float_as_uint(rf.y), __float_as_uint(rf.z),
                      __float_as_uint(rf.w)};
     float key[4];
