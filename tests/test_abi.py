@@ -196,6 +196,18 @@ def test_tree_layout_checks_without_device(wrs):
         assert "WRS_LBVH_FULL" in wrs.last_error()
 
 
+def test_tree_layout_follows_the_traversal(wrs):
+    """A trace that walks the 4-wide nodes (width 4, or the packet schedule at any width) needs
+    only the 4-wide-only layout; the binary traversal needs the full one."""
+    P = wrs.TraceParams
+    assert wrs.tree_layout(P(width=4)) == wrs.LBVH_WIDE
+    assert wrs.tree_layout(P(width=4, schedule=wrs.SCHEDULE_PERSISTENT)) == wrs.LBVH_WIDE
+    assert wrs.tree_layout(P(width=2, schedule=wrs.SCHEDULE_PACKET)) == wrs.LBVH_WIDE
+    for sched in (wrs.SCHEDULE_PER_PIXEL, wrs.SCHEDULE_PERSISTENT):
+        for width in (0, 2):
+            assert wrs.tree_layout(P(width=width, schedule=sched)) == wrs.LBVH_FULL
+
+
 def test_cpu_tensors_are_rejected(wrs):
     import torch
     with pytest.raises(ValueError):
