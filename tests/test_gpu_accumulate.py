@@ -166,3 +166,42 @@ def test_window_1080p_sampled(wrs):
         wrs.check_status(win.status)
         err = np.abs(img.cpu().numpy().reshape(-1, 4)[pix].astype(np.float64) - ref["rgba"])
         assert err.max() <= MAX_ABS and err.mean() <= MEAN_ABS, (sched, width, err.max())
+
+
+def test_two_slot_window_overlapped_streams(wrs):
+    """A window with two copies of its set, pushed on one stream and traced on another while the
+    previous frame's views still trace: each step's views equal a one-copy window's bitwise, and
+    the current set equals the oracle's accumulation record for record."""
+    from paper_2006_14726_b300.accumulate import FrameWindow
+    fr = _frames(64, 48, 6, 330)
+    one = FrameWindow(3, 64, 48, decay=0.5)
+    two = FrameWindow(3, 64, 48, decay=0.5, slots=2, layout=wrs.LBVH_WIDE)
+    build, draw = torch.cuda.Stream(priority=-1), torch.cuda.Stream()
+    cams = [synth.orbit(fr[0][2], (0, 1, 0), a, 56, 40) for a in (2.0, -3.0, 5.0)]
+    p = wrs.TraceParams(k_chunk=2, width=4)
+    frames_in = [(_cuda(r), _cuda(d), c) for r, d, c in reversed(fr)]
+    # every output allocated up front: a buffer the allocator hands out again on the default
+    # stream could still be in use there when the draw stream writes it
+    ref_imgs = [[torch.empty(40, 56, 4, device="cuda") for _ in cams] for _ in frames_in]
+    imgs = [[torch.empty(40, 56, 4, device="cuda") for _ in cams] for _ in frames_in]
+    torch.cuda.synchronize()
+    for (rgba, depth, cam), ref_o, outs in zip(frames_in, ref_imgs, imgs):
+        one.push(rgba, depth, cam)
+        for c, o in zip(cams, ref_o):
+            one.trace(c, p, out=o)
+        two.push(rgba, depth, cam, stream=build)  # overlaps the previous frame's views
+        for c, o in zip(cams, outs):
+            two.trace(c, p, out=o, stream=draw)
+    torch.cuda.synchronize()
+    wrs.check_status(two.status)
+    for a, b in zip(ref_imgs, imgs):
+        for x, y in zip(a, b):
+            assert torch.equal(x.view(torch.int32), y.view(torch.int32))
+    _assert_same(two.splats, oracle.accumulate(fr[:3], decay=0.5))
+    # pushes with no trace between them, alternating streams: each rebuild also waits for the
+    # last build of the copy it overwrites
+    for i, (rgba, depth, cam) in enumerate(frames_in):
+        two.push(rgba, depth, cam, stream=build if i % 2 else None)
+    torch.cuda.synchronize()
+    wrs.check_status(two.status)
+    _assert_same(two.splats, oracle.accumulate(fr[:3], decay=0.5))
