@@ -1181,9 +1181,21 @@ def extras(line, args, wrs, autotune, synth, torch, groups, params, leaf, rank, 
     barrier()
     ms_acc = max_over_ranks(acc_time(10))
     ms_rebuild = max_over_ranks(_time_ms(torch, win.rebuild, 10))
-    clis_t = groups[(nxt[0] - 1) % len(groups)][3]  # the views of the newest frame in the window
-    ms_tr = max_over_ranks(_time_ms(torch, lambda: [win.trace(c, aparams, out=o)
-                                                    for c, o in zip(clis_t, outs)], 10))
+    # the 4 traces alone, over 4 more steps (each push on this stream, then the 4 views between
+    # two events): windows of the same kind as the timed loop's
+    tr = []
+    for _ in range(4):
+        rgba_a, depth_a, srv_a, clis_a = groups[nxt[0] % len(groups)]
+        nxt[0] += 1
+        win.push(rgba_a, depth_a, srv_a)
+        ta, tb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ta.record()
+        for f in range(FRAMES_PER_IMAGE):
+            win.trace(clis_a[f], aparams, out=outs[f])
+        tb.record()
+        torch.cuda.synchronize()
+        tr.append(ta.elapsed_time(tb))
+    ms_tr = max_over_ranks(statistics.mean(tr))
     wrs.check_status(win.status)
     line["accumulate"] = {"frames": F_WIN, "decay": 0.9, "splats": win.splats.count(),
                           "client_frames_per_server_frame": FRAMES_PER_IMAGE,
