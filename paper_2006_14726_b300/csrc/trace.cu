@@ -1525,6 +1525,9 @@ __device__ __forceinline__ void backward_pixel_packet(const Scene& sc, const Com
     bool run = inside && !(g.x == 0.f && g.y == 0.f && g.z == 0.f && g.w == 0.f);
     if (run && flt.count && flt.count[ray_base + (size_t)y * cam.width + x] <= flt.cap)
         run = false;  // its recorded list serves
+    // a warp none of whose rays runs (no gradient, or every list recorded) has nothing to do: it
+    // leaves before the ray set-up (only warp-wide syncs follow, no block barrier)
+    if (!__any_sync(0xffffffffu, run)) return;
     const RayCtx rc = make_ray_ctx(sc, cam, inside ? x : 0, inside ? y : 0);
     if (rc.n == 0) return;  // the same for every thread of the launch
     float b_key[wrs::kBwdChunks];
