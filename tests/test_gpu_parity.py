@@ -215,10 +215,11 @@ def test_lbvh_duplicate_centres_and_tiny_counts(wrs):
 # trace
 # ---------------------------------------------------------------------------------------------
 def _trace_pair(wrs, rgba, depth, srv, cli, H=0, beta=0.0, opacity=None, scale=None, leaf=1,
-                k=8, block=128, pixels=None, schedule=0, width=2):
+                k=8, block=128, pixels=None, schedule=0, width=2, layout=0):
     ref_sp = oracle.unproject(rgba, depth, srv)
     sp = _gpu_splats(wrs, rgba, depth, srv)
-    bvh, srt = wrs.build_lbvh(sp, leaf, radius_scale=None if scale is None else _cuda(scale))
+    bvh, srt = wrs.build_lbvh(sp, leaf, radius_scale=None if scale is None else _cuda(scale),
+                              layout=layout)
     st = wrs.new_status()
     params = wrs.TraceParams(max_hits=H, edge_softness=beta, k_chunk=k, block=block,
                              schedule=schedule, width=width)
@@ -304,15 +305,16 @@ def test_trace_large_sampled(wrs):
 
 
 def test_trace_large_full_image(wrs):
-    """Every pixel of a full-size frame in the launch the tuner picks on B300 (one thread per
-    pixel, 4-wide nodes, K 1, leaf 1): 1920x1080 server image (about 2 M splats) warped to a
-    1920x1080 client 10 degrees away, against the oracle's full image, with the composited-hit
-    count equal to the oracle's."""
+    """Every pixel of a full-size frame in the benchmark's configuration (the launch the tuner
+    picks on B300: one thread per pixel, 4-wide nodes, K 1, leaf 1, 128-thread blocks, on a tree
+    of the 4-wide-only layout): 1920x1080 server image (about 2 M splats) warped to a 1920x1080
+    client 10 degrees away, against the oracle's full image, with the composited-hit count equal
+    to the oracle's."""
     rgba, depth = synth.synthetic_server_image(1920, 1080, 52)
     srv = synth.LARGE.server_cam()
     cli = synth.orbit(srv, (0.0, 1.0, 0.3), 10.0)
     got, ref, (bvh, srt, params) = _trace_pair(wrs, rgba, depth, srv, cli, k=1, schedule=0,
-                                               width=4)
+                                               width=4, layout=wrs.LBVH_WIDE)
     m = _assert_close(got, ref["rgba"], "large full image")
     assert m < 1e-5  # hard edges: identical hit lists, only compositing rounding remains
     cnt = wrs.trace_count(bvh, srt, cli, params)
