@@ -5,7 +5,10 @@ One step = one new server depth image of the large workload followed by its fram
 unproject (Eq. 1, footprint radius, compaction) + LBVH rebuild + 4 client frames traced and
 composited (1920x1080 server image of a 512^3 u8 Fourier volume, about 2.07 M splats, 1920x1080
 client, poses within 20 degrees, a new depth image every 4 frames).  value = client primary rays
-per second over the whole job (all ranks), Mrays/s.
+per second over the whole job (all ranks), Mrays/s, of K steps run as a client runs them: the next
+frame's unproject and LBVH build (two buffer slots, a build stream of higher priority) overlap
+this frame's 4 traces.  The same K steps one after another on one stream are reported as
+`sequential`, with the stage split.
 
 Also reported on the same line: LBVH build and unproject ms, trace-only Mrays/s, the roofline of
 the trace kernel, the batched workload (64 sessions, one launch replayed from a CUDA graph vs 64
