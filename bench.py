@@ -727,8 +727,8 @@ def main():
                                      "measured_by": "wrs_fma_peak: FFMA warp instructions per "
                                                     "second of an FMA-only kernel, one wave of "
                                                     "8 x 256 threads per SM",
-                                     "note": "the kernel's binding limit (ALU pipe 69 %, issue "
-                                             "70-71 % under ncu); the hbm entry is the "
+                                     "note": "the kernel's binding limit (ALU pipe 71 %, issue "
+                                             "68-69 % under ncu); the hbm entry is the "
                                              "counted-bytes roofline"}
 
     if not args.no_extras:
